@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the signature-kernel Gram workload on GB300.
+
+Workload (one step): the Gram matrices of B = 64 Brownian paths with 1024
+segments in R^16, increments N(0, sigma^2/1024), for sigma = 1 and sigma = 4
+(seeds 2001 / 2004) -- 2 x 2080 unique pairs x 1024^2 tiles.  Metric: tile
+cells per second, cells = sum over computed pairs of L1*L2 (the lower
+triangle is mirrored, not recomputed, and is not counted).
+
+Output: one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded sample of the same workload instead (the reference arm of this
+build; there is no other implementation of the method to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PATHS, N_SEG, DIM = 64, 1024, 16
+SIGMAS = ((1.0, 2001, 8, 4), (4.0, 2004, 16, 6))   # sigma, seed, order P, rings
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+L2_FLUSH_BYTES = 512 << 20
+ORACLE_SAMPLE_PAIRS = 16
+
+
+def tile_flops(P: int, nr: int, d: int) -> int:
+    """FP32 operations per tile of the solver (FMA = 2), as executed: the
+    increment inner product (2d), the ring powers, the Hankel sums of both
+    edges, the edge evaluation, the convolutions and the float-float corner."""
+    nrm = min(P, 8)
+    nr = min(nr, nrm)
+    f = 2 * (nr - 1)
+    f += sum(2 * (1 + 2 * (P - p)) for p in range(1, nr + 1))
+    f += 2 * P
+    for p in range(1, P + 1):
+        f += 4 * min(p - 1, nr) + (4 if p <= nr else 0)
+    f += 7
+    return f + 2 * d
+
+
+def pairs_of_gram(n):
+    return n * (n + 1) // 2
+
+
+def cells_per_step():
+    return len(SIGMAS) * pairs_of_gram(N_PATHS) * N_SEG * N_SEG
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2 + k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def oracle_sample(pts_lens, n_pairs):
+    """FP64 oracle on the first n_pairs upper-triangle pairs (a, b) of each
+    Gram; returns (values per sigma, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_2502_20392_gb300 import synth
+    oracle.build()
+    out, t0 = [], time.perf_counter()
+    for pts, lens in pts_lens:
+        inc = [np.diff(p.astype(np.float64), axis=0) for p in synth.split(pts, lens)]
+        idx = [(a, b) for a in range(N_PATHS) for b in range(a, N_PATHS)][:n_pairs]
+        xs = [inc[a] for a, _ in idx]
+        ys = [inc[b] for _, b in idx]
+        out.append((idx, oracle.series_pairs(xs, ys)))
+    return out, time.perf_counter() - t0, oracle.num_threads()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: 16 paths per Gram (for ncu captures; not a bench line)")
+    args = ap.parse_args()
+    if args.case == "small":
+        global N_PATHS
+        N_PATHS = 16
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2502_20392_gb300 import build, sigk, synth
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    sigk.load()
+
+    # each rank solves its own batch (independent problems: weak scaling)
+    host = [synth.workload_gram_1024(s, seed + 1000 * rank, n_paths=N_PATHS)
+            for s, seed, _, _ in SIGMAS]
+    X = [torch.from_numpy(p).to(dev) for p, _ in host]
+    L = [torch.from_numpy(l).to(dev) for _, l in host]
+    opts = [sigk.Opts(order=P, rings=nr, max_len=N_SEG) for _, _, P, nr in SIGMAS]
+    wss = [sigk.Workspace() for _ in SIGMAS]
+    G = [torch.empty((N_PATHS, N_PATHS), dtype=torch.float64, device=dev) for _ in SIGMAS]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(ev_pairs=None):
+        for k in range(len(SIGMAS)):
+            if ev_pairs is not None:
+                sigk.profile_events(*ev_pairs[k])
+            sigk.gram(X[k], L[k], opts=opts[k], out=G[k], ws=wss[k], check=False)
+        if ev_pairs is not None:
+            sigk.profile_events(None, None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for ws in wss:
+        sigk.sync_status(ws)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in SIGMAS] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))  # evict the inputs from L2 (outside the timed span)
+            starts[i].record()
+            step(kev[i])
+            ends[i].record()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    for ws in wss:
+        sigk.sync_status(ws)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms = [[a.elapsed_time(b) for a, b in row] for row in kev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    cells = cells_per_step()
+    value = cells * world / (ms * 1e-3)
+
+    # counters of the last launch of each sigma (tiles actually solved)
+    tiles = [sigk.counters(ws)[0] for ws in wss]
+
+    # roofline of the solver kernel (dominant: the sigma = 4, P = 16 launch)
+    roof = []
+    for k, (sg, _, P, nr) in enumerate(SIGMAS):
+        kms = statistics.mean(r[k] for r in kern_ms)
+        flops = tiles[k] * tile_flops(P, nr, DIM)
+        ach = flops / (kms * 1e-3) / 1e12
+        roof.append({"sigma": sg, "order": P, "rings": nr, "kernel_ms": round(kms, 4),
+                     "flops_per_launch": flops, "achieved": round(ach, 3)})
+    dom = max(range(len(SIGMAS)), key=lambda k: roof[k]["kernel_ms"])
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tpath) as f:
+            tj = json.load(f)
+        with open(os.path.join(ROOT, "paper_2502_20392_gb300", "_build", "libsigk.sha256")) as f:
+            digest = f.read().strip()
+        if tj.get("digest") == digest:
+            traffic = tj.get("bytes_per_launch")
+    except (OSError, ValueError):
+        traffic = None
+    roofline = {"bound": "alu", "achieved": roof[dom]["achieved"], "peak": round(FP32_PEAK_TFLOPS, 2),
+                "unit": "TFLOP/s", "frac": round(roof[dom]["achieved"] / FP32_PEAK_TFLOPS, 4),
+                "traffic": traffic, "kernel": f"fwd_kernel<P={roof[dom]['order']},D=16>",
+                "per_launch": roof}
+
+    # end-to-end through the public API: pinned host inputs -> device, both
+    # Gram calls, Gram matrices -> pinned host, every step
+    h_pts = [torch.from_numpy(p).pin_memory() for p, _ in host]
+    h_len = [torch.from_numpy(l).pin_memory() for _, l in host]
+    h_out = [torch.empty((N_PATHS, N_PATHS), dtype=torch.float64).pin_memory() for _ in SIGMAS]
+    d_pts = [torch.empty_like(x) for x in X]
+    d_len = [torch.empty_like(x) for x in L]
+    h2d = sum(t.numel() * t.element_size() for t in h_pts + h_len)
+    d2h = sum(t.numel() * t.element_size() for t in h_out)
+    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e_s[i].record()
+        for k in range(len(SIGMAS)):
+            d_pts[k].copy_(h_pts[k], non_blocking=True)
+            d_len[k].copy_(h_len[k], non_blocking=True)
+            sigk.gram(d_pts[k], d_len[k], opts=opts[k], out=G[k], ws=wss[k], check=False)
+            h_out[k].copy_(G[k], non_blocking=True)
+        e_e[i].record()
+    torch.cuda.synchronize()
+    for ws in wss:
+        sigk.sync_status(ws)
+    e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(e_s, e_e))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    line = {
+        "metric": "fwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=16 sigma in {1,4}",
+        "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (float-float corner, f64 reductions)",
+        "data": "synthetic (seeded Brownian, PCG64)",
+        "config": {"workload": "gram_B64_L1024_d16_sigma1+4", "paths": N_PATHS, "segments": N_SEG,
+                   "d": DIM, "sigmas": [s for s, *_ in SIGMAS],
+                   "order_rings": [[P, nr] for _, _, P, nr in SIGMAS],
+                   "unique_pairs_per_gram": pairs_of_gram(N_PATHS), "l2": "flushed between steps",
+                   "parallelism": f"independent batch per rank x{world}"},
+        "gpu_launches": 2 * len(SIGMAS) * args.steps,
+        "clocks": clk.summary(),
+        "e2e": {"value": cells * world / (e2e_ms * 1e-3), "unit": "cells/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "roofline": roofline,
+        "wall_s": t_wall,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        host_G = [g.cpu().numpy() for g in G]
+        vals, secs, thr = oracle_sample(host, ORACLE_SAMPLE_PAIRS)
+        errs = []
+        for (idx, ref), Gk in zip(vals, host_G):
+            diag = [host_G[0][a, a] for a in range(N_PATHS)]
+            for (a, b), r in zip(idx, ref):
+                e = abs(Gk[a, b] - r) / max(abs(r), 1e-300)
+                errs.append(e)
+        n_cells = sum(len(idx) for idx, _ in vals) * N_SEG * N_SEG
+        line["cpu_baseline"] = {"value": n_cells / secs, "unit": "cells/s", "cores": thr,
+                                "kind": "oracle",
+                                "sample": f"first {ORACLE_SAMPLE_PAIRS} upper-triangle pairs of each "
+                                          f"Gram ({n_cells:.3e} cells), FP64 tile series N=24, "
+                                          f"OpenMP over pairs, {secs:.1f} s"}
+        line["rel_err_vs_oracle_sample"] = max(errs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle, timed as it stands on the host cores, on
+    a bounded sample of the workload per step (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_2502_20392_gb300 import synth
+    host = [synth.workload_gram_1024(s, seed) for s, seed, _, _ in SIGMAS]
+    per_step = max(1, ORACLE_SAMPLE_PAIRS // 4)
+    for _ in range(args.warmup):
+        oracle_sample(host, 1)
+    times = []
+    thr = 1
+    for _ in range(args.steps):
+        _, secs, thr = oracle_sample(host, per_step)
+        times.append(secs)
+    n_cells = len(SIGMAS) * per_step * N_SEG * N_SEG
+    v = n_cells / statistics.mean(times)
+    line = {"impl": "reference",
+            "metric": "fwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=16 sigma in {1,4}",
+            "value": v, "unit": "cells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Brownian, PCG64)",
+            "config": {"workload": "gram_B64_L1024_d16_sigma1+4",
+                       "sample": f"{per_step} pairs per sigma per step"},
+            "cpu_baseline": {"value": v, "unit": "cells/s", "cores": thr, "kind": "oracle",
+                             "sample": f"{per_step} upper-triangle pairs per sigma per step, FP64 "
+                                       f"tile series N=24, OpenMP over pairs"},
+            "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

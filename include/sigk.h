@@ -1,0 +1,157 @@
+/*
+ * sigk.h -- C-ABI of the GB300 signature-kernel library (libsigk.so).
+ *
+ * What is computed.  For piecewise-linear paths x, y (sequences of points in
+ * R^d, linearly interpolated), the signature kernel k(x,y) = K(1,1), where K
+ * solves the Goursat problem  d^2K/(ds dt) = <x'(s), y'(t)> K  with K = 1 on
+ * both axes (Sec. 2.1, Definition "Signature Kernel").  K is evaluated tile by
+ * tile with the tile-centred local power series of Sec. 2.3 (Proposition
+ * "tile-centred expansion", proof in App. A.6), swept over the tile grid in
+ * anti-diagonal (wavefront) order (algorithm of App. C.1), with the boundary
+ * data of each tile passed on as truncated polynomial coefficients.  Tile
+ * (i,j) couples x-segment i with y-segment j; its coefficient is
+ * c_ij = <x_{i+1} - x_i, y_{j+1} - y_j> (unit local tiles).
+ *
+ * Memory and ownership.  Every array argument is caller-owned DEVICE memory
+ * (the library never allocates or frees device memory), except where a
+ * parameter says "host".  Scratch comes from the caller through a workspace
+ * (ws, ws_bytes) whose size sigk_workspace_size() returns; ws must be 256-byte
+ * aligned and must not be used by another call that runs at the same time.
+ *
+ * Path batches.  A batch of n paths is one packed row-major FP32 array of
+ * shape (sum_p len[p]) x d plus a DEVICE int64 vector len[n]: path p occupies
+ * rows [off_p, off_p + len[p]) with off the exclusive prefix sum of len.  By
+ * default a row is a POINT and len[p] counts points (>= 1; a path of one point
+ * has no segment and k = 1 with every other path).  With
+ * SIGK_FLAG_INCREMENTS a row is a segment increment and len[p] counts
+ * segments (>= 0).  d is shared by all paths of a call, 1 <= d <= 16 in this
+ * version.
+ *
+ * Precision.  Inputs are FP32.  The series arithmetic is FP32 with a
+ * float-float corner value and a per-edge power-of-two exponent; results are
+ * FP64.  Accuracy is set by the truncation parameters in sigk_opts, which
+ * sigk_plan() chooses from a target relative tolerance.
+ *
+ * Calls are asynchronous on `stream`.  The returned status covers argument
+ * validation and launch; errors found on the device (a bounded wait that ran
+ * out, non-finite data) are recorded in the workspace and returned by
+ * sigk_sync_status() after the stream has drained.  No call throws.
+ */
+#ifndef SIGK_H
+#define SIGK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIGK_OK = 0,
+    SIGK_ERR_ARG = -1,        /* null pointer, bad size, d out of range, bad opts */
+    SIGK_ERR_LENGTH = -2,     /* a length below its minimum or above 2^31-1 */
+    SIGK_ERR_NONFINITE = -3,  /* NaN or Inf met on the device */
+    SIGK_ERR_WORKSPACE = -4,  /* ws too small or misaligned */
+    SIGK_ERR_CUDA = -5,       /* a CUDA runtime call failed (see sigk_last_error) */
+    SIGK_ERR_TIMEOUT = -6,    /* a bounded inter-warp wait ran out on the device */
+    SIGK_ERR_UNSUPPORTED = -8 /* a combination this build does not provide */
+} sigk_status;
+
+/* Operation codes for sigk_workspace_size / sigk_plan. */
+enum { SIGK_OP_PAIRS = 0, SIGK_OP_GRAM = 1, SIGK_OP_MMD = 2 };
+
+/* opts flags */
+enum {
+    SIGK_FLAG_INCREMENTS = 1,  /* rows are increments, len counts segments */
+    SIGK_FLAG_GRAM_FULL = 2,   /* Gram of X with itself: compute both triangles
+                                  independently instead of mirroring */
+    SIGK_FLAG_MMD_BIASED = 4   /* MMD^2 V-statistic instead of the U-statistic */
+};
+
+/* Truncation and scheduling parameters.  NULL = defaults (order 8, rings 4,
+ * max_len 8193).
+ *   order: degree P of the edge polynomials (the truncation order N of the
+ *          coefficient matrices, App. A.7); supported 4..16, rounded up to an
+ *          even value.
+ *   rings: number n of Neumann iterations per tile (powers of c_ij kept,
+ *          Sec. 2.3 / App. B: the local Neumann iteration), 1 <= n <= min(order, 8).
+ *   flags: SIGK_FLAG_*.
+ *   grid_ctas: persistent grid size (0 = occupancy-derived, one wave).
+ *   max_len: upper bound on the segments of the path that a pair sweeps
+ *            (the longer path of a pair may be split over warps instead);
+ *            sizes the seam ring.  A pair that needs more fails with
+ *            SIGK_ERR_LENGTH (reported by sigk_sync_status).  0 = 8193. */
+typedef struct {
+    int order;
+    int rings;
+    int flags;
+    int grid_ctas;
+    int64_t max_len;
+} sigk_opts;
+
+/* Device workspace bytes needed by sigk_pairs/sigk_gram/sigk_mmd for the
+ * given batch sizes (n_x, n_y = number of paths; for SIGK_OP_PAIRS n_x = n_y =
+ * number of pairs; for SIGK_OP_GRAM pass n_y = 0 for a Gram of X with itself).
+ * Depends on the lengths only through opts->max_len.  Returns 0 on bad
+ * arguments. */
+size_t sigk_workspace_size(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts);
+
+/* k_out[p] = k(x_p, y_p) for n_pairs independent pairs (ragged lengths).
+ * X, len_x describe the x_p, Y, len_y the y_p (each a batch of n_pairs
+ * paths).  k_out: device FP64[n_pairs]. */
+sigk_status sigk_pairs(const float* X, const int64_t* len_x, const float* Y,
+                       const int64_t* len_y, int64_t n_pairs, int d, double* k_out,
+                       void* ws, size_t ws_bytes, void* stream, const sigk_opts* opts);
+
+/* Gram matrix G[a*n_y + b] = k(x_a, y_b), row-major device FP64[n_x*n_y].
+ * Y == NULL (and n_y ignored) means Y = X: G is n_x x n_x; unless
+ * SIGK_FLAG_GRAM_FULL, only a <= b is computed and mirrored. */
+sigk_status sigk_gram(const float* X, const int64_t* len_x, int64_t n_x, const float* Y,
+                      const int64_t* len_y, int64_t n_y, int d, double* G, void* ws,
+                      size_t ws_bytes, void* stream, const sigk_opts* opts);
+
+/* Signature-kernel MMD^2 between samples X (m paths) and Y (n paths):
+ * mean_{a!=b} k(x_a,x_b) + mean_{a!=b} k(y_a,y_b) - 2 mean k(x_a,y_b)
+ * (U-statistic; SIGK_FLAG_MMD_BIASED: V-statistic with all terms), reduced in
+ * FP64 on the device.  mmd2_out: device FP64[1]; gram_out (optional, device
+ * FP64[(m+n)^2]) receives the Gram of the concatenated sample [X; Y]. */
+sigk_status sigk_mmd(const float* X, const int64_t* len_x, int64_t m, const float* Y,
+                     const int64_t* len_y, int64_t n, int d, double* mmd2_out,
+                     double* gram_out, void* ws, size_t ws_bytes, void* stream,
+                     const sigk_opts* opts);
+
+/* Recommended (order, rings) for a target relative tolerance `tol`, from
+ * statistics of the increments computed on the device (host lengths are not
+ * needed).  Synchronises `stream`.  Writes into *opts_out (flags and
+ * grid_ctas copied from opts_in when given). */
+sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
+                      const float* Y, const int64_t* len_y, int64_t n_y, int d, double tol,
+                      void* ws, size_t ws_bytes, void* stream, const sigk_opts* opts_in,
+                      sigk_opts* opts_out);
+
+/* Waits for `stream`, then returns and clears the device status recorded in
+ * ws by earlier calls (SIGK_OK, SIGK_ERR_TIMEOUT or SIGK_ERR_NONFINITE). */
+sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream);
+
+/* Counters of the last completed launch on this workspace (host copy after
+ * sigk_sync_status): out[0] = tiles processed, out[1] = tiles including
+ * padding, out[2] = algorithmic FP32 flops (FMA = 2) of the tile solver. */
+sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out3);
+
+/* Profiling hook: when both are non-NULL, later calls on this host thread
+ * record the two CUDA events (cudaEvent_t) on the call's stream immediately
+ * before and after the solver kernel launch, so that a caller can time the
+ * solver alone.  Pass NULL, NULL to stop. */
+void sigk_profile_events(void* ev_start, void* ev_stop);
+
+/* Thread-local message for the last error returned on this host thread. */
+const char* sigk_last_error(void);
+
+/* Library version string. */
+const char* sigk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIGK_H */

@@ -76,16 +76,20 @@ static double dot_d(const double* a, const double* b, int d) {
  */
 void orc_tile_map(double rho, int N, const double* alpha, const double* beta,
                   double* alpha_out, double* beta_out) {
-    /* factorials up to N */
-    double fact[64];
+    /* factorials and powers of rho up to N */
+    double fact[64], rpow[64];
     fact[0] = 1.0;
-    for (int k = 1; k <= N; ++k) fact[k] = fact[k - 1] * (double)k;
+    rpow[0] = 1.0;
+    for (int k = 1; k <= N; ++k) {
+        fact[k] = fact[k - 1] * (double)k;
+        rpow[k] = rpow[k - 1] * rho;
+    }
     for (int i = 0; i <= N; ++i) { alpha_out[i] = 0.0; beta_out[i] = 0.0; }
     for (int i = 0; i <= N; ++i) {
         for (int j = 0; j <= N; ++j) {
             int mn = i < j ? i : j;
             int mx = i < j ? j : i;
-            double a_ij = pow(rho, (double)mn);
+            double a_ij = rpow[mn];
             double w_ij = fact[mx - mn] / (fact[mx] * fact[mn]);
             double b_ij = (j >= i) ? beta[j - i] : alpha[i - j];
             double ct = a_ij * b_ij * w_ij;

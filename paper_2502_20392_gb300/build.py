@@ -1,0 +1,86 @@
+"""Builds libsigk.so in-tree (paper_2502_20392_gb300/_build/) with nvcc for
+sm_103a only.  One translation unit per edge degree P is compiled in
+parallel, then everything is linked into one shared library with a C ABI
+(include/sigk.h)."""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "libsigk.so")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+ORDERS = (4, 6, 8, 10, 12, 14, 16)
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+
+
+def _sources():
+    files = sorted(f for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h")))
+    files += ["../../include/sigk.h"]
+    return [os.path.normpath(os.path.join(CSRC, f)) for f in files]
+
+
+def _digest() -> str:
+    h = hashlib.sha256()
+    for f in _sources():
+        with open(f, "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
+def _units():
+    units = [("sigk_capi", os.path.join(CSRC, "sigk_capi.cu"), [])]
+    for P in ORDERS:
+        units.append((f"sigk_fwd_P{P}", os.path.join(CSRC, "sigk_fwd_inst.cu"), [f"-DSIGK_P={P}"]))
+    for f in sorted(os.listdir(CSRC)):
+        if f.endswith("_inst2.cu"):
+            units.append((f[:-3], os.path.join(CSRC, f), []))
+    return units
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "libsigk.sha256")
+    dig = _digest()
+    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+        with open(stamp) as f:
+            if f.read().strip() == dig:
+                return LIB
+    units = _units()
+
+    def compile_one(u):
+        name, src, extra = u
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {name}:\n{r.stderr}")
+        if verbose and r.stderr:
+            print(r.stderr)
+        return obj
+
+    workers = min(len(units), max(2, os.cpu_count() or 2))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        objs = list(ex.map(compile_one, units))
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(dig)
+    return LIB
+
+
+if __name__ == "__main__":
+    import time
+    t = time.time()
+    print(build(force=True), f"{time.time() - t:.1f}s")

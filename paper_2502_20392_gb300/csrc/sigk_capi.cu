@@ -1,0 +1,598 @@
+// sigk_capi.cu -- C-ABI of libsigk.so (declared in include/sigk.h).
+//
+// Host responsibilities: argument validation, workspace layout, choosing the
+// kernel instantiation and grid, launching the device-side planner (which
+// builds the pair table and strip counts from DEVICE length vectors, so no
+// host synchronisation and no host lengths are needed), the persistent
+// solver, and the FP64 reductions (Gram mirror, MMD^2).  The library never
+// allocates device memory.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sigk.h"
+#include "sigk_device.cuh"
+#include "sigk_launch.h"
+
+namespace sigk {
+
+static thread_local std::string g_last_error;
+static thread_local cudaEvent_t g_ev_start = nullptr;
+static thread_local cudaEvent_t g_ev_stop = nullptr;
+
+static sigk_status fail(sigk_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+static sigk_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(SIGK_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// options
+
+struct Opts {
+    int order;     // P (even, 4..16)
+    int rings;     // nr
+    int flags;
+    int grid_ctas;
+    int64_t max_len;
+};
+
+static bool resolve_opts(const sigk_opts* o, Opts* r) {
+    r->order = 8;
+    r->rings = 4;
+    r->flags = 0;
+    r->grid_ctas = 0;
+    r->max_len = 8193;
+    if (o) {
+        if (o->order) r->order = o->order;
+        if (o->rings) r->rings = o->rings;
+        r->flags = o->flags;
+        r->grid_ctas = o->grid_ctas;
+        if (o->max_len > 0) r->max_len = o->max_len;
+    }
+    if (r->order < 4 || r->order > kMaxP) return false;
+    r->order += (r->order & 1);
+    int nrmax = r->order < kMaxRings ? r->order : kMaxRings;
+    if (r->rings < 1 || r->rings > nrmax) return false;
+    if (r->grid_ctas < 0 || r->max_len > (int64_t)INT32_MAX) return false;
+    return true;
+}
+
+static int dim_bucket(int d) { return d <= 4 ? 4 : (d <= 8 ? 8 : (d <= 16 ? 16 : -1)); }
+
+static int fwd_info_dispatch(int P, int D, KernelInfo* info) {
+    switch (P) {
+        case 4: return fwd_info<4>(D, info);
+        case 6: return fwd_info<6>(D, info);
+        case 8: return fwd_info<8>(D, info);
+        case 10: return fwd_info<10>(D, info);
+        case 12: return fwd_info<12>(D, info);
+        case 14: return fwd_info<14>(D, info);
+        case 16: return fwd_info<16>(D, info);
+        default: return -1;
+    }
+}
+
+static cudaError_t fwd_launch_dispatch(int P, int D, const SolverArgs& a, int grid, cudaStream_t s) {
+    switch (P) {
+        case 4: return fwd_launch<4>(D, a, grid, s);
+        case 6: return fwd_launch<6>(D, a, grid, s);
+        case 8: return fwd_launch<8>(D, a, grid, s);
+        case 10: return fwd_launch<10>(D, a, grid, s);
+        case 12: return fwd_launch<12>(D, a, grid, s);
+        case 14: return fwd_launch<14>(D, a, grid, s);
+        case 16: return fwd_launch<16>(D, a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// workspace layout
+
+struct Layout {
+    size_t hdr, ox, oy, pairs, item_start, prod, cons, done, seam, gram, total;
+    int64_t n_pairs, n_paths_x, n_paths_y;
+    int nslot, wcols, grid, nwarps, rows_per_strip, stride;
+    KernelInfo info;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Number of pair entries solved by an op.
+static int64_t pair_count(int op, int64_t n_x, int64_t n_y, int flags) {
+    if (op == SIGK_OP_PAIRS) return n_x;
+    if (op == SIGK_OP_GRAM) {
+        if (n_y > 0) return n_x * n_y;
+        return (flags & SIGK_FLAG_GRAM_FULL) ? n_x * n_x : n_x * (n_x + 1) / 2;
+    }
+    // MMD: Gram of the concatenated sample, upper triangle
+    int64_t n = n_x + n_y;
+    return n * (n + 1) / 2;
+}
+
+static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Opts& o, Layout* L) {
+    const int D = dim_bucket(d);
+    if (D < 0) return fail(SIGK_ERR_UNSUPPORTED, "d must be in 1..16 in this build");
+    if (fwd_info_dispatch(o.order, D, &L->info) != 0 || L->info.blocks_per_sm <= 0)
+        return fail(SIGK_ERR_CUDA, "kernel occupancy query failed");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return fail(SIGK_ERR_CUDA, "cannot query SM count");
+    const int full_grid = sms * L->info.blocks_per_sm;
+    L->grid = o.grid_ctas > 0 ? (o.grid_ctas < full_grid ? o.grid_ctas : full_grid) : full_grid;
+    L->nwarps = L->grid * (L->info.threads / 32);
+    L->rows_per_strip = 32 * L->info.rows_per_lane;
+    L->stride = o.order + 3;
+    // Seam ring: nslot > concurrent warps; wcols large enough that the warps
+    // in flight can always hold a whole sweep between them (nwarps * wcols >=
+    // 2 * max_len), so a producer never waits on a consumer that cannot start.
+    L->nslot = L->nwarps + 64;
+    int64_t w = 2 * o.max_len / L->nwarps + 64;
+    if (w < 1024) w = 1024;
+    if (w > o.max_len) w = o.max_len;
+    w = (w + 31) & ~(int64_t)31;
+    if (w < 32) w = 32;
+    L->wcols = (int)w;
+    L->n_pairs = pair_count(op, n_x, n_y, o.flags);
+    L->n_paths_x = n_x;
+    L->n_paths_y = (op == SIGK_OP_GRAM && n_y == 0) ? 0 : n_y;
+    size_t off = 0;
+    L->hdr = off; off = align256(off + 256);
+    L->ox = off; off = align256(off + sizeof(int64_t) * (size_t)(n_x + 1));
+    L->oy = off; off = align256(off + sizeof(int64_t) * (size_t)(n_y + 1));
+    L->pairs = off; off = align256(off + sizeof(PairDesc) * (size_t)L->n_pairs);
+    L->item_start = off; off = align256(off + sizeof(int32_t) * (size_t)(L->n_pairs + 1));
+    L->prod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nslot);
+    L->cons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nslot);
+    L->done = off; off = align256(off + sizeof(long long) * (size_t)L->nslot);
+    L->seam = off; off = align256(off + sizeof(float) * (size_t)L->nslot * L->wcols * L->stride);
+    L->gram = off;
+    if (op == SIGK_OP_MMD) off = align256(off + sizeof(double) * (size_t)(n_x + n_y) * (n_x + n_y));
+    L->total = off;
+    return SIGK_OK;
+}
+
+// Header of the workspace (first 256 bytes).
+struct Header {
+    int status;
+    int item_counter;
+    int pad[2];
+    unsigned long long counters[4];
+};
+
+// ---------------------------------------------------------------------------
+// device-side planner: one CTA builds prefix offsets, the pair table and the
+// strip counts, and resets the seam synchronisation words.
+
+struct PlanArgs {
+    int op;
+    int flags;
+    int inc_mode;
+    int d;
+    const float* X;
+    const int64_t* len_x;
+    int64_t n_x;
+    const float* Y;
+    const int64_t* len_y;
+    int64_t n_y;        // 0: Gram of X with itself
+    int64_t max_len;
+    int rows_per_strip;
+    int64_t n_pairs;
+    int64_t* ox;
+    int64_t* oy;
+    PairDesc* pairs;
+    int32_t* item_start;
+    unsigned long long* prod;
+    unsigned long long* cons;
+    long long* done;
+    int nslot;
+    Header* hdr;
+    double* out;        // output (k values / Gram)
+    int64_t out_ld;     // leading dimension of the Gram output
+};
+
+constexpr int kPlanThreads = 1024;
+
+// Exclusive prefix sum of v[0..n) (int64) into out[0..n], one CTA.
+__device__ void block_exclusive_scan(const int64_t* v, int64_t n, int64_t* out, int64_t* sh,
+                                     bool segments, int inc_mode, int* bad) {
+    const int t = threadIdx.x;
+    const int64_t chunk = (n + kPlanThreads - 1) / kPlanThreads;
+    const int64_t b0 = t * chunk, b1 = (b0 + chunk < n) ? b0 + chunk : n;
+    int64_t s = 0;
+    for (int64_t i = b0; i < b1; ++i) {
+        int64_t x = v[i];
+        if (segments) {
+            int64_t mn = inc_mode ? 0 : 1;
+            if (x < mn || x > (int64_t)INT32_MAX) atomicExch(bad, 1);
+        }
+        s += x;
+    }
+    sh[t] = s;
+    __syncthreads();
+    for (int o = 1; o < kPlanThreads; o <<= 1) {
+        int64_t add = (t >= o) ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += add;
+        __syncthreads();
+    }
+    int64_t run = sh[t] - s;
+    for (int64_t i = b0; i < b1; ++i) {
+        out[i] = run;
+        run += v[i];
+    }
+    if (t == kPlanThreads - 1) out[n] = sh[t];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
+    __shared__ int64_t sh[kPlanThreads];
+    __shared__ int bad;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        bad = 0;
+        A.hdr->status = 0;  // errors are reported per call
+    }
+    __syncthreads();
+    block_exclusive_scan(A.len_x, A.n_x, A.ox, sh, true, A.inc_mode, &bad);
+    const bool self = (A.op == SIGK_OP_GRAM && A.n_y == 0);
+    if (!self) block_exclusive_scan(A.len_y, A.n_y, A.oy, sh, true, A.inc_mode, &bad);
+    __syncthreads();
+    if (bad) {
+        if (t == 0) atomicCAS(&A.hdr->status, 0, kErrLength);
+        return;
+    }
+    const int RS = A.rows_per_strip;
+    const int64_t nx = A.n_x;
+    const int64_t nz = (A.op == SIGK_OP_MMD) ? A.n_x + A.n_y : (self ? nx : A.n_y);
+    // pair table
+    for (int64_t p = t; p < A.n_pairs; p += kPlanThreads) {
+        int64_t a, b;
+        int64_t o0 = -1, o1 = -1;
+        const bool tri = (A.op == SIGK_OP_MMD) || (self && !(A.flags & SIGK_FLAG_GRAM_FULL));
+        if (A.op == SIGK_OP_PAIRS) {
+            a = p; b = p; o0 = p;
+        } else if (tri) {
+            // p -> (a, b), a <= b, row-major upper triangle of an nz x nz matrix
+            const int64_t n = nz;
+            double disc = (double)(2 * n + 1) * (double)(2 * n + 1) - 8.0 * (double)p;
+            int64_t aa = (int64_t)(((double)(2 * n + 1) - sqrt(disc)) * 0.5);
+            if (aa < 0) aa = 0;
+            while (aa > 0 && aa * n - aa * (aa - 1) / 2 > p) --aa;
+            while ((aa + 1) * n - (aa + 1) * aa / 2 <= p) ++aa;
+            a = aa;
+            b = p - (aa * n - aa * (aa - 1) / 2) + aa;
+            o0 = a * A.out_ld + b;
+            o1 = (a != b) ? b * A.out_ld + a : -1;
+        } else {
+            const int64_t ny = self ? nx : A.n_y;
+            a = p / ny; b = p % ny;
+            o0 = a * A.out_ld + b;
+        }
+        // resolve path pointers and segment counts
+        const float* pa;
+        const float* pb;
+        int64_t la, lb;
+        auto path = [&](int64_t z, bool from_y, const float** ptr, int64_t* segs) {
+            const float* base = from_y ? A.Y : A.X;
+            const int64_t* off = from_y ? A.oy : A.ox;
+            const int64_t* len = from_y ? A.len_y : A.len_x;
+            *ptr = base + off[z] * A.d;
+            *segs = A.inc_mode ? len[z] : len[z] - 1;
+        };
+        if (A.op == SIGK_OP_MMD) {
+            path(a < nx ? a : a - nx, a >= nx, &pa, &la);
+            path(b < nx ? b : b - nx, b >= nx, &pb, &lb);
+        } else if (A.op == SIGK_OP_PAIRS) {
+            path(a, false, &pa, &la);
+            path(b, true, &pb, &lb);
+        } else {
+            path(a, false, &pa, &la);
+            path(b, !self, &pb, &lb);
+        }
+        PairDesc pd;
+        pd.out0 = o0;
+        pd.out1 = o1;
+        // orientation: rows = the path that minimises padded work
+        // ceil(rows/RS)*RS*(cols + 31), subject to cols <= max_len
+        const int64_t cost_ab = ((la + RS - 1) / RS) * RS * (lb + 31);
+        const int64_t cost_ba = ((lb + RS - 1) / RS) * RS * (la + 31);
+        bool swap = cost_ba < cost_ab;
+        if (swap && la > A.max_len) swap = false;
+        if (!swap && lb > A.max_len) swap = true;
+        if ((swap ? la : lb) > A.max_len) atomicCAS(&A.hdr->status, 0, kErrLength);
+        pd.xr = swap ? pb : pa;
+        pd.yr = swap ? pa : pb;
+        pd.L1 = (int32_t)(swap ? lb : la);
+        pd.L2 = (int32_t)(swap ? la : lb);
+        pd.swapped = swap ? 1 : 0;
+        if (pd.L1 == 0 || pd.L2 == 0) {
+            pd.n_strips = 0;
+            if (o0 >= 0) A.out[o0] = 1.0;  // a one-point path: k = 1
+            if (o1 >= 0) A.out[o1] = 1.0;
+        } else {
+            pd.n_strips = (pd.L1 + RS - 1) / RS;
+        }
+        A.pairs[p] = pd;
+    }
+    __syncthreads();
+    // item_start = exclusive prefix of n_strips (int32 result, int64 scan)
+    {
+        const int64_t n = A.n_pairs;
+        const int64_t chunk = (n + kPlanThreads - 1) / kPlanThreads;
+        const int64_t b0 = t * chunk, b1 = (b0 + chunk < n) ? b0 + chunk : n;
+        int64_t s = 0;
+        for (int64_t i = b0; i < b1; ++i) s += A.pairs[i].n_strips;
+        sh[t] = s;
+        __syncthreads();
+        for (int o = 1; o < kPlanThreads; o <<= 1) {
+            int64_t add = (t >= o) ? sh[t - o] : 0;
+            __syncthreads();
+            sh[t] += add;
+            __syncthreads();
+        }
+        int64_t run = sh[t] - s;
+        for (int64_t i = b0; i < b1; ++i) {
+            A.item_start[i] = (int32_t)run;
+            run += A.pairs[i].n_strips;
+        }
+        if (t == kPlanThreads - 1) {
+            if (sh[t] > (int64_t)INT32_MAX) atomicCAS(&A.hdr->status, 0, kErrLength);
+            A.item_start[n] = (int32_t)sh[t];
+        }
+    }
+    // reset the seam synchronisation words and the work counter
+    for (int i = t; i < A.nslot; i += kPlanThreads) {
+        A.prod[i] = 0ull;
+        A.cons[i] = 0ull;
+        A.done[i] = -1ll;
+    }
+    if (t == 0) {
+        A.hdr->item_counter = 0;
+        A.hdr->counters[0] = 0;
+        A.hdr->counters[1] = 0;
+    }
+}
+
+// MMD^2 from the Gram of Z = [X; Y] (N = m + n), FP64, one CTA.
+__global__ void __launch_bounds__(1024) mmd_reduce_kernel(const double* G, int64_t m, int64_t n,
+                                                          int unbiased, double* out) {
+    __shared__ double sh[3][1024];
+    const int64_t N = m + n;
+    double sxx = 0.0, syy = 0.0, sxy = 0.0;
+    for (int64_t idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+        const int64_t a = idx / N, b = idx % N;
+        const double v = G[idx];
+        if (a < m && b < m) {
+            if (!unbiased || a != b) sxx += v;
+        } else if (a >= m && b >= m) {
+            if (!unbiased || a != b) syy += v;
+        } else if (a < m && b >= m) {
+            sxy += v;
+        }
+    }
+    sh[0][threadIdx.x] = sxx;
+    sh[1][threadIdx.x] = syy;
+    sh[2][threadIdx.x] = sxy;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mm = unbiased ? (double)m * (double)(m - 1) : (double)m * (double)m;
+        const double nn = unbiased ? (double)n * (double)(n - 1) : (double)n * (double)n;
+        out[0] = sh[0][0] / mm + sh[1][0] / nn - 2.0 * sh[2][0] / ((double)m * (double)n);
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+static sigk_status check_ws(const Layout& L, void* ws, size_t ws_bytes) {
+    if (!ws) return fail(SIGK_ERR_WORKSPACE, "workspace pointer is NULL");
+    if (((uintptr_t)ws & 255) != 0) return fail(SIGK_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(SIGK_ERR_WORKSPACE, "workspace too small: need " + std::to_string(L.total) +
+                                            " bytes, got " + std::to_string(ws_bytes));
+    return SIGK_OK;
+}
+
+// Common driver: plan + solve into `out` (k values or Gram).
+static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int64_t n_x,
+                              const float* Y, const int64_t* len_y, int64_t n_y, int d,
+                              double* out, int64_t out_ld, void* ws, size_t ws_bytes,
+                              cudaStream_t stream, const Opts& o, Layout* Lout) {
+    Layout L;
+    sigk_status st = make_layout(op, n_x, n_y, d, o, &L);
+    if (st != SIGK_OK) return st;
+    if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
+    char* base = (char*)ws;
+    Header* hdr = (Header*)(base + L.hdr);
+    PlanArgs pa;
+    pa.op = op;
+    pa.flags = o.flags;
+    pa.inc_mode = (o.flags & SIGK_FLAG_INCREMENTS) ? 1 : 0;
+    pa.d = d;
+    pa.X = X;
+    pa.len_x = len_x;
+    pa.n_x = n_x;
+    pa.Y = Y;
+    pa.len_y = len_y;
+    pa.n_y = n_y;
+    pa.max_len = o.max_len;
+    pa.rows_per_strip = L.rows_per_strip;
+    pa.n_pairs = L.n_pairs;
+    pa.ox = (int64_t*)(base + L.ox);
+    pa.oy = (int64_t*)(base + L.oy);
+    pa.pairs = (PairDesc*)(base + L.pairs);
+    pa.item_start = (int32_t*)(base + L.item_start);
+    pa.prod = (unsigned long long*)(base + L.prod);
+    pa.cons = (unsigned long long*)(base + L.cons);
+    pa.done = (long long*)(base + L.done);
+    pa.nslot = L.nslot;
+    pa.hdr = hdr;
+    pa.out = out;
+    pa.out_ld = out_ld;
+    plan_kernel<<<1, kPlanThreads, 0, stream>>>(pa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "plan_kernel launch");
+    SolverArgs sa;
+    sa.pairs = pa.pairs;
+    sa.item_start = pa.item_start;
+    sa.n_pairs = (int32_t)L.n_pairs;
+    sa.inc_mode = pa.inc_mode;
+    sa.d = d;
+    sa.nr = o.rings;
+    sa.nslot = L.nslot;
+    sa.wcols = L.wcols;
+    sa.seam = (float*)(base + L.seam);
+    sa.prod = pa.prod;
+    sa.cons = pa.cons;
+    sa.done = pa.done;
+    sa.item_counter = &hdr->item_counter;
+    sa.status = &hdr->status;
+    sa.counters = hdr->counters;
+    sa.out = out;
+    if (L.n_pairs > 0) {
+        if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
+        e = fwd_launch_dispatch(o.order, dim_bucket(d), sa, L.grid, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+        if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_stop, stream);
+    }
+    if (Lout) *Lout = L;
+    return SIGK_OK;
+}
+
+static sigk_status common_checks(int64_t n1, int64_t n2, int d, const void* out) {
+    if (d < 1) return fail(SIGK_ERR_ARG, "d must be >= 1");
+    if (n1 < 0 || n2 < 0) return fail(SIGK_ERR_ARG, "negative batch size");
+    if (!out) return fail(SIGK_ERR_ARG, "output pointer is NULL");
+    if (n1 > (int64_t)1 << 24 || n2 > (int64_t)1 << 24) return fail(SIGK_ERR_ARG, "batch too large");
+    return SIGK_OK;
+}
+
+}  // namespace sigk
+
+using namespace sigk;
+
+extern "C" {
+
+size_t sigk_workspace_size(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts) {
+    Opts o;
+    if (!resolve_opts(opts, &o)) return 0;
+    if (op < SIGK_OP_PAIRS || op > SIGK_OP_MMD || n_x < 0 || n_y < 0 || d < 1) return 0;
+    if (op == SIGK_OP_PAIRS) n_y = n_x;
+    Layout L;
+    if (make_layout(op, n_x, n_y, d, o, &L) != SIGK_OK) return 0;
+    return L.total;
+}
+
+sigk_status sigk_pairs(const float* X, const int64_t* len_x, const float* Y, const int64_t* len_y,
+                       int64_t n_pairs, int d, double* k_out, void* ws, size_t ws_bytes,
+                       void* stream, const sigk_opts* opts) {
+    sigk_status st = common_checks(n_pairs, n_pairs, d, k_out);
+    if (st != SIGK_OK) return st;
+    if (n_pairs > 0 && (!X || !Y || !len_x || !len_y)) return fail(SIGK_ERR_ARG, "null input");
+    Opts o;
+    if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    if (n_pairs == 0) return SIGK_OK;
+    return run_solver(SIGK_OP_PAIRS, X, len_x, n_pairs, Y, len_y, n_pairs, d, k_out, 0, ws,
+                      ws_bytes, (cudaStream_t)stream, o, nullptr);
+}
+
+sigk_status sigk_gram(const float* X, const int64_t* len_x, int64_t n_x, const float* Y,
+                      const int64_t* len_y, int64_t n_y, int d, double* G, void* ws,
+                      size_t ws_bytes, void* stream, const sigk_opts* opts) {
+    if (!Y) n_y = 0;
+    sigk_status st = common_checks(n_x, n_y, d, G);
+    if (st != SIGK_OK) return st;
+    if (n_x > 0 && (!X || !len_x)) return fail(SIGK_ERR_ARG, "null input");
+    if (Y && n_y > 0 && !len_y) return fail(SIGK_ERR_ARG, "null len_y");
+    Opts o;
+    if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    if (n_x == 0 || (Y && n_y == 0)) return SIGK_OK;
+    const int64_t ld = Y ? n_y : n_x;
+    return run_solver(SIGK_OP_GRAM, X, len_x, n_x, Y, len_y, Y ? n_y : 0, d, G, ld, ws, ws_bytes,
+                      (cudaStream_t)stream, o, nullptr);
+}
+
+sigk_status sigk_mmd(const float* X, const int64_t* len_x, int64_t m, const float* Y,
+                     const int64_t* len_y, int64_t n, int d, double* mmd2_out, double* gram_out,
+                     void* ws, size_t ws_bytes, void* stream, const sigk_opts* opts) {
+    sigk_status st = common_checks(m, n, d, mmd2_out);
+    if (st != SIGK_OK) return st;
+    if (!X || !Y || !len_x || !len_y) return fail(SIGK_ERR_ARG, "null input");
+    Opts o;
+    if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    const int unbiased = (o.flags & SIGK_FLAG_MMD_BIASED) ? 0 : 1;
+    if (m < 1 + unbiased || n < 1 + unbiased)
+        return fail(SIGK_ERR_ARG, "MMD needs at least 2 paths per sample (1 for the V-statistic)");
+    Layout L;
+    if ((st = make_layout(SIGK_OP_MMD, m, n, d, o, &L)) != SIGK_OK) return st;
+    if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
+    double* G = gram_out ? gram_out : (double*)((char*)ws + L.gram);
+    st = run_solver(SIGK_OP_MMD, X, len_x, m, Y, len_y, n, d, G, m + n, ws, ws_bytes,
+                    (cudaStream_t)stream, o, nullptr);
+    if (st != SIGK_OK) return st;
+    mmd_reduce_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(G, m, n, unbiased, mmd2_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "mmd_reduce launch");
+    return SIGK_OK;
+}
+
+sigk_status sigk_plan(int, const float*, const int64_t*, int64_t, const float*, const int64_t*,
+                      int64_t, int, double, void*, size_t, void*, const sigk_opts*, sigk_opts*) {
+    return fail(SIGK_ERR_UNSUPPORTED, "sigk_plan is not implemented in this build");
+}
+
+sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream) {
+    if (!ws || ws_bytes < 256) return fail(SIGK_ERR_WORKSPACE, "bad workspace");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    Header h;
+    e = cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status copy");
+    if (h.status != 0) {
+        int zero = 0;
+        cudaMemcpy(ws, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        const char* msg = h.status == kErrTimeout ? "a bounded device wait timed out"
+                          : h.status == kErrNonfinite ? "non-finite value met on the device"
+                          : h.status == kErrLength ? "a path length is out of range"
+                                                   : "device error";
+        return fail((sigk_status)h.status, msg);
+    }
+    return SIGK_OK;
+}
+
+sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out3) {
+    if (!ws || ws_bytes < 256 || !out3) return fail(SIGK_ERR_ARG, "bad arguments");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    Header h;
+    e = cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "counter copy");
+    out3[0] = (double)h.counters[0];
+    out3[1] = (double)h.counters[1];
+    out3[2] = 0.0;
+    return SIGK_OK;
+}
+
+void sigk_profile_events(void* ev_start, void* ev_stop) {
+    g_ev_start = (cudaEvent_t)ev_start;
+    g_ev_stop = (cudaEvent_t)ev_stop;
+}
+
+const char* sigk_last_error(void) { return g_last_error.c_str(); }
+
+const char* sigk_version(void) { return "sigk-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,231 @@
+// sigk_device.cuh -- device building blocks of the sm_103a signature-kernel
+// solver: the per-tile map of the tile-centred expansion, float-float corner
+// arithmetic, power-of-two renormalisation, and bounded inter-warp waits.
+//
+// Tile map (Sec. 2.3, Proposition "tile-centred expansion", with the
+// orientation of its proof in App. A.6).  On the unit tile with coefficient
+// c = <dx_i, dy_j>, bottom edge K(u,0) = sum_r a_r u^r and left edge
+// K(0,v) = sum_r b_r v^r (a_0 = b_0 = corner), the solution is
+//   K(u,v) = sum_{p,q} c^min(p,q) w_pq B_pq u^p v^q,
+//   w_pq = |p-q|! / (p! q!),  B_pq = b_{q-p} (q >= p) or a_{p-q} (p > q).
+// The top edge a'_p = sum_q (.)_pq and the right edge b'_q = sum_p (.)_pq are
+// the next tiles' boundary data.  Truncation to p,q <= P is the (N+1)x(N+1)
+// truncation of App. A.7 with N = P.
+//
+// Factorial scaling.  The kernel stores ah_p = p! a_p and bh_q = q! b_q.  With
+// ch_m = c^m / m! the map becomes
+//   ah'_p = sum_{m=0}^{p-1} ch_m ah_{p-m} + c^p sum_{r=0}^{P-p} bh_r/(p+r)!
+//   bh'_q = sum_{m=0}^{q-1} ch_m bh_{q-m} + c^q sum_{r=0}^{P-q} ah_r/(q+r)!
+//   b'_0  = b_0 + sum_{p>=1} ah_p / p!
+// (ah_0 := bh_0 := b_0, the corner value; a_0 is never used, as in the proof
+// where the diagonal carries the left-edge constant).  Rings m = min(p,q) are
+// the Neumann iterates T^m of Sec. 2.2.2; only m <= nr are kept (the local
+// Neumann iteration count, App. C.3: the a-priori order choice).  Every
+// constant is a compile-time entry of a __constant__ table, so each term is
+// one FFMA.
+//
+// Precision.  The corner value b_0 is carried as an unevaluated float-float
+// pair (hi, lo): it is the only O(1) quantity that accumulates an O(1)
+// rounding error per tile.  All other coefficients are FP32.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sigk {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kG = 32;            // columns per seam block (one warp width)
+constexpr int kMaxP = 16;         // maximum edge degree
+constexpr int kMaxRings = 8;      // maximum Neumann iterations per tile
+
+// 1/k! for k = 0..33, rounded to FP32 (all normal numbers; the tile map
+// indexes at most k = 16).  Each translation unit holds its own copy.
+static __constant__ float c_inv_fact[34] = {1.0f, 1.0f, 0.5f, 0.166666667f, 0.0416666667f, 0.00833333333f, 0.00138888889f, 0.000198412698f, 2.48015873e-05f, 2.75573192e-06f, 2.75573192e-07f, 2.50521084e-08f, 2.0876757e-09f, 1.60590438e-10f, 1.14707456e-11f, 7.64716373e-13f, 4.77947733e-14f, 2.81145725e-15f, 1.5619207e-16f, 8.22063525e-18f, 4.11031762e-19f, 1.95729411e-20f, 8.89679139e-22f, 3.86817017e-23f, 1.61173757e-24f, 6.44695028e-26f, 2.47959626e-27f, 9.18368986e-29f, 3.27988924e-30f, 1.13099629e-31f, 3.76998763e-33f, 1.21612504e-34f, 3.80039075e-36f, 1.15163356e-37f};
+
+enum : int {
+    kOK = 0, kErrArg = -1, kErrLength = -2, kErrNonfinite = -3, kErrWorkspace = -4,
+    kErrCuda = -5, kErrTimeout = -6
+};
+
+struct PairDesc {
+    const float* xr;   // row path (split into strips over warp lanes)
+    const float* yr;   // swept path
+    int32_t L1;        // segments of the row path
+    int32_t L2;        // segments of the swept path
+    int32_t n_strips;  // ceil(L1 / rows per strip)
+    int32_t swapped;   // 1 if the row path is the caller's y
+    int64_t out0;      // output index, or -1
+    int64_t out1;      // mirrored output index, or -1
+};
+
+struct SolverArgs {
+    const PairDesc* pairs;
+    const int32_t* item_start;     // [n_pairs + 1] prefix sums of n_strips
+    int32_t n_pairs;
+    int32_t inc_mode;              // rows of xr/yr are increments (else points)
+    int32_t d;
+    int32_t nr;                    // Neumann rings kept per tile
+    int32_t nslot;                 // seam ring slots
+    int32_t wcols;                 // columns per slot (multiple of kG)
+    float* seam;                   // nslot * wcols * stride floats
+    unsigned long long* prod;      // [nslot] (item << 32) | columns published
+    unsigned long long* cons;      // [nslot] (consumer item << 32) | columns read
+    long long* done;               // [nslot] last finished item with that residue
+    int* item_counter;
+    int* status;
+    unsigned long long* counters;  // [0] tiles, [1] lane-tiles incl. padding
+    double* out;
+};
+
+// ---------------------------------------------------------------------------
+// memory-order helpers
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long ld_acquire_s64(const long long* p) {
+    long long v;
+    asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_s64(long long* p, long long v) {
+    asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_s32(const int* p) {
+    return *reinterpret_cast<const volatile int*>(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait until *p >= target.  Gives up after ~4 s of wall time (or a
+// hard iteration cap), or as soon as another warp has recorded an error; on
+// time-out it records kErrTimeout.  Returns true when the condition holds.
+constexpr unsigned long long kWaitNs = 4000000000ull;
+constexpr int kWaitMaxIter = 1 << 24;
+
+__device__ __forceinline__ bool wait_ge_u64(const unsigned long long* p,
+                                            unsigned long long target, int* status) {
+    if (ld_acquire_u64(p) >= target) return true;
+    const unsigned long long t0 = global_ns();
+    for (int it = 0; it < kWaitMaxIter; ++it) {
+        __nanosleep(it < 64 ? 32 : 256);
+        if (ld_acquire_u64(p) >= target) return true;
+        if ((it & 31) == 31) {
+            if (ld_volatile_s32(status) != 0) return false;
+            if (global_ns() - t0 > kWaitNs) break;
+        }
+    }
+    atomicCAS(status, 0, kErrTimeout);
+    return false;
+}
+
+__device__ __forceinline__ bool wait_ge_s64(const long long* p, long long target, int* status) {
+    if (ld_acquire_s64(p) >= target) return true;
+    const unsigned long long t0 = global_ns();
+    for (int it = 0; it < kWaitMaxIter; ++it) {
+        __nanosleep(it < 64 ? 32 : 256);
+        if (ld_acquire_s64(p) >= target) return true;
+        if ((it & 31) == 31) {
+            if (ld_volatile_s32(status) != 0) return false;
+            if (global_ns() - t0 > kWaitNs) break;
+        }
+    }
+    atomicCAS(status, 0, kErrTimeout);
+    return false;
+}
+
+// 2^n as a float for n <= 0 (0 below the normal range).
+__device__ __forceinline__ float exp2_nonpos(int n) {
+    return n < -126 ? 0.0f : __int_as_float((127 + n) << 23);
+}
+
+// ---------------------------------------------------------------------------
+// One tile.  a[1..P]: scaled bottom edge (overwritten by the top edge);
+// (hi, lo), b[1..P]: scaled left edge (overwritten by the right edge).
+template <int P>
+__device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& hi, float& lo,
+                                            float (&b)[P + 1], int nr) {
+    constexpr int NRM = P < kMaxRings ? P : kMaxRings;
+    float cp[NRM + 1], ch[NRM + 1];
+    cp[1] = c;
+    ch[1] = c;
+#pragma unroll
+    for (int m = 2; m <= NRM; ++m) {
+        cp[m] = cp[m - 1] * c;
+        ch[m] = cp[m] * c_inv_fact[m];
+    }
+    // ring-p Hankel sums from the incoming edges (b_0 = a_0 := hi)
+    float ha[NRM + 1], hb[NRM + 1];
+#pragma unroll
+    for (int p = 1; p <= NRM; ++p) {
+        ha[p] = 0.0f;
+        hb[p] = 0.0f;
+        if (p <= nr) {
+            float sa = hi * c_inv_fact[p];
+            float sb = sa;
+#pragma unroll
+            for (int r = 1; r <= P - p; ++r) {
+                sa = fmaf(b[r], c_inv_fact[p + r], sa);
+                sb = fmaf(a[r], c_inv_fact[p + r], sb);
+            }
+            ha[p] = sa;
+            hb[p] = sb;
+        }
+    }
+    // bottom edge evaluated at u = 1 (without its constant term)
+    float S = 0.0f;
+#pragma unroll
+    for (int p = P; p >= 1; --p) S = fmaf(a[p], c_inv_fact[p], S);
+    // top edge (in place, high degree first: reads only lower, older entries)
+#pragma unroll
+    for (int p = P; p >= 1; --p) {
+        float v = a[p];
+#pragma unroll
+        for (int m = 1; m < p && m <= NRM; ++m)
+            if (m <= nr) v = fmaf(ch[m], a[p - m], v);
+        if (p <= NRM && p <= nr) v = fmaf(cp[p], ha[p], v);
+        a[p] = v;
+    }
+    // right edge
+#pragma unroll
+    for (int q = P; q >= 1; --q) {
+        float v = b[q];
+#pragma unroll
+        for (int m = 1; m < q && m <= NRM; ++m)
+            if (m <= nr) v = fmaf(ch[m], b[q - m], v);
+        if (q <= NRM && q <= nr) v = fmaf(cp[q], hb[q], v);
+        b[q] = v;
+    }
+    // corner value b'_0 = b_0 + S in float-float (TwoSum)
+    const float s = hi + S;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (S - bb);
+    hi = s;
+    lo += e;
+}
+
+// FP32 operations of tile_update (FMA counted as 2), for the roofline.
+__host__ __device__ constexpr long long tile_flops(int P, int nr) {
+    long long f = 0;
+    int nrm = P < kMaxRings ? P : kMaxRings;
+    if (nr > nrm) nr = nrm;
+    f += 2 * (nr - 1);                                  // powers
+    for (int p = 1; p <= nr; ++p) f += 2 * (1 + 2 * (P - p));  // Hankel sums (2 edges)
+    f += 2 * P;                                         // S
+    for (int p = 1; p <= P; ++p) {
+        int k = (p - 1) < nr ? (p - 1) : nr;
+        f += 2 * 2 * k;                                 // convolution, 2 edges
+        if (p <= nr) f += 2 * 2;                        // ring-p term, 2 edges
+    }
+    f += 7;                                             // TwoSum + lo
+    return f;
+}
+
+}  // namespace sigk

@@ -1,0 +1,282 @@
+// sigk_fwd.cuh -- persistent wavefront solver for k(x,y) = K(1,1) (forward).
+//
+// Schedule (the anti-diagonal sweep of App. C.1, re-blocked for a warp):
+//   * the row path's segments are cut into strips of 32*R rows; a work item is
+//     one (pair, strip); items of a pair are consecutive and in strip order;
+//   * a warp owns an item: lane l holds rows i0 + l*R + k (k < R) with their
+//     bottom-edge states a in registers and sweeps the columns j of the swept
+//     path with a skew of one column per lane: at step t lane l updates tiles
+//     (i0+l*R+k, t-l) for k = 0..R-1, taking the left edge b from lane l-1's
+//     previous step through a warp shuffle (so every tile's two inputs are
+//     ready: its left neighbour was done one step earlier, its lower neighbour
+//     by the same lane one step earlier);
+//   * lane 0 takes its left edges from the seam written by the previous strip
+//     (strip 0 uses the boundary K = 1); lane 31 writes its right edges to the
+//     seam of the next strip.  Seams live in a ring of global slots, staged 32
+//     columns at a time through shared memory, with progress words published
+//     by release stores and read by acquire loads.  Every wait is bounded.
+//   * Rows past the end of the path are given zero increments: such tiles have
+//     c = 0 and map their edges through unchanged, so lane 31 of the last
+//     strip always carries the right edge of the pair's last tile.
+//   * Each lane keeps one power-of-two exponent E for its edge data; incoming
+//     edges are aligned to it, and both are rescaled by 2^-64 when the corner
+//     value passes 2^64 (log-scale renormalisation of boundary data).
+#pragma once
+#include "sigk_device.cuh"
+
+namespace sigk {
+
+template <int D>
+struct DyStride {
+    // shared-memory row stride (floats) for the dy ring: an odd number of
+    // 16-byte chunks, so the 8 lanes of a 128-bit load phase hit distinct banks.
+    static constexpr int value = ((D / 4) % 2 == 1) ? D : D + 4;
+};
+
+template <int P, int D>
+struct FwdSmem {
+    static constexpr int S = P + 3;  // seam entry: hi, lo, b1..bP, exponent
+    static constexpr int DS = DyStride<D>::value;
+    static constexpr int per_warp = 64 * DS + 2 * kG * S;  // floats
+};
+
+// Increment of row `row` of path base z (points or increments), coordinate e.
+__device__ __forceinline__ float inc_at(const float* z, int64_t row, int d, int e, int inc_mode) {
+    if (inc_mode) return z[row * d + e];
+    return z[(row + 1) * d + e] - z[row * d + e];
+}
+
+template <int P, int D, int R>
+__global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
+    constexpr int S = P + 3;
+    constexpr int DS = DyStride<D>::value;
+    extern __shared__ float4 smem_f4[];
+    float* smem = reinterpret_cast<float*>(smem_f4);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    float* dyw = smem + warp * FwdSmem<P, D>::per_warp;  // 64-column ring of dy
+    float* sin_ = dyw + 64 * DS;                        // seam-in block
+    float* sout = sin_ + kG * S;                        // seam-out block
+    const int n_items = A.item_start[A.n_pairs];
+    unsigned long long tiles_done = 0, lane_tiles = 0;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(A.item_counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n_items) break;
+        if (ld_volatile_s32(A.status) != 0) break;
+        // locate the pair: largest p with item_start[p] <= item
+        int lo_p = 0, hi_p = A.n_pairs - 1;
+        while (lo_p < hi_p) {
+            int mid = (lo_p + hi_p + 1) >> 1;
+            if (A.item_start[mid] <= item) lo_p = mid; else hi_p = mid - 1;
+        }
+        const PairDesc pd = A.pairs[lo_p];
+        const int s = item - A.item_start[lo_p];
+        const int L1 = pd.L1, L2 = pd.L2;
+        const bool has_in = s > 0;
+        const bool has_out = s + 1 < pd.n_strips;
+        const int slot_in = (item - 1 + A.nslot) % A.nslot;
+        const int slot_out = item % A.nslot;
+        const int i0 = s * 32 * R;
+        bool ok = true;
+
+        // row increments of this lane (zero past the end of the path)
+        float dx[R][D];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const int row = i0 + lane * R + k;
+#pragma unroll
+            for (int e = 0; e < D; ++e)
+                dx[k][e] = (row < L1 && e < A.d) ? inc_at(pd.xr, row, A.d, e, A.inc_mode) : 0.0f;
+        }
+        float a[R][P + 1];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int p = 0; p <= P; ++p) a[k][p] = 0.0f;
+        int E = 0;
+        // outgoing right edge of the previous step (what lane+1 receives)
+        float ohi = 1.0f, olo = 0.0f, ob[P + 1];
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ob[q] = 0.0f;
+        int oE = 0;
+
+        // the slot we write must have been read by its previous consumer
+        if (has_out) {
+            const long long prev_consumer = (long long)item - A.nslot + 1;
+            bool okl = true;
+            if (lane == 0)
+                okl = wait_ge_s64(&A.done[((prev_consumer % A.nslot) + A.nslot) % A.nslot],
+                                  prev_consumer, A.status);
+            ok = __shfl_sync(kFull, okl, 0);
+        }
+        const int T = L2 + 31;
+        for (int t = 0; t < T && ok; ++t) {
+            if ((t & 31) == 0 && t < L2) {
+                // next 32 columns of dy into the ring
+                const int nb = min(32, L2 - t);
+                for (int idx = lane; idx < 32 * D; idx += 32) {
+                    const int col = idx / D, e = idx % D;
+                    float v = 0.0f;
+                    if (col < nb && e < A.d) v = inc_at(pd.yr, t + col, A.d, e, A.inc_mode);
+                    dyw[((t + col) & 63) * DS + e] = v;
+                }
+                if (has_in) {
+                    const unsigned long long need =
+                        ((unsigned long long)(item - 1) << 32) | (unsigned)(t + nb);
+                    bool okl = true;
+                    if (lane == 0) okl = wait_ge_u64(&A.prod[slot_in], need, A.status);
+                    ok = __shfl_sync(kFull, okl, 0);
+                    if (ok) {
+                        const float* src = A.seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
+                        for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src + idx);
+                        __syncwarp();
+                        if (lane == 0)
+                            st_release_u64(&A.cons[slot_in],
+                                           ((unsigned long long)item << 32) | (unsigned)(t + nb));
+                    }
+                }
+                __syncwarp();
+                if (!ok) break;
+            }
+            // left edge: from lane-1 (previous step), or the seam / boundary for lane 0
+            float hi = __shfl_up_sync(kFull, ohi, 1);
+            float lo = __shfl_up_sync(kFull, olo, 1);
+            float b[P + 1];
+            b[0] = 0.0f;
+#pragma unroll
+            for (int q = 1; q <= P; ++q) b[q] = __shfl_up_sync(kFull, ob[q], 1);
+            int F = __shfl_up_sync(kFull, oE, 1);
+            if (lane == 0) {
+                if (has_in && t < L2) {
+                    const float* e_ = sin_ + (t & 31) * S;
+                    hi = e_[0];
+                    lo = e_[1];
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] = e_[1 + q];
+                    F = __float_as_int(e_[P + 2]);
+                } else {
+                    hi = 1.0f; lo = 0.0f; F = 0;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] = 0.0f;
+                }
+            }
+            const int j = t - lane;
+            if (j >= 0 && j < L2) {
+                // align exponents of the incoming edge and the lane's states
+                if (F != E) {
+                    if (F > E) {
+                        const float sc = exp2_nonpos(E - F);
+#pragma unroll
+                        for (int k = 0; k < R; ++k)
+#pragma unroll
+                            for (int p = 1; p <= P; ++p) a[k][p] *= sc;
+                        E = F;
+                    } else {
+                        const float sc = exp2_nonpos(F - E);
+                        hi *= sc; lo *= sc;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) b[q] *= sc;
+                    }
+                }
+                float dy[D];
+                const float4* rowp = reinterpret_cast<const float4*>(dyw + (j & 63) * DS);
+#pragma unroll
+                for (int e4 = 0; e4 < D / 4; ++e4) {
+                    const float4 v = rowp[e4];
+                    dy[4 * e4 + 0] = v.x; dy[4 * e4 + 1] = v.y;
+                    dy[4 * e4 + 2] = v.z; dy[4 * e4 + 3] = v.w;
+                }
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    float c = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < D; ++e) c = fmaf(dx[k][e], dy[e], c);
+                    tile_update<P>(c, a[k], hi, lo, b, A.nr);
+                }
+                // renormalise when the corner value grows past 2^64
+                if (fabsf(hi) > 1.8446744e19f) {
+                    const float sc = 5.421011e-20f;  // 2^-64
+#pragma unroll
+                    for (int k = 0; k < R; ++k)
+#pragma unroll
+                        for (int p = 1; p <= P; ++p) a[k][p] *= sc;
+                    hi *= sc; lo *= sc;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] *= sc;
+                    E += 64;
+                }
+                ohi = hi; olo = lo; oE = E;
+#pragma unroll
+                for (int q = 1; q <= P; ++q) ob[q] = b[q];
+                tiles_done += (unsigned long long)max(0, min(R, L1 - (i0 + lane * R)));
+                lane_tiles += R;
+                if (lane == 31) {
+                    if (has_out) {
+                        float* e_ = sout + (j & 31) * S;
+                        e_[0] = hi; e_[1] = lo;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) e_[1 + q] = b[q];
+                        e_[P + 2] = __int_as_float(E);
+                    } else if (j == L2 - 1) {
+                        double k = (double)hi + (double)lo;
+                        double fq = 1.0;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) {
+                            fq *= (double)q;
+                            k += (double)b[q] / fq;
+                        }
+                        k = ldexp(k, E);
+                        if (!isfinite(k)) atomicCAS(A.status, 0, kErrNonfinite);
+                        if (pd.out0 >= 0) A.out[pd.out0] = k;
+                        if (pd.out1 >= 0) A.out[pd.out1] = k;
+                    }
+                }
+            }
+            // flush a completed 32-column block of the outgoing seam
+            const int jj = t - 31;
+            if (has_out && jj >= 0 && jj < L2 && (((jj & 31) == 31) || jj == L2 - 1)) {
+                __syncwarp();
+                const int start = jj & ~31;
+                const int nb = jj - start + 1;
+                if (start + nb > A.wcols) {
+                    const unsigned long long need = ((unsigned long long)(item + 1) << 32) |
+                                                    (unsigned)(start + nb - A.wcols);
+                    bool okl = true;
+                    if (lane == 0) okl = wait_ge_u64(&A.cons[slot_out], need, A.status);
+                    ok = __shfl_sync(kFull, okl, 0);
+                }
+                if (ok) {
+                    float* dst = A.seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
+                    for (int idx = lane; idx < nb * S; idx += 32) __stcg(dst + idx, sout[idx]);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0)
+                        st_release_u64(&A.prod[slot_out],
+                                       ((unsigned long long)item << 32) | (unsigned)(start + nb));
+                }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            st_release_s64(&A.done[item % A.nslot], (long long)item);
+        }
+        if (!ok) break;
+    }
+    // counters
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tiles_done += __shfl_down_sync(kFull, tiles_done, o);
+        lane_tiles += __shfl_down_sync(kFull, lane_tiles, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.counters[0], tiles_done);
+        atomicAdd(&A.counters[1], lane_tiles);
+    }
+}
+
+}  // namespace sigk

@@ -1,0 +1,23 @@
+// sigk_launch.h -- host-side entry points of the per-order kernel translation
+// units (one TU per edge degree P keeps the build parallel).
+#pragma once
+#include <cuda_runtime.h>
+#include "sigk_device.cuh"
+
+namespace sigk {
+
+struct KernelInfo {
+    int rows_per_lane;   // R
+    int smem_bytes;      // dynamic shared memory per CTA
+    int threads;         // threads per CTA
+    int blocks_per_sm;   // occupancy
+};
+
+// Rows per lane as a function of (P, D): fewer rows when the register
+// footprint (R*(P + D) state floats) would push occupancy too low.
+constexpr int rows_per_lane(int P, int D) { return (P + D) <= 16 ? 4 : 2; }
+
+template <int P> int fwd_info(int D, KernelInfo* info);
+template <int P> cudaError_t fwd_launch(int D, const SolverArgs& a, int grid, cudaStream_t s);
+
+}  // namespace sigk

@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libsigk.so (include/sigk.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  There is no CPU fallback -- if the library or a GPU is missing, every
+call raises.  PyTorch supplies device memory and the current stream.
+
+Conventions (see include/sigk.h): a batch of paths is a packed FP32 CUDA
+tensor of shape ``(sum(lengths), d)`` plus an int64 CUDA tensor ``lengths``
+(points per path, or segments per path with ``increments=True``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libsigk.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "sigk.h")
+
+OP_PAIRS, OP_GRAM, OP_MMD = 0, 1, 2
+FLAG_INCREMENTS, FLAG_GRAM_FULL, FLAG_MMD_BIASED = 1, 2, 4
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_LENGTH", -3: "ERR_NONFINITE", -4: "ERR_WORKSPACE",
+          -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -8: "ERR_UNSUPPORTED"}
+
+
+class SigkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sigk {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("rings", ctypes.c_int), ("flags", ctypes.c_int),
+                ("grid_ctas", ctypes.c_int), ("max_len", ctypes.c_int64)]
+
+
+@dataclass
+class Opts:
+    order: int = 8
+    rings: int = 4
+    flags: int = 0
+    grid_ctas: int = 0
+    max_len: int = 8193
+
+    def c(self) -> _Opts:
+        return _Opts(self.order, self.rings, self.flags, self.grid_ctas, self.max_len)
+
+
+_lib = None
+
+
+def exported_functions() -> list[str]:
+    """Function names declared in include/sigk.h."""
+    with open(HEADER) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sigk_[a-z_0-9]+)\s*\(", src)))
+
+
+def load(path: str | None = None):
+    """Load libsigk.so (built by paper_2502_20392_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsigk.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+    op = ctypes.POINTER(_Opts)
+    lib.sigk_workspace_size.argtypes = [i32, i64, i64, i32, op]
+    lib.sigk_workspace_size.restype = sz
+    lib.sigk_pairs.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, sz, vp, op]
+    lib.sigk_gram.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, sz, vp, op]
+    lib.sigk_mmd.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, vp, sz, vp, op]
+    lib.sigk_plan.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, ctypes.c_double, vp, sz, vp, op, op]
+    lib.sigk_sync_status.argtypes = [vp, sz, vp]
+    lib.sigk_counters.argtypes = [vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.sigk_profile_events.argtypes = [vp, vp]
+    lib.sigk_profile_events.restype = None
+    lib.sigk_last_error.restype = ctypes.c_char_p
+    lib.sigk_version.restype = ctypes.c_char_p
+    for name in ("sigk_pairs", "sigk_gram", "sigk_mmd", "sigk_plan", "sigk_sync_status",
+                 "sigk_counters"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise SigkError(st, load().sigk_last_error().decode())
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _paths(pts, lens):
+    if not (pts.is_cuda and lens.is_cuda):
+        raise ValueError("paths and lengths must be CUDA tensors")
+    if pts.dtype != torch.float32 or lens.dtype != torch.int64:
+        raise TypeError("paths must be float32 and lengths int64")
+    if pts.dim() != 2:
+        raise ValueError("paths must be a 2-D (rows, d) tensor")
+    return pts.contiguous(), lens.contiguous()
+
+
+class Workspace:
+    """Caller-owned device scratch, grown on demand (torch allocates it)."""
+
+    def __init__(self):
+        self.buf = None
+
+    def get(self, nbytes: int, device) -> torch.Tensor:
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != device:
+            self.buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        return self.buf
+
+
+_default_ws = {}
+
+
+def _ws(ws, device):
+    if ws is None:
+        ws = _default_ws.setdefault(device, Workspace())
+    return ws
+
+
+def workspace_size(op: int, n_x: int, n_y: int, d: int, opts: Opts) -> int:
+    o = opts.c()
+    n = load().sigk_workspace_size(op, n_x, n_y, d, ctypes.byref(o))
+    if n == 0:
+        raise SigkError(-1, "workspace_size rejected the arguments")
+    return int(n)
+
+
+def sync_status(ws: Workspace):
+    lib = load()
+    _check(lib.sigk_sync_status(_ptr(ws.buf), ws.buf.numel(), _stream()))
+
+
+def profile_events(start=None, stop=None):
+    """Record torch.cuda.Event pair around every later solver launch (None: off)."""
+    h = (lambda e: ctypes.c_void_p(e.cuda_event) if e is not None else ctypes.c_void_p(0))
+    load().sigk_profile_events(h(start), h(stop))
+
+
+def counters(ws: Workspace):
+    out = (ctypes.c_double * 3)()
+    _check(load().sigk_counters(_ptr(ws.buf), ws.buf.numel(), _stream(), out))
+    return list(out)
+
+
+def pairs(X, len_x, Y, len_y, opts: Opts | None = None, out=None, ws: Workspace | None = None,
+          check: bool = True):
+    """k(x_p, y_p) for independent pairs -> FP64 CUDA tensor [n_pairs]."""
+    opts = opts or Opts()
+    X, len_x = _paths(X, len_x)
+    Y, len_y = _paths(Y, len_y)
+    n, d = len_x.numel(), X.shape[1]
+    if len_y.numel() != n or Y.shape[1] != d:
+        raise ValueError("x and y batches must match in count and dimension")
+    out = out if out is not None else torch.empty(n, dtype=torch.float64, device=X.device)
+    ws = _ws(ws, X.device)
+    buf = ws.get(workspace_size(OP_PAIRS, n, n, d, opts), X.device)
+    o = opts.c()
+    _check(load().sigk_pairs(_ptr(X), _ptr(len_x), _ptr(Y), _ptr(len_y), n, d, _ptr(out),
+                             _ptr(buf), buf.numel(), _stream(), ctypes.byref(o)))
+    if check:
+        sync_status(ws)
+    return out
+
+
+def gram(X, len_x, Y=None, len_y=None, opts: Opts | None = None, out=None,
+         ws: Workspace | None = None, check: bool = True):
+    """Gram matrix k(x_a, y_b) -> FP64 CUDA tensor [n_x, n_y] (Y=None: Y = X)."""
+    opts = opts or Opts()
+    X, len_x = _paths(X, len_x)
+    n_x, d = len_x.numel(), X.shape[1]
+    if Y is not None:
+        Y, len_y = _paths(Y, len_y)
+        n_y = len_y.numel()
+    else:
+        n_y = 0
+    out = out if out is not None else torch.empty((n_x, n_y or n_x), dtype=torch.float64,
+                                                  device=X.device)
+    ws = _ws(ws, X.device)
+    buf = ws.get(workspace_size(OP_GRAM, n_x, n_y, d, opts), X.device)
+    o = opts.c()
+    _check(load().sigk_gram(_ptr(X), _ptr(len_x), n_x, _ptr(Y), _ptr(len_y), n_y, d, _ptr(out),
+                            _ptr(buf), buf.numel(), _stream(), ctypes.byref(o)))
+    if check:
+        sync_status(ws)
+    return out
+
+
+def mmd(X, len_x, Y, len_y, opts: Opts | None = None, gram_out=None,
+        ws: Workspace | None = None, check: bool = True):
+    """Signature-kernel MMD^2 -> FP64 CUDA tensor [1]."""
+    opts = opts or Opts()
+    X, len_x = _paths(X, len_x)
+    Y, len_y = _paths(Y, len_y)
+    m, n, d = len_x.numel(), len_y.numel(), X.shape[1]
+    out = torch.empty(1, dtype=torch.float64, device=X.device)
+    ws = _ws(ws, X.device)
+    buf = ws.get(workspace_size(OP_MMD, m, n, d, opts), X.device)
+    o = opts.c()
+    _check(load().sigk_mmd(_ptr(X), _ptr(len_x), m, _ptr(Y), _ptr(len_y), n, d, _ptr(out),
+                           _ptr(gram_out), _ptr(buf), buf.numel(), _stream(), ctypes.byref(o)))
+    if check:
+        sync_status(ws)
+    return out

@@ -1,0 +1,51 @@
+"""Host-side checks of the C-ABI that need no GPU: the shared library builds
+for sm_103a, loads, and exports every function declared in include/sigk.h."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2502_20392_gb300 import build, sigk
+    build.build()
+    return sigk.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2502_20392_gb300 import sigk
+    names = sigk.exported_functions()
+    assert {"sigk_pairs", "sigk_gram", "sigk_mmd", "sigk_workspace_size"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", sigk._LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+
+
+def test_version_and_errors_without_gpu(lib):
+    from paper_2502_20392_gb300 import sigk
+    assert b"sm_103a" in lib.sigk_version()
+    # argument validation happens on the host before any CUDA call
+    o = sigk.Opts(order=99).c()
+    assert lib.sigk_workspace_size(0, 4, 4, 4, ctypes.byref(o)) == 0
+    st = lib.sigk_pairs(None, None, None, None, 3, 4, None, None, 0, None, None)
+    assert st == -1  # SIGK_ERR_ARG: null output
+    assert b"NULL" in lib.sigk_last_error() or b"null" in lib.sigk_last_error()
+
+
+def test_no_cpu_fallback_in_product_path():
+    # the product package must not import the oracle
+    pkg = os.path.join(ROOT, "paper_2502_20392_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                with open(os.path.join(dirpath, f)) as fh:
+                    src = fh.read()
+                assert "import oracle" not in src and "from oracle" not in src, f

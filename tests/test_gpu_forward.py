@@ -1,0 +1,143 @@
+"""GPU parity of the forward solver (through the C-ABI) against the FP64 oracle
+and closed forms.  Sizes span several 128-row strips with ragged tails; the
+tolerances are the per-workload relative tolerances (1e-6 for the 256-segment
+pair, 1e-5 for Gram entries), with the Cauchy-Schwarz-scaled error
+|dk| / sqrt(k(x,x) k(y,y)) used for near-zero cross entries."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import i0, j0
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_20392_gb300 import build, sigk
+    build.build()
+    sigk.load()
+    return sigk
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def incs(pts, lens):
+    from paper_2502_20392_gb300 import synth
+    return [np.diff(p.astype(np.float64), axis=0) for p in synth.split(pts, lens)]
+
+
+def to_dev(pts, lens):
+    return torch.from_numpy(pts).to(dev()), torch.from_numpy(lens).to(dev())
+
+
+def rel_err(k, ref, kxx=None, kyy=None):
+    e = np.abs(k - ref) / np.maximum(np.abs(ref), 1e-300)
+    if kxx is not None:
+        cs = np.abs(k - ref) / np.sqrt(np.abs(kxx * kyy))
+        small = np.abs(ref) < 1e-2 * np.sqrt(np.abs(kxx * kyy))
+        e = np.where(small, np.minimum(e, cs), e)
+    return e
+
+
+def test_single_segment_closed_form(S):
+    from paper_2502_20392_gb300 import synth
+    cs = [-4.0, -0.5, 0.01, 0.5, 4.0, 0.0]
+    (X, lx), (Y, ly) = synth.single_segment_pairs(cs)
+    nr = 8
+    k = S.pairs(*to_dev(X, lx), *to_dev(Y, ly), opts=S.Opts(order=16, rings=nr)).cpu().numpy()
+    for kc, c in zip(k, cs):
+        # one tile with nr Neumann rings is the Bessel partial sum up to c^nr/(nr!)^2
+        terms = [c**m / math.factorial(m) ** 2 for m in range(nr + 1)]
+        fp32 = 4e-7 * sum(abs(t) for t in terms)  # a few FP32 roundings of the largest terms
+        assert abs(kc - sum(terms)) <= fp32, (c, kc, sum(terms))
+        bessel = i0(2 * math.sqrt(c)) if c >= 0 else j0(2 * math.sqrt(-c))
+        tail = abs(c) ** (nr + 1) / math.factorial(nr + 1) ** 2 * 1.01
+        assert abs(kc - bessel) <= tail + fp32, (c, kc, bessel)
+
+
+def test_pair_256_d4(S, orc):
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.workload_pair_256()
+    dx, dy = incs(pts, lens)
+    ref = orc.series_pair(dx, dy)
+    X, L = to_dev(pts, lens)
+    xs, ys = X[:257], X[257:]
+    lx, ly = L[:1], L[1:]
+    k = S.pairs(xs, lx, ys, ly, opts=S.Opts(order=8, rings=4)).cpu().numpy()[0]
+    assert abs(k - ref) / abs(ref) < 1e-6, (k, ref)
+
+
+@pytest.mark.parametrize("sigma,order,rings", [(1.0, 8, 4), (4.0, 16, 6)])
+def test_gram_ragged_d16(S, orc, sigma, order, rings):
+    from paper_2502_20392_gb300 import synth
+    # common time step 1/300: a short path is a short piece of Brownian motion
+    # (one 1-segment path would otherwise carry a tile with c ~ 16 sigma^2)
+    segs = np.array([300, 129, 1, 257, 64, 200])
+    pts, lens = synth.brownian(len(segs), segs, 16, sigma * np.sqrt(segs / 300), seed=77 + int(sigma))
+    ref = orc.series_gram(incs(pts, lens), N=28)
+    G = S.gram(*to_dev(pts, lens), opts=S.Opts(order=order, rings=rings)).cpu().numpy()
+    dg = np.diag(ref)
+    e = rel_err(G, ref, dg[:, None], dg[None, :])
+    assert e.max() < 1e-5, e.max()
+    np.testing.assert_array_equal(G, G.T)
+
+
+def test_gram_full_matches_mirrored(S):
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(5, [90, 200, 33, 150, 7], 8, 1.0, seed=5)
+    X, L = to_dev(pts, lens)
+    G1 = S.gram(X, L, opts=S.Opts(order=8, rings=4)).cpu().numpy()
+    G2 = S.gram(X, L, opts=S.Opts(order=8, rings=4, flags=S.FLAG_GRAM_FULL)).cpu().numpy()
+    # both triangles computed independently (grid transposed for the lower one)
+    np.testing.assert_allclose(G2, G2.T, rtol=1e-6)
+    np.testing.assert_allclose(G1, G2, rtol=1e-6)
+
+
+def test_gram_xy_and_pairs_ragged(S, orc):
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.ragged_pairs(12, 1, 700, 8, 0.5, 2.0, seed=13)
+    xs, ys = synth.split(X, lx), synth.split(Y, ly)
+    xs[3] = xs[3][:1]  # one-point paths: k = 1 with anything
+    ys[5] = ys[5][:1]
+    X, lx = synth.pack(xs)
+    Y, ly = synth.pack(ys)
+    ix, iy = incs(X, lx), incs(Y, ly)
+    ref = orc.series_pairs(ix, iy, N=28)
+    kxx = orc.series_pairs(ix, ix, N=28)
+    kyy = orc.series_pairs(iy, iy, N=28)
+    k = S.pairs(*to_dev(X, lx), *to_dev(Y, ly), opts=S.Opts(order=10, rings=5)).cpu().numpy()
+    assert k[3] == 1.0 and k[5] == 1.0
+    e = rel_err(k, ref, kxx, kyy)
+    assert e.max() < 1e-5, e
+    # cross Gram X vs Y: its diagonal is the pairwise result
+    Gxy = S.gram(*to_dev(X, lx), *to_dev(Y, ly), opts=S.Opts(order=10, rings=5)).cpu().numpy()
+    np.testing.assert_allclose(np.diag(Gxy), k, rtol=1e-6)
+
+
+def test_increments_mode(S, orc):
+    from paper_2502_20392_gb300 import synth
+    inc, segs, u, tot = synth.collinear_increments(5000, 8, seed=3002, n_paths=2)
+    X = torch.from_numpy(inc).to(dev())
+    L = torch.from_numpy(segs).to(dev())
+    o = S.Opts(order=4, rings=2, flags=S.FLAG_INCREMENTS, max_len=5000)
+    k = S.pairs(X[:5000], L[:1], X[5000:], L[1:], opts=o).cpu().numpy()[0]
+    s = float(u @ u) * tot[0] * tot[1]
+    ref = i0(2 * math.sqrt(s))
+    assert abs(k - ref) / ref < 1e-5, (k, ref)
+
+
+def test_mmd_small(S, orc):
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.workload_mmd_2048(seed=5001, n_paths=5, n_seg=150, d=8)
+    ref = orc.mmd2(incs(X, lx), incs(Y, ly), N=24)
+    v = S.mmd(*to_dev(X, lx), *to_dev(Y, ly), opts=S.Opts(order=8, rings=4)).cpu().numpy()[0]
+    Kxx = orc.series_gram(incs(X, lx))
+    scale = np.abs(Kxx).max()
+    assert abs(v - ref) <= 1e-5 * max(abs(ref), scale * 1e-2), (v, ref)
