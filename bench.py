@@ -185,6 +185,10 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in SIGMAS] for _ in range(args.steps)]
+    for row in kev:  # torch creates an event on first record: do it before handing out handles
+        for a, b in row:
+            a.record()
+            b.record()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
