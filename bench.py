@@ -297,9 +297,11 @@ def main():
         vals, secs, thr = oracle_sample(host, ORACLE_SAMPLE_PAIRS)
         errs = []
         for (idx, ref), Gk in zip(vals, host_G):
-            diag = [host_G[0][a, a] for a in range(N_PATHS)]
             for (a, b), r in zip(idx, ref):
                 e = abs(Gk[a, b] - r) / max(abs(r), 1e-300)
+                cs_scale = (abs(Gk[a, a] * Gk[b, b])) ** 0.5
+                if abs(r) < 1e-2 * cs_scale:  # near-zero cross entry: Cauchy-Schwarz scale
+                    e = min(e, abs(Gk[a, b] - r) / cs_scale)
                 errs.append(e)
         n_cells = sum(len(idx) for idx, _ in vals) * N_SEG * N_SEG
         line["cpu_baseline"] = {"value": n_cells / secs, "unit": "cells/s", "cores": thr,

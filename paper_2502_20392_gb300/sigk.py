@@ -144,6 +144,10 @@ def workspace_size(op: int, n_x: int, n_y: int, d: int, opts: Opts) -> int:
 
 
 def sync_status(ws: Workspace):
+    """Wait for the stream and raise if a device-side error was recorded."""
+    if ws.buf is None:
+        torch.cuda.current_stream().synchronize()
+        return
     lib = load()
     _check(lib.sigk_sync_status(_ptr(ws.buf), ws.buf.numel(), _stream()))
 
