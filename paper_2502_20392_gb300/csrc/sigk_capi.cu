@@ -136,7 +136,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     // 2 * max_len), so a producer never waits on a consumer that cannot start.
     L->nslot = L->nwarps + 64;
     int64_t w = 2 * o.max_len / L->nwarps + 64;
-    if (w < 1024) w = 1024;
+    if (w < 256) w = 256;
     if (w > o.max_len) w = o.max_len;
     w = (w + 31) & ~(int64_t)31;
     if (w < 32) w = 32;
