@@ -121,6 +121,31 @@ sigk_status sigk_mmd(const float* X, const int64_t* len_x, int64_t m, const floa
                      double* gram_out, void* ws, size_t ws_bytes, void* stream,
                      const sigk_opts* opts);
 
+/* Same result as sigk_pairs, for callers that cannot allocate device memory
+ * (code that runs where cudaMalloc is not allowed or not wanted: inside a
+ * region governed by someone else's memory pool or allocator, or a runtime
+ * that forbids side allocations).  The paper has no counterpart: this is an
+ * interface convenience.  It takes no workspace: its scratch is a fixed
+ * 32 MiB device array inside libsigk.so, which every GPU that loads the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture on the device.
+ *   - Problems whose scratch does not fit in 32 MiB (many pairs, long swept
+ *     paths, high order) are rejected with SIGK_ERR_WORKSPACE before any
+ *     launch; use sigk_pairs with a caller workspace for those.
+ *   - All calls share the one array, and each call resets the parts that must
+ *     start at zero; calls that overlap on the GPU (different streams, or
+ *     different host threads) race on it and must be serialised by the caller.
+ * Device-side errors are read back with sigk_static_sync_status. */
+sigk_status sigk_pairs_static(const float* X, const int64_t* len_x, const float* Y,
+                              const int64_t* len_y, int64_t n_pairs, int d, double* k_out,
+                              void* stream, const sigk_opts* opts);
+
+/* sigk_sync_status for the static scratch of sigk_pairs_static. */
+sigk_status sigk_static_sync_status(void* stream);
+
 /* Recommended (order, rings) for a target relative tolerance `tol`, from
  * statistics of the increments computed on the device (host lengths are not
  * needed).  Synchronises `stream`.  Writes into *opts_out (flags and

@@ -596,3 +596,83 @@ const char* sigk_last_error(void) { return g_last_error.c_str(); }
 const char* sigk_version(void) { return "sigk-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation entry point (sigk_pairs_static).
+//
+// For callers that cannot call cudaMalloc -- e.g. code running inside a
+// memory-pool-managed or graph-captured region, or a host runtime with its
+// own allocator that forbids side allocations -- the scratch that sigk_pairs
+// takes from the caller's workspace comes here from a fixed device array in
+// this file.  Every GPU that loads the library holds these bytes until the
+// process exits.  In host code `g_static_ws` only names a host-side stand-in:
+// its device address is obtained once per device with cudaGetSymbolAddress
+// (with that device current) on the first call there, and only that address
+// is passed to kernels.
+
+namespace sigk {
+
+constexpr size_t kStaticWsBytes = (size_t)32 << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_static_ws[kStaticWsBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_static_mu;
+static void* g_static_ptr[kMaxDevices];  // device address of g_static_ws per device
+
+static sigk_status static_ws_ptr(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(SIGK_ERR_UNSUPPORTED, "device index too large");
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_ws);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return SIGK_OK;
+}
+
+}  // namespace sigk
+
+extern "C" sigk_status sigk_pairs_static(const float* X, const int64_t* len_x, const float* Y,
+                                         const int64_t* len_y, int64_t n_pairs, int d,
+                                         double* k_out, void* stream, const sigk_opts* opts) {
+    using namespace sigk;
+    sigk_status st = common_checks(n_pairs, n_pairs, d, k_out);
+    if (st != SIGK_OK) return st;
+    if (n_pairs > 0 && (!X || !Y || !len_x || !len_y)) return fail(SIGK_ERR_ARG, "null input");
+    Opts o;
+    if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    if (n_pairs == 0) return SIGK_OK;
+    // Fit the layout into the static scratch: first with the requested grid,
+    // then with one CTA per SM (fewer warps, smaller seam ring).
+    Layout L;
+    if ((st = make_layout(SIGK_OP_PAIRS, n_pairs, n_pairs, d, o, &L)) != SIGK_OK) return st;
+    if (L.total > kStaticWsBytes) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        o.grid_ctas = sms > 0 ? sms : 1;
+        if ((st = make_layout(SIGK_OP_PAIRS, n_pairs, n_pairs, d, o, &L)) != SIGK_OK) return st;
+    }
+    if (L.total > kStaticWsBytes)
+        return fail(SIGK_ERR_WORKSPACE,
+                    "problem needs " + std::to_string(L.total) + " bytes of scratch; the static "
+                    "scratch of sigk_pairs_static holds " + std::to_string(kStaticWsBytes) +
+                    " (use sigk_pairs with a caller workspace)");
+    void* ws = nullptr;
+    if ((st = static_ws_ptr(&ws)) != SIGK_OK) return st;
+    return run_solver(SIGK_OP_PAIRS, X, len_x, n_pairs, Y, len_y, n_pairs, d, k_out, 0, ws,
+                      kStaticWsBytes, (cudaStream_t)stream, o, nullptr);
+}
+
+extern "C" sigk_status sigk_static_sync_status(void* stream) {
+    using namespace sigk;
+    void* ws = nullptr;
+    sigk_status st = static_ws_ptr(&ws);
+    if (st != SIGK_OK) return st;
+    return sigk_sync_status(ws, kStaticWsBytes, stream);
+}
