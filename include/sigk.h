@@ -121,6 +121,37 @@ sigk_status sigk_mmd(const float* X, const int64_t* len_x, int64_t m, const floa
                      double* gram_out, void* ws, size_t ws_bytes, void* stream,
                      const sigk_opts* opts);
 
+/* Workspace bytes for sigk_backward (same arguments as sigk_workspace_size).
+ * Includes the forward seam store, which needs up to
+ * n_pairs * (ceil(max_len/32) - 1) * max_len * (order + 3) floats. */
+size_t sigk_backward_workspace_size(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts);
+
+/* Gradients by the adjoint of the solver (reverse-mode differentiation of the
+ * truncated FP32 scheme; the paper has no gradient -- this is the adjoint of
+ * the tile map of Sec. 2.3 swept in reverse wavefront order).
+ * The call runs a training forward that stores the right-edge seam of every
+ * 32-row strip (checkpointed wavefront boundaries), then the adjoint kernel,
+ * which replays each strip from its stored seam, rebuilds every tile's inputs
+ * by inverting the tile's bottom-to-top update, and chains dk/dc_ij to the
+ * increments on the fly.
+ *   op, X, len_x, n_x, Y, len_y, n_y, d: as in sigk_pairs / sigk_gram /
+ *     sigk_mmd (SIGK_OP_GRAM with Y == NULL: Gram of X with itself).
+ *   grad_out (device FP64): upstream gradient of the op's output --
+ *     [n_pairs] (PAIRS), [n_x * n_y] row-major (GRAM; n_x * n_x when
+ *     Y == NULL), [1] (MMD).
+ *   grad_X, grad_Y (device FP32, same layout as X and Y, or NULL to skip):
+ *     OVERWRITTEN with dL/dX, dL/dY (L = <grad_out, output>); gradients are
+ *     with respect to the points, or to the increments with
+ *     SIGK_FLAG_INCREMENTS.  For a Gram of X with itself only grad_X is used.
+ *   value_out (device FP64): receives the forward output (k values, Gram,
+ *     or MMD^2); required for PAIRS and GRAM, optional for MMD.
+ * Errors on the device are reported by sigk_sync_status. */
+sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t n_x,
+                          const float* Y, const int64_t* len_y, int64_t n_y, int d,
+                          const double* grad_out, float* grad_X, float* grad_Y,
+                          double* value_out, void* ws, size_t ws_bytes, void* stream,
+                          const sigk_opts* opts);
+
 /* Same result as sigk_pairs, for callers that cannot allocate device memory
  * (code that runs where cudaMalloc is not allowed or not wanted: inside a
  * region governed by someone else's memory pool or allocator, or a runtime
@@ -159,9 +190,9 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
  * ws by earlier calls (SIGK_OK, SIGK_ERR_TIMEOUT or SIGK_ERR_NONFINITE). */
 sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream);
 
-/* Counters of the last completed launch on this workspace (host copy after
- * sigk_sync_status): out[0] = tiles processed, out[1] = tiles including
- * padding, out[2] = algorithmic FP32 flops (FMA = 2) of the tile solver. */
+/* Counters of the last call on this workspace (synchronises `stream`):
+ * out[0] = tiles solved by the forward, out[1] = lane-tiles including strip
+ * padding, out[2] = tiles solved by the adjoint kernel. */
 sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out3);
 
 /* Profiling hook: when both are non-NULL, later calls on this host thread

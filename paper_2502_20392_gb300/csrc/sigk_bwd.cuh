@@ -1,0 +1,444 @@
+// sigk_bwd.cuh -- reverse-mode (adjoint) sweep of the wavefront solver.
+//
+// Runs after a training forward that stored every strip's right-edge seam
+// (the checkpointed wavefront boundaries; strips of 32 rows, one row per
+// lane).  One work item = (pair, strip), strips of a pair in DECREASING order.
+//
+// Pass A replays the strip's forward from its stored input seam and keeps, per
+// lane and column, the lane's incoming left edge and the exponent decisions
+// (a record of P+3 floats) in a per-warp scratch area; it ends with each
+// lane's bottom-edge state after the last column in registers.
+//
+// Pass B sweeps the columns in reverse with the mirrored skew (lane 31 first).
+// At each tile it rebuilds the tile's bottom-edge input by inverting the
+// bottom-to-top update (tile_inverse_a) from the known top edge and the stored
+// left edge, then applies the adjoint of the tile map (tile_adjoint): the
+// adjoint of the right edge arrives from lane+1 (or, for lane 31, from the
+// next strip's adjoint seam or the seed at the last tile), the adjoint of the
+// top edge is the lane's own state from the column above.  dk/dc_ij is
+// chained at once to the increments: dk/ddx_i += g dy_j (registers),
+// dk/ddy_j += g dx_i (a shared-memory column accumulator flushed with
+// atomics), g = dk/dc_ij times the pair's upstream weight.
+#pragma once
+#include "sigk_device.cuh"
+#include "sigk_fwd.cuh"
+
+namespace sigk {
+
+struct BwdArgs {
+    const PairDesc* pairs;
+    const int32_t* item_start;
+    int32_t n_pairs;
+    int32_t inc_mode;
+    int32_t d;
+    int32_t nr;
+    const float* store;          // forward seams, per pair (training forward)
+    const int64_t* store_off;    // [n_pairs] float offsets into store
+    const int32_t* pair_exp;     // [n_pairs] exponent of the final value
+    const double* pair_w;        // [n_pairs] upstream weight of each pair
+    float* rec;                  // per-warp records
+    int64_t rec_stride;          // floats per warp
+    int32_t nslot;               // adjoint seam ring
+    int32_t wcols;
+    float* aseam;
+    unsigned long long* prod;
+    unsigned long long* cons;
+    long long* done;
+    int* item_counter;
+    int* status;
+    unsigned long long* counters;
+};
+
+template <int P, int D>
+struct BwdSmem {
+    static constexpr int S = P + 3;   // record / forward seam entry
+    static constexpr int SA = P + 1;  // adjoint seam entry: corner, b1..bP
+    static constexpr int DS = DyStride<D>::value;
+    static constexpr int per_warp = 64 * DS + 32 * S + 2 * 32 * SA + 64 * D;
+};
+
+__device__ __forceinline__ float exp2_nonneg(int n) {
+    return __int_as_float((127 + (n > 127 ? 127 : n)) << 23);
+}
+
+// exponent word of a record: F/64 (15 bits) | E_before/64 (16 bits) | bump
+__device__ __forceinline__ int pack_exp(int F, int Eb, int bump) {
+    return ((F >> 6) << 17) | (((Eb >> 6) & 0xFFFF) << 1) | bump;
+}
+__device__ __forceinline__ void unpack_exp(int w, int& F, int& Eb, int& bump) {
+    bump = w & 1;
+    Eb = ((int)(short)((w >> 1) & 0xFFFF)) * 64;
+    F = (w >> 17) * 64;
+}
+
+// increment gradient v of segment `row` -> points (+v at row+1, -v at row) or
+// increments (+v at row)
+template <int D>
+__device__ __forceinline__ void add_inc_grad(float* g, int64_t row, int d, int inc_mode,
+                                             const float (&v)[D]) {
+    if (!g) return;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        if (e < d && v[e] != 0.0f) {
+            if (inc_mode) {
+                atomicAdd(g + row * d + e, v[e]);
+            } else {
+                atomicAdd(g + (row + 1) * d + e, v[e]);
+                atomicAdd(g + row * d + e, -v[e]);
+            }
+        }
+    }
+}
+
+template <int P, int D>
+__global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
+    constexpr int S = P + 3;
+    constexpr int SA = P + 1;
+    constexpr int DS = DyStride<D>::value;
+    extern __shared__ float4 smem_f4[];
+    float* smem = reinterpret_cast<float*>(smem_f4);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
+    float* dyw = smem + warp * BwdSmem<P, D>::per_warp;  // 64-column ring of dy
+    float* sin_ = dyw + 64 * DS;                        // forward seam-in block
+    float* ain = sin_ + 32 * S;                         // adjoint seam-in block
+    float* aout = ain + 32 * SA;                        // adjoint seam-out block
+    float* colacc = aout + 32 * SA;                     // 64 x D column gradient
+    float* rec = A.rec + (size_t)gwarp * A.rec_stride;
+    const int n_items = A.item_start[A.n_pairs];
+    unsigned long long tiles = 0;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(A.item_counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n_items) break;
+        if (ld_volatile_s32(A.status) != 0) break;
+        int lo_p = 0, hi_p = A.n_pairs - 1;
+        while (lo_p < hi_p) {
+            int mid = (lo_p + hi_p + 1) >> 1;
+            if (A.item_start[mid] <= item) lo_p = mid; else hi_p = mid - 1;
+        }
+        const PairDesc pd = A.pairs[lo_p];
+        const int nst = pd.n_strips;
+        const int s = nst - 1 - (item - A.item_start[lo_p]);  // reverse strip order
+        const int L1 = pd.L1, L2 = pd.L2;
+        const int row = s * 32 + lane;
+        const bool has_row = row < L1;
+        const float* st_base = A.store + A.store_off[lo_p];
+        bool ok = true;
+
+        float dx[D];
+#pragma unroll
+        for (int e = 0; e < D; ++e)
+            dx[e] = (has_row && e < A.d) ? inc_at(pd.xr, row, A.d, e, A.inc_mode) : 0.0f;
+
+        // ------------------------- pass A: forward replay ------------------------
+        float a[P + 1];
+#pragma unroll
+        for (int p = 0; p <= P; ++p) a[p] = 0.0f;
+        int E = 0;
+        float ohi = 1.0f, olo = 0.0f, ob[P + 1];
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ob[q] = 0.0f;
+        int oE = 0;
+        const int T = L2 + 31;
+        for (int t = 0; t < T; ++t) {
+            if ((t & 31) == 0 && t < L2) {
+                const int nb = min(32, L2 - t);
+                for (int idx = lane; idx < 32 * D; idx += 32) {
+                    const int col = idx / D, e = idx % D;
+                    float v = 0.0f;
+                    if (col < nb && e < A.d) v = inc_at(pd.yr, t + col, A.d, e, A.inc_mode);
+                    dyw[((t + col) & 63) * DS + e] = v;
+                }
+                if (s > 0) {
+                    const float* src = st_base + ((size_t)(s - 1) * L2 + t) * S;
+                    for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = src[idx];
+                }
+                __syncwarp();
+            }
+            float hi = __shfl_up_sync(kFull, ohi, 1);
+            float lo = __shfl_up_sync(kFull, olo, 1);
+            float b[P + 1];
+            b[0] = 0.0f;
+#pragma unroll
+            for (int q = 1; q <= P; ++q) b[q] = __shfl_up_sync(kFull, ob[q], 1);
+            int F = __shfl_up_sync(kFull, oE, 1);
+            if (lane == 0) {
+                if (s > 0 && t < L2) {
+                    const float* e_ = sin_ + (t & 31) * S;
+                    hi = e_[0];
+                    lo = e_[1];
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] = e_[1 + q];
+                    F = __float_as_int(e_[P + 2]);
+                } else {
+                    hi = 1.0f; lo = 0.0f; F = 0;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] = 0.0f;
+                }
+            }
+            const int j = t - lane;
+            if (j >= 0 && j < L2) {
+                // record of the incoming left edge, before alignment
+                float* r = rec + (size_t)t * S * 32 + lane;
+                r[0] = hi;
+                r[32] = lo;
+#pragma unroll
+                for (int q = 1; q <= P; ++q) r[(1 + q) * 32] = b[q];
+                const int Eb = E;
+                if (F != E) {
+                    if (F > E) {
+                        const float sc = exp2_nonpos(E - F);
+#pragma unroll
+                        for (int p = 1; p <= P; ++p) a[p] *= sc;
+                        E = F;
+                    } else {
+                        const float sc = exp2_nonpos(F - E);
+                        hi *= sc; lo *= sc;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) b[q] *= sc;
+                    }
+                }
+                const float4* rowp = reinterpret_cast<const float4*>(dyw + (j & 63) * DS);
+                float c = 0.0f;
+#pragma unroll
+                for (int e4 = 0; e4 < D / 4; ++e4) {
+                    const float4 v = rowp[e4];
+                    c = fmaf(dx[4 * e4 + 0], v.x, c);
+                    c = fmaf(dx[4 * e4 + 1], v.y, c);
+                    c = fmaf(dx[4 * e4 + 2], v.z, c);
+                    c = fmaf(dx[4 * e4 + 3], v.w, c);
+                }
+                tile_update<P>(c, a, hi, lo, b, A.nr);
+                int bump = 0;
+                if (fabsf(hi) > 1.8446744e19f) {
+                    const float sc = 5.421011e-20f;
+#pragma unroll
+                    for (int p = 1; p <= P; ++p) a[p] *= sc;
+                    hi *= sc; lo *= sc;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] *= sc;
+                    E += 64;
+                    bump = 1;
+                }
+                r[(P + 2) * 32] = __int_as_float(pack_exp(F, Eb, bump));
+                ohi = hi; olo = lo; oE = E;
+#pragma unroll
+                for (int q = 1; q <= P; ++q) ob[q] = b[q];
+            }
+        }
+        __syncwarp();
+
+        // ------------------------- pass B: reverse sweep -------------------------
+        const double wsc_d = A.pair_w[lo_p] * ldexp(1.0, A.pair_exp[lo_p]);
+        const float wsc = (float)wsc_d;
+        const bool last_strip = (s == nst - 1);
+        const bool has_ain = !last_strip;
+        const bool has_aout = s > 0;
+        const int slot_in = (item - 1 + A.nslot) % A.nslot;
+        const int slot_out = item % A.nslot;
+        if (has_aout) {
+            const long long prev_consumer = (long long)item - A.nslot + 1;
+            bool okl = true;
+            if (lane == 0)
+                okl = wait_ge_s64(&A.done[((prev_consumer % A.nslot) + A.nslot) % A.nslot],
+                                  prev_consumer, A.status);
+            ok = __shfl_sync(kFull, okl, 0);
+        }
+        float Ab[P + 1];
+#pragma unroll
+        for (int p = 0; p <= P; ++p) Ab[p] = 0.0f;
+        float gx[D];
+#pragma unroll
+        for (int e = 0; e < D; ++e) gx[e] = 0.0f;
+        for (int idx = lane; idx < 64 * D; idx += 32) colacc[idx] = 0.0f;
+        float oB0 = 0.0f, oBb[P + 1];
+#pragma unroll
+        for (int q = 0; q <= P; ++q) oBb[q] = 0.0f;
+        const int lp = 31 - lane;
+        __syncwarp();
+        for (int tp = 0; tp < T && ok; ++tp) {
+            if ((tp & 31) == 0 && tp < L2) {
+                const int nb = min(32, L2 - tp);
+                // dy for reverse columns jr in [tp, tp+nb): j = L2-1-jr
+                for (int idx = lane; idx < 32 * D; idx += 32) {
+                    const int col = idx / D, e = idx % D;
+                    float v = 0.0f;
+                    if (col < nb && e < A.d) v = inc_at(pd.yr, L2 - 1 - (tp + col), A.d, e, A.inc_mode);
+                    dyw[((tp + col) & 63) * DS + e] = v;
+                }
+                if (has_ain) {
+                    const unsigned long long need =
+                        ((unsigned long long)(item - 1) << 32) | (unsigned)(tp + nb);
+                    bool okl = true;
+                    if (lane == 0) okl = wait_ge_u64(&A.prod[slot_in], need, A.status);
+                    ok = __shfl_sync(kFull, okl, 0);
+                    if (ok) {
+                        const float* src = A.aseam + ((size_t)slot_in * A.wcols + (tp % A.wcols)) * SA;
+                        for (int idx = lane; idx < nb * SA; idx += 32) ain[idx] = __ldcg(src + idx);
+                        __syncwarp();
+                        if (lane == 0)
+                            st_release_u64(&A.cons[slot_in],
+                                           ((unsigned long long)item << 32) | (unsigned)(tp + nb));
+                    }
+                }
+                __syncwarp();
+                if (!ok) break;
+            }
+            // adjoint of the right edge: from lane+1, or seam / seed for lane 31
+            float B0 = __shfl_down_sync(kFull, oB0, 1);
+            float Bb[P + 1];
+            Bb[0] = 0.0f;
+#pragma unroll
+            for (int q = 1; q <= P; ++q) Bb[q] = __shfl_down_sync(kFull, oBb[q], 1);
+            if (lane == 31) {
+                if (has_ain && tp < L2) {
+                    const float* e_ = ain + (tp & 31) * SA;
+                    B0 = e_[0];
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) Bb[q] = e_[q];
+                } else {
+                    const bool seed = last_strip && tp == 0;  // k = b0 + sum_q bh_q / q!
+                    B0 = seed ? 1.0f : 0.0f;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) Bb[q] = seed ? c_inv_fact[q] : 0.0f;
+                }
+            }
+            const int jr = tp - lp;
+            if (jr >= 0 && jr < L2) {
+                const int j = L2 - 1 - jr;
+                const int t = j + lane;  // pass-A step of this record
+                const float* r = rec + (size_t)t * S * 32 + lane;
+                float hi = r[0];
+                float b[P + 1];
+                b[0] = 0.0f;
+#pragma unroll
+                for (int q = 1; q <= P; ++q) b[q] = r[(1 + q) * 32];
+                int F, Eb, bump;
+                unpack_exp(__float_as_int(r[(P + 2) * 32]), F, Eb, bump);
+                const int Em = F > Eb ? F : Eb;
+                if (bump) {  // undo the renormalisation after this tile
+                    const float up = 1.8446744e19f, dn = 5.421011e-20f;
+#pragma unroll
+                    for (int p = 1; p <= P; ++p) { a[p] *= up; Ab[p] *= dn; }
+                    B0 *= dn;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) Bb[q] *= dn;
+                }
+                if (F < Em) {  // the incoming edge was scaled to the lane exponent
+                    const float sc = exp2_nonpos(F - Em);
+                    hi *= sc;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] *= sc;
+                }
+                const float4* rowp = reinterpret_cast<const float4*>(dyw + (jr & 63) * DS);
+                float dy[D];
+#pragma unroll
+                for (int e4 = 0; e4 < D / 4; ++e4) {
+                    const float4 v = rowp[e4];
+                    dy[4 * e4 + 0] = v.x; dy[4 * e4 + 1] = v.y;
+                    dy[4 * e4 + 2] = v.z; dy[4 * e4 + 3] = v.w;
+                }
+                float c = 0.0f;
+#pragma unroll
+                for (int e = 0; e < D; ++e) c = fmaf(dx[e], dy[e], c);
+                float ain_[P + 1], ha[P + 1];
+                tile_inverse_a<P>(c, a, hi, b, A.nr, ain_, ha);
+                const float cbar = tile_adjoint<P>(c, ain_, hi, b, ha, Ab, B0, Bb, A.nr);
+                // undo the alignment of this step
+                if (Eb < Em) {
+                    const float dn = exp2_nonpos(Eb - Em), up = exp2_nonneg(Em - Eb);
+#pragma unroll
+                    for (int p = 1; p <= P; ++p) { a[p] = ain_[p] * up; Ab[p] *= dn; }
+                } else {
+#pragma unroll
+                    for (int p = 1; p <= P; ++p) a[p] = ain_[p];
+                }
+                if (F < Em) {
+                    const float sc = exp2_nonpos(F - Em);
+                    B0 *= sc;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) Bb[q] *= sc;
+                }
+                const float g = cbar * wsc;
+                float* ca = colacc + (jr & 63) * D;
+#pragma unroll
+                for (int e = 0; e < D; ++e) {
+                    gx[e] = fmaf(g, dy[e], gx[e]);
+                    ca[e] = fmaf(g, dx[e], ca[e]);
+                }
+                oB0 = B0;
+#pragma unroll
+                for (int q = 1; q <= P; ++q) oBb[q] = Bb[q];
+                if (lane == 0 && has_aout) {
+                    float* e_ = aout + (jr & 31) * SA;
+                    e_[0] = B0;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) e_[q] = Bb[q];
+                }
+                tiles += has_row ? 1ull : 0ull;
+            }
+            __syncwarp();
+            // lane 0 closed a block of 32 reverse columns: flush gradients and seam
+            const int jj = tp - 31;
+            if (jj >= 0 && jj < L2 && (((jj & 31) == 31) || jj == L2 - 1)) {
+                const int start = jj & ~31;
+                const int nb = jj - start + 1;
+                if (pd.gyr) {
+                    for (int idx = lane; idx < nb * D; idx += 32) {
+                        const int col = idx / D, e = idx % D;
+                        float* cell = colacc + ((start + col) & 63) * D + e;
+                        const float v = *cell;
+                        *cell = 0.0f;
+                        if (e < A.d && v != 0.0f) {
+                            const int64_t jcol = L2 - 1 - (start + col);
+                            if (A.inc_mode) {
+                                atomicAdd(pd.gyr + jcol * A.d + e, v);
+                            } else {
+                                atomicAdd(pd.gyr + (jcol + 1) * A.d + e, v);
+                                atomicAdd(pd.gyr + jcol * A.d + e, -v);
+                            }
+                        }
+                    }
+                } else {
+                    for (int idx = lane; idx < nb * D; idx += 32)
+                        colacc[((start + idx / D) & 63) * D + idx % D] = 0.0f;
+                }
+                if (has_aout) {
+                    if (start + nb > A.wcols) {
+                        const unsigned long long need = ((unsigned long long)(item + 1) << 32) |
+                                                        (unsigned)(start + nb - A.wcols);
+                        bool okl = true;
+                        if (lane == 0) okl = wait_ge_u64(&A.cons[slot_out], need, A.status);
+                        ok = __shfl_sync(kFull, okl, 0);
+                    }
+                    if (ok) {
+                        float* dst = A.aseam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * SA;
+                        for (int idx = lane; idx < nb * SA; idx += 32) __stcg(dst + idx, aout[idx]);
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0)
+                            st_release_u64(&A.prod[slot_out],
+                                           ((unsigned long long)item << 32) | (unsigned)(start + nb));
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (has_row) add_inc_grad<D>(pd.gxr, row, A.d, A.inc_mode, gx);
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            st_release_s64(&A.done[item % A.nslot], (long long)item);
+        }
+        if (!ok) break;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tiles += __shfl_down_sync(kFull, tiles, o);
+    if (lane == 0) atomicAdd(&A.counters[2], tiles);
+}
+
+}  // namespace sigk

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/sigk.h"
+#include "sigk_bwd.cuh"
 #include "sigk_device.cuh"
 #include "sigk_launch.h"
 
@@ -67,30 +68,37 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
 
 static int dim_bucket(int d) { return d <= 4 ? 4 : (d <= 8 ? 8 : (d <= 16 ? 16 : -1)); }
 
-static int fwd_info_dispatch(int P, int D, KernelInfo* info) {
-    switch (P) {
-        case 4: return fwd_info<4>(D, info);
-        case 6: return fwd_info<6>(D, info);
-        case 8: return fwd_info<8>(D, info);
-        case 10: return fwd_info<10>(D, info);
-        case 12: return fwd_info<12>(D, info);
-        case 14: return fwd_info<14>(D, info);
-        case 16: return fwd_info<16>(D, info);
-        default: return -1;
+#define SIGK_DISPATCH_P(FN, ...)                 \
+    switch (P) {                                 \
+        case 4: return FN<4>(__VA_ARGS__);       \
+        case 6: return FN<6>(__VA_ARGS__);       \
+        case 8: return FN<8>(__VA_ARGS__);       \
+        case 10: return FN<10>(__VA_ARGS__);     \
+        case 12: return FN<12>(__VA_ARGS__);     \
+        case 14: return FN<14>(__VA_ARGS__);     \
+        case 16: return FN<16>(__VA_ARGS__);     \
+        default: break;                          \
     }
+
+static int fwd_info_dispatch(int P, int D, int R, KernelInfo* info) {
+    SIGK_DISPATCH_P(fwd_info, D, R, info)
+    return -1;
 }
 
-static cudaError_t fwd_launch_dispatch(int P, int D, const SolverArgs& a, int grid, cudaStream_t s) {
-    switch (P) {
-        case 4: return fwd_launch<4>(D, a, grid, s);
-        case 6: return fwd_launch<6>(D, a, grid, s);
-        case 8: return fwd_launch<8>(D, a, grid, s);
-        case 10: return fwd_launch<10>(D, a, grid, s);
-        case 12: return fwd_launch<12>(D, a, grid, s);
-        case 14: return fwd_launch<14>(D, a, grid, s);
-        case 16: return fwd_launch<16>(D, a, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
+static cudaError_t fwd_launch_dispatch(int P, int D, int R, const SolverArgs& a, int grid,
+                                       cudaStream_t s) {
+    SIGK_DISPATCH_P(fwd_launch, D, R, a, grid, s)
+    return cudaErrorInvalidValue;
+}
+
+static int bwd_info_dispatch(int P, int D, KernelInfo* info) {
+    SIGK_DISPATCH_P(bwd_info, D, info)
+    return -1;
+}
+
+static cudaError_t bwd_launch_dispatch(int P, int D, const BwdArgs& a, int grid, cudaStream_t s) {
+    SIGK_DISPATCH_P(bwd_launch, D, a, grid, s)
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -98,6 +106,12 @@ static cudaError_t fwd_launch_dispatch(int P, int D, const SolverArgs& a, int gr
 
 struct Layout {
     size_t hdr, ox, oy, pairs, item_start, prod, cons, done, seam, gram, total;
+    // backward sections (train == true)
+    size_t store, store_off, pair_exp, pair_w, rec, bprod, bcons, bdone, aseam;
+    int64_t store_floats, rec_stride;
+    int bnslot, bwcols, bgrid, bnwarps;
+    KernelInfo binfo;
+    bool train;
     int64_t n_pairs, n_paths_x, n_paths_y;
     int nslot, wcols, grid, nwarps, rows_per_strip, stride;
     KernelInfo info;
@@ -117,10 +131,12 @@ static int64_t pair_count(int op, int64_t n_x, int64_t n_y, int flags) {
     return n * (n + 1) / 2;
 }
 
-static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Opts& o, Layout* L) {
+static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Opts& o, Layout* L,
+                               bool train = false) {
     const int D = dim_bucket(d);
     if (D < 0) return fail(SIGK_ERR_UNSUPPORTED, "d must be in 1..16 in this build");
-    if (fwd_info_dispatch(o.order, D, &L->info) != 0 || L->info.blocks_per_sm <= 0)
+    L->train = train;
+    if (fwd_info_dispatch(o.order, D, train ? 1 : 0, &L->info) != 0 || L->info.blocks_per_sm <= 0)
         return fail(SIGK_ERR_CUDA, "kernel occupancy query failed");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -156,6 +172,34 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->seam = off; off = align256(off + sizeof(float) * (size_t)L->nslot * L->wcols * L->stride);
     L->gram = off;
     if (op == SIGK_OP_MMD) off = align256(off + sizeof(double) * (size_t)(n_x + n_y) * (n_x + n_y));
+    if (train) {
+        if (bwd_info_dispatch(o.order, D, &L->binfo) != 0 || L->binfo.blocks_per_sm <= 0)
+            return fail(SIGK_ERR_CUDA, "backward occupancy query failed");
+        L->bgrid = sms * L->binfo.blocks_per_sm;
+        if (o.grid_ctas > 0 && o.grid_ctas < L->bgrid) L->bgrid = o.grid_ctas;
+        L->bnwarps = L->bgrid * (L->binfo.threads / 32);
+        L->bnslot = L->bnwarps + 64;
+        int64_t bw = 2 * o.max_len / L->bnwarps + 64;
+        if (bw < 256) bw = 256;
+        if (bw > o.max_len) bw = o.max_len;
+        bw = (bw + 31) & ~(int64_t)31;
+        if (bw < 32) bw = 32;
+        L->bwcols = (int)bw;
+        // forward seams of every strip boundary: (strips - 1) x swept columns
+        const int64_t strips = (o.max_len + 31) / 32;
+        L->store_floats = L->n_pairs * (strips > 1 ? strips - 1 : 0) * o.max_len * L->stride;
+        L->rec_stride = (o.max_len + 31) * (int64_t)L->stride * 32;
+        L->store = off; off = align256(off + sizeof(float) * (size_t)L->store_floats);
+        L->store_off = off; off = align256(off + sizeof(int64_t) * (size_t)L->n_pairs);
+        L->pair_exp = off; off = align256(off + sizeof(int32_t) * (size_t)L->n_pairs);
+        L->pair_w = off; off = align256(off + sizeof(double) * (size_t)L->n_pairs);
+        L->rec = off; off = align256(off + sizeof(float) * (size_t)L->bnwarps * L->rec_stride);
+        L->bprod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->bnslot);
+        L->bcons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->bnslot);
+        L->bdone = off; off = align256(off + sizeof(long long) * (size_t)L->bnslot);
+        L->aseam = off;
+        off = align256(off + sizeof(float) * (size_t)L->bnslot * L->bwcols * (o.order + 1));
+    }
     L->total = off;
     return SIGK_OK;
 }
@@ -164,7 +208,8 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
 struct Header {
     int status;
     int item_counter;
-    int pad[2];
+    int bwd_item_counter;
+    int pad;
     unsigned long long counters[4];
 };
 
@@ -197,6 +242,19 @@ struct PlanArgs {
     Header* hdr;
     double* out;        // output (k values / Gram)
     int64_t out_ld;     // leading dimension of the Gram output
+    // training (backward) extras; train == 0 leaves them unused
+    int train;
+    int stride;         // seam entry floats (P + 3)
+    int64_t store_cap;  // floats available for the forward seam store
+    int64_t* store_off;
+    double* pair_w;
+    const double* grad_out;
+    float* gX;
+    float* gY;
+    unsigned long long* bprod;
+    unsigned long long* bcons;
+    long long* bdone;
+    int bnslot;
 };
 
 constexpr int kPlanThreads = 1024;
@@ -281,22 +339,51 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         const float* pa;
         const float* pb;
         int64_t la, lb;
-        auto path = [&](int64_t z, bool from_y, const float** ptr, int64_t* segs) {
+        float* ga = nullptr;
+        float* gb = nullptr;
+        auto path = [&](int64_t z, bool from_y, const float** ptr, int64_t* segs, float** g) {
             const float* base = from_y ? A.Y : A.X;
             const int64_t* off = from_y ? A.oy : A.ox;
             const int64_t* len = from_y ? A.len_y : A.len_x;
+            float* gbase = from_y ? A.gY : A.gX;
             *ptr = base + off[z] * A.d;
             *segs = A.inc_mode ? len[z] : len[z] - 1;
+            *g = gbase ? gbase + off[z] * A.d : nullptr;
         };
         if (A.op == SIGK_OP_MMD) {
-            path(a < nx ? a : a - nx, a >= nx, &pa, &la);
-            path(b < nx ? b : b - nx, b >= nx, &pb, &lb);
+            path(a < nx ? a : a - nx, a >= nx, &pa, &la, &ga);
+            path(b < nx ? b : b - nx, b >= nx, &pb, &lb, &gb);
         } else if (A.op == SIGK_OP_PAIRS) {
-            path(a, false, &pa, &la);
-            path(b, true, &pb, &lb);
+            path(a, false, &pa, &la, &ga);
+            path(b, true, &pb, &lb, &gb);
         } else {
-            path(a, false, &pa, &la);
-            path(b, !self, &pb, &lb);
+            path(a, false, &pa, &la, &ga);
+            path(b, !self, &pb, &lb, &gb);
+        }
+        if (A.train) {
+            // upstream weight of this pair's k value
+            double w = 0.0;
+            if (A.op == SIGK_OP_PAIRS) {
+                w = A.grad_out[p];
+            } else if (A.op == SIGK_OP_GRAM) {
+                w = A.grad_out[o0];
+                if (o1 >= 0) w += A.grad_out[o1];
+            } else {  // MMD^2 = mean k(x,x') + mean k(y,y') - 2 mean k(x,y)
+                const int64_t m = nx, n = A.n_y;
+                const bool unb = !(A.flags & SIGK_FLAG_MMD_BIASED);
+                double cf;
+                if (a < m && b < m) {
+                    cf = (a == b) ? (unb ? 0.0 : 1.0 / ((double)m * m))
+                                  : (unb ? 2.0 / ((double)m * (m - 1)) : 2.0 / ((double)m * m));
+                } else if (a >= m && b >= m) {
+                    cf = (a == b) ? (unb ? 0.0 : 1.0 / ((double)n * n))
+                                  : (unb ? 2.0 / ((double)n * (n - 1)) : 2.0 / ((double)n * n));
+                } else {
+                    cf = -2.0 / ((double)m * n);
+                }
+                w = A.grad_out[0] * cf;
+            }
+            A.pair_w[p] = w;
         }
         PairDesc pd;
         pd.out0 = o0;
@@ -311,6 +398,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         if ((swap ? la : lb) > A.max_len) atomicCAS(&A.hdr->status, 0, kErrLength);
         pd.xr = swap ? pb : pa;
         pd.yr = swap ? pa : pb;
+        pd.gxr = A.train ? (swap ? gb : ga) : nullptr;
+        pd.gyr = A.train ? (swap ? ga : gb) : nullptr;
         pd.L1 = (int32_t)(swap ? lb : la);
         pd.L2 = (int32_t)(swap ? la : lb);
         pd.swapped = swap ? 1 : 0;
@@ -357,8 +446,52 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
     }
     if (t == 0) {
         A.hdr->item_counter = 0;
+        A.hdr->bwd_item_counter = 0;
         A.hdr->counters[0] = 0;
         A.hdr->counters[1] = 0;
+        A.hdr->counters[2] = 0;
+    }
+    if (!A.train) return;
+    for (int i = t; i < A.bnslot; i += kPlanThreads) {
+        A.bprod[i] = 0ull;
+        A.bcons[i] = 0ull;
+        A.bdone[i] = -1ll;
+    }
+    // gradient outputs are accumulated with atomics: zero them
+    if (A.gX) {
+        const int64_t nxf = (int64_t)A.ox[A.n_x] * A.d;
+        for (int64_t i = t; i < nxf; i += kPlanThreads) A.gX[i] = 0.0f;
+    }
+    if (A.gY && !self) {
+        const int64_t nyf = (int64_t)A.oy[A.n_y] * A.d;
+        for (int64_t i = t; i < nyf; i += kPlanThreads) A.gY[i] = 0.0f;
+    }
+    // per-pair offsets of the forward seam store: (strips - 1) x L2 x stride
+    __syncthreads();
+    {
+        const int64_t n = A.n_pairs;
+        const int64_t chunk = (n + kPlanThreads - 1) / kPlanThreads;
+        const int64_t b0 = t * chunk, b1 = (b0 + chunk < n) ? b0 + chunk : n;
+        auto sz = [&](int64_t i) -> int64_t {
+            const PairDesc& q = A.pairs[i];
+            return q.n_strips > 1 ? (int64_t)(q.n_strips - 1) * q.L2 * A.stride : 0;
+        };
+        int64_t s = 0;
+        for (int64_t i = b0; i < b1; ++i) s += sz(i);
+        sh[t] = s;
+        __syncthreads();
+        for (int o = 1; o < kPlanThreads; o <<= 1) {
+            int64_t add = (t >= o) ? sh[t - o] : 0;
+            __syncthreads();
+            sh[t] += add;
+            __syncthreads();
+        }
+        int64_t run = sh[t] - s;
+        for (int64_t i = b0; i < b1; ++i) {
+            A.store_off[i] = run;
+            run += sz(i);
+        }
+        if (t == kPlanThreads - 1 && sh[t] > A.store_cap) atomicCAS(&A.hdr->status, 0, kErrWorkspace);
     }
 }
 
@@ -406,18 +539,30 @@ static sigk_status check_ws(const Layout& L, void* ws, size_t ws_bytes) {
     return SIGK_OK;
 }
 
-// Common driver: plan + solve into `out` (k values or Gram).
+// Backward extras for run_solver (train mode).
+struct TrainArgs {
+    const double* grad_out;
+    float* gX;
+    float* gY;
+};
+
+// Common driver: plan + solve into `out` (k values or Gram).  With `tr`, the
+// forward runs in training mode (one row per lane, every strip seam stored)
+// and the adjoint kernel follows, accumulating gradients into tr->gX/gY.
 static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int64_t n_x,
                               const float* Y, const int64_t* len_y, int64_t n_y, int d,
                               double* out, int64_t out_ld, void* ws, size_t ws_bytes,
-                              cudaStream_t stream, const Opts& o, Layout* Lout) {
+                              cudaStream_t stream, const Opts& o, Layout* Lout,
+                              const TrainArgs* tr = nullptr) {
     Layout L;
-    sigk_status st = make_layout(op, n_x, n_y, d, o, &L);
+    const bool train = tr != nullptr;
+    sigk_status st = make_layout(op, n_x, n_y, d, o, &L, train);
     if (st != SIGK_OK) return st;
     if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
     char* base = (char*)ws;
     Header* hdr = (Header*)(base + L.hdr);
     PlanArgs pa;
+    memset(&pa, 0, sizeof(pa));
     pa.op = op;
     pa.flags = o.flags;
     pa.inc_mode = (o.flags & SIGK_FLAG_INCREMENTS) ? 1 : 0;
@@ -442,10 +587,25 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     pa.hdr = hdr;
     pa.out = out;
     pa.out_ld = out_ld;
+    if (train) {
+        pa.train = 1;
+        pa.stride = L.stride;
+        pa.store_cap = L.store_floats;
+        pa.store_off = (int64_t*)(base + L.store_off);
+        pa.pair_w = (double*)(base + L.pair_w);
+        pa.grad_out = tr->grad_out;
+        pa.gX = tr->gX;
+        pa.gY = tr->gY;
+        pa.bprod = (unsigned long long*)(base + L.bprod);
+        pa.bcons = (unsigned long long*)(base + L.bcons);
+        pa.bdone = (long long*)(base + L.bdone);
+        pa.bnslot = L.bnslot;
+    }
     plan_kernel<<<1, kPlanThreads, 0, stream>>>(pa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "plan_kernel launch");
     SolverArgs sa;
+    memset(&sa, 0, sizeof(sa));
     sa.pairs = pa.pairs;
     sa.item_start = pa.item_start;
     sa.n_pairs = (int32_t)L.n_pairs;
@@ -462,10 +622,44 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     sa.status = &hdr->status;
     sa.counters = hdr->counters;
     sa.out = out;
+    if (train) {
+        sa.store = (float*)(base + L.store);
+        sa.store_off = pa.store_off;
+        sa.pair_exp = (int32_t*)(base + L.pair_exp);
+    }
     if (L.n_pairs > 0) {
-        if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
-        e = fwd_launch_dispatch(o.order, dim_bucket(d), sa, L.grid, stream);
+        if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_start, stream);
+        e = fwd_launch_dispatch(o.order, dim_bucket(d), train ? 1 : 0, sa, L.grid, stream);
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+        if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_stop, stream);
+    }
+    if (train && L.n_pairs > 0) {
+        BwdArgs ba;
+        memset(&ba, 0, sizeof(ba));
+        ba.pairs = pa.pairs;
+        ba.item_start = pa.item_start;
+        ba.n_pairs = (int32_t)L.n_pairs;
+        ba.inc_mode = pa.inc_mode;
+        ba.d = d;
+        ba.nr = o.rings;
+        ba.store = sa.store;
+        ba.store_off = pa.store_off;
+        ba.pair_exp = sa.pair_exp;
+        ba.pair_w = pa.pair_w;
+        ba.rec = (float*)(base + L.rec);
+        ba.rec_stride = L.rec_stride;
+        ba.nslot = L.bnslot;
+        ba.wcols = L.bwcols;
+        ba.aseam = (float*)(base + L.aseam);
+        ba.prod = pa.bprod;
+        ba.cons = pa.bcons;
+        ba.done = pa.bdone;
+        ba.item_counter = &hdr->bwd_item_counter;
+        ba.status = &hdr->status;
+        ba.counters = hdr->counters;
+        if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
+        e = bwd_launch_dispatch(o.order, dim_bucket(d), ba, L.bgrid, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "backward launch");
         if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_stop, stream);
     }
     if (Lout) *Lout = L;
@@ -549,6 +743,65 @@ sigk_status sigk_mmd(const float* X, const int64_t* len_x, int64_t m, const floa
     return SIGK_OK;
 }
 
+size_t sigk_backward_workspace_size(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts) {
+    Opts o;
+    if (!resolve_opts(opts, &o)) return 0;
+    if (op < SIGK_OP_PAIRS || op > SIGK_OP_MMD || n_x < 0 || n_y < 0 || d < 1) return 0;
+    if (op == SIGK_OP_PAIRS) n_y = n_x;
+    Layout L;
+    if (make_layout(op, n_x, n_y, d, o, &L, true) != SIGK_OK) return 0;
+    return L.total;
+}
+
+sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t n_x, const float* Y,
+                          const int64_t* len_y, int64_t n_y, int d, const double* grad_out,
+                          float* grad_X, float* grad_Y, double* value_out, void* ws,
+                          size_t ws_bytes, void* stream, const sigk_opts* opts) {
+    if (op < SIGK_OP_PAIRS || op > SIGK_OP_MMD) return fail(SIGK_ERR_ARG, "bad op");
+    if (!grad_out) return fail(SIGK_ERR_ARG, "grad_out is NULL");
+    if (op == SIGK_OP_GRAM && !Y) n_y = 0;
+    if (op == SIGK_OP_PAIRS) n_y = n_x;
+    sigk_status st = common_checks(n_x, n_y, d, grad_out);
+    if (st != SIGK_OK) return st;
+    if (n_x > 0 && (!X || !len_x)) return fail(SIGK_ERR_ARG, "null X input");
+    if (op != SIGK_OP_GRAM || Y) {
+        if (n_y > 0 && (!Y || !len_y)) return fail(SIGK_ERR_ARG, "null Y input");
+    }
+    Opts o;
+    if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    if (n_x == 0 || (op != SIGK_OP_GRAM && n_y == 0)) return SIGK_OK;
+    const int unbiased = (o.flags & SIGK_FLAG_MMD_BIASED) ? 0 : 1;
+    if (op == SIGK_OP_MMD && (n_x < 1 + unbiased || n_y < 1 + unbiased))
+        return fail(SIGK_ERR_ARG, "MMD needs at least 2 paths per sample (1 for the V-statistic)");
+    Layout L;
+    if ((st = make_layout(op, n_x, n_y, d, o, &L, true)) != SIGK_OK) return st;
+    if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
+    TrainArgs tr{grad_out, grad_X, (op == SIGK_OP_GRAM && !Y) ? nullptr : grad_Y};
+    double* vals = nullptr;
+    int64_t ld = 0;
+    if (op == SIGK_OP_MMD) {
+        vals = (double*)((char*)ws + L.gram);
+        ld = n_x + n_y;
+    } else if (op == SIGK_OP_GRAM) {
+        if (!value_out) return fail(SIGK_ERR_ARG, "Gram backward needs value_out [n_x*n_y] as scratch");
+        vals = value_out;
+        ld = Y ? n_y : n_x;
+    } else {
+        if (!value_out) return fail(SIGK_ERR_ARG, "pairs backward needs value_out [n_pairs] as scratch");
+        vals = value_out;
+    }
+    st = run_solver(op, X, len_x, n_x, (op == SIGK_OP_GRAM && !Y) ? nullptr : Y, len_y,
+                    (op == SIGK_OP_GRAM && !Y) ? 0 : n_y, d, vals, ld, ws, ws_bytes,
+                    (cudaStream_t)stream, o, nullptr, &tr);
+    if (st != SIGK_OK) return st;
+    if (op == SIGK_OP_MMD && value_out) {
+        mmd_reduce_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(vals, n_x, n_y, unbiased, value_out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "mmd_reduce launch");
+    }
+    return SIGK_OK;
+}
+
 sigk_status sigk_plan(int, const float*, const int64_t*, int64_t, const float*, const int64_t*,
                       int64_t, int, double, void*, size_t, void*, const sigk_opts*, sigk_opts*) {
     return fail(SIGK_ERR_UNSUPPORTED, "sigk_plan is not implemented in this build");
@@ -582,7 +835,7 @@ sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out3)
     if (e != cudaSuccess) return cuda_fail(e, "counter copy");
     out3[0] = (double)h.counters[0];
     out3[1] = (double)h.counters[1];
-    out3[2] = 0.0;
+    out3[2] = (double)h.counters[2];
     return SIGK_OK;
 }
 

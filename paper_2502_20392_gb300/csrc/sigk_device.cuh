@@ -56,6 +56,8 @@ struct PairDesc {
     int32_t swapped;   // 1 if the row path is the caller's y
     int64_t out0;      // output index, or -1
     int64_t out1;      // mirrored output index, or -1
+    float* gxr;        // gradient rows of the row path (backward), or null
+    float* gyr;        // gradient rows of the swept path (backward), or null
 };
 
 struct SolverArgs {
@@ -75,6 +77,12 @@ struct SolverArgs {
     int* status;
     unsigned long long* counters;  // [0] tiles, [1] lane-tiles incl. padding
     double* out;
+    // training forward (backward pass follows): every strip's right-edge seam
+    // goes to a per-pair store instead of the ring, and the final exponent of
+    // each pair is recorded.  store == nullptr: inference.
+    float* store;
+    const int64_t* store_off;      // [n_pairs] float offsets into store
+    int32_t* pair_exp;             // [n_pairs] or null
 };
 
 // ---------------------------------------------------------------------------
@@ -209,6 +217,131 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& h
     const float e = (hi - (s - bb)) + (S - bb);
     hi = s;
     lo += e;
+}
+
+// Inverse of the bottom-to-top edge update of tile_update, given the tile's
+// left edge (hi, b) and its top edge a2: the update is unit lower triangular
+// in the degree (a'_p = a_p + sum_{m<p} ch_m a_{p-m} + c^p ha_p(b)), so the
+// bottom edge is recovered degree by degree.  Used by the reverse sweep to
+// rebuild each tile's inputs from the stored left edges instead of storing
+// every tile.  ha (rings p <= nr) is returned for the adjoint.
+template <int P>
+__device__ __forceinline__ void tile_inverse_a(float c, const float (&a2)[P + 1], float hi,
+                                               const float (&b)[P + 1], int nr,
+                                               float (&a)[P + 1], float (&ha)[P + 1]) {
+    constexpr int NRM = P < kMaxRings ? P : kMaxRings;
+    float cp[NRM + 1], ch[NRM + 1];
+    cp[1] = c;
+    ch[1] = c;
+#pragma unroll
+    for (int m = 2; m <= NRM; ++m) {
+        cp[m] = cp[m - 1] * c;
+        ch[m] = cp[m] * c_inv_fact[m];
+    }
+#pragma unroll
+    for (int p = 1; p <= P; ++p) {
+        float v = a2[p];
+        ha[p] = 0.0f;
+        if (p <= NRM && p <= nr) {
+            float sa = hi * c_inv_fact[p];
+#pragma unroll
+            for (int r = 1; r <= P - p; ++r) sa = fmaf(b[r], c_inv_fact[p + r], sa);
+            ha[p] = sa;
+            v = fmaf(-cp[p], sa, v);
+        }
+#pragma unroll
+        for (int m = 1; m < p && m <= NRM; ++m)
+            if (m <= nr) v = fmaf(-ch[m], a[p - m], v);
+        a[p] = v;
+    }
+    a[0] = 0.0f;
+}
+
+// Reverse-mode adjoint of tile_update (the exact derivative of the truncated
+// FP32 scheme, with the float-float corner treated as one real b0 = hi + lo).
+// Forward inputs: c, a (bottom edge), hi, b (left edge), ha (ring Hankel sums
+// of b, from tile_inverse_a).  Adjoint inputs: A2 (top edge), B02 (corner),
+// B2 (right edge).  Outputs overwrite them with the adjoints of the bottom edge
+// (A), the corner (B0) and the left edge (B); returns dk/dc.
+template <int P>
+__device__ __forceinline__ float tile_adjoint(float c, const float (&a)[P + 1], float hi,
+                                              const float (&b)[P + 1], const float (&ha)[P + 1],
+                                              float (&A)[P + 1], float& B0, float (&B)[P + 1],
+                                              int nr) {
+    constexpr int NRM = P < kMaxRings ? P : kMaxRings;
+    float cp[NRM + 1], ch[NRM + 1];
+    cp[1] = c;
+    ch[1] = c;
+#pragma unroll
+    for (int m = 2; m <= NRM; ++m) {
+        cp[m] = cp[m - 1] * c;
+        ch[m] = cp[m] * c_inv_fact[m];
+    }
+    // hb from the bottom edge (as in the forward)
+    float hb[NRM + 1];
+#pragma unroll
+    for (int p = 1; p <= NRM; ++p) {
+        hb[p] = 0.0f;
+        if (p <= nr) {
+            float sb = hi * c_inv_fact[p];
+#pragma unroll
+            for (int r = 1; r <= P - p; ++r) sb = fmaf(a[r], c_inv_fact[p + r], sb);
+            hb[p] = sb;
+        }
+    }
+    // c-bar contributions: d ch_m / dc = ch_{m-1}, d cp_m / dc = m cp_{m-1}
+    float cbar = 0.0f;
+    // correlation sums chb_m = sum_p A2_p a_{p-m} + B2_p b_{p-m}
+#pragma unroll
+    for (int m = 1; m <= NRM; ++m) {
+        if (m <= nr) {
+            float chb = 0.0f;
+#pragma unroll
+            for (int p = m + 1; p <= P; ++p) {
+                chb = fmaf(A[p], a[p - m], chb);
+                chb = fmaf(B[p], b[p - m], chb);
+            }
+            const float dch = (m == 1) ? 1.0f : ch[m - 1];
+            cbar = fmaf(chb, dch, cbar);
+            // ring-m Hankel term: d/dcp_m (cp_m (A2_m ha_m + B2_m hb_m))
+            const float dcp = (m == 1) ? 1.0f : (float)m * cp[m - 1];
+            cbar = fmaf(fmaf(A[m], ha[m], B[m] * hb[m]), dcp, cbar);
+        }
+    }
+    // transposed Hankel: hab_p = cp_p A2_p feeds B_r and the corner
+    float hab[NRM + 1], hbb[NRM + 1];
+#pragma unroll
+    for (int p = 1; p <= NRM; ++p) {
+        hab[p] = (p <= nr) ? cp[p] * A[p] : 0.0f;
+        hbb[p] = (p <= nr) ? cp[p] * B[p] : 0.0f;
+    }
+    // transposed convolution (low degree first: reads only higher, older entries)
+    const float Sbar = B0;
+#pragma unroll
+    for (int s = 1; s <= P; ++s) {
+        float va = A[s], vb = B[s];
+#pragma unroll
+        for (int m = 1; m <= NRM && s + m <= P; ++m)
+            if (m <= nr) {
+                va = fmaf(ch[m], A[s + m], va);
+                vb = fmaf(ch[m], B[s + m], vb);
+            }
+        va = fmaf(Sbar, c_inv_fact[s], va);  // corner b0' = b0 + sum_p a_p / p!
+#pragma unroll
+        for (int p = 1; p <= NRM && p + s <= P; ++p) {
+            va = fmaf(hbb[p], c_inv_fact[p + s], va);  // hb_p reads a_s
+            vb = fmaf(hab[p], c_inv_fact[p + s], vb);  // ha_p reads b_s
+        }
+        A[s] = va;
+        B[s] = vb;
+    }
+    float b0 = B0;
+#pragma unroll
+    for (int p = 1; p <= NRM; ++p) b0 = fmaf(hab[p] + hbb[p], c_inv_fact[p], b0);
+    B0 = b0;
+    A[0] = 0.0f;
+    B[0] = 0.0f;
+    return cbar;
 }
 
 // FP32 operations of tile_update (FMA counted as 2), for the roofline.

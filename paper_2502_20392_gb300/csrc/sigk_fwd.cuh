@@ -80,6 +80,8 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
         const int slot_in = (item - 1 + A.nslot) % A.nslot;
         const int slot_out = item % A.nslot;
         const int i0 = s * 32 * R;
+        const bool train = A.store != nullptr;
+        float* st_pair = train ? A.store + A.store_off[lo_p] : nullptr;
         bool ok = true;
 
         // row increments of this lane (zero past the end of the path)
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
         int oE = 0;
 
         // the slot we write must have been read by its previous consumer
-        if (has_out) {
+        if (has_out && !train) {
             const long long prev_consumer = (long long)item - A.nslot + 1;
             bool okl = true;
             if (lane == 0)
@@ -130,7 +132,9 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                     if (lane == 0) okl = wait_ge_u64(&A.prod[slot_in], need, A.status);
                     ok = __shfl_sync(kFull, okl, 0);
                     if (ok) {
-                        const float* src = A.seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
+                        const float* src =
+                            train ? st_pair + ((size_t)(s - 1) * L2 + t) * S
+                                  : A.seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
                         for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src + idx);
                         __syncwarp();
                         if (lane == 0)
@@ -232,6 +236,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                         if (!isfinite(k)) atomicCAS(A.status, 0, kErrNonfinite);
                         if (pd.out0 >= 0) A.out[pd.out0] = k;
                         if (pd.out1 >= 0) A.out[pd.out1] = k;
+                        if (A.pair_exp) A.pair_exp[lo_p] = E;
                     }
                 }
             }
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                 __syncwarp();
                 const int start = jj & ~31;
                 const int nb = jj - start + 1;
-                if (start + nb > A.wcols) {
+                if (!train && start + nb > A.wcols) {
                     const unsigned long long need = ((unsigned long long)(item + 1) << 32) |
                                                     (unsigned)(start + nb - A.wcols);
                     bool okl = true;
@@ -249,7 +254,8 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                     ok = __shfl_sync(kFull, okl, 0);
                 }
                 if (ok) {
-                    float* dst = A.seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
+                    float* dst = train ? st_pair + ((size_t)s * L2 + start) * S
+                                       : A.seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
                     for (int idx = lane; idx < nb * S; idx += 32) __stcg(dst + idx, sout[idx]);
                     __threadfence();
                     __syncwarp();

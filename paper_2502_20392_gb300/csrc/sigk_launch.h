@@ -17,7 +17,13 @@ struct KernelInfo {
 // footprint (R*(P + D) state floats) would push occupancy too low.
 constexpr int rows_per_lane(int P, int D) { return (P + D) <= 16 ? 4 : 2; }
 
-template <int P> int fwd_info(int D, KernelInfo* info);
-template <int P> cudaError_t fwd_launch(int D, const SolverArgs& a, int grid, cudaStream_t s);
+// R = 0: the inference rows-per-lane rows_per_lane(P, D); R = 1: one row per
+// lane (the training forward, whose strips the backward kernel replays).
+template <int P> int fwd_info(int D, int R, KernelInfo* info);
+template <int P> cudaError_t fwd_launch(int D, int R, const SolverArgs& a, int grid, cudaStream_t s);
+
+struct BwdArgs;
+template <int P> int bwd_info(int D, KernelInfo* info);
+template <int P> cudaError_t bwd_launch(int D, const BwdArgs& a, int grid, cudaStream_t s);
 
 }  // namespace sigk

@@ -78,6 +78,9 @@ def load(path: str | None = None):
     lib.sigk_gram.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, sz, vp, op]
     lib.sigk_mmd.argtypes = [vp, vp, i64, vp, vp, i64, i32, vp, vp, vp, sz, vp, op]
     lib.sigk_plan.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, ctypes.c_double, vp, sz, vp, op, op]
+    lib.sigk_backward_workspace_size.argtypes = [i32, i64, i64, i32, op]
+    lib.sigk_backward_workspace_size.restype = sz
+    lib.sigk_backward.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, op]
     lib.sigk_sync_status.argtypes = [vp, sz, vp]
     lib.sigk_counters.argtypes = [vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sigk_profile_events.argtypes = [vp, vp]
@@ -85,7 +88,7 @@ def load(path: str | None = None):
     lib.sigk_last_error.restype = ctypes.c_char_p
     lib.sigk_version.restype = ctypes.c_char_p
     for name in ("sigk_pairs", "sigk_gram", "sigk_mmd", "sigk_plan", "sigk_sync_status",
-                 "sigk_counters"):
+                 "sigk_counters", "sigk_backward"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -223,3 +226,113 @@ def mmd(X, len_x, Y, len_y, opts: Opts | None = None, gram_out=None,
     if check:
         sync_status(ws)
     return out
+
+
+def backward_workspace_size(op: int, n_x: int, n_y: int, d: int, opts: Opts) -> int:
+    o = opts.c()
+    n = load().sigk_backward_workspace_size(op, n_x, n_y, d, ctypes.byref(o))
+    if n == 0:
+        raise SigkError(-1, "backward_workspace_size rejected the arguments")
+    return int(n)
+
+
+def backward(op: int, X, len_x, Y, len_y, grad_out, opts: Opts | None = None,
+             need_x: bool = True, need_y: bool = True, ws: Workspace | None = None,
+             check: bool = True):
+    """Adjoint of pairs / gram / mmd.  Returns (grad_X, grad_Y, value):
+    gradients w.r.t. the points (increments with FLAG_INCREMENTS) as FP32
+    tensors shaped like X and Y (None where not requested; for a Gram of X with
+    itself grad_Y is None), and the forward output recomputed by the call."""
+    opts = opts or Opts()
+    X, len_x = _paths(X, len_x)
+    n_x, d = len_x.numel(), X.shape[1]
+    self_gram = op == OP_GRAM and Y is None
+    if Y is not None:
+        Y, len_y = _paths(Y, len_y)
+        n_y = len_y.numel()
+    else:
+        n_y = 0 if self_gram else n_x
+    if op == OP_PAIRS:
+        n_y = n_x
+        vshape = (n_x,)
+    elif op == OP_GRAM:
+        vshape = (n_x, n_y or n_x)
+    else:
+        vshape = (1,)
+    value = torch.empty(vshape, dtype=torch.float64, device=X.device)
+    gout = grad_out.to(device=X.device, dtype=torch.float64).contiguous()
+    gX = torch.empty_like(X) if need_x else None
+    gY = torch.empty_like(Y) if (need_y and Y is not None and not self_gram) else None
+    ws = _ws(ws, X.device)
+    buf = ws.get(backward_workspace_size(op, n_x, n_y, d, opts), X.device)
+    o = opts.c()
+    _check(load().sigk_backward(op, _ptr(X), _ptr(len_x), n_x, _ptr(Y), _ptr(len_y), n_y, d,
+                                _ptr(gout), _ptr(gX), _ptr(gY), _ptr(value), _ptr(buf),
+                                buf.numel(), _stream(), ctypes.byref(o)))
+    if check:
+        sync_status(ws)
+    return gX, gY, value
+
+
+class _PairsFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, Y, len_x, len_y, opts):
+        ctx.save_for_backward(X, Y, len_x, len_y)
+        ctx.opts = opts
+        return pairs(X.detach(), len_x, Y.detach(), len_y, opts=opts)
+
+    @staticmethod
+    def backward(ctx, g):
+        X, Y, len_x, len_y = ctx.saved_tensors
+        gX, gY, _ = backward(OP_PAIRS, X.detach(), len_x, Y.detach(), len_y, g, ctx.opts,
+                             need_x=ctx.needs_input_grad[0], need_y=ctx.needs_input_grad[1])
+        return gX, gY, None, None, None
+
+
+class _GramFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, Y, len_x, len_y, opts):
+        ctx.save_for_backward(X, Y if Y is not None else X, len_x, len_y if len_y is not None else len_x)
+        ctx.self_gram = Y is None
+        ctx.opts = opts
+        return gram(X.detach(), len_x, None if Y is None else Y.detach(), len_y, opts=opts)
+
+    @staticmethod
+    def backward(ctx, g):
+        X, Y, len_x, len_y = ctx.saved_tensors
+        if ctx.self_gram:
+            gX, _, _ = backward(OP_GRAM, X.detach(), len_x, None, None, g, ctx.opts)
+            return gX, None, None, None, None
+        gX, gY, _ = backward(OP_GRAM, X.detach(), len_x, Y.detach(), len_y, g, ctx.opts,
+                             need_x=ctx.needs_input_grad[0], need_y=ctx.needs_input_grad[1])
+        return gX, gY, None, None, None
+
+
+class _MMDFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, Y, len_x, len_y, opts):
+        ctx.save_for_backward(X, Y, len_x, len_y)
+        ctx.opts = opts
+        return mmd(X.detach(), len_x, Y.detach(), len_y, opts=opts)
+
+    @staticmethod
+    def backward(ctx, g):
+        X, Y, len_x, len_y = ctx.saved_tensors
+        gX, gY, _ = backward(OP_MMD, X.detach(), len_x, Y.detach(), len_y, g, ctx.opts,
+                             need_x=ctx.needs_input_grad[0], need_y=ctx.needs_input_grad[1])
+        return gX, gY, None, None, None
+
+
+def sig_kernel_pairs(X, len_x, Y, len_y, opts: Opts | None = None):
+    """Differentiable k(x_p, y_p) (torch.autograd)."""
+    return _PairsFn.apply(X, Y, len_x, len_y, opts or Opts())
+
+
+def sig_kernel_gram(X, len_x, Y=None, len_y=None, opts: Opts | None = None):
+    """Differentiable Gram matrix (torch.autograd); Y=None: Gram of X with itself."""
+    return _GramFn.apply(X, Y, len_x, len_y, opts or Opts())
+
+
+def sig_kernel_mmd(X, len_x, Y, len_y, opts: Opts | None = None):
+    """Differentiable signature-kernel MMD^2 (torch.autograd)."""
+    return _MMDFn.apply(X, Y, len_x, len_y, opts or Opts())

@@ -1,0 +1,165 @@
+"""GPU parity of the adjoint (sigk_backward through the C-ABI, and the
+torch.autograd wrappers) against FP64 central finite differences of the oracle
+and the single-tile closed form.  Gradients are with respect to the points;
+the tolerance is 1e-4 relative to the largest gradient entry (the
+differentiation workload's tolerance)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import i1, j1
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+OPTS = dict(order=12, rings=6)
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_20392_gb300 import build, sigk
+    build.build()
+    sigk.load()
+    return sigk
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def incs(paths):
+    return [np.diff(p.astype(np.float64), axis=0) for p in paths]
+
+
+def fd_points(f, paths, which, coords, h=1e-3):
+    """Central differences (one Richardson step) of scalar f(list of point
+    arrays) w.r.t. flat coordinates of paths[which] (FP64)."""
+    out = []
+    base = [p.astype(np.float64) for p in paths]
+    for c in coords:
+        vals = []
+        for hh in (h, h / 2):
+            pp = [b.copy() for b in base]
+            pp[which].reshape(-1)[c] += hh
+            fp = f(pp)
+            pp[which].reshape(-1)[c] -= 2 * hh
+            fm = f(pp)
+            vals.append((fp - fm) / (2 * hh))
+        out.append((4 * vals[1] - vals[0]) / 3)
+    return np.array(out)
+
+
+def test_single_segment_gradient_closed_form(S):
+    from paper_2502_20392_gb300 import synth
+    cs = [0.3, 1.7, -0.9]
+    (X, lx), (Y, ly) = synth.single_segment_pairs(cs)
+    Xd, Yd = torch.from_numpy(X).to(dev()), torch.from_numpy(Y).to(dev())
+    lxd, lyd = torch.from_numpy(lx).to(dev()), torch.from_numpy(ly).to(dev())
+    g = torch.ones(len(cs), dtype=torch.float64)
+    gX, gY, val = S.backward(S.OP_PAIRS, Xd, lxd, Yd, lyd, g, S.Opts(order=16, rings=8))
+    gX = gX.cpu().numpy().reshape(len(cs), 2, 4)
+    for p, c in enumerate(cs):
+        # d/dc of I0(2 sqrt c) (c > 0) or J0(2 sqrt(-c)) (c < 0)
+        dk = i1(2 * math.sqrt(c)) / math.sqrt(c) if c > 0 else j1(2 * math.sqrt(-c)) / math.sqrt(-c)
+        # dk/d(dx) = dk/dc * dy, dy = e_0; point 1 gets +, point 0 gets -
+        assert gX[p, 1, 0] == pytest.approx(dk, rel=2e-5)
+        assert gX[p, 0, 0] == pytest.approx(-dk, rel=2e-5)
+        assert np.abs(gX[p, :, 1:]).max() == 0.0
+
+
+@pytest.mark.parametrize("d", [4, 8])
+def test_pairs_gradient_vs_fd(S, orc, d):
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.ragged_pairs(3, 20, 90, d, 0.7, 1.5, seed=60 + d)
+    xs, ys = synth.split(X, lx), synth.split(Y, ly)
+    xs[1] = np.concatenate([xs[1], xs[1][-1:] + 0.05 * np.random.default_rng(1).standard_normal(
+        (200, d)).cumsum(0).astype(np.float32)])  # one path over several 32-row strips
+    X, lx = synth.pack(xs)
+    rng = np.random.default_rng(7)
+    w = rng.standard_normal(3)
+    gX, gY, val = S.backward(S.OP_PAIRS, torch.from_numpy(X).to(dev()),
+                             torch.from_numpy(lx).to(dev()), torch.from_numpy(Y).to(dev()),
+                             torch.from_numpy(ly).to(dev()), torch.from_numpy(w),
+                             S.Opts(**OPTS, max_len=400))
+    gX = synth.split(gX.cpu().numpy(), lx)
+    gY = synth.split(gY.cpu().numpy(), ly)
+    for p in range(3):
+        for which, g in ((0, gX[p]), (1, gY[p])):
+            def f(pp):
+                return orc.series_pair(*incs(pp))
+            coords = rng.choice(g.size, size=min(12, g.size), replace=False)
+            ref = fd_points(f, [xs[p], ys[p]], which, coords)
+            got = g.reshape(-1)[coords]
+            scale = np.abs(ref).max()
+            # the upstream weight w[p] is part of the computed gradient
+            np.testing.assert_allclose(got, ref * w[p], atol=1e-4 * scale * abs(w[p]),
+                                       err_msg=f"pair {p} side {which}")
+
+
+def test_gram_self_gradient_vs_fd(S, orc):
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(4, [40, 70, 33, 100], 8, 1.0, seed=91)
+    paths = synth.split(pts, lens)
+    rng = np.random.default_rng(3)
+    W = rng.standard_normal((4, 4))  # not symmetric: both triangles weigh in
+    gX, _, G = S.backward(S.OP_GRAM, torch.from_numpy(pts).to(dev()),
+                          torch.from_numpy(lens).to(dev()), None, None, torch.from_numpy(W),
+                          S.Opts(**OPTS, max_len=128))
+    gX = synth.split(gX.cpu().numpy(), lens)
+    ref_G = orc.series_gram(incs(paths))
+    np.testing.assert_allclose(G.cpu().numpy(), ref_G, rtol=1e-5)
+    for a in (0, 3):
+        def f(pp):
+            return float((W * orc.series_gram(incs(pp))).sum())
+        coords = rng.choice(gX[a].size, size=10, replace=False)
+        ref = fd_points(f, paths, a, coords)
+        np.testing.assert_allclose(gX[a].reshape(-1)[coords], ref, atol=1e-4 * np.abs(ref).max())
+
+
+def test_mmd_gradient_vs_fd(S, orc):
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.workload_mmd_2048(seed=5001, n_paths=4, n_seg=120, d=8)
+    xs, ys = synth.split(X, lx), synth.split(Y, ly)
+    gX, gY, v = S.backward(S.OP_MMD, torch.from_numpy(X).to(dev()), torch.from_numpy(lx).to(dev()),
+                           torch.from_numpy(Y).to(dev()), torch.from_numpy(ly).to(dev()),
+                           torch.ones(1, dtype=torch.float64), S.Opts(**OPTS, max_len=128))
+    ref_v = orc.mmd2(incs(xs), incs(ys))
+    assert v.item() == pytest.approx(ref_v, rel=1e-5, abs=1e-7)
+    gX = gX.cpu().numpy()
+    rng = np.random.default_rng(11)
+    coords = rng.choice(gX.size, size=20, replace=False)
+
+    def f(pp):
+        return orc.mmd2(incs(pp[:4]), incs(pp[4:]))
+
+    # coordinates of the packed X: map to (path, local index)
+    off = np.concatenate([[0], np.cumsum(lx)]) * 8
+    got, ref = [], []
+    for c in coords:
+        p = int(np.searchsorted(off, c, side="right") - 1)
+        got.append(gX.reshape(-1)[c])
+        ref.append(fd_points(f, xs + ys, p, [c - off[p]])[0])
+    got, ref = np.array(got), np.array(ref)
+    np.testing.assert_allclose(got, ref, atol=1e-4 * np.abs(ref).max())
+
+
+def test_autograd_matches_backward(S):
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.workload_mmd_2048(seed=7, n_paths=3, n_seg=64, d=4)
+    Xd = torch.from_numpy(X).to(dev()).requires_grad_(True)
+    Yd = torch.from_numpy(Y).to(dev()).requires_grad_(True)
+    lxd, lyd = torch.from_numpy(lx).to(dev()), torch.from_numpy(ly).to(dev())
+    o = S.Opts(**OPTS, max_len=64)
+    m = S.sig_kernel_mmd(Xd, lxd, Yd, lyd, o)
+    gX, gY = torch.autograd.grad(m.sum(), (Xd, Yd))
+    rX, rY, v = S.backward(S.OP_MMD, Xd.detach(), lxd, Yd.detach(), lyd,
+                           torch.ones(1, dtype=torch.float64), o)
+    torch.testing.assert_close(gX, rX)
+    torch.testing.assert_close(gY, rY)
+    assert m.item() == pytest.approx(v.item(), rel=1e-6)
+    Gm = S.sig_kernel_gram(Xd, lxd, None, None, o)
+    (gG,) = torch.autograd.grad(Gm.sum(), (Xd,))
+    assert torch.isfinite(gG).all()
