@@ -42,8 +42,25 @@ def tile_flops(P: int, nr: int, d: int) -> int:
     f += 2 * P
     for p in range(1, P + 1):
         f += 4 * min(p - 1, nr) + (4 if p <= nr else 0)
-    f += 7
+    f += 7 + 12  # float-float corner; compensated first-order coefficients
     return f + 2 * d
+
+
+def adjoint_tile_flops(P: int, nr: int, d: int) -> int:
+    """FP32 operations per tile of the adjoint kernel (FMA = 2): the forward
+    replay of pass A (tile_flops), and in pass B the increment dot, the
+    inverse bottom-edge update, the tile adjoint and the two gradient FMAs."""
+    nrm = min(P, 8)
+    nr = min(nr, nrm)
+    inv = 2 * (nr - 1) + sum(2 * (1 + 2 * (P - p)) for p in range(1, nr + 1))
+    inv += sum(2 * min(p - 1, nr) + (2 if p <= nr else 0) for p in range(1, P + 1))
+    adj = 2 * (nr - 1) + sum(2 * (1 + 2 * (P - p)) for p in range(1, nr + 1))  # hb
+    adj += sum(4 * (P - m) + 6 for m in range(1, nr + 1))                     # chb, cbar
+    adj += 2 * nr                                                              # hab, hbb
+    for s_ in range(1, P + 1):
+        adj += 4 * min(nr, P - s_) + 2 + 4 * min(nr, P - s_)                   # conv^T, S, Hankel^T
+    adj += 2 * nr
+    return tile_flops(P, nr, d) + 2 * d + inv + adj + 4 * d
 
 
 def pairs_of_gram(n):
@@ -52,6 +69,9 @@ def pairs_of_gram(n):
 
 def cells_per_step():
     return len(SIGMAS) * pairs_of_gram(N_PATHS) * N_SEG * N_SEG
+
+
+BWD_SIGMA = 0  # index into SIGMAS of the Gram whose adjoint is part of the step
 
 
 class ClockSampler:
@@ -167,11 +187,19 @@ def main():
     G = [torch.empty((N_PATHS, N_PATHS), dtype=torch.float64, device=dev) for _ in SIGMAS]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    # upstream gradient of the Gram in the adjoint (a fixed dense weighting)
+    W = torch.from_numpy(np.random.default_rng(7).standard_normal((N_PATHS, N_PATHS))).to(dev)
+    bws = sigk.Workspace()
+
     def step(ev_pairs=None):
         for k in range(len(SIGMAS)):
             if ev_pairs is not None:
                 sigk.profile_events(*ev_pairs[k])
             sigk.gram(X[k], L[k], opts=opts[k], out=G[k], ws=wss[k], check=False)
+        if ev_pairs is not None:
+            sigk.profile_events(*ev_pairs[len(SIGMAS)])
+        k = BWD_SIGMA
+        sigk.backward(sigk.OP_GRAM, X[k], L[k], None, None, W, opts[k], ws=bws, check=False)
         if ev_pairs is not None:
             sigk.profile_events(None, None)
 
@@ -184,7 +212,7 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in SIGMAS] for _ in range(args.steps)]
+            for _ in range(len(SIGMAS) + 1)] for _ in range(args.steps)]
     for row in kev:  # torch creates an event on first record: do it before handing out handles
         for a, b in row:
             a.record()
@@ -203,7 +231,7 @@ def main():
         t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
-    for ws in wss:
+    for ws in wss + [bws]:
         sigk.sync_status(ws)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     kern_ms = [[a.elapsed_time(b) for a, b in row] for row in kev]
@@ -218,6 +246,7 @@ def main():
 
     # counters of the last launch of each sigma (tiles actually solved)
     tiles = [sigk.counters(ws)[0] for ws in wss]
+    bcnt = sigk.counters(bws)
 
     # roofline of the solver kernel (dominant: the sigma = 4, P = 16 launch)
     roof = []
@@ -227,7 +256,13 @@ def main():
         ach = flops / (kms * 1e-3) / 1e12
         roof.append({"sigma": sg, "order": P, "rings": nr, "kernel_ms": round(kms, 4),
                      "flops_per_launch": flops, "achieved": round(ach, 3)})
-    dom = max(range(len(SIGMAS)), key=lambda k: roof[k]["kernel_ms"])
+    sg, _, P, nr = SIGMAS[BWD_SIGMA]
+    kms = statistics.mean(r[len(SIGMAS)] for r in kern_ms)
+    flops = bcnt[2] * adjoint_tile_flops(P, nr, DIM)
+    roof.append({"sigma": sg, "order": P, "rings": nr, "kernel": "bwd_kernel (adjoint)",
+                 "kernel_ms": round(kms, 4), "flops_per_launch": flops,
+                 "achieved": round(flops / (kms * 1e-3) / 1e12, 3)})
+    dom = max(range(len(roof)), key=lambda k: roof[k]["kernel_ms"])
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -241,8 +276,10 @@ def main():
         traffic = None
     roofline = {"bound": "alu", "achieved": roof[dom]["achieved"], "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": round(roof[dom]["achieved"] / FP32_PEAK_TFLOPS, 4),
-                "traffic": traffic, "kernel": f"fwd_kernel<P={roof[dom]['order']},D=16>",
+                "traffic": traffic,
+                "kernel": roof[dom].get("kernel", f"fwd_kernel<P={roof[dom]['order']},D=16>"),
                 "per_launch": roof}
+    fwd_ms = sum(statistics.mean(r[k] for r in kern_ms) for k in range(len(SIGMAS)))
 
     # end-to-end through the public API: pinned host inputs -> device, both
     # Gram calls, Gram matrices -> pinned host, every step
@@ -251,8 +288,9 @@ def main():
     h_out = [torch.empty((N_PATHS, N_PATHS), dtype=torch.float64).pin_memory() for _ in SIGMAS]
     d_pts = [torch.empty_like(x) for x in X]
     d_len = [torch.empty_like(x) for x in L]
+    h_grad = torch.empty_like(h_pts[BWD_SIGMA]).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in h_pts + h_len)
-    d2h = sum(t.numel() * t.element_size() for t in h_out)
+    d2h = sum(t.numel() * t.element_size() for t in h_out + [h_grad])
     e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for i in range(args.steps):
@@ -263,9 +301,13 @@ def main():
             d_len[k].copy_(h_len[k], non_blocking=True)
             sigk.gram(d_pts[k], d_len[k], opts=opts[k], out=G[k], ws=wss[k], check=False)
             h_out[k].copy_(G[k], non_blocking=True)
+        k = BWD_SIGMA
+        gX, _, _ = sigk.backward(sigk.OP_GRAM, d_pts[k], d_len[k], None, None, W, opts[k],
+                                 ws=bws, check=False)
+        h_grad.copy_(gX, non_blocking=True)
         e_e[i].record()
     torch.cuda.synchronize()
-    for ws in wss:
+    for ws in wss + [bws]:
         sigk.sync_status(ws)
     e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(e_s, e_e))
     if world > 1:
@@ -274,8 +316,11 @@ def main():
         e2e_ms = float(t.item())
 
     line = {
-        "metric": "fwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=16 sigma in {1,4}",
-        "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "metric": "fwd & fwd+bwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=16 "
+                  "sigma in {1,4}",
+        "value": value,
+        "fwd_only": {"value": cells * world / (fwd_ms * 1e-3), "unit": "cells/s",
+                     "ms": fwd_ms, "note": "forward solver kernels of both Grams alone"}, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (float-float corner, f64 reductions)",
         "data": "synthetic (seeded Brownian, PCG64)",
@@ -283,8 +328,10 @@ def main():
                    "d": DIM, "sigmas": [s for s, *_ in SIGMAS],
                    "order_rings": [[P, nr] for _, _, P, nr in SIGMAS],
                    "unique_pairs_per_gram": pairs_of_gram(N_PATHS), "l2": "flushed between steps",
+                   "step": "forward Gram (sigma 1 and 4) + adjoint of the sigma=1 Gram "
+                           "(upstream: fixed dense weights)",
                    "parallelism": f"independent batch per rank x{world}"},
-        "gpu_launches": 2 * len(SIGMAS) * args.steps,
+        "gpu_launches": (2 * len(SIGMAS) + 3) * args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": cells * world / (e2e_ms * 1e-3), "unit": "cells/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

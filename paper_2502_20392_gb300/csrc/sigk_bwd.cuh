@@ -51,7 +51,7 @@ struct BwdArgs {
 
 template <int P, int D>
 struct BwdSmem {
-    static constexpr int S = P + 3;   // record / forward seam entry
+    static constexpr int S = P + 4;   // record / forward seam entry
     static constexpr int SA = P + 1;  // adjoint seam entry: corner, b1..bP
     static constexpr int DS = DyStride<D>::value;
     static constexpr int per_warp = 64 * DS + 32 * S + 2 * 32 * SA + 64 * D;
@@ -90,9 +90,11 @@ __device__ __forceinline__ void add_inc_grad(float* g, int64_t row, int d, int i
     }
 }
 
+constexpr int bwd_min_blocks(int P, int D) { return (P <= 8 && D <= 8) ? 4 : 3; }
+
 template <int P, int D>
-__global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
-    constexpr int S = P + 3;
+__global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs A) {
+    constexpr int S = P + 4;
     constexpr int SA = P + 1;
     constexpr int DS = DyStride<D>::value;
     extern __shared__ float4 smem_f4[];
@@ -135,11 +137,11 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
             dx[e] = (has_row && e < A.d) ? inc_at(pd.xr, row, A.d, e, A.inc_mode) : 0.0f;
 
         // ------------------------- pass A: forward replay ------------------------
-        float a[P + 1];
+        float a[P + 1], a1lo = 0.0f;
 #pragma unroll
         for (int p = 0; p <= P; ++p) a[p] = 0.0f;
         int E = 0;
-        float ohi = 1.0f, olo = 0.0f, ob[P + 1];
+        float ohi = 1.0f, olo = 0.0f, ob1lo = 0.0f, ob[P + 1];
 #pragma unroll
         for (int q = 0; q <= P; ++q) ob[q] = 0.0f;
         int oE = 0;
@@ -161,6 +163,7 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
             }
             float hi = __shfl_up_sync(kFull, ohi, 1);
             float lo = __shfl_up_sync(kFull, olo, 1);
+            float b1lo = __shfl_up_sync(kFull, ob1lo, 1);
             float b[P + 1];
             b[0] = 0.0f;
 #pragma unroll
@@ -171,11 +174,12 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
                     const float* e_ = sin_ + (t & 31) * S;
                     hi = e_[0];
                     lo = e_[1];
+                    b1lo = e_[2];
 #pragma unroll
-                    for (int q = 1; q <= P; ++q) b[q] = e_[1 + q];
-                    F = __float_as_int(e_[P + 2]);
+                    for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
+                    F = __float_as_int(e_[P + 3]);
                 } else {
-                    hi = 1.0f; lo = 0.0f; F = 0;
+                    hi = 1.0f; lo = 0.0f; b1lo = 0.0f; F = 0;
 #pragma unroll
                     for (int q = 1; q <= P; ++q) b[q] = 0.0f;
                 }
@@ -186,18 +190,20 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
                 float* r = rec + (size_t)t * S * 32 + lane;
                 r[0] = hi;
                 r[32] = lo;
+                r[64] = b1lo;
 #pragma unroll
-                for (int q = 1; q <= P; ++q) r[(1 + q) * 32] = b[q];
+                for (int q = 1; q <= P; ++q) r[(2 + q) * 32] = b[q];
                 const int Eb = E;
                 if (F != E) {
                     if (F > E) {
                         const float sc = exp2_nonpos(E - F);
+                        a1lo *= sc;
 #pragma unroll
                         for (int p = 1; p <= P; ++p) a[p] *= sc;
                         E = F;
                     } else {
                         const float sc = exp2_nonpos(F - E);
-                        hi *= sc; lo *= sc;
+                        hi *= sc; lo *= sc; b1lo *= sc;
 #pragma unroll
                         for (int q = 1; q <= P; ++q) b[q] *= sc;
                     }
@@ -212,20 +218,21 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
                     c = fmaf(dx[4 * e4 + 2], v.z, c);
                     c = fmaf(dx[4 * e4 + 3], v.w, c);
                 }
-                tile_update<P>(c, a, hi, lo, b, A.nr);
+                tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, A.nr);
                 int bump = 0;
                 if (fabsf(hi) > 1.8446744e19f) {
                     const float sc = 5.421011e-20f;
+                    a1lo *= sc;
 #pragma unroll
                     for (int p = 1; p <= P; ++p) a[p] *= sc;
-                    hi *= sc; lo *= sc;
+                    hi *= sc; lo *= sc; b1lo *= sc;
 #pragma unroll
                     for (int q = 1; q <= P; ++q) b[q] *= sc;
                     E += 64;
                     bump = 1;
                 }
-                r[(P + 2) * 32] = __int_as_float(pack_exp(F, Eb, bump));
-                ohi = hi; olo = lo; oE = E;
+                r[(P + 3) * 32] = __int_as_float(pack_exp(F, Eb, bump));
+                ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
 #pragma unroll
                 for (int q = 1; q <= P; ++q) ob[q] = b[q];
             }
@@ -248,6 +255,7 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
                                   prev_consumer, A.status);
             ok = __shfl_sync(kFull, okl, 0);
         }
+        a[1] += a1lo;  // the reverse sweep carries the first-order term as one float
         float Ab[P + 1];
 #pragma unroll
         for (int p = 0; p <= P; ++p) Ab[p] = 0.0f;
@@ -316,9 +324,10 @@ __global__ void __launch_bounds__(128) bwd_kernel(BwdArgs A) {
                 float b[P + 1];
                 b[0] = 0.0f;
 #pragma unroll
-                for (int q = 1; q <= P; ++q) b[q] = r[(1 + q) * 32];
+                for (int q = 1; q <= P; ++q) b[q] = r[(2 + q) * 32];
+                b[1] += r[64];  // first-order term as one float
                 int F, Eb, bump;
-                unpack_exp(__float_as_int(r[(P + 2) * 32]), F, Eb, bump);
+                unpack_exp(__float_as_int(r[(P + 3) * 32]), F, Eb, bump);
                 const int Em = F > Eb ? F : Eb;
                 if (bump) {  // undo the renormalisation after this tile
                     const float up = 1.8446744e19f, dn = 5.421011e-20f;

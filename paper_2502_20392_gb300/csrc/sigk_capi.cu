@@ -114,6 +114,7 @@ struct Layout {
     bool train;
     int64_t n_pairs, n_paths_x, n_paths_y;
     int nslot, wcols, grid, nwarps, rows_per_strip, stride;
+    int64_t nwords;
     KernelInfo info;
 };
 
@@ -146,11 +147,18 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->grid = o.grid_ctas > 0 ? (o.grid_ctas < full_grid ? o.grid_ctas : full_grid) : full_grid;
     L->nwarps = L->grid * (L->info.threads / 32);
     L->rows_per_strip = 32 * L->info.rows_per_lane;
-    L->stride = o.order + 3;
+    L->stride = o.order + 4;
     // Seam ring: nslot > concurrent warps; wcols large enough that the warps
     // in flight can always hold a whole sweep between them (nwarps * wcols >=
     // 2 * max_len), so a producer never waits on a consumer that cannot start.
     L->nslot = L->nwarps + 64;
+    // training: one progress word per work item (seams are not reused)
+    L->nwords = L->nslot;
+    if (train) {
+        const int64_t items = (int64_t)pair_count(op, n_x, n_y, o.flags) *
+                              ((o.max_len + L->rows_per_strip - 1) / L->rows_per_strip);
+        if (items > L->nwords) L->nwords = items;
+    }
     int64_t w = 2 * o.max_len / L->nwarps + 64;
     if (w < 256) w = 256;
     if (w > o.max_len) w = o.max_len;
@@ -166,9 +174,9 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->oy = off; off = align256(off + sizeof(int64_t) * (size_t)(n_y + 1));
     L->pairs = off; off = align256(off + sizeof(PairDesc) * (size_t)L->n_pairs);
     L->item_start = off; off = align256(off + sizeof(int32_t) * (size_t)(L->n_pairs + 1));
-    L->prod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nslot);
-    L->cons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nslot);
-    L->done = off; off = align256(off + sizeof(long long) * (size_t)L->nslot);
+    L->prod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
+    L->cons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
+    L->done = off; off = align256(off + sizeof(long long) * (size_t)L->nwords);
     L->seam = off; off = align256(off + sizeof(float) * (size_t)L->nslot * L->wcols * L->stride);
     L->gram = off;
     if (op == SIGK_OP_MMD) off = align256(off + sizeof(double) * (size_t)(n_x + n_y) * (n_x + n_y));
@@ -583,7 +591,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     pa.prod = (unsigned long long*)(base + L.prod);
     pa.cons = (unsigned long long*)(base + L.cons);
     pa.done = (long long*)(base + L.done);
-    pa.nslot = L.nslot;
+    pa.nslot = (int)L.nwords;
     pa.hdr = hdr;
     pa.out = out;
     pa.out_ld = out_ld;

@@ -158,8 +158,8 @@ __device__ __forceinline__ float exp2_nonpos(int n) {
 // One tile.  a[1..P]: scaled bottom edge (overwritten by the top edge);
 // (hi, lo), b[1..P]: scaled left edge (overwritten by the right edge).
 template <int P>
-__device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& hi, float& lo,
-                                            float (&b)[P + 1], int nr) {
+__device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a1lo, float& hi,
+                                            float& lo, float (&b)[P + 1], float& b1lo, int nr) {
     constexpr int NRM = P < kMaxRings ? P : kMaxRings;
     float cp[NRM + 1], ch[NRM + 1];
     cp[1] = c;
@@ -188,12 +188,12 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& h
         }
     }
     // bottom edge evaluated at u = 1 (without its constant term)
-    float S = 0.0f;
+    float S = a1lo;
 #pragma unroll
     for (int p = P; p >= 1; --p) S = fmaf(a[p], c_inv_fact[p], S);
     // top edge (in place, high degree first: reads only lower, older entries)
 #pragma unroll
-    for (int p = P; p >= 1; --p) {
+    for (int p = P; p >= 2; --p) {
         float v = a[p];
 #pragma unroll
         for (int m = 1; m < p && m <= NRM; ++m)
@@ -203,13 +203,25 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& h
     }
     // right edge
 #pragma unroll
-    for (int q = P; q >= 1; --q) {
+    for (int q = P; q >= 2; --q) {
         float v = b[q];
 #pragma unroll
         for (int m = 1; m < q && m <= NRM; ++m)
             if (m <= nr) v = fmaf(ch[m], b[q - m], v);
         if (q <= NRM && q <= nr) v = fmaf(cp[q], hb[q], v);
         b[q] = v;
+    }
+    // first-order coefficients: compensated (TwoSum) accumulation.  Along a
+    // long row or column they gather ~L increments of only a few ulps each,
+    // whose plain FP32 rounding is biased rather than random.
+    {
+        const float da = cp[1] * ha[1], db = cp[1] * hb[1];
+        const float sa = a[1] + da, sb = b[1] + db;
+        const float ta = sa - a[1], tb = sb - b[1];
+        a1lo += (a[1] - (sa - ta)) + (da - ta);
+        b1lo += (b[1] - (sb - tb)) + (db - tb);
+        a[1] = sa;
+        b[1] = sb;
     }
     // corner value b'_0 = b_0 + S in float-float (TwoSum)
     const float s = hi + S;
@@ -358,6 +370,7 @@ __host__ __device__ constexpr long long tile_flops(int P, int nr) {
         if (p <= nr) f += 2 * 2;                        // ring-p term, 2 edges
     }
     f += 7;                                             // TwoSum + lo
+    f += 12;                                            // compensated a1, b1
     return f;
 }
 

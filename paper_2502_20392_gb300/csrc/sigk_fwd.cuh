@@ -35,7 +35,7 @@ struct DyStride {
 
 template <int P, int D>
 struct FwdSmem {
-    static constexpr int S = P + 3;  // seam entry: hi, lo, b1..bP, exponent
+    static constexpr int S = P + 4;  // seam entry: hi, lo, b1lo, b1..bP, exponent
     static constexpr int DS = DyStride<D>::value;
     static constexpr int per_warp = 64 * DS + 2 * kG * S;  // floats
 };
@@ -46,9 +46,15 @@ __device__ __forceinline__ float inc_at(const float* z, int64_t row, int d, int 
     return z[(row + 1) * d + e] - z[row * d + e];
 }
 
+// CTAs per SM the register allocation must allow (128 threads each): the
+// largest count that ptxas meets without spilling for that instantiation.
+constexpr int fwd_min_blocks(int P, int D, int R) {
+    return R == 1 ? 4 : (R == 2 ? (P <= 8 ? 4 : 3) : (P <= 4 ? 4 : 3));
+}
+
 template <int P, int D, int R>
-__global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
-    constexpr int S = P + 3;
+__global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(SolverArgs A) {
+    constexpr int S = P + 4;
     constexpr int DS = DyStride<D>::value;
     extern __shared__ float4 smem_f4[];
     float* smem = reinterpret_cast<float*>(smem_f4);
@@ -93,18 +99,24 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
             for (int e = 0; e < D; ++e)
                 dx[k][e] = (row < L1 && e < A.d) ? inc_at(pd.xr, row, A.d, e, A.inc_mode) : 0.0f;
         }
-        float a[R][P + 1];
+        float a[R][P + 1], a1lo[R];
 #pragma unroll
-        for (int k = 0; k < R; ++k)
+        for (int k = 0; k < R; ++k) {
+            a1lo[k] = 0.0f;
 #pragma unroll
             for (int p = 0; p <= P; ++p) a[k][p] = 0.0f;
+        }
         int E = 0;
         // outgoing right edge of the previous step (what lane+1 receives)
-        float ohi = 1.0f, olo = 0.0f, ob[P + 1];
+        float ohi = 1.0f, olo = 0.0f, ob1lo = 0.0f, ob[P + 1];
 #pragma unroll
         for (int q = 0; q <= P; ++q) ob[q] = 0.0f;
         int oE = 0;
 
+        // progress words: per slot (inference) or per item (training, where
+        // the seams are not reused and a slot's word could be overtaken)
+        const int pw_in = train ? item - 1 : slot_in;
+        const int pw_out = train ? item : slot_out;
         // the slot we write must have been read by its previous consumer
         if (has_out && !train) {
             const long long prev_consumer = (long long)item - A.nslot + 1;
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                     const unsigned long long need =
                         ((unsigned long long)(item - 1) << 32) | (unsigned)(t + nb);
                     bool okl = true;
-                    if (lane == 0) okl = wait_ge_u64(&A.prod[slot_in], need, A.status);
+                    if (lane == 0) okl = wait_ge_u64(&A.prod[pw_in], need, A.status);
                     ok = __shfl_sync(kFull, okl, 0);
                     if (ok) {
                         const float* src =
@@ -137,7 +149,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                                   : A.seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
                         for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src + idx);
                         __syncwarp();
-                        if (lane == 0)
+                        if (lane == 0 && !train)
                             st_release_u64(&A.cons[slot_in],
                                            ((unsigned long long)item << 32) | (unsigned)(t + nb));
                     }
@@ -148,6 +160,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
             // left edge: from lane-1 (previous step), or the seam / boundary for lane 0
             float hi = __shfl_up_sync(kFull, ohi, 1);
             float lo = __shfl_up_sync(kFull, olo, 1);
+            float b1lo = __shfl_up_sync(kFull, ob1lo, 1);
             float b[P + 1];
             b[0] = 0.0f;
 #pragma unroll
@@ -158,11 +171,12 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                     const float* e_ = sin_ + (t & 31) * S;
                     hi = e_[0];
                     lo = e_[1];
+                    b1lo = e_[2];
 #pragma unroll
-                    for (int q = 1; q <= P; ++q) b[q] = e_[1 + q];
-                    F = __float_as_int(e_[P + 2]);
+                    for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
+                    F = __float_as_int(e_[P + 3]);
                 } else {
-                    hi = 1.0f; lo = 0.0f; F = 0;
+                    hi = 1.0f; lo = 0.0f; b1lo = 0.0f; F = 0;
 #pragma unroll
                     for (int q = 1; q <= P; ++q) b[q] = 0.0f;
                 }
@@ -174,13 +188,15 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                     if (F > E) {
                         const float sc = exp2_nonpos(E - F);
 #pragma unroll
-                        for (int k = 0; k < R; ++k)
+                        for (int k = 0; k < R; ++k) {
+                            a1lo[k] *= sc;
 #pragma unroll
                             for (int p = 1; p <= P; ++p) a[k][p] *= sc;
+                        }
                         E = F;
                     } else {
                         const float sc = exp2_nonpos(F - E);
-                        hi *= sc; lo *= sc;
+                        hi *= sc; lo *= sc; b1lo *= sc;
 #pragma unroll
                         for (int q = 1; q <= P; ++q) b[q] *= sc;
                     }
@@ -198,21 +214,23 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                     float c = 0.0f;
 #pragma unroll
                     for (int e = 0; e < D; ++e) c = fmaf(dx[k][e], dy[e], c);
-                    tile_update<P>(c, a[k], hi, lo, b, A.nr);
+                    tile_update<P>(c, a[k], a1lo[k], hi, lo, b, b1lo, A.nr);
                 }
                 // renormalise when the corner value grows past 2^64
                 if (fabsf(hi) > 1.8446744e19f) {
                     const float sc = 5.421011e-20f;  // 2^-64
 #pragma unroll
-                    for (int k = 0; k < R; ++k)
+                    for (int k = 0; k < R; ++k) {
+                        a1lo[k] *= sc;
 #pragma unroll
                         for (int p = 1; p <= P; ++p) a[k][p] *= sc;
-                    hi *= sc; lo *= sc;
+                    }
+                    hi *= sc; lo *= sc; b1lo *= sc;
 #pragma unroll
                     for (int q = 1; q <= P; ++q) b[q] *= sc;
                     E += 64;
                 }
-                ohi = hi; olo = lo; oE = E;
+                ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
 #pragma unroll
                 for (int q = 1; q <= P; ++q) ob[q] = b[q];
                 tiles_done += (unsigned long long)max(0, min(R, L1 - (i0 + lane * R)));
@@ -220,12 +238,12 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                 if (lane == 31) {
                     if (has_out) {
                         float* e_ = sout + (j & 31) * S;
-                        e_[0] = hi; e_[1] = lo;
+                        e_[0] = hi; e_[1] = lo; e_[2] = b1lo;
 #pragma unroll
-                        for (int q = 1; q <= P; ++q) e_[1 + q] = b[q];
-                        e_[P + 2] = __int_as_float(E);
+                        for (int q = 1; q <= P; ++q) e_[2 + q] = b[q];
+                        e_[P + 3] = __int_as_float(E);
                     } else if (j == L2 - 1) {
-                        double k = (double)hi + (double)lo;
+                        double k = (double)hi + (double)lo + (double)b1lo;
                         double fq = 1.0;
 #pragma unroll
                         for (int q = 1; q <= P; ++q) {
@@ -260,7 +278,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(SolverArgs A) {
                     __threadfence();
                     __syncwarp();
                     if (lane == 0)
-                        st_release_u64(&A.prod[slot_out],
+                        st_release_u64(&A.prod[pw_out],
                                        ((unsigned long long)item << 32) | (unsigned)(start + nb));
                 }
                 __syncwarp();

@@ -1,0 +1,160 @@
+"""GPU parity at the workloads' full sizes, in the launch configurations the
+benchmark uses, checked on outputs the FP64 oracle can compute one by one and
+on properties that hold at any size.
+
+* Gram B=64, L=1024, d=16, sigma in {1, 4}: sampled entries (rel 1e-5, or the
+  Cauchy-Schwarz scale for near-zero cross entries), exact mirror, PSD of the
+  normalised Gram.
+* One pair of 1e6-segment paths in R^8: the collinear variant against the
+  closed form I0(2 sqrt(<X,Y>)) (rel 1e-4); the Brownian pair's 1e4-segment
+  prefix against the oracle (rel 1e-4); the full Brownian pair's symmetry
+  k(x,y) = k(y,x) (rel 1e-4); O(L) workspace.
+* MMD^2 between two batches of 32 paths, 2048 segments, d=8 (drifted Y):
+  sampled Gram entries, the FP64 reduction, and dMMD^2/dX on 20 random
+  coordinates against FP64 central differences of the oracle (rel 1e-4 of the
+  largest entry)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import i0
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GRAM_OPTS = {1.0: dict(order=8, rings=4), 4.0: dict(order=16, rings=6)}
+LONG_OPTS = dict(order=4, rings=2)
+MMD_OPTS = dict(order=6, rings=4)
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_20392_gb300 import build, sigk
+    build.build()
+    sigk.load()
+    return sigk
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def incs(paths):
+    return [np.diff(p.astype(np.float64), axis=0) for p in paths]
+
+
+@pytest.mark.parametrize("sigma", [1.0, 4.0])
+def test_gram_B64_L1024_d16(S, orc, sigma):
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.workload_gram_1024(sigma)
+    G = S.gram(torch.from_numpy(pts).to(dev()), torch.from_numpy(lens).to(dev()),
+               opts=S.Opts(**GRAM_OPTS[sigma], max_len=1024)).cpu().numpy()
+    assert np.isfinite(G).all()
+    np.testing.assert_array_equal(G, G.T)
+    paths = incs(synth.split(pts, lens))
+    rng = np.random.default_rng(int(sigma))
+    idx = [(a, a) for a in (0, 17, 63)] + [tuple(sorted(rng.choice(64, 2, replace=False)))
+                                            for _ in range(21)]
+    ref = orc.series_pairs([paths[a] for a, _ in idx], [paths[b] for _, b in idx], N=20)
+    for (a, b), r in zip(idx, ref):
+        e = abs(G[a, b] - r) / abs(r)
+        scale = math.sqrt(abs(G[a, a] * G[b, b]))
+        if abs(r) < 1e-2 * scale:
+            e = min(e, abs(G[a, b] - r) / scale)
+        assert e < 1e-5, (a, b, G[a, b], r)
+    dg = np.sqrt(np.diag(G))
+    w = np.linalg.eigvalsh(G / dg[:, None] / dg[None, :])
+    assert w.min() > -1e-6
+
+
+def test_long_pair_collinear_closed_form(S):
+    from paper_2502_20392_gb300 import synth
+    inc, segs, u, tot = synth.collinear_increments(1_000_000, 8, seed=3002, n_paths=2)
+    X = torch.from_numpy(inc).to(dev())
+    L = torch.from_numpy(segs).to(dev())
+    o = S.Opts(**LONG_OPTS, flags=S.FLAG_INCREMENTS, max_len=1_000_000)
+    ws = S.Workspace()
+    k = S.pairs(X[:1_000_000], L[:1], X[1_000_000:], L[1:], opts=o, ws=ws).item()
+    ref = i0(2 * math.sqrt(float(u @ u) * tot[0] * tot[1]))
+    assert abs(k - ref) / ref < 1e-4, (k, ref)
+    # O(L) device memory: the workspace is a few bytes per segment
+    assert ws.buf.numel() < 200 * 1_000_000, ws.buf.numel()
+
+
+def test_long_pair_brownian_prefix_and_symmetry(S, orc):
+    from paper_2502_20392_gb300 import synth
+    inc, segs = synth.workload_long_pair()
+    X = torch.from_numpy(inc).to(dev())
+    n = 1_000_000
+    o = S.Opts(**LONG_OPTS, flags=S.FLAG_INCREMENTS, max_len=n)
+    # 1e4-segment prefix against the oracle
+    m = 10_000
+    Xp = torch.cat([X[:m], X[n:n + m]])
+    Lp = torch.tensor([m, m], dtype=torch.int64, device=dev())
+    kp = S.pairs(Xp[:m], Lp[:1], Xp[m:], Lp[1:], opts=o).item()
+    ref = orc.series_pair(inc[:m].astype(np.float64), inc[n:n + m].astype(np.float64), N=6)
+    assert abs(kp - ref) / abs(ref) < 1e-4, (kp, ref)
+    # full pair: symmetry in x and y
+    L1 = torch.tensor([n], dtype=torch.int64, device=dev())
+    k_xy = S.pairs(X[:n], L1, X[n:], L1, opts=o).item()
+    k_yx = S.pairs(X[n:], L1, X[:n], L1, opts=o).item()
+    assert np.isfinite(k_xy)
+    assert abs(k_xy - k_yx) / abs(k_xy) < 1e-4, (k_xy, k_yx)
+
+
+def test_mmd_2x32_L2048_d8_value_and_gradient(S, orc):
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.workload_mmd_2048()
+    xs, ys = synth.split(X, lx), synth.split(Y, ly)
+    o = S.Opts(**MMD_OPTS, max_len=2048)
+    Xd, lxd = torch.from_numpy(X).to(dev()), torch.from_numpy(lx).to(dev())
+    Yd, lyd = torch.from_numpy(Y).to(dev()), torch.from_numpy(ly).to(dev())
+    Gz = torch.empty((64, 64), dtype=torch.float64, device=dev())
+    v = S.mmd(Xd, lxd, Yd, lyd, opts=o, gram_out=Gz).item()
+    Gz = Gz.cpu().numpy()
+    # the FP64 reduction of the Gram of [X; Y]
+    m = n = 32
+    Kxx, Kyy, Kxy = Gz[:m, :m], Gz[m:, m:], Gz[:m, m:]
+    u = ((Kxx.sum() - np.trace(Kxx)) / (m * (m - 1)) + (Kyy.sum() - np.trace(Kyy)) / (n * (n - 1))
+         - 2 * Kxy.mean())
+    assert v == pytest.approx(u, rel=1e-9, abs=1e-12)
+    # sampled Gram entries against the oracle
+    zs = incs(xs + ys)
+    rng = np.random.default_rng(5)
+    idx = [tuple(sorted(rng.choice(64, 2, replace=False))) for _ in range(16)] + [(3, 3), (40, 40)]
+    ref = orc.series_pairs([zs[a] for a, _ in idx], [zs[b] for _, b in idx], N=8)
+    for (a, b), r in zip(idx, ref):
+        assert abs(Gz[a, b] - r) <= 1e-5 * max(abs(r), 1e-2 * math.sqrt(Gz[a, a] * Gz[b, b])), (a, b)
+    # gradient w.r.t. X on 20 random coordinates vs FP64 central differences
+    gX, _, v2 = S.backward(S.OP_MMD, Xd, lxd, Yd, lyd, torch.ones(1, dtype=torch.float64), o,
+                           need_y=False)
+    assert v2.item() == pytest.approx(v, rel=1e-6)
+    gX = gX.cpu().numpy()
+    coords = rng.choice(X.size, size=20, replace=False)
+    h = 1e-3
+    pts_per_path = 2049
+    xs64 = [p.astype(np.float64) for p in xs]
+    px, py, wts = [], [], []
+    for c in coords:
+        a, loc = divmod(int(c), pts_per_path * 8)
+        for sgn in (1.0, -1.0):
+            pa = xs64[a].copy()
+            pa.reshape(-1)[loc] += sgn * h
+            ia = np.diff(pa, axis=0)
+            for b in range(64):
+                if b == a:
+                    continue  # U-statistic: the diagonal term has weight 0
+                zb = zs[b]
+                wgt = (2.0 / (m * (m - 1))) if b < m else (-2.0 / (m * n))
+                px.append(ia)
+                py.append(zb)
+                wts.append(sgn * wgt)
+    kv = orc.series_pairs(px, py, N=4)
+    per = len(kv) // len(coords)
+    fd = np.array([np.dot(kv[i * per:(i + 1) * per], wts[i * per:(i + 1) * per]) / (2 * h)
+                   for i in range(len(coords))])
+    got = gX.reshape(-1)[coords]
+    np.testing.assert_allclose(got, fd, atol=1e-4 * np.abs(fd).max())
