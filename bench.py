@@ -42,7 +42,7 @@ def tile_flops(P: int, nr: int, d: int) -> int:
     f += 2 * P
     for p in range(1, P + 1):
         f += 4 * min(p - 1, nr) + (4 if p <= nr else 0)
-    f += 7 + 12  # float-float corner; compensated first-order coefficients
+    f += 10 + 18  # float-float corner; compensated first-order coefficients
     return f + 2 * d
 
 

@@ -214,21 +214,28 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
     // first-order coefficients: compensated (TwoSum) accumulation.  Along a
     // long row or column they gather ~L increments of only a few ulps each,
     // whose plain FP32 rounding is biased rather than random.
+    // The pair is renormalised (Fast2Sum) so that the high part stays the
+    // nearest float to the full value: the Hankel sums and convolutions read
+    // only the high part.
     {
         const float da = cp[1] * ha[1], db = cp[1] * hb[1];
         const float sa = a[1] + da, sb = b[1] + db;
         const float ta = sa - a[1], tb = sb - b[1];
-        a1lo += (a[1] - (sa - ta)) + (da - ta);
-        b1lo += (b[1] - (sb - tb)) + (db - tb);
-        a[1] = sa;
-        b[1] = sb;
+        const float la = a1lo + ((a[1] - (sa - ta)) + (da - ta));
+        const float lb = b1lo + ((b[1] - (sb - tb)) + (db - tb));
+        a[1] = sa + la;
+        b[1] = sb + lb;
+        a1lo = la - (a[1] - sa);
+        b1lo = lb - (b[1] - sb);
     }
-    // corner value b'_0 = b_0 + S in float-float (TwoSum)
+    // corner value b'_0 = b_0 + S in float-float: TwoSum, then Fast2Sum
+    // renormalisation so that hi is the nearest float to hi + lo (hi is what
+    // the next tiles' Hankel sums read)
     const float s = hi + S;
     const float bb = s - hi;
-    const float e = (hi - (s - bb)) + (S - bb);
-    hi = s;
-    lo += e;
+    const float t = lo + ((hi - (s - bb)) + (S - bb));
+    hi = s + t;
+    lo = t - (hi - s);
 }
 
 // Inverse of the bottom-to-top edge update of tile_update, given the tile's
@@ -369,8 +376,8 @@ __host__ __device__ constexpr long long tile_flops(int P, int nr) {
         f += 2 * 2 * k;                                 // convolution, 2 edges
         if (p <= nr) f += 2 * 2;                        // ring-p term, 2 edges
     }
-    f += 7;                                             // TwoSum + lo
-    f += 12;                                            // compensated a1, b1
+    f += 10;                                            // float-float corner
+    f += 18;                                            // compensated a1, b1
     return f;
 }
 
