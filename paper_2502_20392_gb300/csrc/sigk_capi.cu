@@ -11,6 +11,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
+#include <cmath>
 
 #include <cuda_runtime.h>
 
@@ -538,6 +540,145 @@ __global__ void __launch_bounds__(1024) mmd_reduce_kernel(const double* G, int64
 
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// a-priori truncation statistics (sigk_plan), one warp per pair:
+//   [0] L1, [1] L2 (segments as solved: row path, swept path)
+//   [2] C_a: max over rows i and sampled points J of |<dx_i, y_J - y_0>| -- the
+//       accumulated coupling that sets the size of the bottom-edge coefficients
+//       a_p ~ C_a^p / (p!)^2; [3] C_b: the same with the roles swapped
+//   [4 + m - 2], m = 2..9: (sum_i |dx_i|^m) * (sum_j |dy_j|^m), an upper bound
+//       on sum_ij |c_ij|^m (Cauchy-Schwarz), the size of the dropped ring m
+constexpr int kStatFields = 12;
+constexpr int kStatStride = 16;  // sampled points: every 16th, plus the last
+
+__device__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+__device__ float warp_max_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// max over rows i of path `a` and sampled points J of path `b` of
+// |<da_i, b_J - b_0>| (at most ~1024 samples of J, always including the end)
+constexpr int kStatDmax = 16;
+
+__device__ float coupling_max(const float* a, int La, const float* b, int Lb, int d, int inc_mode,
+                              int lane) {
+    const int stride = max(kStatStride, (Lb + 1023) / 1024);
+    float B[kStatDmax];
+#pragma unroll
+    for (int e = 0; e < kStatDmax; ++e) B[e] = 0.0f;
+    float best = 0.0f;
+    int Jprev = 0;
+    for (int J = min(stride, Lb);; J = min(J + stride, Lb)) {
+        // B = b_J - b_0 (points), or the running sum of the increments
+#pragma unroll
+        for (int e = 0; e < kStatDmax; ++e) {
+            if (e < d) {
+                if (inc_mode) {
+                    for (int j = Jprev; j < J; ++j) B[e] += b[(int64_t)j * d + e];
+                } else {
+                    B[e] = b[(int64_t)J * d + e] - b[e];
+                }
+            }
+        }
+        for (int i = lane; i < La; i += 32) {
+            float dot = 0.0f;
+#pragma unroll
+            for (int e = 0; e < kStatDmax; ++e)
+                if (e < d) dot = fmaf(inc_at(a, i, d, e, inc_mode), B[e], dot);
+            best = fmaxf(best, fabsf(dot));
+        }
+        Jprev = J;
+        if (J >= Lb) break;
+    }
+    return warp_max_f(best);
+}
+
+__global__ void pair_stats_kernel(const PairDesc* pairs, int64_t n_pairs, int d, int inc_mode,
+                                  double* out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_pairs;
+         p += warps) {
+        const PairDesc pd = pairs[p];
+        double* o = out + p * kStatFields;
+        double sx[8], sy[8];
+        for (int m = 0; m < 8; ++m) { sx[m] = 0.0; sy[m] = 0.0; }
+        for (int i = lane; i < pd.L1; i += 32) {
+            double n2 = 0.0;
+            for (int e = 0; e < d; ++e) {
+                const double v = inc_at(pd.xr, i, d, e, inc_mode);
+                n2 += v * v;
+            }
+            const double n1 = sqrt(n2);
+            double pw = n2;
+            for (int m = 0; m < 8; ++m) { sx[m] += pw; pw *= n1; }
+        }
+        for (int j = lane; j < pd.L2; j += 32) {
+            double n2 = 0.0;
+            for (int e = 0; e < d; ++e) {
+                const double v = inc_at(pd.yr, j, d, e, inc_mode);
+                n2 += v * v;
+            }
+            const double n1 = sqrt(n2);
+            double pw = n2;
+            for (int m = 0; m < 8; ++m) { sy[m] += pw; pw *= n1; }
+        }
+        for (int m = 0; m < 8; ++m) { sx[m] = warp_sum_d(sx[m]); sy[m] = warp_sum_d(sy[m]); }
+        float ca = 0.0f, cb = 0.0f;
+        if (pd.L1 > 0 && pd.L2 > 0) {
+            ca = coupling_max(pd.xr, pd.L1, pd.yr, pd.L2, d, inc_mode, lane);
+            cb = coupling_max(pd.yr, pd.L2, pd.xr, pd.L1, d, inc_mode, lane);
+        }
+        if (lane == 0) {
+            o[0] = pd.L1;
+            o[1] = pd.L2;
+            o[2] = ca;
+            o[3] = cb;
+            for (int m = 0; m < 8; ++m) o[4 + m] = sx[m] * sy[m];
+        }
+    }
+}
+
+// Smallest (order P, rings n) with the estimated truncation errors below
+// tol/10, relative to the local kernel scale (App. C.3: a-priori order search
+// from the largest coupling in the grid, here per pair and for two knobs):
+//   rings: sum_ij |c_ij|^{n+1} / ((n+1)!)^2 <= tol/10 (the dropped ring n+1)
+//   order: max(L1, L2) * (1.25 C)^{P+1} / ((P+1)!)^2 <= tol/10, C the sampled
+//          coupling (the dropped edge coefficient of degree P+1, over a row)
+static void choose_order(const double* st, int64_t n, double tol, int* P_out, int* nr_out,
+                         int64_t* max_swept) {
+    const double target = 0.1 * tol;
+    int P = 4, nr = 1;
+    double fact[40];
+    fact[0] = 1.0;
+    for (int k = 1; k < 40; ++k) fact[k] = fact[k - 1] * k;
+    for (int64_t p = 0; p < n; ++p) {
+        const double* o = st + p * kStatFields;
+        if (o[0] <= 0 || o[1] <= 0) continue;
+        if ((int64_t)o[1] > *max_swept) *max_swept = (int64_t)o[1];
+        int r = 1;
+        while (r < kMaxRings && o[4 + (r + 1) - 2] / (fact[r + 1] * fact[r + 1]) > target) ++r;
+        if (r > nr) nr = r;
+        const double C = 1.25 * (o[2] > o[3] ? o[2] : o[3]);
+        const double Lm = o[0] > o[1] ? o[0] : o[1];
+        int q = 4;
+        while (q < kMaxP && Lm * pow(C, q + 1) / (fact[q + 1] * fact[q + 1]) > target) ++q;
+        if (q > P) P = q;
+    }
+    if (P < nr) P = nr;
+    P += (P & 1);
+    if (P > kMaxP) P = kMaxP;
+    if (nr > (P < kMaxRings ? P : kMaxRings)) nr = P < kMaxRings ? P : kMaxRings;
+    *P_out = P;
+    *nr_out = nr;
+}
+
 static sigk_status check_ws(const Layout& L, void* ws, size_t ws_bytes) {
     if (!ws) return fail(SIGK_ERR_WORKSPACE, "workspace pointer is NULL");
     if (((uintptr_t)ws & 255) != 0) return fail(SIGK_ERR_WORKSPACE, "workspace must be 256-byte aligned");
@@ -810,9 +951,88 @@ sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t 
     return SIGK_OK;
 }
 
-sigk_status sigk_plan(int, const float*, const int64_t*, int64_t, const float*, const int64_t*,
-                      int64_t, int, double, void*, size_t, void*, const sigk_opts*, sigk_opts*) {
-    return fail(SIGK_ERR_UNSUPPORTED, "sigk_plan is not implemented in this build");
+sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x, const float* Y,
+                      const int64_t* len_y, int64_t n_y, int d, double tol, void* ws,
+                      size_t ws_bytes, void* stream, const sigk_opts* opts_in, sigk_opts* opts_out) {
+    if (!opts_out) return fail(SIGK_ERR_ARG, "opts_out is NULL");
+    if (!(tol > 0.0) || tol >= 1.0) return fail(SIGK_ERR_ARG, "tol must be in (0, 1)");
+    if (op < SIGK_OP_PAIRS || op > SIGK_OP_MMD) return fail(SIGK_ERR_ARG, "bad op");
+    if (op == SIGK_OP_GRAM && !Y) n_y = 0;
+    if (op == SIGK_OP_PAIRS) n_y = n_x;
+    sigk_status st = common_checks(n_x, n_y, d, opts_out);
+    if (st != SIGK_OK) return st;
+    Opts o;
+    if (!resolve_opts(opts_in, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    o.order = kMaxP;  // layout for the largest order (the planner's seam stride)
+    o.rings = 1;
+    Layout L;
+    if ((st = make_layout(op, n_x, n_y, d, o, &L)) != SIGK_OK) return st;
+    if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
+    const size_t need = sizeof(double) * kStatFields * (size_t)L.n_pairs;
+    if (need > L.total - L.seam) return fail(SIGK_ERR_WORKSPACE, "workspace too small for plan statistics");
+    char* base = (char*)ws;
+    cudaStream_t strm = (cudaStream_t)stream;
+    // the planner builds the pair table; its k outputs go to a scratch area
+    double* scratch_out = (double*)(base + L.seam);
+    PlanArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.op = op;
+    pa.flags = o.flags & ~SIGK_FLAG_GRAM_FULL;
+    pa.inc_mode = (o.flags & SIGK_FLAG_INCREMENTS) ? 1 : 0;
+    pa.d = d;
+    pa.X = X; pa.len_x = len_x; pa.n_x = n_x;
+    pa.Y = (op == SIGK_OP_GRAM && !Y) ? nullptr : Y;
+    pa.len_y = len_y;
+    pa.n_y = (op == SIGK_OP_GRAM && !Y) ? 0 : n_y;
+    pa.max_len = (int64_t)INT32_MAX;  // no swept-length limit while planning
+    pa.rows_per_strip = L.rows_per_strip;
+    pa.n_pairs = L.n_pairs;
+    pa.ox = (int64_t*)(base + L.ox);
+    pa.oy = (int64_t*)(base + L.oy);
+    pa.pairs = (PairDesc*)(base + L.pairs);
+    pa.item_start = (int32_t*)(base + L.item_start);
+    pa.prod = (unsigned long long*)(base + L.prod);
+    pa.cons = (unsigned long long*)(base + L.cons);
+    pa.done = (long long*)(base + L.done);
+    pa.nslot = (int)L.nwords;
+    pa.hdr = (Header*)(base + L.hdr);
+    pa.out = scratch_out;
+    pa.out_ld = 0;
+    if (op != SIGK_OP_PAIRS) {
+        // Gram-shaped ops write k at a*ld+b; give them a large enough scratch
+        const int64_t nz = (op == SIGK_OP_MMD) ? n_x + n_y : n_x;
+        const int64_t ncol = (op == SIGK_OP_GRAM && Y) ? n_y : nz;
+        pa.out_ld = ncol;
+        if (sizeof(double) * (size_t)((op == SIGK_OP_MMD ? nz : n_x) * ncol) + need > L.total - L.seam)
+            return fail(SIGK_ERR_WORKSPACE, "workspace too small for plan scratch");
+        scratch_out = (double*)(base + L.seam + need);
+        pa.out = scratch_out;
+    }
+    plan_kernel<<<1, kPlanThreads, 0, strm>>>(pa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "plan_kernel launch");
+    double* stats = (double*)(base + L.seam);
+    const int threads = 256;
+    const int64_t blocks = (L.n_pairs + (threads / 32) - 1) / (threads / 32);
+    pair_stats_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), threads, 0, strm>>>(
+        pa.pairs, L.n_pairs, d, pa.inc_mode, stats);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pair_stats launch");
+    if ((e = cudaStreamSynchronize(strm)) != cudaSuccess) return cuda_fail(e, "plan synchronize");
+    Header h;
+    if ((e = cudaMemcpy(&h, base + L.hdr, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "plan status copy");
+    if (h.status != 0) return fail((sigk_status)h.status, "invalid lengths");
+    std::vector<double> hs((size_t)kStatFields * L.n_pairs);
+    if ((e = cudaMemcpy(hs.data(), stats, need, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "plan stats copy");
+    int P = 4, nr = 1;
+    int64_t max_swept = 1;
+    choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept);
+    *opts_out = opts_in ? *opts_in : sigk_opts{0, 0, 0, 0, 0};
+    opts_out->order = P;
+    opts_out->rings = nr;
+    if (opts_out->max_len < max_swept) opts_out->max_len = max_swept;
+    return SIGK_OK;
 }
 
 sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream) {

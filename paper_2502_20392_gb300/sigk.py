@@ -336,3 +336,30 @@ def sig_kernel_gram(X, len_x, Y=None, len_y=None, opts: Opts | None = None):
 def sig_kernel_mmd(X, len_x, Y, len_y, opts: Opts | None = None):
     """Differentiable signature-kernel MMD^2 (torch.autograd)."""
     return _MMDFn.apply(X, Y, len_x, len_y, opts or Opts())
+
+
+def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | None = None,
+         ws: Workspace | None = None) -> Opts:
+    """A-priori (order, rings) for relative tolerance `tol` from device
+    statistics of the increments (synchronises the stream)."""
+    opts = opts or Opts()
+    X, len_x = _paths(X, len_x)
+    n_x, d = len_x.numel(), X.shape[1]
+    if Y is not None:
+        Y, len_y = _paths(Y, len_y)
+        n_y = len_y.numel()
+    else:
+        n_y = 0 if op == OP_GRAM else n_x
+    big = Opts(order=16, rings=1, flags=opts.flags, grid_ctas=opts.grid_ctas, max_len=opts.max_len)
+    nb = workspace_size(op, n_x, n_y if op != OP_PAIRS else n_x, d, big)
+    npairs = n_x if op == OP_PAIRS else (n_x * (n_x + 1) // 2 if n_y == 0 else
+                                         (n_x * n_y if op == OP_GRAM else (n_x + n_y) ** 2))
+    nb += 8 * (12 * npairs + (n_x + n_y) ** 2 + n_x * max(n_y, n_x)) + 4096
+    ws = _ws(ws, X.device)
+    buf = ws.get(nb, X.device)
+    o_in = opts.c()
+    o_out = _Opts()
+    _check(load().sigk_plan(op, _ptr(X), _ptr(len_x), n_x, _ptr(Y), _ptr(len_y), n_y, d,
+                            float(tol), _ptr(buf), buf.numel(), _stream(), ctypes.byref(o_in),
+                            ctypes.byref(o_out)))
+    return Opts(o_out.order, o_out.rings, o_out.flags, o_out.grid_ctas, o_out.max_len)

@@ -141,3 +141,52 @@ def test_mmd_small(S, orc):
     Kxx = orc.series_gram(incs(X, lx))
     scale = np.abs(Kxx).max()
     assert abs(v - ref) <= 1e-5 * max(abs(ref), scale * 1e-2), (v, ref)
+
+
+@pytest.mark.parametrize("sigma", [1.0, 3.0])
+def test_plan_meets_tolerance(S, orc, sigma):
+    # sigk_plan picks (order, rings) from device statistics of the increments;
+    # the planned launch must meet the requested tolerance against the oracle
+    from paper_2502_20392_gb300 import synth
+    segs = np.array([300, 211, 257, 180, 299, 64])
+    pts, lens = synth.brownian(len(segs), segs, 8, sigma * np.sqrt(segs / 300), seed=123)
+    X, L = to_dev(pts, lens)
+    tols = (1e-4, 1e-6)
+    plans = [S.plan(S.OP_GRAM, X, L, tol=t) for t in tols]
+    assert plans[1].order >= plans[0].order and plans[1].rings >= plans[0].rings
+    ref = orc.series_gram(incs(pts, lens), N=28)
+    dg = np.diag(ref)
+    for t, o in zip(tols, plans):
+        G = S.gram(X, L, opts=o).cpu().numpy()
+        e = rel_err(G, ref, dg[:, None], dg[None, :])
+        assert e.max() < max(t, 2e-6), (t, o, e.max())
+
+
+def test_cuda_graph_capture_and_replay(S, orc):
+    # the C-ABI launches no host synchronisation, allocation or copy, so a call
+    # with a preallocated workspace can be captured and replayed on new inputs
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(6, 200, 8, 1.0, seed=9)
+    X, L = to_dev(pts, lens)
+    o = S.Opts(order=8, rings=4, max_len=200)
+    ws = S.Workspace()
+    ws.get(S.workspace_size(S.OP_GRAM, 6, 0, 8, o), X.device)
+    G = torch.empty((6, 6), dtype=torch.float64, device=X.device)
+    S.gram(X, L, opts=o, out=G, ws=ws)  # warm-up outside capture
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            S.gram(X, L, opts=o, out=G, ws=ws, check=False)
+    torch.cuda.current_stream().wait_stream(s)
+    pts2, _ = synth.brownian(6, 200, 8, 1.0, seed=10)
+    X.copy_(torch.from_numpy(pts2))
+    G.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    S.sync_status(ws)
+    eager = S.gram(X, L, opts=o).cpu().numpy()
+    np.testing.assert_array_equal(G.cpu().numpy(), eager)
+    ref = orc.series_gram(incs(pts2, lens))
+    np.testing.assert_allclose(G.cpu().numpy(), ref, rtol=1e-5)

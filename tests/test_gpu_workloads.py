@@ -47,6 +47,18 @@ def incs(paths):
 
 
 @pytest.mark.parametrize("sigma", [1.0, 4.0])
+def test_plan_for_gram_workload(S, sigma):
+    # the a-priori choice for the Gram workload covers the launch settings the
+    # benchmark uses (which the entry test below checks against the oracle)
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.workload_gram_1024(sigma)
+    o = S.plan(S.OP_GRAM, torch.from_numpy(pts).to(dev()), torch.from_numpy(lens).to(dev()),
+               tol=1e-5)
+    assert o.max_len >= 1024
+    assert o.order >= GRAM_OPTS[sigma]["order"] - 2 and o.rings >= GRAM_OPTS[sigma]["rings"] - 1, o
+
+
+@pytest.mark.parametrize("sigma", [1.0, 4.0])
 def test_gram_B64_L1024_d16(S, orc, sigma):
     from paper_2502_20392_gb300 import synth
     pts, lens = synth.workload_gram_1024(sigma)
