@@ -79,15 +79,24 @@ enum {
  *   flags: SIGK_FLAG_*.
  *   grid_ctas: persistent grid size (0 = occupancy-derived, one wave).
  *   max_len: upper bound on the segments of the path that a pair sweeps
- *            (the longer path of a pair may be split over warps instead);
- *            sizes the seam ring.  A pair that needs more fails with
- *            SIGK_ERR_LENGTH (reported by sigk_sync_status).  0 = 8193. */
+ *            (the longer path of a pair may be split over warps instead),
+ *            counted after refinement; sizes the seam ring.  A pair that needs
+ *            more fails with SIGK_ERR_LENGTH (reported by sigk_sync_status).
+ *            0 = 8193.
+ *   refine_c: 0 = off.  Otherwise every path p is refined: each of its
+ *            segments is split into s_p equal collinear pieces, s_p =
+ *            ceil(max_i |dz_i| / sqrt(refine_c)) (at most 64), so that every
+ *            tile satisfies |c| <= refine_c by Cauchy-Schwarz.  Exact (the
+ *            kernel is invariant under collinear insertion); it trades more
+ *            tiles for tiles the series resolves in FP32 (large |c| needs
+ *            orders and rings beyond 16 and 8, and negative c cancels). */
 typedef struct {
     int order;
     int rings;
     int flags;
     int grid_ctas;
     int64_t max_len;
+    float refine_c;
 } sigk_opts;
 
 /* Device workspace bytes needed by sigk_pairs/sigk_gram/sigk_mmd for the
@@ -177,10 +186,16 @@ sigk_status sigk_pairs_static(const float* X, const int64_t* len_x, const float*
 /* sigk_sync_status for the static scratch of sigk_pairs_static. */
 sigk_status sigk_static_sync_status(void* stream);
 
-/* Recommended (order, rings) for a target relative tolerance `tol`, from
- * statistics of the increments computed on the device (host lengths are not
- * needed).  Synchronises `stream`.  Writes into *opts_out (flags and
- * grid_ctas copied from opts_in when given). */
+/* A-priori truncation choice (App. C.3: order search from the largest
+ * coupling in the grid).  Runs the planner and a statistics kernel on the
+ * device: per pair the sampled coupling C = max |<dx_i, y_J - y_0>| (the size
+ * of the edge coefficients, a_p ~ C^p/(p!)^2) and the ring bounds
+ * sum |c|^m <= (sum |dx|^m)(sum |dy|^m); then picks the smallest order P and
+ * rings n with max(L1,L2) (1.25 C)^(P+1)/((P+1)!)^2 <= tol/10 and
+ * sum|c|^(n+1)/((n+1)!)^2 <= tol/10.  If the Cauchy-Schwarz bound on a tile
+ * exceeds 1 it also sets refine_c = 1 and plans the refined problem.
+ * Synchronises `stream`.  Writes into *opts_out (other fields copied from
+ * opts_in when given; max_len raised to the longest swept path, refined). */
 sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
                       const float* Y, const int64_t* len_y, int64_t n_y, int d, double tol,
                       void* ws, size_t ws_bytes, void* stream, const sigk_opts* opts_in,

@@ -71,20 +71,23 @@ __device__ __forceinline__ void unpack_exp(int w, int& F, int& Eb, int& bump) {
     F = (w >> 17) * 64;
 }
 
-// increment gradient v of segment `row` -> points (+v at row+1, -v at row) or
-// increments (+v at row)
+// gradient v of virtual row `vrow` (refinement s) -> its segment vrow / s
+// (scaled 1/s), then points (+ at segment+1, - at segment) or increments
 template <int D>
-__device__ __forceinline__ void add_inc_grad(float* g, int64_t row, int d, int inc_mode,
+__device__ __forceinline__ void add_inc_grad(float* g, int64_t vrow, int d, int inc_mode, int s,
                                              const float (&v)[D]) {
     if (!g) return;
+    const int64_t row = vrow / s;
+    const float sc = 1.0f / (float)s;
 #pragma unroll
     for (int e = 0; e < D; ++e) {
         if (e < d && v[e] != 0.0f) {
+            const float w = v[e] * sc;
             if (inc_mode) {
-                atomicAdd(g + row * d + e, v[e]);
+                atomicAdd(g + row * d + e, w);
             } else {
-                atomicAdd(g + (row + 1) * d + e, v[e]);
-                atomicAdd(g + row * d + e, -v[e]);
+                atomicAdd(g + (row + 1) * d + e, w);
+                atomicAdd(g + row * d + e, -w);
             }
         }
     }
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         float dx[D];
 #pragma unroll
         for (int e = 0; e < D; ++e)
-            dx[e] = (has_row && e < A.d) ? inc_at(pd.xr, row, A.d, e, A.inc_mode) : 0.0f;
+            dx[e] = (has_row && e < A.d) ? inc_ref(pd.xr, row, A.d, e, A.inc_mode, pd.sx) : 0.0f;
 
         // ------------------------- pass A: forward replay ------------------------
         float a[P + 1], a1lo = 0.0f;
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 for (int idx = lane; idx < 32 * D; idx += 32) {
                     const int col = idx / D, e = idx % D;
                     float v = 0.0f;
-                    if (col < nb && e < A.d) v = inc_at(pd.yr, t + col, A.d, e, A.inc_mode);
+                    if (col < nb && e < A.d) v = inc_ref(pd.yr, t + col, A.d, e, A.inc_mode, pd.sy);
                     dyw[((t + col) & 63) * DS + e] = v;
                 }
                 if (s > 0) {
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 for (int idx = lane; idx < 32 * D; idx += 32) {
                     const int col = idx / D, e = idx % D;
                     float v = 0.0f;
-                    if (col < nb && e < A.d) v = inc_at(pd.yr, L2 - 1 - (tp + col), A.d, e, A.inc_mode);
+                    if (col < nb && e < A.d) v = inc_ref(pd.yr, L2 - 1 - (tp + col), A.d, e, A.inc_mode, pd.sy);
                     dyw[((tp + col) & 63) * DS + e] = v;
                 }
                 if (has_ain) {
@@ -403,12 +406,13 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                         const float v = *cell;
                         *cell = 0.0f;
                         if (e < A.d && v != 0.0f) {
-                            const int64_t jcol = L2 - 1 - (start + col);
+                            const int64_t jcol = (L2 - 1 - (start + col)) / pd.sy;
+                            const float w = v * (1.0f / (float)pd.sy);
                             if (A.inc_mode) {
-                                atomicAdd(pd.gyr + jcol * A.d + e, v);
+                                atomicAdd(pd.gyr + jcol * A.d + e, w);
                             } else {
-                                atomicAdd(pd.gyr + (jcol + 1) * A.d + e, v);
-                                atomicAdd(pd.gyr + jcol * A.d + e, -v);
+                                atomicAdd(pd.gyr + (jcol + 1) * A.d + e, w);
+                                atomicAdd(pd.gyr + jcol * A.d + e, -w);
                             }
                         }
                     }
@@ -437,7 +441,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 __syncwarp();
             }
         }
-        if (has_row) add_inc_grad<D>(pd.gxr, row, A.d, A.inc_mode, gx);
+        if (has_row) add_inc_grad<D>(pd.gxr, row, A.d, A.inc_mode, pd.sx, gx);
         __syncwarp();
         if (lane == 0) {
             __threadfence();

@@ -45,6 +45,7 @@ struct Opts {
     int flags;
     int grid_ctas;
     int64_t max_len;
+    float refine_c;  // 0: no refinement
 };
 
 static bool resolve_opts(const sigk_opts* o, Opts* r) {
@@ -53,13 +54,16 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
     r->flags = 0;
     r->grid_ctas = 0;
     r->max_len = 8193;
+    r->refine_c = 0.0f;
     if (o) {
         if (o->order) r->order = o->order;
         if (o->rings) r->rings = o->rings;
         r->flags = o->flags;
         r->grid_ctas = o->grid_ctas;
         if (o->max_len > 0) r->max_len = o->max_len;
+        r->refine_c = o->refine_c;
     }
+    if (!(r->refine_c >= 0.0f) || r->refine_c > 1e30f) return false;
     if (r->order < 4 || r->order > kMaxP) return false;
     r->order += (r->order & 1);
     int nrmax = r->order < kMaxRings ? r->order : kMaxRings;
@@ -107,7 +111,7 @@ static cudaError_t bwd_launch_dispatch(int P, int D, const BwdArgs& a, int grid,
 // workspace layout
 
 struct Layout {
-    size_t hdr, ox, oy, pairs, item_start, prod, cons, done, seam, gram, total;
+    size_t hdr, ox, oy, sx, sy, pairs, item_start, prod, cons, done, seam, gram, total;
     // backward sections (train == true)
     size_t store, store_off, pair_exp, pair_w, rec, bprod, bcons, bdone, aseam;
     int64_t store_floats, rec_stride;
@@ -174,6 +178,8 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->hdr = off; off = align256(off + 256);
     L->ox = off; off = align256(off + sizeof(int64_t) * (size_t)(n_x + 1));
     L->oy = off; off = align256(off + sizeof(int64_t) * (size_t)(n_y + 1));
+    L->sx = off; off = align256(off + sizeof(int32_t) * (size_t)(n_x + 1));
+    L->sy = off; off = align256(off + sizeof(int32_t) * (size_t)(n_y + 1));
     L->pairs = off; off = align256(off + sizeof(PairDesc) * (size_t)L->n_pairs);
     L->item_start = off; off = align256(off + sizeof(int32_t) * (size_t)(L->n_pairs + 1));
     L->prod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
@@ -243,6 +249,8 @@ struct PlanArgs {
     int64_t n_pairs;
     int64_t* ox;
     int64_t* oy;
+    const int32_t* sX;  // per-path refinement factors (null: 1)
+    const int32_t* sY;
     PairDesc* pairs;
     int32_t* item_start;
     unsigned long long* prod;
@@ -253,8 +261,9 @@ struct PlanArgs {
     double* out;        // output (k values / Gram)
     int64_t out_ld;     // leading dimension of the Gram output
     // training (backward) extras; train == 0 leaves them unused
+    int phase;          // 1: prefix sums; 2: pair table, items, resets; 3: both
     int train;
-    int stride;         // seam entry floats (P + 3)
+    int stride;         // seam entry floats (P + 4)
     int64_t store_cap;  // floats available for the forward seam store
     int64_t* store_off;
     double* pair_w;
@@ -305,19 +314,23 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
     __shared__ int64_t sh[kPlanThreads];
     __shared__ int bad;
     const int t = threadIdx.x;
-    if (t == 0) {
-        bad = 0;
-        A.hdr->status = 0;  // errors are reported per call
-    }
-    __syncthreads();
-    block_exclusive_scan(A.len_x, A.n_x, A.ox, sh, true, A.inc_mode, &bad);
     const bool self = (A.op == SIGK_OP_GRAM && A.n_y == 0);
-    if (!self) block_exclusive_scan(A.len_y, A.n_y, A.oy, sh, true, A.inc_mode, &bad);
-    __syncthreads();
-    if (bad) {
-        if (t == 0) atomicCAS(&A.hdr->status, 0, kErrLength);
-        return;
+    if (A.phase & 1) {
+        if (t == 0) {
+            bad = 0;
+            A.hdr->status = 0;  // errors are reported per call
+        }
+        __syncthreads();
+        block_exclusive_scan(A.len_x, A.n_x, A.ox, sh, true, A.inc_mode, &bad);
+        if (!self) block_exclusive_scan(A.len_y, A.n_y, A.oy, sh, true, A.inc_mode, &bad);
+        __syncthreads();
+        if (bad) {
+            if (t == 0) atomicCAS(&A.hdr->status, 0, kErrLength);
+            return;
+        }
     }
+    if (!(A.phase & 2)) return;
+    if (ld_volatile_s32(&A.hdr->status) != 0) return;
     const int RS = A.rows_per_strip;
     const int64_t nx = A.n_x;
     const int64_t nz = (A.op == SIGK_OP_MMD) ? A.n_x + A.n_y : (self ? nx : A.n_y);
@@ -351,24 +364,28 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         int64_t la, lb;
         float* ga = nullptr;
         float* gb = nullptr;
-        auto path = [&](int64_t z, bool from_y, const float** ptr, int64_t* segs, float** g) {
+        int32_t ra = 1, rb = 1;
+        auto path = [&](int64_t z, bool from_y, const float** ptr, int64_t* segs, float** g,
+                        int32_t* rf) {
             const float* base = from_y ? A.Y : A.X;
             const int64_t* off = from_y ? A.oy : A.ox;
             const int64_t* len = from_y ? A.len_y : A.len_x;
+            const int32_t* sf = from_y ? A.sY : A.sX;
             float* gbase = from_y ? A.gY : A.gX;
             *ptr = base + off[z] * A.d;
-            *segs = A.inc_mode ? len[z] : len[z] - 1;
+            *rf = sf ? sf[z] : 1;
+            *segs = (A.inc_mode ? len[z] : len[z] - 1) * (int64_t)(*rf);
             *g = gbase ? gbase + off[z] * A.d : nullptr;
         };
         if (A.op == SIGK_OP_MMD) {
-            path(a < nx ? a : a - nx, a >= nx, &pa, &la, &ga);
-            path(b < nx ? b : b - nx, b >= nx, &pb, &lb, &gb);
+            path(a < nx ? a : a - nx, a >= nx, &pa, &la, &ga, &ra);
+            path(b < nx ? b : b - nx, b >= nx, &pb, &lb, &gb, &rb);
         } else if (A.op == SIGK_OP_PAIRS) {
-            path(a, false, &pa, &la, &ga);
-            path(b, true, &pb, &lb, &gb);
+            path(a, false, &pa, &la, &ga, &ra);
+            path(b, true, &pb, &lb, &gb, &rb);
         } else {
-            path(a, false, &pa, &la, &ga);
-            path(b, !self, &pb, &lb, &gb);
+            path(a, false, &pa, &la, &ga, &ra);
+            path(b, !self, &pb, &lb, &gb, &rb);
         }
         if (A.train) {
             // upstream weight of this pair's k value
@@ -410,6 +427,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         pd.yr = swap ? pa : pb;
         pd.gxr = A.train ? (swap ? gb : ga) : nullptr;
         pd.gyr = A.train ? (swap ? ga : gb) : nullptr;
+        pd.sx = swap ? rb : ra;
+        pd.sy = swap ? ra : rb;
+        if (la > (int64_t)INT32_MAX || lb > (int64_t)INT32_MAX) atomicCAS(&A.hdr->status, 0, kErrLength);
         pd.L1 = (int32_t)(swap ? lb : la);
         pd.L2 = (int32_t)(swap ? la : lb);
         pd.swapped = swap ? 1 : 0;
@@ -505,6 +525,37 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
     }
 }
 
+// Per-path refinement factors: s = ceil(max_i |dz_i| / sqrt(refine_c)),
+// clamped to [1, 64]; one warp per path.  The planner multiplies the path's
+// segment count by s and the kernels read segment v / s scaled by 1/s.
+__global__ void refine_kernel(const float* Z, const int64_t* len, const int64_t* offs, int64_t n,
+                              int d, int inc_mode, float refine_c, int32_t* s_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n; p += warps) {
+        const int64_t off = offs[p];
+        const int64_t segs = inc_mode ? len[p] : len[p] - 1;
+        const float* z = Z + off * d;
+        float mx = 0.0f;
+        for (int64_t i = lane; i < segs; i += 32) {
+            float n2 = 0.0f;
+            for (int e = 0; e < d; ++e) {
+                const float v = inc_mode ? z[i * d + e] : z[(i + 1) * d + e] - z[i * d + e];
+                n2 = fmaf(v, v, n2);
+            }
+            mx = fmaxf(mx, n2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
+        if (lane == 0) {
+            float f = ceilf(sqrtf(mx) / sqrtf(refine_c));
+            if (!(f >= 1.0f)) f = 1.0f;
+            if (f > 64.0f) f = 64.0f;
+            s_out[p] = (int32_t)f;
+        }
+    }
+}
+
 // MMD^2 from the Gram of Z = [X; Y] (N = m + n), FP64, one CTA.
 __global__ void __launch_bounds__(1024) mmd_reduce_kernel(const double* G, int64_t m, int64_t n,
                                                           int unbiased, double* out) {
@@ -548,7 +599,9 @@ __global__ void __launch_bounds__(1024) mmd_reduce_kernel(const double* G, int64
 //       a_p ~ C_a^p / (p!)^2; [3] C_b: the same with the roles swapped
 //   [4 + m - 2], m = 2..9: (sum_i |dx_i|^m) * (sum_j |dy_j|^m), an upper bound
 //       on sum_ij |c_ij|^m (Cauchy-Schwarz), the size of the dropped ring m
-constexpr int kStatFields = 12;
+//   [12], [13]: max_i |dx_i|, max_j |dy_j| (their product bounds every |c_ij|)
+// (all for the refined problem when refinement is on)
+constexpr int kStatFields = 14;
 constexpr int kStatStride = 16;  // sampled points: every 16th, plus the last
 
 __device__ double warp_sum_d(double v) {
@@ -607,40 +660,56 @@ __global__ void pair_stats_kernel(const PairDesc* pairs, int64_t n_pairs, int d,
          p += warps) {
         const PairDesc pd = pairs[p];
         double* o = out + p * kStatFields;
+        // statistics of the ORIGINAL segments, scaled to the refined problem at
+        // the end: a segment split in s pieces gives s increments dz/s
+        const int L1o = pd.sx > 0 ? pd.L1 / pd.sx : pd.L1;
+        const int L2o = pd.sy > 0 ? pd.L2 / pd.sy : pd.L2;
         double sx[8], sy[8];
+        double mx = 0.0, my = 0.0;
         for (int m = 0; m < 8; ++m) { sx[m] = 0.0; sy[m] = 0.0; }
-        for (int i = lane; i < pd.L1; i += 32) {
+        for (int i = lane; i < L1o; i += 32) {
             double n2 = 0.0;
             for (int e = 0; e < d; ++e) {
                 const double v = inc_at(pd.xr, i, d, e, inc_mode);
                 n2 += v * v;
             }
+            mx = fmax(mx, n2);
             const double n1 = sqrt(n2);
             double pw = n2;
             for (int m = 0; m < 8; ++m) { sx[m] += pw; pw *= n1; }
         }
-        for (int j = lane; j < pd.L2; j += 32) {
+        for (int j = lane; j < L2o; j += 32) {
             double n2 = 0.0;
             for (int e = 0; e < d; ++e) {
                 const double v = inc_at(pd.yr, j, d, e, inc_mode);
                 n2 += v * v;
             }
+            my = fmax(my, n2);
             const double n1 = sqrt(n2);
             double pw = n2;
             for (int m = 0; m < 8; ++m) { sy[m] += pw; pw *= n1; }
         }
         for (int m = 0; m < 8; ++m) { sx[m] = warp_sum_d(sx[m]); sy[m] = warp_sum_d(sy[m]); }
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            mx = fmax(mx, __shfl_xor_sync(kFull, mx, o2));
+            my = fmax(my, __shfl_xor_sync(kFull, my, o2));
+        }
         float ca = 0.0f, cb = 0.0f;
-        if (pd.L1 > 0 && pd.L2 > 0) {
-            ca = coupling_max(pd.xr, pd.L1, pd.yr, pd.L2, d, inc_mode, lane);
-            cb = coupling_max(pd.yr, pd.L2, pd.xr, pd.L1, d, inc_mode, lane);
+        if (L1o > 0 && L2o > 0) {
+            ca = coupling_max(pd.xr, L1o, pd.yr, L2o, d, inc_mode, lane);
+            cb = coupling_max(pd.yr, L2o, pd.xr, L1o, d, inc_mode, lane);
         }
         if (lane == 0) {
+            const double fx = pd.sx > 0 ? pd.sx : 1, fy = pd.sy > 0 ? pd.sy : 1;
             o[0] = pd.L1;
             o[1] = pd.L2;
-            o[2] = ca;
-            o[3] = cb;
-            for (int m = 0; m < 8; ++m) o[4 + m] = sx[m] * sy[m];
+            o[2] = ca / fx;  // refined rows carry dx / sx
+            o[3] = cb / fy;
+            for (int m = 0; m < 8; ++m)  // sum over refined increments of |dz/s|^m
+                o[4 + m] = sx[m] * pow(fx, 1.0 - (m + 2)) * sy[m] * pow(fy, 1.0 - (m + 2));
+            o[12] = sqrt(mx) / fx;  // largest refined increment norms
+            o[13] = sqrt(my) / fy;
         }
     }
 }
@@ -652,7 +721,8 @@ __global__ void pair_stats_kernel(const PairDesc* pairs, int64_t n_pairs, int d,
 //   order: max(L1, L2) * (1.25 C)^{P+1} / ((P+1)!)^2 <= tol/10, C the sampled
 //          coupling (the dropped edge coefficient of degree P+1, over a row)
 static void choose_order(const double* st, int64_t n, double tol, int* P_out, int* nr_out,
-                         int64_t* max_swept) {
+                         int64_t* max_swept, double* max_tile_c) {
+    *max_tile_c = 0.0;
     const double target = 0.1 * tol;
     int P = 4, nr = 1;
     double fact[40];
@@ -662,6 +732,7 @@ static void choose_order(const double* st, int64_t n, double tol, int* P_out, in
         const double* o = st + p * kStatFields;
         if (o[0] <= 0 || o[1] <= 0) continue;
         if ((int64_t)o[1] > *max_swept) *max_swept = (int64_t)o[1];
+        if (o[12] * o[13] > *max_tile_c) *max_tile_c = o[12] * o[13];
         int r = 1;
         while (r < kMaxRings && o[4 + (r + 1) - 2] / (fact[r + 1] * fact[r + 1]) > target) ++r;
         if (r > nr) nr = r;
@@ -686,6 +757,39 @@ static sigk_status check_ws(const Layout& L, void* ws, size_t ws_bytes) {
         return fail(SIGK_ERR_WORKSPACE, "workspace too small: need " + std::to_string(L.total) +
                                             " bytes, got " + std::to_string(ws_bytes));
     return SIGK_OK;
+}
+
+// Planner launches: prefix sums, then (with refinement) the per-path factors,
+// then the pair table.  Without refinement one launch does both phases.
+static cudaError_t launch_planner(PlanArgs pa, const Opts& o, const Layout& L, char* base,
+                                  cudaStream_t stream) {
+    pa.sX = nullptr;
+    pa.sY = nullptr;
+    if (o.refine_c <= 0.0f) {
+        pa.phase = 3;
+        plan_kernel<<<1, kPlanThreads, 0, stream>>>(pa);
+        return cudaGetLastError();
+    }
+    pa.phase = 1;
+    plan_kernel<<<1, kPlanThreads, 0, stream>>>(pa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int32_t* sX = (int32_t*)(base + L.sx);
+    int32_t* sY = (int32_t*)(base + L.sy);
+    const bool self = (pa.op == SIGK_OP_GRAM && pa.n_y == 0);
+    auto blocks = [](int64_t n) { return (unsigned)((n + 7) / 8 < 4096 ? (n + 7) / 8 : 4096); };
+    if (pa.n_x > 0)
+        refine_kernel<<<blocks(pa.n_x), 256, 0, stream>>>(pa.X, pa.len_x, pa.ox, pa.n_x, pa.d,
+                                                            pa.inc_mode, o.refine_c, sX);
+    if (!self && pa.n_y > 0)
+        refine_kernel<<<blocks(pa.n_y), 256, 0, stream>>>(pa.Y, pa.len_y, pa.oy, pa.n_y, pa.d,
+                                                            pa.inc_mode, o.refine_c, sY);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    pa.sX = sX;
+    pa.sY = self ? sX : sY;
+    pa.phase = 2;
+    plan_kernel<<<1, kPlanThreads, 0, stream>>>(pa);
+    return cudaGetLastError();
 }
 
 // Backward extras for run_solver (train mode).
@@ -750,9 +854,8 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         pa.bdone = (long long*)(base + L.bdone);
         pa.bnslot = L.bnslot;
     }
-    plan_kernel<<<1, kPlanThreads, 0, stream>>>(pa);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "plan_kernel launch");
+    cudaError_t e = launch_planner(pa, o, L, base, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "planner launch");
     SolverArgs sa;
     memset(&sa, 0, sizeof(sa));
     sa.pairs = pa.pairs;
@@ -1008,9 +1111,8 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
         scratch_out = (double*)(base + L.seam + need);
         pa.out = scratch_out;
     }
-    plan_kernel<<<1, kPlanThreads, 0, strm>>>(pa);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "plan_kernel launch");
+    cudaError_t e = launch_planner(pa, o, L, base, strm);
+    if (e != cudaSuccess) return cuda_fail(e, "planner launch");
     double* stats = (double*)(base + L.seam);
     const int threads = 256;
     const int64_t blocks = (L.n_pairs + (threads / 32) - 1) / (threads / 32);
@@ -1027,10 +1129,35 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
         return cuda_fail(e, "plan stats copy");
     int P = 4, nr = 1;
     int64_t max_swept = 1;
-    choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept);
-    *opts_out = opts_in ? *opts_in : sigk_opts{0, 0, 0, 0, 0};
+    double max_c = 0.0;
+    choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept, &max_c);
+    // Tiles whose |c| may exceed 1 (Cauchy-Schwarz) are refined and the refined
+    // problem is planned again.
+    const float kRefineC = 1.0f;
+    if (max_c > (double)kRefineC && o.refine_c <= 0.0f) {
+        Opts o2 = o;
+        o2.refine_c = kRefineC;
+        if ((e = launch_planner(pa, o2, L, base, strm)) != cudaSuccess)
+            return cuda_fail(e, "planner launch");
+        pair_stats_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), threads, 0, strm>>>(
+            pa.pairs, L.n_pairs, d, pa.inc_mode, stats);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pair_stats launch");
+        if ((e = cudaStreamSynchronize(strm)) != cudaSuccess) return cuda_fail(e, "plan synchronize");
+        if ((e = cudaMemcpy(&h, base + L.hdr, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "plan status copy");
+        if (h.status != 0) return fail((sigk_status)h.status, "invalid lengths");
+        if ((e = cudaMemcpy(hs.data(), stats, need, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(e, "plan stats copy");
+        P = 4; nr = 1; max_swept = 1;
+        choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept, &max_c);
+        o.refine_c = kRefineC;
+    }
+    sigk_opts zero;
+    memset(&zero, 0, sizeof(zero));
+    *opts_out = opts_in ? *opts_in : zero;
     opts_out->order = P;
     opts_out->rings = nr;
+    opts_out->refine_c = o.refine_c;
     if (opts_out->max_len < max_swept) opts_out->max_len = max_swept;
     return SIGK_OK;
 }

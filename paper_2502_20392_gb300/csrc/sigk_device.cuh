@@ -54,6 +54,8 @@ struct PairDesc {
     int32_t L2;        // segments of the swept path
     int32_t n_strips;  // ceil(L1 / rows per strip)
     int32_t swapped;   // 1 if the row path is the caller's y
+    int32_t sx;        // refinement of the row path: each segment in sx pieces
+    int32_t sy;        // refinement of the swept path
     int64_t out0;      // output index, or -1
     int64_t out1;      // mirrored output index, or -1
     float* gxr;        // gradient rows of the row path (backward), or null

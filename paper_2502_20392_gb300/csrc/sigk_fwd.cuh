@@ -46,6 +46,16 @@ __device__ __forceinline__ float inc_at(const float* z, int64_t row, int d, int 
     return z[(row + 1) * d + e] - z[row * d + e];
 }
 
+// Increment of VIRTUAL row v of a path whose every segment is split into s
+// equal collinear pieces: segment v / s, scaled by 1/s.  Splitting leaves the
+// kernel unchanged (reparametrisation / collinear-insertion invariance) and
+// divides every tile coefficient c by the product of the two factors.
+__device__ __forceinline__ float inc_ref(const float* z, int64_t v, int d, int e, int inc_mode,
+                                         int s) {
+    if (s == 1) return inc_at(z, v, d, e, inc_mode);
+    return inc_at(z, v / s, d, e, inc_mode) * (1.0f / (float)s);
+}
+
 // CTAs per SM the register allocation must allow (128 threads each): the
 // largest count that ptxas meets without spilling for that instantiation.
 constexpr int fwd_min_blocks(int P, int D, int R) {
@@ -97,7 +107,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
             const int row = i0 + lane * R + k;
 #pragma unroll
             for (int e = 0; e < D; ++e)
-                dx[k][e] = (row < L1 && e < A.d) ? inc_at(pd.xr, row, A.d, e, A.inc_mode) : 0.0f;
+                dx[k][e] = (row < L1 && e < A.d) ? inc_ref(pd.xr, row, A.d, e, A.inc_mode, pd.sx) : 0.0f;
         }
         float a[R][P + 1], a1lo[R];
 #pragma unroll
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                 for (int idx = lane; idx < 32 * D; idx += 32) {
                     const int col = idx / D, e = idx % D;
                     float v = 0.0f;
-                    if (col < nb && e < A.d) v = inc_at(pd.yr, t + col, A.d, e, A.inc_mode);
+                    if (col < nb && e < A.d) v = inc_ref(pd.yr, t + col, A.d, e, A.inc_mode, pd.sy);
                     dyw[((t + col) & 63) * DS + e] = v;
                 }
                 if (has_in) {

@@ -35,7 +35,8 @@ class SigkError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("rings", ctypes.c_int), ("flags", ctypes.c_int),
-                ("grid_ctas", ctypes.c_int), ("max_len", ctypes.c_int64)]
+                ("grid_ctas", ctypes.c_int), ("max_len", ctypes.c_int64),
+                ("refine_c", ctypes.c_float)]
 
 
 @dataclass
@@ -45,9 +46,11 @@ class Opts:
     flags: int = 0
     grid_ctas: int = 0
     max_len: int = 8193
+    refine_c: float = 0.0
 
     def c(self) -> _Opts:
-        return _Opts(self.order, self.rings, self.flags, self.grid_ctas, self.max_len)
+        return _Opts(self.order, self.rings, self.flags, self.grid_ctas, self.max_len,
+                     self.refine_c)
 
 
 _lib = None
@@ -350,7 +353,8 @@ def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | 
         n_y = len_y.numel()
     else:
         n_y = 0 if op == OP_GRAM else n_x
-    big = Opts(order=16, rings=1, flags=opts.flags, grid_ctas=opts.grid_ctas, max_len=opts.max_len)
+    big = Opts(order=16, rings=1, flags=opts.flags, grid_ctas=opts.grid_ctas, max_len=opts.max_len,
+               refine_c=opts.refine_c)
     nb = workspace_size(op, n_x, n_y if op != OP_PAIRS else n_x, d, big)
     npairs = n_x if op == OP_PAIRS else (n_x * (n_x + 1) // 2 if n_y == 0 else
                                          (n_x * n_y if op == OP_GRAM else (n_x + n_y) ** 2))
@@ -362,4 +366,5 @@ def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | 
     _check(load().sigk_plan(op, _ptr(X), _ptr(len_x), n_x, _ptr(Y), _ptr(len_y), n_y, d,
                             float(tol), _ptr(buf), buf.numel(), _stream(), ctypes.byref(o_in),
                             ctypes.byref(o_out)))
-    return Opts(o_out.order, o_out.rings, o_out.flags, o_out.grid_ctas, o_out.max_len)
+    return Opts(o_out.order, o_out.rings, o_out.flags, o_out.grid_ctas, o_out.max_len,
+                o_out.refine_c)

@@ -163,3 +163,25 @@ def test_autograd_matches_backward(S):
     Gm = S.sig_kernel_gram(Xd, lxd, None, None, o)
     (gG,) = torch.autograd.grad(Gm.sum(), (Xd,))
     assert torch.isfinite(gG).all()
+
+
+def test_gradient_with_refinement(S, orc):
+    # gradients of refined virtual segments are folded back to the segments
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(2, [3, 5], 4, 1.0, seed=17)  # rough: |c| up to ~2
+    xs = synth.split(pts, lens)
+    o = S.Opts(order=12, rings=6, refine_c=0.25, max_len=400)
+    Xd = torch.from_numpy(xs[0]).to(dev())
+    Yd = torch.from_numpy(xs[1]).to(dev())
+    l0 = torch.tensor([4], device=dev())
+    l1 = torch.tensor([6], device=dev())
+    gX, gY, val = S.backward(S.OP_PAIRS, Xd, l0, Yd, l1, torch.ones(1, dtype=torch.float64), o)
+    ref = orc.series_pair(*incs(xs), N=30)
+    assert val.item() == pytest.approx(ref, rel=1e-5)
+
+    def f(pp):
+        return orc.series_pair(*incs(pp), N=30)
+    gx_ref = fd_points(f, xs, 0, range(xs[0].size))
+    gy_ref = fd_points(f, xs, 1, range(xs[1].size))
+    np.testing.assert_allclose(gX.cpu().numpy().ravel(), gx_ref, atol=1e-4 * np.abs(gx_ref).max())
+    np.testing.assert_allclose(gY.cpu().numpy().ravel(), gy_ref, atol=1e-4 * np.abs(gy_ref).max())

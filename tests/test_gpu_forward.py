@@ -190,3 +190,25 @@ def test_cuda_graph_capture_and_replay(S, orc):
     np.testing.assert_array_equal(G.cpu().numpy(), eager)
     ref = orc.series_gram(incs(pts2, lens))
     np.testing.assert_allclose(G.cpu().numpy(), ref, rtol=1e-5)
+
+
+def test_refinement_resolves_large_tiles(S, orc):
+    # a one-segment path in R^16 with unit increments gives tiles with
+    # |c| ~ 16 that orders <= 16 and rings <= 8 cannot resolve; refinement
+    # (every segment split into s equal collinear pieces, which leaves k
+    # unchanged) brings every tile below |c| = refine_c
+    from paper_2502_20392_gb300 import synth
+    segs = [300, 129, 1, 257, 64, 200]
+    pts, lens = synth.brownian(len(segs), segs, 16, 1.0, seed=78)
+    ref = orc.series_gram(incs(pts, lens), N=30)
+    X, L = to_dev(pts, lens)
+    o = S.Opts(order=12, rings=6, refine_c=1.0, max_len=20000)
+    G = S.gram(X, L, opts=o).cpu().numpy()
+    dg = np.diag(ref)
+    e = rel_err(G, ref, dg[:, None], dg[None, :])
+    assert e.max() < 1e-5, e.max()
+    # the planner turns refinement on by itself for this input
+    op = S.plan(S.OP_GRAM, X, L, tol=1e-5)
+    assert op.refine_c > 0
+    G2 = S.gram(X, L, opts=op).cpu().numpy()
+    assert rel_err(G2, ref, dg[:, None], dg[None, :]).max() < 1e-5
