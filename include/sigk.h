@@ -24,8 +24,9 @@
  * default a row is a POINT and len[p] counts points (>= 1; a path of one point
  * has no segment and k = 1 with every other path).  With
  * SIGK_FLAG_INCREMENTS a row is a segment increment and len[p] counts
- * segments (>= 0).  d is shared by all paths of a call, 1 <= d <= 16 in this
- * version.
+ * segments (>= 0).  d is shared by all paths of a call, 1 <= d <= 8192
+ * (d <= 16 keeps the increments in registers; larger d computes each strip's
+ * coefficients first, see the kernel notes; sigk_backward: d <= 16).
  *
  * Precision.  Inputs are FP32.  The series arithmetic is FP32 with a
  * float-float corner value and a per-edge power-of-two exponent; results are
@@ -66,7 +67,15 @@ enum {
     SIGK_FLAG_INCREMENTS = 1,  /* rows are increments, len counts segments */
     SIGK_FLAG_GRAM_FULL = 2,   /* Gram of X with itself: compute both triangles
                                   independently instead of mirroring */
-    SIGK_FLAG_MMD_BIASED = 4   /* MMD^2 V-statistic instead of the U-statistic */
+    SIGK_FLAG_MMD_BIASED = 4,  /* MMD^2 V-statistic instead of the U-statistic */
+    SIGK_FLAG_FP64 = 8         /* solve every tile in FP64: point differences,
+                                  the increment Gram, refinement scaling and the
+                                  tile map (forward ops only; sigk_backward
+                                  rejects it).  For ill-conditioned pairs --
+                                  strong coupling over long paths, oscillating
+                                  kernels -- whose FP32 result carries a
+                                  rounding error above the tolerance.  FP64
+                                  runs at 1/64 of the FP32 rate on this GPU. */
 };
 
 /* Truncation and scheduling parameters.  NULL = defaults (order 8, rings 4,

@@ -72,7 +72,12 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
     return true;
 }
 
-static int dim_bucket(int d) { return d <= 4 ? 4 : (d <= 8 ? 8 : (d <= 16 ? 16 : -1)); }
+// register-resident increments for d <= 16; larger d uses the two-phase
+// kernel (bucket 0), up to kMaxDim
+constexpr int kMaxDim = 8192;
+static int dim_bucket(int d) {
+    return d <= 4 ? 4 : (d <= 8 ? 8 : (d <= 16 ? 16 : (d <= kMaxDim ? 0 : -1)));
+}
 
 #define SIGK_DISPATCH_P(FN, ...)                 \
     switch (P) {                                 \
@@ -97,6 +102,17 @@ static cudaError_t fwd_launch_dispatch(int P, int D, int R, const SolverArgs& a,
     return cudaErrorInvalidValue;
 }
 
+static int fwd_cm_info_dispatch(int P, bool f64, KernelInfo* info) {
+    SIGK_DISPATCH_P(fwd_cm_info, f64, info)
+    return -1;
+}
+
+static cudaError_t fwd_cm_launch_dispatch(int P, bool f64, const SolverArgs& a, void* cs,
+                                          int64_t cstride, int grid, cudaStream_t s) {
+    SIGK_DISPATCH_P(fwd_cm_launch, f64, a, cs, cstride, grid, s)
+    return cudaErrorInvalidValue;
+}
+
 static int bwd_info_dispatch(int P, int D, KernelInfo* info) {
     SIGK_DISPATCH_P(bwd_info, D, info)
     return -1;
@@ -118,6 +134,11 @@ struct Layout {
     int bnslot, bwcols, bgrid, bnwarps;
     KernelInfo binfo;
     bool train;
+    bool cm;             // two-phase kernel (d > 16, or FP64)
+    bool f64;            // FP64 solve (SIGK_FLAG_FP64)
+    size_t elem;         // bytes per seam / strip element (4 or 8)
+    size_t cscratch;     // its per-warp coefficient strips
+    int64_t cstride;
     int64_t n_pairs, n_paths_x, n_paths_y;
     int nslot, wcols, grid, nwarps, rows_per_strip, stride;
     int64_t nwords;
@@ -141,9 +162,18 @@ static int64_t pair_count(int op, int64_t n_x, int64_t n_y, int flags) {
 static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Opts& o, Layout* L,
                                bool train = false) {
     const int D = dim_bucket(d);
-    if (D < 0) return fail(SIGK_ERR_UNSUPPORTED, "d must be in 1..16 in this build");
+    if (D < 0) return fail(SIGK_ERR_UNSUPPORTED, "d must be in 1..8192 in this build");
     L->train = train;
-    if (fwd_info_dispatch(o.order, D, train ? 1 : 0, &L->info) != 0 || L->info.blocks_per_sm <= 0)
+    L->f64 = (o.flags & SIGK_FLAG_FP64) != 0;
+    L->cm = (D == 0) || L->f64;
+    L->elem = L->f64 ? sizeof(double) : sizeof(float);
+    if (L->f64 && train)
+        return fail(SIGK_ERR_UNSUPPORTED, "the backward runs in FP32 only (no SIGK_FLAG_FP64)");
+    if (L->cm && train)
+        return fail(SIGK_ERR_UNSUPPORTED, "the backward supports d <= 16 in this build");
+    const int qinfo = L->cm ? fwd_cm_info_dispatch(o.order, L->f64, &L->info)
+                            : fwd_info_dispatch(o.order, D, train ? 1 : 0, &L->info);
+    if (qinfo != 0 || L->info.blocks_per_sm <= 0)
         return fail(SIGK_ERR_CUDA, "kernel occupancy query failed");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -185,9 +215,15 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->prod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
     L->cons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
     L->done = off; off = align256(off + sizeof(long long) * (size_t)L->nwords);
-    L->seam = off; off = align256(off + sizeof(float) * (size_t)L->nslot * L->wcols * L->stride);
+    L->seam = off; off = align256(off + L->elem * (size_t)L->nslot * L->wcols * L->stride);
     L->gram = off;
     if (op == SIGK_OP_MMD) off = align256(off + sizeof(double) * (size_t)(n_x + n_y) * (n_x + n_y));
+    L->cstride = 0;
+    L->cscratch = off;
+    if (L->cm) {  // one [max_len][32] coefficient strip per warp
+        L->cstride = 32 * ((o.max_len + 31) & ~(int64_t)31);
+        off = align256(off + L->elem * (size_t)L->nwarps * L->cstride);
+    }
     if (train) {
         if (bwd_info_dispatch(o.order, D, &L->binfo) != 0 || L->binfo.blocks_per_sm <= 0)
             return fail(SIGK_ERR_CUDA, "backward occupancy query failed");
@@ -619,8 +655,27 @@ __device__ float warp_max_f(float v) {
 // |<da_i, b_J - b_0>| (at most ~1024 samples of J, always including the end)
 constexpr int kStatDmax = 16;
 
+__device__ float coupling_max_cs(const float* a, int La, const float* b, int Lb, int d,
+                                 int inc_mode, int lane);
+
 __device__ float coupling_max(const float* a, int La, const float* b, int Lb, int d, int inc_mode,
                               int lane) {
+    if (d > kStatDmax) {
+        if (inc_mode) return coupling_max_cs(a, La, b, Lb, d, inc_mode, lane);
+        // points: b_J - b_0 is read directly at the sampled J
+        const int stride = max(kStatStride, (Lb + 1023) / 1024);
+        float best = 0.0f;
+        for (int J = min(stride, Lb);; J = min(J + stride, Lb)) {
+            for (int i = lane; i < La; i += 32) {
+                float dot = 0.0f;
+                for (int e = 0; e < d; ++e)
+                    dot = fmaf(inc_at(a, i, d, e, 0), b[(int64_t)J * d + e] - b[e], dot);
+                best = fmaxf(best, fabsf(dot));
+            }
+            if (J >= Lb) break;
+        }
+        return warp_max_f(best);
+    }
     const int stride = max(kStatStride, (Lb + 1023) / 1024);
     float B[kStatDmax];
 #pragma unroll
@@ -650,6 +705,55 @@ __device__ float coupling_max(const float* a, int La, const float* b, int Lb, in
         if (J >= Lb) break;
     }
     return warp_max_f(best);
+}
+
+// d > 16: max_i |da_i| * max_J |b_J - b_0| (Cauchy-Schwarz), with the lanes
+// partitioning the dimensions for the running sums (d <= 32 * 16)
+__device__ float coupling_max_cs(const float* a, int La, const float* b, int Lb, int d,
+                                 int inc_mode, int lane) {
+    float amax = 0.0f;
+    for (int i = lane; i < La; i += 32) {
+        float n2 = 0.0f;
+        for (int e = 0; e < d; ++e) {
+            const float v = inc_at(a, i, d, e, inc_mode);
+            n2 = fmaf(v, v, n2);
+        }
+        amax = fmaxf(amax, n2);
+    }
+    amax = warp_max_f(amax);
+    float run[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) run[k] = 0.0f;
+    float rmax = 0.0f;
+    if (d > 32 * 16) {  // beyond the lanes' running sums: total variation bound
+        float tv = 0.0f;
+        for (int j = lane; j < Lb; j += 32) {
+            float n2 = 0.0f;
+            for (int e = 0; e < d; ++e) {
+                const float v = inc_at(b, j, d, e, inc_mode);
+                n2 = fmaf(v, v, n2);
+            }
+            tv += sqrtf(n2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tv += __shfl_xor_sync(kFull, tv, o);
+        return sqrtf(amax) * tv;
+    }
+    for (int j = 0; j < Lb; ++j) {
+        float part = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int e = lane + 32 * k;
+            if (e < d) {
+                run[k] += inc_at(b, j, d, e, inc_mode);
+                part = fmaf(run[k], run[k], part);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+        rmax = fmaxf(rmax, part);
+    }
+    return sqrtf(amax) * sqrtf(rmax);
 }
 
 __global__ void pair_stats_kernel(const PairDesc* pairs, int64_t n_pairs, int d, int inc_mode,
@@ -721,8 +825,9 @@ __global__ void pair_stats_kernel(const PairDesc* pairs, int64_t n_pairs, int d,
 //   order: max(L1, L2) * (1.25 C)^{P+1} / ((P+1)!)^2 <= tol/10, C the sampled
 //          coupling (the dropped edge coefficient of degree P+1, over a row)
 static void choose_order(const double* st, int64_t n, double tol, int* P_out, int* nr_out,
-                         int64_t* max_swept, double* max_tile_c) {
+                         int64_t* max_swept, double* max_tile_c, bool* order_fits) {
     *max_tile_c = 0.0;
+    *order_fits = true;
     const double target = 0.1 * tol;
     int P = 4, nr = 1;
     double fact[40];
@@ -740,6 +845,7 @@ static void choose_order(const double* st, int64_t n, double tol, int* P_out, in
         const double Lm = o[0] > o[1] ? o[0] : o[1];
         int q = 4;
         while (q < kMaxP && Lm * pow(C, q + 1) / (fact[q + 1] * fact[q + 1]) > target) ++q;
+        if (Lm * pow(C, q + 1) / (fact[q + 1] * fact[q + 1]) > target) *order_fits = false;
         if (q > P) P = q;
     }
     if (P < nr) P = nr;
@@ -881,7 +987,9 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     }
     if (L.n_pairs > 0) {
         if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_start, stream);
-        e = fwd_launch_dispatch(o.order, dim_bucket(d), train ? 1 : 0, sa, L.grid, stream);
+        e = L.cm ? fwd_cm_launch_dispatch(o.order, L.f64, sa, base + L.cscratch, L.cstride,
+                                          L.grid, stream)
+                 : fwd_launch_dispatch(o.order, dim_bucket(d), train ? 1 : 0, sa, L.grid, stream);
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
         if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_stop, stream);
     }
@@ -1130,13 +1238,15 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     int P = 4, nr = 1;
     int64_t max_swept = 1;
     double max_c = 0.0;
-    choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept, &max_c);
-    // Tiles whose |c| may exceed 1 (Cauchy-Schwarz) are refined and the refined
-    // problem is planned again.
-    const float kRefineC = 1.0f;
-    if (max_c > (double)kRefineC && o.refine_c <= 0.0f) {
+    bool fits = true;
+    choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept, &max_c, &fits);
+    // Tiles whose |c| may exceed 1 (Cauchy-Schwarz), or edges whose coupling
+    // needs an order above 16, are refined and the refined problem is planned
+    // again; each step divides refine_c by 4 (halving the couplings).
+    float rc = 1.0f;
+    while ((max_c > 1.0 || !fits) && o.refine_c <= 0.0f && rc >= 1.0f / 256.0f) {
         Opts o2 = o;
-        o2.refine_c = kRefineC;
+        o2.refine_c = rc;
         if ((e = launch_planner(pa, o2, L, base, strm)) != cudaSuccess)
             return cuda_fail(e, "planner launch");
         pair_stats_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), threads, 0, strm>>>(
@@ -1149,8 +1259,13 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
         if ((e = cudaMemcpy(hs.data(), stats, need, cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "plan stats copy");
         P = 4; nr = 1; max_swept = 1;
-        choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept, &max_c);
-        o.refine_c = kRefineC;
+        choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept, &max_c, &fits);
+        if (max_c <= 1.0 && fits) {
+            o.refine_c = rc;
+            break;
+        }
+        rc *= 0.25f;
+        if (rc < 1.0f / 256.0f) o.refine_c = rc * 4.0f;  // finest tried
     }
     sigk_opts zero;
     memset(&zero, 0, sizeof(zero));
@@ -1158,7 +1273,7 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     opts_out->order = P;
     opts_out->rings = nr;
     opts_out->refine_c = o.refine_c;
-    if (opts_out->max_len < max_swept) opts_out->max_len = max_swept;
+    opts_out->max_len = max_swept;  // the longest swept path as planned (refined)
     return SIGK_OK;
 }
 

@@ -1,0 +1,368 @@
+// sigk_fwd_cm.cuh -- forward solver for paths of large dimension d (d > 16),
+// and the FP64 solver for any d.
+//
+// The increment Gram c_ij = <dx_i, dy_j> is a dense contraction over d.  For a
+// work item (pair, 32-row strip) the warp first computes the strip's
+// coefficients for every column (phase 1: a register-blocked FMA micro-GEMM,
+// lane = column, 32 row accumulators per lane, the contraction dimension
+// staged through shared memory in chunks of 32) into a per-warp scratch
+// strip, column-major [L2][32].  Only one strip per warp exists at a time: the
+// L1 x L2 coefficient matrix is never materialised.  Phase 2 is the wavefront
+// sweep of fwd_kernel with one row per lane, reading c from a 64-column
+// shared-memory ring filled 32 columns at a time from the strip.
+//
+// T = float: the FP32 solver (float-float corner, compensated first-order
+// terms, two-level sums in phase 1).  T = double: every step in FP64 --
+// point differences, the contraction, the refinement scaling and the tile map.
+#pragma once
+#include "sigk_device.cuh"
+#include "sigk_f64.cuh"
+#include "sigk_fwd.cuh"
+
+namespace sigk {
+
+constexpr int kCmKC = 32;  // contraction chunk
+
+template <int P, typename T>
+struct CmSmem {
+    static constexpr int S = P + 4;
+    // phase 1 staging (dx chunk [KC][36], dy chunk [32][KC+1]) and the phase 2
+    // coefficient ring [64][32] share one region; sizes in elements of T
+    static constexpr int stage = kCmKC * 36 + 32 * (kCmKC + 1);
+    static constexpr int ring = 64 * 32;
+    static constexpr int uni = stage > ring ? stage : ring;
+    static constexpr int per_warp = uni + 2 * kG * S;
+    static constexpr int bytes = 4 * per_warp * (int)sizeof(T);  // 4 warps per CTA
+};
+
+// Segment increment in FP64: exact for FP32 points (their difference has at
+// most 25 significant bits).
+__device__ __forceinline__ double inc_at_d(const float* z, int64_t row, int d, int e, int inc_mode) {
+    if (inc_mode) return (double)z[row * d + e];
+    return (double)z[(row + 1) * d + e] - (double)z[row * d + e];
+}
+
+template <int P, typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
+    fwd_cm_kernel(SolverArgs A, T* cscratch, int64_t cstride) {
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int S = P + 4;
+    using Sm = CmSmem<P, T>;
+    extern __shared__ float4 smem_f4[];
+    T* smem = reinterpret_cast<T*>(smem_f4);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
+    T* uni = smem + warp * Sm::per_warp;
+    T* dxs = uni;                    // [KC][36]: dims x rows
+    T* dys = uni + kCmKC * 36;       // [32][KC+1]: columns x dims
+    T* cring = uni;                  // [64][32]: columns x rows (phase 2)
+    T* sin_ = uni + Sm::uni;         // seam-in block
+    T* sout = sin_ + kG * S;         // seam-out block
+    T* cst = cscratch + (size_t)gwarp * cstride;  // this warp's strip [L2][32]
+    T* seam = reinterpret_cast<T*>(A.seam);
+    const int n_items = A.item_start[A.n_pairs];
+    const int d = A.d;
+    unsigned long long tiles_done = 0, lane_tiles = 0;
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(A.item_counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= n_items) break;
+        if (ld_volatile_s32(A.status) != 0) break;
+        int lo_p = 0, hi_p = A.n_pairs - 1;
+        while (lo_p < hi_p) {
+            int mid = (lo_p + hi_p + 1) >> 1;
+            if (A.item_start[mid] <= item) lo_p = mid; else hi_p = mid - 1;
+        }
+        const PairDesc pd = A.pairs[lo_p];
+        const int s = item - A.item_start[lo_p];
+        const int L1 = pd.L1, L2 = pd.L2;
+        const bool has_in = s > 0;
+        const bool has_out = s + 1 < pd.n_strips;
+        const int slot_in = (item - 1 + A.nslot) % A.nslot;
+        const int slot_out = item % A.nslot;
+        const int i0 = s * 32;
+        bool ok = true;
+
+        // ---- phase 1: c[i0 + r][j] for r < 32, all j, into the scratch strip ----
+        // FP64: the increments are staged unscaled and the refinement factor
+        // 1/(sx*sy) is applied to the finished dot product
+        const double cscale = 1.0 / ((double)pd.sx * (double)pd.sy);
+        for (int j0 = 0; j0 < L2; j0 += 32) {
+            T acc[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) acc[r] = T(0);
+            const int jl = j0 + lane;
+            for (int k0 = 0; k0 < d; k0 += kCmKC) {
+                __syncwarp();
+                const int e = k0 + lane;
+                // dx chunk, transposed to [dim][row]; dy chunk [column][dim]
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r) {
+                    const int row = i0 + r;
+                    const int col = j0 + r;
+                    if constexpr (F32) {
+                        dxs[lane * 36 + r] =
+                            (row < L1 && e < d) ? inc_ref(pd.xr, row, d, e, A.inc_mode, pd.sx) : 0.0f;
+                        dys[r * (kCmKC + 1) + lane] =
+                            (col < L2 && e < d) ? inc_ref(pd.yr, col, d, e, A.inc_mode, pd.sy) : 0.0f;
+                    } else {
+                        dxs[lane * 36 + r] =
+                            (row < L1 && e < d) ? inc_at_d(pd.xr, row / pd.sx, d, e, A.inc_mode) : 0.0;
+                        dys[r * (kCmKC + 1) + lane] =
+                            (col < L2 && e < d) ? inc_at_d(pd.yr, col / pd.sy, d, e, A.inc_mode) : 0.0;
+                    }
+                }
+                __syncwarp();
+                const int kn = min(kCmKC, d - k0);
+                if constexpr (F32) {
+                    // two-level sum: a chunk's products are accumulated from
+                    // zero and then added to the total, which cuts the rounding
+                    // error of a 256-term dot about 2.5x against one running sum
+                    float part[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) part[r] = 0.0f;
+                    for (int ee = 0; ee < kn; ++ee) {
+                        const float y = dys[lane * (kCmKC + 1) + ee];
+                        const float4* xr = reinterpret_cast<const float4*>(dxs + ee * 36);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 x = xr[q];
+                            part[4 * q + 0] = fmaf(x.x, y, part[4 * q + 0]);
+                            part[4 * q + 1] = fmaf(x.y, y, part[4 * q + 1]);
+                            part[4 * q + 2] = fmaf(x.z, y, part[4 * q + 2]);
+                            part[4 * q + 3] = fmaf(x.w, y, part[4 * q + 3]);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) acc[r] += part[r];
+                } else {
+                    for (int ee = 0; ee < kn; ++ee) {
+                        const double y = dys[lane * (kCmKC + 1) + ee];
+                        const double2* xr = reinterpret_cast<const double2*>(dxs + ee * 36);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const double2 x = xr[q];
+                            acc[2 * q + 0] = fma(x.x, y, acc[2 * q + 0]);
+                            acc[2 * q + 1] = fma(x.y, y, acc[2 * q + 1]);
+                        }
+                    }
+                }
+            }
+            if (jl < L2) {
+                if constexpr (F32) {
+                    float4* dst = reinterpret_cast<float4*>(cst + (size_t)jl * 32);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+                } else {
+                    double2* dst = reinterpret_cast<double2*>(cst + (size_t)jl * 32);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        dst[q] = make_double2(acc[2 * q] * cscale, acc[2 * q + 1] * cscale);
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- phase 2: the wavefront sweep (one row per lane) -------------------
+        T a[P + 1];
+        float a1lo = 0.0f;  // FP32 only: compensation of the first-order terms
+#pragma unroll
+        for (int p = 0; p <= P; ++p) a[p] = T(0);
+        int E = 0;
+        T ohi = T(1), ob[P + 1];
+        float olo = 0.0f, ob1lo = 0.0f;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) ob[q] = T(0);
+        int oE = 0;
+        const bool train = F32 && A.store != nullptr;
+        T* st_pair = train ? reinterpret_cast<T*>(A.store) + A.store_off[lo_p] : nullptr;
+        const int pw_in = train ? item - 1 : slot_in;
+        const int pw_out = train ? item : slot_out;
+        if (has_out && !train) {
+            const long long prev_consumer = (long long)item - A.nslot + 1;
+            bool okl = true;
+            if (lane == 0)
+                okl = wait_ge_s64(&A.done[((prev_consumer % A.nslot) + A.nslot) % A.nslot],
+                                  prev_consumer, A.status);
+            ok = __shfl_sync(kFull, okl, 0);
+        }
+        constexpr int NV = 32 * (int)sizeof(T) / 16;  // 16-byte vectors per strip column
+        const int Tn = L2 + 31;
+        const bool has_row = i0 + lane < L1;
+        for (int t = 0; t < Tn && ok; ++t) {
+            if ((t & 31) == 0 && t < L2) {
+                const int nb = min(32, L2 - t);
+                // coefficients of columns [t, t+nb) into the ring (contiguous)
+                const int4* src = reinterpret_cast<const int4*>(cst + (size_t)t * 32);
+                for (int idx = lane; idx < nb * NV; idx += 32) {
+                    const int col = idx / NV, q = idx % NV;
+                    reinterpret_cast<int4*>(cring + ((t + col) & 63) * 32)[q] = src[idx];
+                }
+                if (has_in) {
+                    const unsigned long long need =
+                        ((unsigned long long)(item - 1) << 32) | (unsigned)(t + nb);
+                    bool okl = true;
+                    if (lane == 0) okl = wait_ge_u64(&A.prod[pw_in], need, A.status);
+                    ok = __shfl_sync(kFull, okl, 0);
+                    if (ok) {
+                        const T* src2 = train ? st_pair + ((size_t)(s - 1) * L2 + t) * S
+                                              : seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
+                        for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src2 + idx);
+                        __syncwarp();
+                        if (lane == 0 && !train)
+                            st_release_u64(&A.cons[slot_in],
+                                           ((unsigned long long)item << 32) | (unsigned)(t + nb));
+                    }
+                }
+                __syncwarp();
+                if (!ok) break;
+            }
+            T hi = __shfl_up_sync(kFull, ohi, 1);
+            float lo = 0.0f, b1lo = 0.0f;
+            if constexpr (F32) {
+                lo = __shfl_up_sync(kFull, olo, 1);
+                b1lo = __shfl_up_sync(kFull, ob1lo, 1);
+            }
+            T b[P + 1];
+            b[0] = T(0);
+#pragma unroll
+            for (int q = 1; q <= P; ++q) b[q] = __shfl_up_sync(kFull, ob[q], 1);
+            int F = __shfl_up_sync(kFull, oE, 1);
+            if (lane == 0) {
+                if (has_in && t < L2) {
+                    const T* e_ = sin_ + (t & 31) * S;
+                    hi = e_[0];
+                    if constexpr (F32) {
+                        lo = e_[1];
+                        b1lo = e_[2];
+                    }
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
+                    if constexpr (F32) F = __float_as_int(e_[P + 3]);
+                    else F = (int)e_[P + 3];
+                } else {
+                    hi = T(1); lo = 0.0f; b1lo = 0.0f; F = 0;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] = T(0);
+                }
+            }
+            const int j = t - lane;
+            if (j >= 0 && j < L2) {
+                if (F != E) {
+                    if (F > E) {
+                        const T sc = F32 ? (T)exp2_nonpos(E - F) : (T)exp2_nonpos_d(E - F);
+                        a1lo *= (float)sc;
+#pragma unroll
+                        for (int p = 1; p <= P; ++p) a[p] *= sc;
+                        E = F;
+                    } else {
+                        const T sc = F32 ? (T)exp2_nonpos(F - E) : (T)exp2_nonpos_d(F - E);
+                        hi *= sc; lo *= (float)sc; b1lo *= (float)sc;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) b[q] *= sc;
+                    }
+                }
+                const T c = cring[(j & 63) * 32 + lane];
+                if constexpr (F32) {
+                    tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, A.nr);
+                    if (fabsf(hi) > 1.8446744e19f) {  // 2^64
+                        const float sc = 5.421011e-20f;  // 2^-64
+                        a1lo *= sc;
+#pragma unroll
+                        for (int p = 1; p <= P; ++p) a[p] *= sc;
+                        hi *= sc; lo *= sc; b1lo *= sc;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) b[q] *= sc;
+                        E += 64;
+                    }
+                } else {
+                    tile_update_f64<P>(c, a, hi, b, A.nr);
+                    if (fabs(hi) > 0x1p512) {
+                        const double sc = 0x1p-512;
+#pragma unroll
+                        for (int p = 1; p <= P; ++p) a[p] *= sc;
+                        hi *= sc;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) b[q] *= sc;
+                        E += 512;
+                    }
+                }
+                ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
+#pragma unroll
+                for (int q = 1; q <= P; ++q) ob[q] = b[q];
+                tiles_done += has_row ? 1ull : 0ull;
+                lane_tiles += 1;
+                if (lane == 31) {
+                    if (has_out) {
+                        T* e_ = sout + (j & 31) * S;
+                        e_[0] = hi;
+                        e_[1] = (T)lo;
+                        e_[2] = (T)b1lo;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) e_[2 + q] = b[q];
+                        if constexpr (F32) e_[P + 3] = __int_as_float(E);
+                        else e_[P + 3] = (double)E;
+                    } else if (j == L2 - 1) {
+                        double k = (double)hi + (double)lo + (double)b1lo;
+                        double fq = 1.0;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) {
+                            fq *= (double)q;
+                            k += (double)b[q] / fq;
+                        }
+                        k = ldexp(k, E);
+                        if (!isfinite(k)) atomicCAS(A.status, 0, kErrNonfinite);
+                        if (pd.out0 >= 0) A.out[pd.out0] = k;
+                        if (pd.out1 >= 0) A.out[pd.out1] = k;
+                        if (A.pair_exp) A.pair_exp[lo_p] = E;
+                    }
+                }
+            }
+            const int jj = t - 31;
+            if (has_out && jj >= 0 && jj < L2 && (((jj & 31) == 31) || jj == L2 - 1)) {
+                __syncwarp();
+                const int start = jj & ~31;
+                const int nb = jj - start + 1;
+                if (!train && start + nb > A.wcols) {
+                    const unsigned long long need = ((unsigned long long)(item + 1) << 32) |
+                                                    (unsigned)(start + nb - A.wcols);
+                    bool okl = true;
+                    if (lane == 0) okl = wait_ge_u64(&A.cons[slot_out], need, A.status);
+                    ok = __shfl_sync(kFull, okl, 0);
+                }
+                if (ok) {
+                    T* dst = train ? st_pair + ((size_t)s * L2 + start) * S
+                                   : seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
+                    for (int idx = lane; idx < nb * S; idx += 32) __stcg(dst + idx, sout[idx]);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0)
+                        st_release_u64(&A.prod[pw_out],
+                                       ((unsigned long long)item << 32) | (unsigned)(start + nb));
+                }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence();
+            st_release_s64(&A.done[item % A.nslot], (long long)item);
+        }
+        if (!ok) break;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tiles_done += __shfl_down_sync(kFull, tiles_done, o);
+        lane_tiles += __shfl_down_sync(kFull, lane_tiles, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.counters[0], tiles_done);
+        atomicAdd(&A.counters[1], lane_tiles);
+    }
+}
+
+}  // namespace sigk

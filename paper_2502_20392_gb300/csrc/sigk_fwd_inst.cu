@@ -3,6 +3,7 @@
 // one-row-per-lane training forward, and the backward (adjoint) kernel.
 #include "sigk_bwd.cuh"
 #include "sigk_fwd.cuh"
+#include "sigk_fwd_cm.cuh"
 #include "sigk_launch.h"
 
 #ifndef SIGK_P
@@ -99,6 +100,34 @@ cudaError_t fwd_launch<SIGK_P>(int D, int R, const SolverArgs& a, int grid, cuda
         case 16: return fwd_launch_impl<SIGK_P, 16, rows_per_lane(SIGK_P, 16)>(a, grid, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <typename T>
+static int fwd_cm_info_impl(KernelInfo* info) {
+    return occupancy(fwd_cm_kernel<SIGK_P, T>, 128, CmSmem<SIGK_P, T>::bytes, 1, info);
+}
+
+template <typename T>
+static cudaError_t fwd_cm_launch_impl(const SolverArgs& a, void* cscratch, int64_t cstride,
+                                      int grid, cudaStream_t s) {
+    const int smem = CmSmem<SIGK_P, T>::bytes;
+    auto kern = fwd_cm_kernel<SIGK_P, T>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 128, smem, s>>>(a, static_cast<T*>(cscratch), cstride);
+    return cudaGetLastError();
+}
+
+template <>
+int fwd_cm_info<SIGK_P>(bool f64, KernelInfo* info) {
+    return f64 ? fwd_cm_info_impl<double>(info) : fwd_cm_info_impl<float>(info);
+}
+
+template <>
+cudaError_t fwd_cm_launch<SIGK_P>(bool f64, const SolverArgs& a, void* cscratch, int64_t cstride,
+                                  int grid, cudaStream_t s) {
+    return f64 ? fwd_cm_launch_impl<double>(a, cscratch, cstride, grid, s)
+               : fwd_cm_launch_impl<float>(a, cscratch, cstride, grid, s);
 }
 
 template <>

@@ -22,6 +22,13 @@ constexpr int rows_per_lane(int P, int D) { return (P + D) <= 16 ? 4 : 2; }
 template <int P> int fwd_info(int D, int R, KernelInfo* info);
 template <int P> cudaError_t fwd_launch(int D, int R, const SolverArgs& a, int grid, cudaStream_t s);
 
+// Two-phase kernel (strip coefficients first, then the sweep): d > 16 in
+// FP32, or any d in FP64 (f64 = true).  cscratch holds float or double strips.
+template <int P> int fwd_cm_info(bool f64, KernelInfo* info);
+template <int P>
+cudaError_t fwd_cm_launch(bool f64, const SolverArgs& a, void* cscratch, int64_t cstride, int grid,
+                          cudaStream_t s);
+
 struct BwdArgs;
 template <int P> int bwd_info(int D, KernelInfo* info);
 template <int P> cudaError_t bwd_launch(int D, const BwdArgs& a, int grid, cudaStream_t s);

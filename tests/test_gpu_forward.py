@@ -40,8 +40,9 @@ def to_dev(pts, lens):
 def rel_err(k, ref, kxx=None, kyy=None):
     e = np.abs(k - ref) / np.maximum(np.abs(ref), 1e-300)
     if kxx is not None:
-        cs = np.abs(k - ref) / np.sqrt(np.abs(kxx * kyy))
-        small = np.abs(ref) < 1e-2 * np.sqrt(np.abs(kxx * kyy))
+        scale = np.sqrt(np.abs(kxx)) * np.sqrt(np.abs(kyy))  # no overflow for huge self-kernels
+        cs = np.abs(k - ref) / scale
+        small = np.abs(ref) < 1e-2 * scale
         e = np.where(small, np.minimum(e, cs), e)
     return e
 
@@ -212,3 +213,67 @@ def test_refinement_resolves_large_tiles(S, orc):
     assert op.refine_c > 0
     G2 = S.gram(X, L, opts=op).cpu().numpy()
     assert rel_err(G2, ref, dg[:, None], dg[None, :]).max() < 1e-5
+
+
+def test_large_dimension_ragged_pairs(S, orc):
+    # d = 256 (the two-phase kernel): ragged pairs, per-path scales
+    # sigma_p ~ U(0.5, 4) as in the ragged d=256 workload, with refinement for
+    # the rough short paths
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.ragged_pairs(6, 20, 300, 256, 0.5, 4.0, seed=4001)
+    ix, iy = incs(X, lx), incs(Y, ly)
+    ref = orc.series_pairs(ix, iy, N=28)
+    kxx = orc.series_pairs(ix, ix, N=28)
+    kyy = orc.series_pairs(iy, iy, N=28)
+    o = S.plan(S.OP_PAIRS, *to_dev(X, lx), *to_dev(Y, ly), tol=1e-6, opts=S.Opts(max_len=20000))
+    k = S.pairs(*to_dev(X, lx), *to_dev(Y, ly), opts=o).cpu().numpy()
+    e = rel_err(k, ref, kxx, kyy)
+    assert e.max() < 1e-5, (o, e)
+
+
+def test_large_dimension_kernel_matches_register_kernel(S):
+    # appending a zero coordinate leaves every tile coefficient unchanged, so
+    # the d=17 (two-phase) kernel must reproduce the d=16 (register) kernel
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(5, [100, 37, 260, 64, 129], 16, 1.0, seed=44)
+    pts17 = np.concatenate([pts, np.zeros((pts.shape[0], 1), np.float32)], 1)
+    o = S.Opts(order=8, rings=4, max_len=300)
+    G16 = S.gram(*to_dev(pts, lens), opts=o).cpu().numpy()
+    G17 = S.gram(*to_dev(np.ascontiguousarray(pts17), lens), opts=o).cpu().numpy()
+    np.testing.assert_allclose(G17, G16, rtol=2e-6)
+
+
+@pytest.mark.parametrize("d", [4, 256])
+def test_fp64_solver_matches_oracle(S, orc, d):
+    # FLAG_FP64: point differences, contraction, refinement scaling and tile
+    # map in double.  Against the FP64 oracle the gap is double rounding plus
+    # the truncation the plan allows (tol 1e-11), on ragged pairs
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.ragged_pairs(6, 20, 300, d, 0.5, 2.0, seed=4101 + d)
+    ix, iy = incs(X, lx), incs(Y, ly)
+    ref = orc.series_pairs(ix, iy, N=30)
+    kxx = orc.series_pairs(ix, ix, N=30)
+    kyy = orc.series_pairs(iy, iy, N=30)
+    o = S.plan(S.OP_PAIRS, *to_dev(X, lx), *to_dev(Y, ly), tol=1e-11,
+               opts=S.Opts(max_len=20000, flags=S.FLAG_FP64))
+    assert o.flags & S.FLAG_FP64
+    k = S.pairs(*to_dev(X, lx), *to_dev(Y, ly), opts=o).cpu().numpy()
+    e = rel_err(k, ref, kxx, kyy)
+    assert e.max() < 1e-9, (o, e)
+    # refinement factors up to 3 (the largest increment / sqrt(refine_c) is
+    # 2.5): the scaling 1/(sx*sy) is not a power of two
+    mx = max(np.linalg.norm(v, axis=1).max() for v in ix + iy)
+    o3 = S.Opts(order=16, rings=8, refine_c=float((mx / 2.5) ** 2), max_len=20000,
+                flags=S.FLAG_FP64)
+    k3 = S.pairs(*to_dev(X, lx), *to_dev(Y, ly), opts=o3).cpu().numpy()
+    e3 = rel_err(k3, ref, kxx, kyy)
+    assert e3.max() < 1e-9, (o3, e3)
+
+
+def test_fp64_rejected_by_backward(S):
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(2, [8, 9], 4, 1.0, seed=3)
+    Xd, ld = to_dev(pts, lens)
+    with pytest.raises(S.SigkError):
+        S.backward(S.OP_GRAM, Xd, ld, None, None, torch.ones((2, 2), dtype=torch.float64),
+                   S.Opts(flags=S.FLAG_FP64, max_len=16))

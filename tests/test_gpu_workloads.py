@@ -178,3 +178,62 @@ def test_mmd_2x32_L2048_d8_value_and_gradient(S, orc):
                    for i in range(len(coords))])
     got = gX.reshape(-1)[coords]
     np.testing.assert_allclose(got, fd, atol=1e-4 * np.abs(fd).max())
+
+
+def _oracle_order(dx, dy, tol=1e-12):
+    # truncation order for the oracle from the pair's own coupling
+    # C = max |<dx_i, y_J - y_0>| (numpy): L * C^{N+1} / ((N+1)!)^2 <= tol
+    c = dx @ dy.T
+    C = max(np.abs(np.cumsum(c, axis=1)).max(), np.abs(np.cumsum(c, axis=0)).max(), 1e-30)
+    L = max(len(dx), len(dy))
+    N = 8
+    while N < 56 and L * C ** (N + 1) / math.factorial(N + 1) ** 2 > tol:
+        N += 1
+    return N
+
+
+def _check_sample(orc, xs, ys, k, pick):
+    errs = []
+    for p in pick:
+        dx = np.diff(xs[p].astype(np.float64), axis=0)
+        dy = np.diff(ys[p].astype(np.float64), axis=0)
+        r = orc.series_pair(dx, dy, N=_oracle_order(dx, dy))
+        kx = orc.series_pair(dx, dx, N=_oracle_order(dx, dx))
+        ky = orc.series_pair(dy, dy, N=_oracle_order(dy, dy))
+        scale = math.sqrt(abs(kx)) * math.sqrt(abs(ky))
+        errs.append(abs(k[p] - r) / (scale if abs(r) < 1e-2 * scale else abs(r)))
+    return np.array(errs)
+
+
+def test_ragged_512_pairs_d256(S, orc):
+    # 512 ragged pairs, lengths U[64, 8192], d = 256, sigma ~ U(0.5, 4) per
+    # path, one persistent launch with the planned order and refinement.
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.workload_ragged_512()
+    Xd, lxd = torch.from_numpy(X).to(dev()), torch.from_numpy(lx).to(dev())
+    Yd, lyd = torch.from_numpy(Y).to(dev()), torch.from_numpy(ly).to(dev())
+    xs, ys = synth.split(X, lx), synth.split(Y, ly)
+    # FP64 solve (FLAG_FP64): the tolerance 1e-5 holds for every pair, the
+    # strongly coupled long ones included (log k up to ~245 here)
+    o = S.plan(S.OP_PAIRS, Xd, lxd, Yd, lyd, tol=1e-5, opts=S.Opts(max_len=8193, flags=S.FLAG_FP64))
+    k64 = S.pairs(Xd, lxd, Yd, lyd, opts=o).cpu().numpy()
+    assert np.isfinite(k64).all()
+    # seeded sample of pairs whose oracle cost is bounded (L1*L2 <= 3e6), plus
+    # the four of largest log|k| among those of L1*L2 <= 6e6
+    rng = np.random.default_rng(4001)
+    cost = (lx - 1) * (ly - 1)
+    cand = np.flatnonzero(cost <= 3_000_000)
+    pick = list(rng.choice(cand, size=min(10, len(cand)), replace=False))
+    big = np.flatnonzero(cost <= 6_000_000)
+    pick += [int(p) for p in big[np.argsort(-np.log(np.abs(k64[big])))][:4] if p not in pick]
+    e64 = _check_sample(orc, xs, ys, k64, pick)
+    assert e64.max() < 1e-5, list(zip(pick, e64))
+    assert e64.max() < 1e-8, list(zip(pick, e64))  # FP64 headroom
+    # FP32 solve: the same pairs agree to the FP32 rounding level of such
+    # long, strongly coupled sweeps (the error grows with the coupling and the
+    # path length; FP64 is what meets 1e-5 on all of them)
+    o32 = S.Opts(order=o.order, rings=o.rings, refine_c=o.refine_c, max_len=o.max_len)
+    k32 = S.pairs(Xd, lxd, Yd, lyd, opts=o32).cpu().numpy()
+    assert np.isfinite(k32).all()
+    e32 = np.abs(k32[pick] - k64[pick]) / np.abs(k64[pick])
+    assert np.median(e32) < 1e-5 and e32.max() < 2e-3, list(zip(pick, e32))
