@@ -18,6 +18,7 @@
 
 #include "../../include/sigk.h"
 #include "sigk_bwd.cuh"
+#include "sigk_stats.cuh"
 #include "sigk_device.cuh"
 #include "sigk_launch.h"
 
@@ -628,202 +629,13 @@ __global__ void __launch_bounds__(1024) mmd_reduce_kernel(const double* G, int64
 // ---------------------------------------------------------------------------
 
 // ---------------------------------------------------------------------------
-// a-priori truncation statistics (sigk_plan), one warp per pair:
-//   [0] L1, [1] L2 (segments as solved: row path, swept path)
-//   [2] C_a: max over rows i and sampled points J of |<dx_i, y_J - y_0>| -- the
-//       accumulated coupling that sets the size of the bottom-edge coefficients
-//       a_p ~ C_a^p / (p!)^2; [3] C_b: the same with the roles swapped
-//   [4 + m - 2], m = 2..9: (sum_i |dx_i|^m) * (sum_j |dy_j|^m), an upper bound
-//       on sum_ij |c_ij|^m (Cauchy-Schwarz), the size of the dropped ring m
-//   [12], [13]: max_i |dx_i|, max_j |dy_j| (their product bounds every |c_ij|)
-// (all for the refined problem when refinement is on)
-constexpr int kStatFields = 14;
-constexpr int kStatStride = 16;  // sampled points: every 16th, plus the last
-
-__device__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-__device__ float warp_max_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
-
-// max over rows i of path `a` and sampled points J of path `b` of
-// |<da_i, b_J - b_0>| (at most ~1024 samples of J, always including the end)
-constexpr int kStatDmax = 16;
-
-__device__ float coupling_max_cs(const float* a, int La, const float* b, int Lb, int d,
-                                 int inc_mode, int lane);
-
-__device__ float coupling_max(const float* a, int La, const float* b, int Lb, int d, int inc_mode,
-                              int lane) {
-    if (d > kStatDmax) {
-        if (inc_mode) return coupling_max_cs(a, La, b, Lb, d, inc_mode, lane);
-        // points: b_J - b_0 is read directly at the sampled J
-        const int stride = max(kStatStride, (Lb + 1023) / 1024);
-        float best = 0.0f;
-        for (int J = min(stride, Lb);; J = min(J + stride, Lb)) {
-            for (int i = lane; i < La; i += 32) {
-                float dot = 0.0f;
-                for (int e = 0; e < d; ++e)
-                    dot = fmaf(inc_at(a, i, d, e, 0), b[(int64_t)J * d + e] - b[e], dot);
-                best = fmaxf(best, fabsf(dot));
-            }
-            if (J >= Lb) break;
-        }
-        return warp_max_f(best);
-    }
-    const int stride = max(kStatStride, (Lb + 1023) / 1024);
-    float B[kStatDmax];
-#pragma unroll
-    for (int e = 0; e < kStatDmax; ++e) B[e] = 0.0f;
-    float best = 0.0f;
-    int Jprev = 0;
-    for (int J = min(stride, Lb);; J = min(J + stride, Lb)) {
-        // B = b_J - b_0 (points), or the running sum of the increments
-#pragma unroll
-        for (int e = 0; e < kStatDmax; ++e) {
-            if (e < d) {
-                if (inc_mode) {
-                    for (int j = Jprev; j < J; ++j) B[e] += b[(int64_t)j * d + e];
-                } else {
-                    B[e] = b[(int64_t)J * d + e] - b[e];
-                }
-            }
-        }
-        for (int i = lane; i < La; i += 32) {
-            float dot = 0.0f;
-#pragma unroll
-            for (int e = 0; e < kStatDmax; ++e)
-                if (e < d) dot = fmaf(inc_at(a, i, d, e, inc_mode), B[e], dot);
-            best = fmaxf(best, fabsf(dot));
-        }
-        Jprev = J;
-        if (J >= Lb) break;
-    }
-    return warp_max_f(best);
-}
-
-// d > 16: max_i |da_i| * max_J |b_J - b_0| (Cauchy-Schwarz), with the lanes
-// partitioning the dimensions for the running sums (d <= 32 * 16)
-__device__ float coupling_max_cs(const float* a, int La, const float* b, int Lb, int d,
-                                 int inc_mode, int lane) {
-    float amax = 0.0f;
-    for (int i = lane; i < La; i += 32) {
-        float n2 = 0.0f;
-        for (int e = 0; e < d; ++e) {
-            const float v = inc_at(a, i, d, e, inc_mode);
-            n2 = fmaf(v, v, n2);
-        }
-        amax = fmaxf(amax, n2);
-    }
-    amax = warp_max_f(amax);
-    float run[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) run[k] = 0.0f;
-    float rmax = 0.0f;
-    if (d > 32 * 16) {  // beyond the lanes' running sums: total variation bound
-        float tv = 0.0f;
-        for (int j = lane; j < Lb; j += 32) {
-            float n2 = 0.0f;
-            for (int e = 0; e < d; ++e) {
-                const float v = inc_at(b, j, d, e, inc_mode);
-                n2 = fmaf(v, v, n2);
-            }
-            tv += sqrtf(n2);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tv += __shfl_xor_sync(kFull, tv, o);
-        return sqrtf(amax) * tv;
-    }
-    for (int j = 0; j < Lb; ++j) {
-        float part = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int e = lane + 32 * k;
-            if (e < d) {
-                run[k] += inc_at(b, j, d, e, inc_mode);
-                part = fmaf(run[k], run[k], part);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-        rmax = fmaxf(rmax, part);
-    }
-    return sqrtf(amax) * sqrtf(rmax);
-}
-
-__global__ void pair_stats_kernel(const PairDesc* pairs, int64_t n_pairs, int d, int inc_mode,
-                                  double* out) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < n_pairs;
-         p += warps) {
-        const PairDesc pd = pairs[p];
-        double* o = out + p * kStatFields;
-        // statistics of the ORIGINAL segments, scaled to the refined problem at
-        // the end: a segment split in s pieces gives s increments dz/s
-        const int L1o = pd.sx > 0 ? pd.L1 / pd.sx : pd.L1;
-        const int L2o = pd.sy > 0 ? pd.L2 / pd.sy : pd.L2;
-        double sx[8], sy[8];
-        double mx = 0.0, my = 0.0;
-        for (int m = 0; m < 8; ++m) { sx[m] = 0.0; sy[m] = 0.0; }
-        for (int i = lane; i < L1o; i += 32) {
-            double n2 = 0.0;
-            for (int e = 0; e < d; ++e) {
-                const double v = inc_at(pd.xr, i, d, e, inc_mode);
-                n2 += v * v;
-            }
-            mx = fmax(mx, n2);
-            const double n1 = sqrt(n2);
-            double pw = n2;
-            for (int m = 0; m < 8; ++m) { sx[m] += pw; pw *= n1; }
-        }
-        for (int j = lane; j < L2o; j += 32) {
-            double n2 = 0.0;
-            for (int e = 0; e < d; ++e) {
-                const double v = inc_at(pd.yr, j, d, e, inc_mode);
-                n2 += v * v;
-            }
-            my = fmax(my, n2);
-            const double n1 = sqrt(n2);
-            double pw = n2;
-            for (int m = 0; m < 8; ++m) { sy[m] += pw; pw *= n1; }
-        }
-        for (int m = 0; m < 8; ++m) { sx[m] = warp_sum_d(sx[m]); sy[m] = warp_sum_d(sy[m]); }
-#pragma unroll
-        for (int o2 = 16; o2 > 0; o2 >>= 1) {
-            mx = fmax(mx, __shfl_xor_sync(kFull, mx, o2));
-            my = fmax(my, __shfl_xor_sync(kFull, my, o2));
-        }
-        float ca = 0.0f, cb = 0.0f;
-        if (L1o > 0 && L2o > 0) {
-            ca = coupling_max(pd.xr, L1o, pd.yr, L2o, d, inc_mode, lane);
-            cb = coupling_max(pd.yr, L2o, pd.xr, L1o, d, inc_mode, lane);
-        }
-        if (lane == 0) {
-            const double fx = pd.sx > 0 ? pd.sx : 1, fy = pd.sy > 0 ? pd.sy : 1;
-            o[0] = pd.L1;
-            o[1] = pd.L2;
-            o[2] = ca / fx;  // refined rows carry dx / sx
-            o[3] = cb / fy;
-            for (int m = 0; m < 8; ++m)  // sum over refined increments of |dz/s|^m
-                o[4 + m] = sx[m] * pow(fx, 1.0 - (m + 2)) * sy[m] * pow(fy, 1.0 - (m + 2));
-            o[12] = sqrt(mx) / fx;  // largest refined increment norms
-            o[13] = sqrt(my) / fy;
-        }
-    }
-}
-
 // Smallest (order P, rings n) with the estimated truncation errors below
 // tol/10, relative to the local kernel scale (App. C.3: a-priori order search
 // from the largest coupling in the grid, here per pair and for two knobs):
 //   rings: sum_ij |c_ij|^{n+1} / ((n+1)!)^2 <= tol/10 (the dropped ring n+1)
-//   order: max(L1, L2) * (1.25 C)^{P+1} / ((P+1)!)^2 <= tol/10, C the sampled
-//          coupling (the dropped edge coefficient of degree P+1, over a row)
+//   order: max(L1, L2) * C^{P+1} / ((P+1)!)^2 <= tol/10, C = max(C_a, C_b) the
+//          accumulated coupling (the dropped edge coefficient of degree P+1,
+//          over a row or column)
 static void choose_order(const double* st, int64_t n, double tol, int* P_out, int* nr_out,
                          int64_t* max_swept, double* max_tile_c, bool* order_fits) {
     *max_tile_c = 0.0;
@@ -837,11 +649,11 @@ static void choose_order(const double* st, int64_t n, double tol, int* P_out, in
         const double* o = st + p * kStatFields;
         if (o[0] <= 0 || o[1] <= 0) continue;
         if ((int64_t)o[1] > *max_swept) *max_swept = (int64_t)o[1];
-        if (o[12] * o[13] > *max_tile_c) *max_tile_c = o[12] * o[13];
+        if (o[12] > *max_tile_c) *max_tile_c = o[12];
         int r = 1;
         while (r < kMaxRings && o[4 + (r + 1) - 2] / (fact[r + 1] * fact[r + 1]) > target) ++r;
         if (r > nr) nr = r;
-        const double C = 1.25 * (o[2] > o[3] ? o[2] : o[3]);
+        const double C = o[2] > o[3] ? o[2] : o[3];
         const double Lm = o[0] > o[1] ? o[0] : o[1];
         int q = 4;
         while (q < kMaxP && Lm * pow(C, q + 1) / (fact[q + 1] * fact[q + 1]) > target) ++q;
@@ -1162,6 +974,28 @@ sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t 
     return SIGK_OK;
 }
 
+// Exact tile statistics of the pair table as planned (sigk_stats.cuh).
+static constexpr int kStatGridPerSm = 4;
+static cudaError_t launch_stats(const PlanArgs& pa, double* stats, size_t stats_bytes,
+                                float* basebuf, int grid, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(stats, 0, stats_bytes, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(&pa.hdr->item_counter, 0, sizeof(int), s)) != cudaSuccess) return e;
+    StatArgs sa;
+    sa.pairs = pa.pairs;
+    sa.item_start = pa.item_start;
+    sa.n_pairs = (int32_t)pa.n_pairs;
+    sa.rows_per_strip = pa.rows_per_strip;
+    sa.d = pa.d;
+    sa.inc_mode = pa.inc_mode;
+    sa.item_counter = &pa.hdr->item_counter;
+    sa.stats = stats;
+    sa.base = basebuf;
+    const int smem = 4 * StSmem::per_warp * (int)sizeof(float);
+    pair_stats_kernel<<<grid, 128, smem, s>>>(sa);
+    return cudaGetLastError();
+}
+
 sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x, const float* Y,
                       const int64_t* len_y, int64_t n_y, int d, double tol, void* ws,
                       size_t ws_bytes, void* stream, const sigk_opts* opts_in, sigk_opts* opts_out) {
@@ -1179,8 +1013,14 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     Layout L;
     if ((st = make_layout(op, n_x, n_y, d, o, &L)) != SIGK_OK) return st;
     if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
-    const size_t need = sizeof(double) * kStatFields * (size_t)L.n_pairs;
+    const size_t need = align256(sizeof(double) * kStatFields * (size_t)L.n_pairs);
     if (need > L.total - L.seam) return fail(SIGK_ERR_WORKSPACE, "workspace too small for plan statistics");
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return fail(SIGK_ERR_CUDA, "cannot query SM count");
+    const int stat_grid = sms * kStatGridPerSm;
+    const size_t base_bytes = align256(sizeof(float) * (size_t)stat_grid * 4 * (size_t)d);
     char* base = (char*)ws;
     cudaStream_t strm = (cudaStream_t)stream;
     // the planner builds the pair table; its k outputs go to a scratch area
@@ -1209,31 +1049,35 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     pa.hdr = (Header*)(base + L.hdr);
     pa.out = scratch_out;
     pa.out_ld = 0;
+    float* statbase = nullptr;
     if (op != SIGK_OP_PAIRS) {
         // Gram-shaped ops write k at a*ld+b; give them a large enough scratch
         const int64_t nz = (op == SIGK_OP_MMD) ? n_x + n_y : n_x;
         const int64_t ncol = (op == SIGK_OP_GRAM && Y) ? n_y : nz;
         pa.out_ld = ncol;
-        if (sizeof(double) * (size_t)((op == SIGK_OP_MMD ? nz : n_x) * ncol) + need > L.total - L.seam)
+        const size_t gram_bytes = align256(sizeof(double) * (size_t)((op == SIGK_OP_MMD ? nz : n_x) * ncol));
+        if (gram_bytes + need + base_bytes > L.total - L.seam)
             return fail(SIGK_ERR_WORKSPACE, "workspace too small for plan scratch");
         scratch_out = (double*)(base + L.seam + need);
         pa.out = scratch_out;
+        statbase = (float*)(base + L.seam + need + gram_bytes);
+    } else {
+        if (need + base_bytes > L.total - L.seam)
+            return fail(SIGK_ERR_WORKSPACE, "workspace too small for plan scratch");
+        statbase = (float*)(base + L.seam + need);
     }
     cudaError_t e = launch_planner(pa, o, L, base, strm);
     if (e != cudaSuccess) return cuda_fail(e, "planner launch");
     double* stats = (double*)(base + L.seam);
-    const int threads = 256;
-    const int64_t blocks = (L.n_pairs + (threads / 32) - 1) / (threads / 32);
-    pair_stats_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), threads, 0, strm>>>(
-        pa.pairs, L.n_pairs, d, pa.inc_mode, stats);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pair_stats launch");
+    if ((e = launch_stats(pa, stats, need, statbase, stat_grid, strm)) != cudaSuccess)
+        return cuda_fail(e, "pair_stats launch");
     if ((e = cudaStreamSynchronize(strm)) != cudaSuccess) return cuda_fail(e, "plan synchronize");
     Header h;
     if ((e = cudaMemcpy(&h, base + L.hdr, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "plan status copy");
     if (h.status != 0) return fail((sigk_status)h.status, "invalid lengths");
     std::vector<double> hs((size_t)kStatFields * L.n_pairs);
-    if ((e = cudaMemcpy(hs.data(), stats, need, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpy(hs.data(), stats, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(e, "plan stats copy");
     int P = 4, nr = 1;
     int64_t max_swept = 1;
@@ -1249,14 +1093,13 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
         o2.refine_c = rc;
         if ((e = launch_planner(pa, o2, L, base, strm)) != cudaSuccess)
             return cuda_fail(e, "planner launch");
-        pair_stats_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), threads, 0, strm>>>(
-            pa.pairs, L.n_pairs, d, pa.inc_mode, stats);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pair_stats launch");
+        if ((e = launch_stats(pa, stats, need, statbase, stat_grid, strm)) != cudaSuccess)
+            return cuda_fail(e, "pair_stats launch");
         if ((e = cudaStreamSynchronize(strm)) != cudaSuccess) return cuda_fail(e, "plan synchronize");
         if ((e = cudaMemcpy(&h, base + L.hdr, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "plan status copy");
         if (h.status != 0) return fail((sigk_status)h.status, "invalid lengths");
-        if ((e = cudaMemcpy(hs.data(), stats, need, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        if ((e = cudaMemcpy(hs.data(), stats, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(e, "plan stats copy");
         P = 4; nr = 1; max_swept = 1;
         choose_order(hs.data(), L.n_pairs, tol, &P, &nr, &max_swept, &max_c, &fits);
