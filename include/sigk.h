@@ -68,7 +68,7 @@ enum {
     SIGK_FLAG_GRAM_FULL = 2,   /* Gram of X with itself: compute both triangles
                                   independently instead of mirroring */
     SIGK_FLAG_MMD_BIASED = 4,  /* MMD^2 V-statistic instead of the U-statistic */
-    SIGK_FLAG_FP64 = 8         /* solve every tile in FP64: point differences,
+    SIGK_FLAG_FP64 = 8,        /* solve every tile in FP64: point differences,
                                   the increment Gram, refinement scaling and the
                                   tile map (forward ops only; sigk_backward
                                   rejects it).  For ill-conditioned pairs --
@@ -76,6 +76,13 @@ enum {
                                   kernels -- whose FP32 result carries a
                                   rounding error above the tolerance.  FP64
                                   runs at 1/64 of the FP32 rate on this GPU. */
+    SIGK_FLAG_PAIR_MAJOR = 16  /* schedule each pair's strips as consecutive
+                                  work items (smaller seam ring) instead of the
+                                  default strip-major order, where strip l of
+                                  every pair is scheduled before strip l+1 of
+                                  any, longest pairs first, whenever the ring
+                                  for whole strips fits in 8 GiB.  Results are
+                                  identical; only the schedule differs. */
 };
 
 /* Truncation and scheduling parameters.  NULL = defaults (order 8, rings 4,

@@ -2,7 +2,8 @@
 //
 // Runs after a training forward that stored every strip's right-edge seam
 // (the checkpointed wavefront boundaries; strips of 32 rows, one row per
-// lane).  One work item = (pair, strip), strips of a pair in DECREASING order.
+// lane).  One work item = (pair, strip), strips of a pair in DECREASING order
+// (the schedule's k-th item of a pair is strip n_strips - 1 - k).
 //
 // Pass A replays the strip's forward from its stored input seam and keeps, per
 // lane and column, the lane's incoming left edge and the exponent decisions
@@ -27,7 +28,7 @@ namespace sigk {
 
 struct BwdArgs {
     const PairDesc* pairs;
-    const int32_t* item_start;
+    Schedule sched;              // item k of a pair is its strip n_strips - 1 - k
     int32_t n_pairs;
     int32_t inc_mode;
     int32_t d;
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     float* aout = ain + 32 * SA;                        // adjoint seam-out block
     float* colacc = aout + 32 * SA;                     // 64 x D column gradient
     float* rec = A.rec + (size_t)gwarp * A.rec_stride;
-    const int n_items = A.item_start[A.n_pairs];
+    const int n_items = A.sched.hdr[2];
     unsigned long long tiles = 0;
 
     for (;;) {
@@ -120,14 +121,11 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         item = __shfl_sync(kFull, item, 0);
         if (item >= n_items) break;
         if (ld_volatile_s32(A.status) != 0) break;
-        int lo_p = 0, hi_p = A.n_pairs - 1;
-        while (lo_p < hi_p) {
-            int mid = (lo_p + hi_p + 1) >> 1;
-            if (A.item_start[mid] <= item) lo_p = mid; else hi_p = mid - 1;
-        }
+        const ItemRef ir = decode_item(A.sched, A.pairs, item);
+        const int lo_p = ir.pair;
         const PairDesc pd = A.pairs[lo_p];
         const int nst = pd.n_strips;
-        const int s = nst - 1 - (item - A.item_start[lo_p]);  // reverse strip order
+        const int s = nst - 1 - ir.k;  // reverse strip order
         const int L1 = pd.L1, L2 = pd.L2;
         const int row = s * 32 + lane;
         const bool has_row = row < L1;
@@ -246,18 +244,11 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         const double wsc_d = A.pair_w[lo_p] * ldexp(1.0, A.pair_exp[lo_p]);
         const float wsc = (float)wsc_d;
         const bool last_strip = (s == nst - 1);
-        const bool has_ain = !last_strip;
-        const bool has_aout = s > 0;
-        const int slot_in = (item - 1 + A.nslot) % A.nslot;
+        const bool has_ain = ir.prev >= 0;   // adjoint seam of strip s + 1
+        const bool has_aout = ir.next >= 0;  // consumed by strip s - 1
+        const int slot_in = has_ain ? ir.prev % A.nslot : 0;
         const int slot_out = item % A.nslot;
-        if (has_aout) {
-            const long long prev_consumer = (long long)item - A.nslot + 1;
-            bool okl = true;
-            if (lane == 0)
-                okl = wait_ge_s64(&A.done[((prev_consumer % A.nslot) + A.nslot) % A.nslot],
-                                  prev_consumer, A.status);
-            ok = __shfl_sync(kFull, okl, 0);
-        }
+        if (has_aout) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
         a[1] += a1lo;  // the reverse sweep carries the first-order term as one float
         float Ab[P + 1];
 #pragma unroll
@@ -283,7 +274,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 }
                 if (has_ain) {
                     const unsigned long long need =
-                        ((unsigned long long)(item - 1) << 32) | (unsigned)(tp + nb);
+                        ((unsigned long long)ir.prev << 32) | (unsigned)(tp + nb);
                     bool okl = true;
                     if (lane == 0) okl = wait_ge_u64(&A.prod[slot_in], need, A.status);
                     ok = __shfl_sync(kFull, okl, 0);
@@ -422,7 +413,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 }
                 if (has_aout) {
                     if (start + nb > A.wcols) {
-                        const unsigned long long need = ((unsigned long long)(item + 1) << 32) |
+                        const unsigned long long need = ((unsigned long long)ir.next << 32) |
                                                         (unsigned)(start + nb - A.wcols);
                         bool okl = true;
                         if (lane == 0) okl = wait_ge_u64(&A.cons[slot_out], need, A.status);

@@ -128,7 +128,8 @@ static cudaError_t bwd_launch_dispatch(int P, int D, const BwdArgs& a, int grid,
 // workspace layout
 
 struct Layout {
-    size_t hdr, ox, oy, sx, sy, pairs, item_start, prod, cons, done, seam, gram, total;
+    size_t hdr, ox, oy, sx, sy, pairs, item_start, order, lvl, prod, cons, done, seam, gram, total;
+    bool strip_major;    // the ring in use can hold whole strips: strip-major allowed
     // backward sections (train == true)
     size_t store, store_off, pair_exp, pair_w, rec, bprod, bcons, bdone, aseam;
     int64_t store_floats, rec_stride;
@@ -148,6 +149,11 @@ struct Layout {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Strip-major schedule limits: strips per pair the level arrays hold, and the
+// largest seam ring (bytes) it may take.
+constexpr int kLevelCap = 4096;
+constexpr double kStripMajorBudget = 8.0 * 1024 * 1024 * 1024;
+
 // Number of pair entries solved by an op.
 static int64_t pair_count(int op, int64_t n_x, int64_t n_y, int flags) {
     if (op == SIGK_OP_PAIRS) return n_x;
@@ -161,7 +167,7 @@ static int64_t pair_count(int op, int64_t n_x, int64_t n_y, int flags) {
 }
 
 static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Opts& o, Layout* L,
-                               bool train = false) {
+                               bool train = false, bool allow_sm = true) {
     const int D = dim_bucket(d);
     if (D < 0) return fail(SIGK_ERR_UNSUPPORTED, "d must be in 1..8192 in this build");
     L->train = train;
@@ -185,10 +191,21 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->nwarps = L->grid * (L->info.threads / 32);
     L->rows_per_strip = 32 * L->info.rows_per_lane;
     L->stride = o.order + 4;
-    // Seam ring: nslot > concurrent warps; wcols large enough that the warps
-    // in flight can always hold a whole sweep between them (nwarps * wcols >=
-    // 2 * max_len), so a producer never waits on a consumer that cannot start.
-    L->nslot = L->nwarps + 64;
+    L->n_pairs = pair_count(op, n_x, n_y, o.flags);
+    // Seam ring, pair-major: nslot > concurrent warps; wcols large enough that
+    // the warps in flight can always hold a whole sweep between them (nwarps *
+    // wcols >= 2 * max_len), so a producer never waits on a consumer that
+    // cannot start.  Strip-major (when the ring fits the budget): a slot holds
+    // a whole strip (wcols >= max_len, no flow control) and nslot covers the
+    // producer-consumer distance (<= n_pairs items) plus the warps in flight,
+    // so a slot is reused only after an item at least nwarps earlier is done.
+    const int64_t wfull = (o.max_len + 31) & ~(int64_t)31;
+    const int64_t nslot_sm = L->n_pairs + L->nwarps + 64;
+    if (o.flags & SIGK_FLAG_PAIR_MAJOR) allow_sm = false;
+    L->strip_major = allow_sm && !train && nslot_sm <= (int64_t)INT32_MAX / 2 &&
+                     (double)nslot_sm * (double)wfull * (double)L->stride * (double)L->elem <=
+                         kStripMajorBudget;
+    L->nslot = L->strip_major ? (int)nslot_sm : L->nwarps + 64;
     // training: one progress word per work item (seams are not reused)
     L->nwords = L->nslot;
     if (train) {
@@ -201,8 +218,8 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     if (w > o.max_len) w = o.max_len;
     w = (w + 31) & ~(int64_t)31;
     if (w < 32) w = 32;
+    if (L->strip_major) w = wfull < 32 ? 32 : wfull;
     L->wcols = (int)w;
-    L->n_pairs = pair_count(op, n_x, n_y, o.flags);
     L->n_paths_x = n_x;
     L->n_paths_y = (op == SIGK_OP_GRAM && n_y == 0) ? 0 : n_y;
     size_t off = 0;
@@ -213,6 +230,8 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->sy = off; off = align256(off + sizeof(int32_t) * (size_t)(n_y + 1));
     L->pairs = off; off = align256(off + sizeof(PairDesc) * (size_t)L->n_pairs);
     L->item_start = off; off = align256(off + sizeof(int32_t) * (size_t)(L->n_pairs + 1));
+    L->order = off; off = align256(off + sizeof(int32_t) * (size_t)(L->n_pairs + 1));
+    L->lvl = off; off = align256(off + sizeof(int32_t) * 2 * (size_t)(kLevelCap + 2));
     L->prod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
     L->cons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
     L->done = off; off = align256(off + sizeof(long long) * (size_t)L->nwords);
@@ -231,12 +250,17 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         L->bgrid = sms * L->binfo.blocks_per_sm;
         if (o.grid_ctas > 0 && o.grid_ctas < L->bgrid) L->bgrid = o.grid_ctas;
         L->bnwarps = L->bgrid * (L->binfo.threads / 32);
-        L->bnslot = L->bnwarps + 64;
+        const int64_t bnslot_sm = L->n_pairs + L->bnwarps + 64;
+        L->strip_major = allow_sm && bnslot_sm <= (int64_t)INT32_MAX / 2 &&
+                         (double)bnslot_sm * (double)wfull * (double)(o.order + 1) * 4.0 <=
+                             kStripMajorBudget;
+        L->bnslot = L->strip_major ? (int)bnslot_sm : L->bnwarps + 64;
         int64_t bw = 2 * o.max_len / L->bnwarps + 64;
         if (bw < 256) bw = 256;
         if (bw > o.max_len) bw = o.max_len;
         bw = (bw + 31) & ~(int64_t)31;
         if (bw < 32) bw = 32;
+        if (L->strip_major) bw = wfull < 32 ? 32 : wfull;
         L->bwcols = (int)bw;
         // forward seams of every strip boundary: (strips - 1) x swept columns
         const int64_t strips = (o.max_len + 31) / 32;
@@ -264,6 +288,8 @@ struct Header {
     int bwd_item_counter;
     int pad;
     unsigned long long counters[4];
+    int sched[4];  // schedule: mode, n_levels, n_items (Schedule::hdr)
+    long long diag[3];  // first timed-out wait: address, target, value seen
 };
 
 // ---------------------------------------------------------------------------
@@ -290,6 +316,10 @@ struct PlanArgs {
     const int32_t* sY;
     PairDesc* pairs;
     int32_t* item_start;
+    int32_t* order;     // strip-major schedule: pairs by decreasing strip count
+    int32_t* lvl;       // level starts [lvl_cap + 2], then a scratch of the same size
+    int lvl_cap;        // largest strip count the level arrays hold
+    int allow_sm;       // strip-major allowed (the seam ring holds whole strips)
     unsigned long long* prod;
     unsigned long long* cons;
     long long* done;
@@ -350,6 +380,7 @@ __device__ void block_exclusive_scan(const int64_t* v, int64_t n, int64_t* out, 
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
     __shared__ int64_t sh[kPlanThreads];
     __shared__ int bad;
+    __shared__ int max_strips;
     const int t = threadIdx.x;
     const bool self = (A.op == SIGK_OP_GRAM && A.n_y == 0);
     if (A.phase & 1) {
@@ -502,9 +533,90 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         }
         if (t == kPlanThreads - 1) {
             if (sh[t] > (int64_t)INT32_MAX) atomicCAS(&A.hdr->status, 0, kErrLength);
+            // training: one progress word per item
+            if (A.train && sh[t] > (int64_t)A.nslot) atomicCAS(&A.hdr->status, 0, kErrWorkspace);
             A.item_start[n] = (int32_t)sh[t];
         }
     }
+    // schedule.  With at most lvl_cap strips per pair the pairs are sorted by
+    // decreasing strip count (counting sort).  Strip-major (mode 1) when it is
+    // allowed and the strip counts are even (the longest pair has at most
+    // twice the mean): level l holds strip l of every pair that has one.
+    // Otherwise pair-major over the sorted pairs (mode 2): the pairs with the
+    // longest chains of strips start first.  Beyond lvl_cap: pair-major in
+    // index order (mode 0).
+    if (t == 0) max_strips = 0;
+    __syncthreads();
+    {
+        int mx = 0;
+        for (int64_t p = t; p < A.n_pairs; p += kPlanThreads) mx = max(mx, A.pairs[p].n_strips);
+        atomicMax(&max_strips, mx);
+    }
+    __syncthreads();
+    const int ms = max_strips;
+    if (ms > 0 && ms <= A.lvl_cap) {
+        int32_t* lvl = A.lvl;
+        int32_t* cur = A.lvl + A.lvl_cap + 2;
+        for (int i = t; i <= ms + 1; i += kPlanThreads) cur[i] = 0;
+        __syncthreads();
+        for (int64_t p = t; p < A.n_pairs; p += kPlanThreads) {
+            const int n = A.pairs[p].n_strips;
+            if (n > 0) atomicAdd(&cur[n], 1);
+        }
+        __syncthreads();
+        if (t == 0) {
+            int above = 0;  // cur[n] := pairs with more than n strips
+            for (int n = ms; n >= 0; --n) {
+                const int h = cur[n];
+                cur[n] = above;
+                above += h;
+            }
+            int run = 0;
+            for (int l = 0; l < ms; ++l) {
+                lvl[l] = run;
+                run += cur[l];
+            }
+            lvl[ms] = run;
+            const int active = cur[0];  // pairs with at least one strip
+            const bool even = (int64_t)ms * active <= 2 * (int64_t)run;
+            A.hdr->sched[0] = (A.allow_sm && even) ? 1 : 2;
+            A.hdr->sched[1] = (A.allow_sm && even) ? ms : active;
+            A.hdr->sched[2] = run;
+        }
+        __syncthreads();
+        for (int64_t p = t; p < A.n_pairs; p += kPlanThreads) {
+            const int n = A.pairs[p].n_strips;
+            if (n > 0) A.order[atomicAdd(&cur[n], 1)] = (int32_t)p;
+        }
+        __syncthreads();
+        if (A.hdr->sched[0] == 2) {
+            // item_start over the sorted pairs
+            const int64_t n = A.hdr->sched[1];
+            const int64_t chunk = (n + kPlanThreads - 1) / kPlanThreads;
+            const int64_t b0 = t * chunk, b1 = (b0 + chunk < n) ? b0 + chunk : n;
+            int64_t sum = 0;
+            for (int64_t i = b0; i < b1; ++i) sum += A.pairs[A.order[i]].n_strips;
+            sh[t] = sum;
+            __syncthreads();
+            for (int o = 1; o < kPlanThreads; o <<= 1) {
+                int64_t add = (t >= o) ? sh[t - o] : 0;
+                __syncthreads();
+                sh[t] += add;
+                __syncthreads();
+            }
+            int64_t run = sh[t] - sum;
+            for (int64_t i = b0; i < b1; ++i) {
+                A.item_start[i] = (int32_t)run;
+                run += A.pairs[A.order[i]].n_strips;
+            }
+            if (t == kPlanThreads - 1) A.item_start[n] = (int32_t)sh[t];
+        }
+    } else if (t == 0) {
+        A.hdr->sched[0] = 0;
+        A.hdr->sched[1] = 0;
+        A.hdr->sched[2] = A.item_start[A.n_pairs];
+    }
+    __syncthreads();
     // reset the seam synchronisation words and the work counter
     for (int i = t; i < A.nslot; i += kPlanThreads) {
         A.prod[i] = 0ull;
@@ -724,10 +836,10 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
                               const float* Y, const int64_t* len_y, int64_t n_y, int d,
                               double* out, int64_t out_ld, void* ws, size_t ws_bytes,
                               cudaStream_t stream, const Opts& o, Layout* Lout,
-                              const TrainArgs* tr = nullptr) {
+                              const TrainArgs* tr = nullptr, bool allow_sm = true) {
     Layout L;
     const bool train = tr != nullptr;
-    sigk_status st = make_layout(op, n_x, n_y, d, o, &L, train);
+    sigk_status st = make_layout(op, n_x, n_y, d, o, &L, train, allow_sm);
     if (st != SIGK_OK) return st;
     if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
     char* base = (char*)ws;
@@ -751,6 +863,10 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     pa.oy = (int64_t*)(base + L.oy);
     pa.pairs = (PairDesc*)(base + L.pairs);
     pa.item_start = (int32_t*)(base + L.item_start);
+    pa.order = (int32_t*)(base + L.order);
+    pa.lvl = (int32_t*)(base + L.lvl);
+    pa.lvl_cap = kLevelCap;
+    pa.allow_sm = L.strip_major ? 1 : 0;
     pa.prod = (unsigned long long*)(base + L.prod);
     pa.cons = (unsigned long long*)(base + L.cons);
     pa.done = (long long*)(base + L.done);
@@ -777,7 +893,11 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     SolverArgs sa;
     memset(&sa, 0, sizeof(sa));
     sa.pairs = pa.pairs;
-    sa.item_start = pa.item_start;
+    sa.sched.hdr = hdr->sched;
+    sa.sched.item_start = pa.item_start;
+    sa.sched.order = pa.order;
+    sa.sched.level_start = pa.lvl;
+    sa.sched.n_pairs = (int32_t)L.n_pairs;
     sa.n_pairs = (int32_t)L.n_pairs;
     sa.inc_mode = pa.inc_mode;
     sa.d = d;
@@ -809,7 +929,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         BwdArgs ba;
         memset(&ba, 0, sizeof(ba));
         ba.pairs = pa.pairs;
-        ba.item_start = pa.item_start;
+        ba.sched = sa.sched;
         ba.n_pairs = (int32_t)L.n_pairs;
         ba.inc_mode = pa.inc_mode;
         ba.d = d;
@@ -983,7 +1103,11 @@ static cudaError_t launch_stats(const PlanArgs& pa, double* stats, size_t stats_
     if ((e = cudaMemsetAsync(&pa.hdr->item_counter, 0, sizeof(int), s)) != cudaSuccess) return e;
     StatArgs sa;
     sa.pairs = pa.pairs;
-    sa.item_start = pa.item_start;
+    sa.sched.hdr = pa.hdr->sched;
+    sa.sched.item_start = pa.item_start;
+    sa.sched.order = pa.order;
+    sa.sched.level_start = pa.lvl;
+    sa.sched.n_pairs = (int32_t)pa.n_pairs;
     sa.n_pairs = (int32_t)pa.n_pairs;
     sa.rows_per_strip = pa.rows_per_strip;
     sa.d = pa.d;
@@ -1042,6 +1166,10 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     pa.oy = (int64_t*)(base + L.oy);
     pa.pairs = (PairDesc*)(base + L.pairs);
     pa.item_start = (int32_t*)(base + L.item_start);
+    pa.order = (int32_t*)(base + L.order);
+    pa.lvl = (int32_t*)(base + L.lvl);
+    pa.lvl_cap = kLevelCap;
+    pa.allow_sm = L.strip_major ? 1 : 0;
     pa.prod = (unsigned long long*)(base + L.prod);
     pa.cons = (unsigned long long*)(base + L.cons);
     pa.done = (long long*)(base + L.done);
@@ -1213,16 +1341,24 @@ extern "C" sigk_status sigk_pairs_static(const float* X, const int64_t* len_x, c
     Opts o;
     if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
     if (n_pairs == 0) return SIGK_OK;
-    // Fit the layout into the static scratch: first with the requested grid,
-    // then with one CTA per SM (fewer warps, smaller seam ring).
+    // Fit the layout into the static scratch: first as sigk_pairs would, then
+    // with the pair-major schedule (a smaller seam ring), then also with one
+    // CTA per SM (fewer warps).
     Layout L;
+    bool sm = true;
     if ((st = make_layout(SIGK_OP_PAIRS, n_pairs, n_pairs, d, o, &L)) != SIGK_OK) return st;
+    if (L.total > kStaticWsBytes) {
+        sm = false;
+        if ((st = make_layout(SIGK_OP_PAIRS, n_pairs, n_pairs, d, o, &L, false, false)) != SIGK_OK)
+            return st;
+    }
     if (L.total > kStaticWsBytes) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         o.grid_ctas = sms > 0 ? sms : 1;
-        if ((st = make_layout(SIGK_OP_PAIRS, n_pairs, n_pairs, d, o, &L)) != SIGK_OK) return st;
+        if ((st = make_layout(SIGK_OP_PAIRS, n_pairs, n_pairs, d, o, &L, false, false)) != SIGK_OK)
+            return st;
     }
     if (L.total > kStaticWsBytes)
         return fail(SIGK_ERR_WORKSPACE,
@@ -1232,7 +1368,7 @@ extern "C" sigk_status sigk_pairs_static(const float* X, const int64_t* len_x, c
     void* ws = nullptr;
     if ((st = static_ws_ptr(&ws)) != SIGK_OK) return st;
     return run_solver(SIGK_OP_PAIRS, X, len_x, n_pairs, Y, len_y, n_pairs, d, k_out, 0, ws,
-                      kStaticWsBytes, (cudaStream_t)stream, o, nullptr);
+                      kStaticWsBytes, (cudaStream_t)stream, o, nullptr, nullptr, sm);
 }
 
 extern "C" sigk_status sigk_static_sync_status(void* stream) {

@@ -62,9 +62,68 @@ struct PairDesc {
     float* gyr;        // gradient rows of the swept path (backward), or null
 };
 
+// Work schedule written by the planner (three ints in the workspace header):
+// [0] mode, [1] n_levels (mode 1) or sorted pairs (mode 2), [2] n_items.
+//   mode 0, pair-major in index order: the strips of a pair are consecutive
+//     items (item_start prefix sums over the pairs); a strip consumes the seam
+//     of item - 1.
+//   mode 1, strip-major: level l holds strip l of every pair that has one,
+//     pairs ordered by decreasing strip count (order[]); level_start[l] is
+//     the first item of level l.  A strip's producer is a whole level earlier,
+//     so a consumer rarely waits.  Used when the strip counts are even.
+//   mode 2, pair-major over order[]: item_start holds the prefix sums in that
+//     order, so the pairs with the longest chains of strips start first.
+struct Schedule {
+    const int* hdr;                // mode, n_levels / sorted pairs, n_items
+    const int32_t* item_start;     // modes 0, 2: [pairs + 1] prefix sums of n_strips
+    const int32_t* order;          // modes 1, 2: pairs by decreasing strip count
+    const int32_t* level_start;    // mode 1: [n_levels + 1]
+    int32_t n_pairs;
+};
+
+struct ItemRef {
+    int pair;   // index into the pair table
+    int k;      // position of the strip in the pair's sequence (0 first)
+    int prev;   // item that produces this strip's incoming seam, or -1
+    int next;   // item that consumes this strip's outgoing seam, or -1
+};
+
+// Largest i in [0, n) with v[i] <= x (v non-decreasing, v[0] <= x).
+__device__ __forceinline__ int upper_index(const int32_t* v, int n, int x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (v[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ ItemRef decode_item(const Schedule& S, const PairDesc* pairs, int item) {
+    ItemRef r;
+    if (S.hdr[0] == 1) {
+        const int nl = S.hdr[1];
+        const int l = upper_index(S.level_start, nl, item);
+        const int rank = item - S.level_start[l];
+        r.pair = S.order[rank];
+        r.k = l;
+        r.prev = l > 0 ? S.level_start[l - 1] + rank : -1;
+        r.next = (l + 1 < nl && rank < S.level_start[l + 2] - S.level_start[l + 1])
+                     ? S.level_start[l + 1] + rank : -1;
+    } else {
+        const bool sorted = S.hdr[0] == 2;
+        const int q = upper_index(S.item_start, sorted ? S.hdr[1] : S.n_pairs, item);
+        const int p = sorted ? S.order[q] : q;
+        r.pair = p;
+        r.k = item - S.item_start[q];
+        r.prev = r.k > 0 ? item - 1 : -1;
+        r.next = r.k + 1 < pairs[p].n_strips ? item + 1 : -1;
+    }
+    return r;
+}
+
 struct SolverArgs {
     const PairDesc* pairs;
-    const int32_t* item_start;     // [n_pairs + 1] prefix sums of n_strips
+    Schedule sched;
     int32_t n_pairs;
     int32_t inc_mode;              // rows of xr/yr are increments (else points)
     int32_t d;
@@ -114,6 +173,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// First time-out of a launch: the status word, then (for diagnosis) the
+// waited-on address, the target and the value last seen, as three 64-bit
+// words at byte 64 of the status word's 256-byte header.
+__device__ __forceinline__ void record_timeout(int* status, const void* p, long long target,
+                                               long long seen) {
+    if (atomicCAS(status, 0, kErrTimeout) == 0) {
+        long long* diag = reinterpret_cast<long long*>(status + 16);
+        diag[0] = (long long)(uintptr_t)p;
+        diag[1] = target;
+        diag[2] = seen;
+    }
+}
+
 // Bounded wait until *p >= target.  Gives up after ~4 s of wall time (or a
 // hard iteration cap), or as soon as another warp has recorded an error; on
 // time-out it records kErrTimeout.  Returns true when the condition holds.
@@ -132,7 +204,7 @@ __device__ __forceinline__ bool wait_ge_u64(const unsigned long long* p,
             if (global_ns() - t0 > kWaitNs) break;
         }
     }
-    atomicCAS(status, 0, kErrTimeout);
+    record_timeout(status, p, (long long)target, (long long)ld_acquire_u64(p));
     return false;
 }
 
@@ -147,8 +219,21 @@ __device__ __forceinline__ bool wait_ge_s64(const long long* p, long long target
             if (global_ns() - t0 > kWaitNs) break;
         }
     }
-    atomicCAS(status, 0, kErrTimeout);
+    record_timeout(status, p, target, ld_acquire_s64(p));
     return false;
+}
+
+// Before item writes seam slot item % nslot: the slot's previous user u =
+// item - nslot must have been read completely by u's consumer.  Lane 0 waits
+// (bounded); the result is broadcast to the warp.
+__device__ __forceinline__ bool wait_slot_free(const Schedule& S, const PairDesc* pairs, int item,
+                                               int nslot, const long long* done, int* status) {
+    bool ok = true;
+    if ((threadIdx.x & 31) == 0 && item >= nslot) {
+        const int c = decode_item(S, pairs, item - nslot).next;
+        if (c >= 0) ok = wait_ge_s64(&done[c % nslot], (long long)c, status);
+    }
+    return __shfl_sync(kFull, ok, 0);
 }
 
 // 2^n as a float for n <= 0 (0 below the normal range).

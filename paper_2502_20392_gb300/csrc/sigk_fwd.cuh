@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
     float* dyw = smem + warp * FwdSmem<P, D>::per_warp;  // 64-column ring of dy
     float* sin_ = dyw + 64 * DS;                        // seam-in block
     float* sout = sin_ + kG * S;                        // seam-out block
-    const int n_items = A.item_start[A.n_pairs];
+    const int n_items = A.sched.hdr[2];
     unsigned long long tiles_done = 0, lane_tiles = 0;
 
     for (;;) {
@@ -82,18 +82,14 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
         item = __shfl_sync(kFull, item, 0);
         if (item >= n_items) break;
         if (ld_volatile_s32(A.status) != 0) break;
-        // locate the pair: largest p with item_start[p] <= item
-        int lo_p = 0, hi_p = A.n_pairs - 1;
-        while (lo_p < hi_p) {
-            int mid = (lo_p + hi_p + 1) >> 1;
-            if (A.item_start[mid] <= item) lo_p = mid; else hi_p = mid - 1;
-        }
+        const ItemRef ir = decode_item(A.sched, A.pairs, item);
+        const int lo_p = ir.pair;
         const PairDesc pd = A.pairs[lo_p];
-        const int s = item - A.item_start[lo_p];
+        const int s = ir.k;
         const int L1 = pd.L1, L2 = pd.L2;
-        const bool has_in = s > 0;
-        const bool has_out = s + 1 < pd.n_strips;
-        const int slot_in = (item - 1 + A.nslot) % A.nslot;
+        const bool has_in = ir.prev >= 0;
+        const bool has_out = ir.next >= 0;
+        const int slot_in = has_in ? ir.prev % A.nslot : 0;
         const int slot_out = item % A.nslot;
         const int i0 = s * 32 * R;
         const bool train = A.store != nullptr;
@@ -125,17 +121,10 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
 
         // progress words: per slot (inference) or per item (training, where
         // the seams are not reused and a slot's word could be overtaken)
-        const int pw_in = train ? item - 1 : slot_in;
+        const int pw_in = train ? ir.prev : slot_in;
         const int pw_out = train ? item : slot_out;
         // the slot we write must have been read by its previous consumer
-        if (has_out && !train) {
-            const long long prev_consumer = (long long)item - A.nslot + 1;
-            bool okl = true;
-            if (lane == 0)
-                okl = wait_ge_s64(&A.done[((prev_consumer % A.nslot) + A.nslot) % A.nslot],
-                                  prev_consumer, A.status);
-            ok = __shfl_sync(kFull, okl, 0);
-        }
+        if (has_out && !train) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
         const int T = L2 + 31;
         for (int t = 0; t < T && ok; ++t) {
             if ((t & 31) == 0 && t < L2) {
@@ -149,7 +138,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                 }
                 if (has_in) {
                     const unsigned long long need =
-                        ((unsigned long long)(item - 1) << 32) | (unsigned)(t + nb);
+                        ((unsigned long long)ir.prev << 32) | (unsigned)(t + nb);
                     bool okl = true;
                     if (lane == 0) okl = wait_ge_u64(&A.prod[pw_in], need, A.status);
                     ok = __shfl_sync(kFull, okl, 0);
@@ -275,7 +264,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                 const int start = jj & ~31;
                 const int nb = jj - start + 1;
                 if (!train && start + nb > A.wcols) {
-                    const unsigned long long need = ((unsigned long long)(item + 1) << 32) |
+                    const unsigned long long need = ((unsigned long long)ir.next << 32) |
                                                     (unsigned)(start + nb - A.wcols);
                     bool okl = true;
                     if (lane == 0) okl = wait_ge_u64(&A.cons[slot_out], need, A.status);

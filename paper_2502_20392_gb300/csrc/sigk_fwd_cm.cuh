@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
     T* sout = sin_ + kG * S;         // seam-out block
     T* cst = cscratch + (size_t)gwarp * cstride;  // this warp's strip [L2][32]
     T* seam = reinterpret_cast<T*>(A.seam);
-    const int n_items = A.item_start[A.n_pairs];
+    const int n_items = A.sched.hdr[2];
     const int d = A.d;
     unsigned long long tiles_done = 0, lane_tiles = 0;
 
@@ -71,17 +71,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         item = __shfl_sync(kFull, item, 0);
         if (item >= n_items) break;
         if (ld_volatile_s32(A.status) != 0) break;
-        int lo_p = 0, hi_p = A.n_pairs - 1;
-        while (lo_p < hi_p) {
-            int mid = (lo_p + hi_p + 1) >> 1;
-            if (A.item_start[mid] <= item) lo_p = mid; else hi_p = mid - 1;
-        }
+        const ItemRef ir = decode_item(A.sched, A.pairs, item);
+        const int lo_p = ir.pair;
         const PairDesc pd = A.pairs[lo_p];
-        const int s = item - A.item_start[lo_p];
+        const int s = ir.k;
         const int L1 = pd.L1, L2 = pd.L2;
-        const bool has_in = s > 0;
-        const bool has_out = s + 1 < pd.n_strips;
-        const int slot_in = (item - 1 + A.nslot) % A.nslot;
+        const bool has_in = ir.prev >= 0;
+        const bool has_out = ir.next >= 0;
+        const int slot_in = has_in ? ir.prev % A.nslot : 0;
         const int slot_out = item % A.nslot;
         const int i0 = s * 32;
         bool ok = true;
@@ -180,16 +177,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         int oE = 0;
         const bool train = F32 && A.store != nullptr;
         T* st_pair = train ? reinterpret_cast<T*>(A.store) + A.store_off[lo_p] : nullptr;
-        const int pw_in = train ? item - 1 : slot_in;
+        const int pw_in = train ? ir.prev : slot_in;
         const int pw_out = train ? item : slot_out;
-        if (has_out && !train) {
-            const long long prev_consumer = (long long)item - A.nslot + 1;
-            bool okl = true;
-            if (lane == 0)
-                okl = wait_ge_s64(&A.done[((prev_consumer % A.nslot) + A.nslot) % A.nslot],
-                                  prev_consumer, A.status);
-            ok = __shfl_sync(kFull, okl, 0);
-        }
+        if (has_out && !train) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
         constexpr int NV = 32 * (int)sizeof(T) / 16;  // 16-byte vectors per strip column
         const int Tn = L2 + 31;
         const bool has_row = i0 + lane < L1;
@@ -204,7 +194,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                 }
                 if (has_in) {
                     const unsigned long long need =
-                        ((unsigned long long)(item - 1) << 32) | (unsigned)(t + nb);
+                        ((unsigned long long)ir.prev << 32) | (unsigned)(t + nb);
                     bool okl = true;
                     if (lane == 0) okl = wait_ge_u64(&A.prod[pw_in], need, A.status);
                     ok = __shfl_sync(kFull, okl, 0);
@@ -328,7 +318,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                 const int start = jj & ~31;
                 const int nb = jj - start + 1;
                 if (!train && start + nb > A.wcols) {
-                    const unsigned long long need = ((unsigned long long)(item + 1) << 32) |
+                    const unsigned long long need = ((unsigned long long)ir.next << 32) |
                                                     (unsigned)(start + nb - A.wcols);
                     bool okl = true;
                     if (lane == 0) okl = wait_ge_u64(&A.cons[slot_out], need, A.status);

@@ -28,7 +28,7 @@ constexpr int kStKC = 32;  // contraction chunk
 
 struct StatArgs {
     const PairDesc* pairs;
-    const int32_t* item_start;  // items of rows_per_strip rows
+    Schedule sched;             // items of rows_per_strip rows (any order)
     int32_t n_pairs;
     int32_t rows_per_strip;
     int32_t d;
@@ -56,21 +56,18 @@ __global__ void __launch_bounds__(128) pair_stats_kernel(StatArgs A) {
     float* dys = dxs + kStKC * 36;                // [32][KC+1]: columns x dims
     float* bs = dys + 32 * (kStKC + 1);           // [KC]: x_{i0} - x_0, this chunk
     float* base = A.base + (size_t)gwarp * A.d;
-    const int n_items = A.item_start[A.n_pairs];
+    const int n_items = A.sched.hdr[2];
     const int d = A.d;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(A.item_counter, 1);
         item = __shfl_sync(kFull, item, 0);
         if (item >= n_items) break;
-        int lo_p = 0, hi_p = A.n_pairs - 1;
-        while (lo_p < hi_p) {
-            int mid = (lo_p + hi_p + 1) >> 1;
-            if (A.item_start[mid] <= item) lo_p = mid; else hi_p = mid - 1;
-        }
+        const ItemRef ir = decode_item(A.sched, A.pairs, item);
+        const int lo_p = ir.pair;
         const PairDesc pd = A.pairs[lo_p];
         const int L1 = pd.L1, L2 = pd.L2;
-        const int s = item - A.item_start[lo_p];
+        const int s = ir.k;
         float mloc = 0.0f, ca = 0.0f, cb = 0.0f;
         float rs[8];
 #pragma unroll

@@ -185,3 +185,17 @@ def test_gradient_with_refinement(S, orc):
     gy_ref = fd_points(f, xs, 1, range(xs[1].size))
     np.testing.assert_allclose(gX.cpu().numpy().ravel(), gx_ref, atol=1e-4 * np.abs(gx_ref).max())
     np.testing.assert_allclose(gY.cpu().numpy().ravel(), gy_ref, atol=1e-4 * np.abs(gy_ref).max())
+
+
+def test_backward_schedules_agree_bitwise(S):
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(5, [300, 1, 90, 500, 47], 8, 1.0, seed=93)
+    Xd, ld = torch.from_numpy(pts).to(dev()), torch.from_numpy(lens).to(dev())
+    W = torch.from_numpy(np.random.default_rng(5).standard_normal((5, 5)))
+    o1 = S.Opts(order=8, rings=4, max_len=512)
+    o2 = S.Opts(order=8, rings=4, max_len=512, flags=S.FLAG_PAIR_MAJOR)
+    g1, _, G1 = S.backward(S.OP_GRAM, Xd, ld, None, None, W, o1)
+    g2, _, G2 = S.backward(S.OP_GRAM, Xd, ld, None, None, W, o2)
+    assert torch.equal(G1, G2)
+    # gradients accumulate with float atomics: equal up to summation order
+    torch.testing.assert_close(g1, g2, rtol=1e-5, atol=1e-6 * float(g1.abs().max()))

@@ -277,3 +277,32 @@ def test_fp64_rejected_by_backward(S):
     with pytest.raises(S.SigkError):
         S.backward(S.OP_GRAM, Xd, ld, None, None, torch.ones((2, 2), dtype=torch.float64),
                    S.Opts(flags=S.FLAG_FP64, max_len=16))
+
+
+def test_schedules_agree_bitwise(S):
+    # strip-major (default) and pair-major schedules run the same arithmetic
+    # per tile: the results must be identical, on ragged lengths with a
+    # one-point path, long row paths (many strips) and refinement
+    from paper_2502_20392_gb300 import synth
+    segs = [700, 1, 33, 257, 1200, 64, 5, 400]
+    pts, lens = synth.brownian(len(segs), segs, 8, 1.5, seed=90)
+    X, L = to_dev(pts, lens)
+    for o in (S.Opts(order=8, rings=4, max_len=1300), S.Opts(order=12, rings=6, refine_c=0.5, max_len=8000)):
+        G1 = S.gram(X, L, opts=o).cpu().numpy()
+        o2 = S.Opts(order=o.order, rings=o.rings, refine_c=o.refine_c, max_len=o.max_len,
+                    flags=S.FLAG_PAIR_MAJOR)
+        G2 = S.gram(X, L, opts=o2).cpu().numpy()
+        assert np.array_equal(G1, G2)
+    # even strip counts (the strip-major schedule) against pair-major
+    pts, lens = synth.brownian(12, 300, 8, 1.5, seed=92)
+    X, L = to_dev(pts, lens)
+    o = S.Opts(order=8, rings=4, max_len=320)
+    G1 = S.gram(X, L, opts=o).cpu().numpy()
+    G2 = S.gram(X, L, opts=S.Opts(order=8, rings=4, max_len=320, flags=S.FLAG_PAIR_MAJOR)).cpu().numpy()
+    assert np.array_equal(G1, G2)
+    (Xp, lxp), (Yp, lyp) = synth.ragged_pairs(9, 1, 600, 40, 0.5, 2.0, seed=91)
+    o = S.Opts(order=10, rings=5, max_len=700)
+    k1 = S.pairs(*to_dev(Xp, lxp), *to_dev(Yp, lyp), opts=o).cpu().numpy()
+    o2 = S.Opts(order=10, rings=5, max_len=700, flags=S.FLAG_PAIR_MAJOR)
+    k2 = S.pairs(*to_dev(Xp, lxp), *to_dev(Yp, lyp), opts=o2).cpu().numpy()
+    assert np.array_equal(k1, k2)
