@@ -55,7 +55,9 @@ struct BwdSmem {
     static constexpr int S = P + 4;   // record / forward seam entry
     static constexpr int SA = P + 1;  // adjoint seam entry: corner, b1..bP
     static constexpr int DS = DyStride<D>::value;
-    static constexpr int per_warp = 64 * DS + 32 * S + 2 * 32 * SA + 64 * D;
+    // dy ring, two record blocks (the first doubles as pass A's seam-in
+    // block), adjoint seam in/out blocks, column gradients, two mbarriers
+    static constexpr int per_warp = 64 * DS + 2 * 32 * S + 2 * 32 * SA + 64 * D + 4;
 };
 
 __device__ __forceinline__ float exp2_nonneg(int n) {
@@ -108,12 +110,25 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
     float* dyw = smem + warp * BwdSmem<P, D>::per_warp;  // 64-column ring of dy
     float* sin_ = dyw + 64 * DS;                        // forward seam-in block
-    float* ain = sin_ + 32 * S;                         // adjoint seam-in block
+    float* rbuf1 = sin_ + 32 * S;                       // second record block
+    float* ain = rbuf1 + 32 * S;                        // adjoint seam-in block
     float* aout = ain + 32 * SA;                        // adjoint seam-out block
     float* colacc = aout + 32 * SA;                     // 64 x D column gradient
+    uint64_t* bars = reinterpret_cast<uint64_t*>(colacc + 64 * D);  // record-load mbarriers
     float* rec = A.rec + (size_t)gwarp * A.rec_stride;
     const int n_items = A.sched.hdr[2];
     unsigned long long tiles = 0;
+    // pass B reads the record block of one pass-A step per step, prefetched
+    // two steps ahead by bulk copies into sin_ / rbuf1 (load n uses buffer
+    // n & 1, barrier phase (n >> 1) & 1; n counts this warp's loads)
+    if (lane == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    unsigned nld = 0;
+    constexpr uint32_t kRecBytes = 32 * S * (uint32_t)sizeof(float);
 
     for (;;) {
         int item = 0;
@@ -261,7 +276,23 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
 #pragma unroll
         for (int q = 0; q <= P; ++q) oBb[q] = 0.0f;
         const int lp = 31 - lane;
+        // the records were written with generic stores: order them (and pass
+        // A's use of sin_) before the bulk copies read them
+        fence_proxy_async_global();
+        fence_proxy_async_smem();
         __syncwarp();
+        const unsigned base = nld;
+        unsigned issued = 0, waited = 0;
+        auto rbuf = [&](unsigned n) { return (n & 1) ? rbuf1 : sin_; };
+        // pass-A step of reverse step tp: every active lane reads t = L2 + 30 - tp
+        auto rec_block = [&](int tp) { return rec + (size_t)(L2 + 30 - tp) * S * 32; };
+        if (ok) {
+            const unsigned first = T < 2 ? (unsigned)T : 2u;
+            if (lane == 0)
+                for (unsigned q = 0; q < first; ++q)
+                    bulk_load(rbuf(base + q), rec_block((int)q), kRecBytes, &bars[(base + q) & 1]);
+            issued = first;
+        }
         for (int tp = 0; tp < T && ok; ++tp) {
             if ((tp & 31) == 0 && tp < L2) {
                 const int nb = min(32, L2 - tp);
@@ -290,6 +321,30 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 __syncwarp();
                 if (!ok) break;
             }
+            // this step's record block
+            float rhi, rb[P + 1], rb1lo;
+            int rexp;
+            {
+                const unsigned n = base + (unsigned)tp;
+                const bool got = mbar_wait(&bars[n & 1], (n >> 1) & 1, A.status);
+                waited = (unsigned)tp + 1;
+                if (!__all_sync(kFull, got)) {
+                    ok = false;
+                    break;
+                }
+                const float* r = rbuf(n) + lane;
+                rhi = r[0];
+                rb1lo = r[64];
+                rb[0] = 0.0f;
+#pragma unroll
+                for (int q = 1; q <= P; ++q) rb[q] = r[(2 + q) * 32];
+                rexp = __float_as_int(r[(P + 3) * 32]);
+                __syncwarp();
+                if (tp + 2 < T) {
+                    if (lane == 0) bulk_load(rbuf(n + 2), rec_block(tp + 2), kRecBytes, &bars[n & 1]);
+                    issued = (unsigned)tp + 3;
+                }
+            }
             // adjoint of the right edge: from lane+1, or seam / seed for lane 31
             float B0 = __shfl_down_sync(kFull, oB0, 1);
             float Bb[P + 1];
@@ -311,17 +366,14 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
             }
             const int jr = tp - lp;
             if (jr >= 0 && jr < L2) {
-                const int j = L2 - 1 - jr;
-                const int t = j + lane;  // pass-A step of this record
-                const float* r = rec + (size_t)t * S * 32 + lane;
-                float hi = r[0];
+                float hi = rhi;
                 float b[P + 1];
                 b[0] = 0.0f;
 #pragma unroll
-                for (int q = 1; q <= P; ++q) b[q] = r[(2 + q) * 32];
-                b[1] += r[64];  // first-order term as one float
+                for (int q = 1; q <= P; ++q) b[q] = rb[q];
+                b[1] += rb1lo;  // first-order term as one float
                 int F, Eb, bump;
-                unpack_exp(__float_as_int(r[(P + 3) * 32]), F, Eb, bump);
+                unpack_exp(rexp, F, Eb, bump);
                 const int Em = F > Eb ? F : Eb;
                 if (bump) {  // undo the renormalisation after this tile
                     const float up = 1.8446744e19f, dn = 5.421011e-20f;
@@ -432,6 +484,14 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 __syncwarp();
             }
         }
+        // record loads still in flight after an early exit: wait for them so
+        // the barrier phases and buffers stay consistent
+        for (unsigned q = waited; q < issued; ++q) {
+            const unsigned n = base + q;
+            mbar_wait(&bars[n & 1], (n >> 1) & 1, A.status);
+        }
+        nld = base + issued;
+        __syncwarp();
         if (has_row) add_inc_grad<D>(pd.gxr, row, A.d, A.inc_mode, pd.sx, gx);
         __syncwarp();
         if (lane == 0) {
