@@ -91,7 +91,9 @@ enum {
  *          coefficient matrices, App. A.7); supported 4..16, rounded up to an
  *          even value.
  *   rings: number n of Neumann iterations per tile (powers of c_ij kept,
- *          Sec. 2.3 / App. B: the local Neumann iteration), 1 <= n <= min(order, 8).
+ *          Sec. 2.3 / App. B: the local Neumann iteration), 1 <= n <= min(order, 8);
+ *          rounded up to an even value (the ring count is compiled into the
+ *          kernels).
  *   flags: SIGK_FLAG_*.
  *   grid_ctas: persistent grid size (0 = occupancy-derived, one wave).
  *   max_len: upper bound on the segments of the path that a pair sweeps
@@ -204,12 +206,14 @@ sigk_status sigk_static_sync_status(void* stream);
 
 /* A-priori truncation choice (App. C.3: order search from the largest
  * coupling in the grid).  Runs the planner and a statistics kernel on the
- * device: per pair the sampled coupling C = max |<dx_i, y_J - y_0>| (the size
- * of the edge coefficients, a_p ~ C^p/(p!)^2) and the ring bounds
- * sum |c|^m <= (sum |dx|^m)(sum |dy|^m); then picks the smallest order P and
- * rings n with max(L1,L2) (1.25 C)^(P+1)/((P+1)!)^2 <= tol/10 and
- * sum|c|^(n+1)/((n+1)!)^2 <= tol/10.  If the Cauchy-Schwarz bound on a tile
- * exceeds 1 it also sets refine_c = 1 and plans the refined problem.
+ * device that forms every tile coefficient of the pair table (a strip
+ * micro-GEMM, nothing stored) and reduces them per pair to the largest |c|,
+ * the ring sums sum |c|^m (m = 2..9) and the couplings C = max over rows and
+ * columns of |<dx_i, y_J - y_0>| and |<x_I - x_0, dy_j>| (the size of the
+ * edge coefficients, a_p ~ C^p/(p!)^2); then picks the smallest order P and
+ * rings n (even) with max(L1,L2) C^(P+1)/((P+1)!)^2 <= tol/10 and
+ * sum|c|^(n+1)/((n+1)!)^2 <= tol/10.  If a tile has |c| > 1 or no order up
+ * to 16 fits, it sets refine_c = 1, 1/4, ... and plans the refined problem.
  * Synchronises `stream`.  Writes into *opts_out (other fields copied from
  * opts_in when given; max_len raised to the longest swept path, refined). */
 sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,

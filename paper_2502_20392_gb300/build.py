@@ -1,7 +1,7 @@
 """Builds libsigk.so in-tree (paper_2502_20392_gb300/_build/) with nvcc for
-sm_103a only.  One translation unit per edge degree P is compiled in
-parallel, then everything is linked into one shared library with a C ABI
-(include/sigk.h)."""
+sm_103a only.  One translation unit per (edge degree P, ring count NR) is
+compiled in parallel, then everything is linked into one shared library with
+a C ABI (include/sigk.h)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -15,6 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsigk.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ORDERS = (4, 6, 8, 10, 12, 14, 16)
+RINGS = (2, 4, 6, 8)
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
@@ -38,7 +39,10 @@ def _digest() -> str:
 def _units():
     units = [("sigk_capi", os.path.join(CSRC, "sigk_capi.cu"), [])]
     for P in ORDERS:
-        units.append((f"sigk_fwd_P{P}", os.path.join(CSRC, "sigk_fwd_inst.cu"), [f"-DSIGK_P={P}"]))
+        for NR in RINGS:
+            if NR <= P:
+                units.append((f"sigk_fwd_P{P}_R{NR}", os.path.join(CSRC, "sigk_fwd_inst.cu"),
+                              [f"-DSIGK_P={P}", f"-DSIGK_NR={NR}"]))
     for f in sorted(os.listdir(CSRC)):
         if f.endswith("_inst2.cu"):
             units.append((f[:-3], os.path.join(CSRC, f), []))

@@ -98,7 +98,7 @@ __device__ __forceinline__ void add_inc_grad(float* g, int64_t vrow, int d, int 
 
 constexpr int bwd_min_blocks(int P, int D) { return (P <= 8 && D <= 8) ? 4 : 3; }
 
-template <int P, int D>
+template <int P, int D, int NR>
 __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs A) {
     constexpr int S = P + 4;
     constexpr int SA = P + 1;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     c = fmaf(dx[4 * e4 + 2], v.z, c);
                     c = fmaf(dx[4 * e4 + 3], v.w, c);
                 }
-                tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, A.nr);
+                tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, NR);
                 int bump = 0;
                 if (fabsf(hi) > 1.8446744e19f) {
                     const float sc = 5.421011e-20f;
@@ -401,8 +401,8 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
 #pragma unroll
                 for (int e = 0; e < D; ++e) c = fmaf(dx[e], dy[e], c);
                 float ain_[P + 1], ha[P + 1];
-                tile_inverse_a<P>(c, a, hi, b, A.nr, ain_, ha);
-                const float cbar = tile_adjoint<P>(c, ain_, hi, b, ha, Ab, B0, Bb, A.nr);
+                tile_inverse_a<P>(c, a, hi, b, NR, ain_, ha);
+                const float cbar = tile_adjoint<P>(c, ain_, hi, b, ha, Ab, B0, Bb, NR);
                 // undo the alignment of this step
                 if (Eb < Em) {
                     const float dn = exp2_nonpos(Eb - Em), up = exp2_nonneg(Em - Eb);

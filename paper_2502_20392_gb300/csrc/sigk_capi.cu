@@ -69,6 +69,7 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
     r->order += (r->order & 1);
     int nrmax = r->order < kMaxRings ? r->order : kMaxRings;
     if (r->rings < 1 || r->rings > nrmax) return false;
+    r->rings += (r->rings & 1);  // compiled ring counts are even (nrmax is even)
     if (r->grid_ctas < 0 || r->max_len > (int64_t)INT32_MAX) return false;
     return true;
 }
@@ -80,47 +81,68 @@ static int dim_bucket(int d) {
     return d <= 4 ? 4 : (d <= 8 ? 8 : (d <= 16 ? 16 : (d <= kMaxDim ? 0 : -1)));
 }
 
-#define SIGK_DISPATCH_P(FN, ...)                 \
-    switch (P) {                                 \
-        case 4: return FN<4>(__VA_ARGS__);       \
-        case 6: return FN<6>(__VA_ARGS__);       \
-        case 8: return FN<8>(__VA_ARGS__);       \
-        case 10: return FN<10>(__VA_ARGS__);     \
-        case 12: return FN<12>(__VA_ARGS__);     \
-        case 14: return FN<14>(__VA_ARGS__);     \
-        case 16: return FN<16>(__VA_ARGS__);     \
-        default: break;                          \
+// (edge degree P, ring count NR) pairs compiled: P even in 4..16, NR even in
+// 2..min(P, 8).  Requested ring counts are rounded up to even.
+#define SIGK_DISPATCH_PNR(FN, ...)                  \
+    switch (P * 16 + NR) {                          \
+        case 66: return FN<4, 2>(__VA_ARGS__); \
+        case 68: return FN<4, 4>(__VA_ARGS__); \
+        case 98: return FN<6, 2>(__VA_ARGS__); \
+        case 100: return FN<6, 4>(__VA_ARGS__); \
+        case 102: return FN<6, 6>(__VA_ARGS__); \
+        case 130: return FN<8, 2>(__VA_ARGS__); \
+        case 132: return FN<8, 4>(__VA_ARGS__); \
+        case 134: return FN<8, 6>(__VA_ARGS__); \
+        case 136: return FN<8, 8>(__VA_ARGS__); \
+        case 162: return FN<10, 2>(__VA_ARGS__); \
+        case 164: return FN<10, 4>(__VA_ARGS__); \
+        case 166: return FN<10, 6>(__VA_ARGS__); \
+        case 168: return FN<10, 8>(__VA_ARGS__); \
+        case 194: return FN<12, 2>(__VA_ARGS__); \
+        case 196: return FN<12, 4>(__VA_ARGS__); \
+        case 198: return FN<12, 6>(__VA_ARGS__); \
+        case 200: return FN<12, 8>(__VA_ARGS__); \
+        case 226: return FN<14, 2>(__VA_ARGS__); \
+        case 228: return FN<14, 4>(__VA_ARGS__); \
+        case 230: return FN<14, 6>(__VA_ARGS__); \
+        case 232: return FN<14, 8>(__VA_ARGS__); \
+        case 258: return FN<16, 2>(__VA_ARGS__); \
+        case 260: return FN<16, 4>(__VA_ARGS__); \
+        case 262: return FN<16, 6>(__VA_ARGS__); \
+        case 264: return FN<16, 8>(__VA_ARGS__); \
+        default: break;                             \
     }
 
-static int fwd_info_dispatch(int P, int D, int R, KernelInfo* info) {
-    SIGK_DISPATCH_P(fwd_info, D, R, info)
+static int fwd_info_dispatch(int P, int NR, int D, int R, KernelInfo* info) {
+    SIGK_DISPATCH_PNR(fwd_info, D, R, info)
     return -1;
 }
 
-static cudaError_t fwd_launch_dispatch(int P, int D, int R, const SolverArgs& a, int grid,
+static cudaError_t fwd_launch_dispatch(int P, int NR, int D, int R, const SolverArgs& a, int grid,
                                        cudaStream_t s) {
-    SIGK_DISPATCH_P(fwd_launch, D, R, a, grid, s)
+    SIGK_DISPATCH_PNR(fwd_launch, D, R, a, grid, s)
     return cudaErrorInvalidValue;
 }
 
-static int fwd_cm_info_dispatch(int P, bool f64, KernelInfo* info) {
-    SIGK_DISPATCH_P(fwd_cm_info, f64, info)
+static int fwd_cm_info_dispatch(int P, int NR, bool f64, KernelInfo* info) {
+    SIGK_DISPATCH_PNR(fwd_cm_info, f64, info)
     return -1;
 }
 
-static cudaError_t fwd_cm_launch_dispatch(int P, bool f64, const SolverArgs& a, void* cs,
+static cudaError_t fwd_cm_launch_dispatch(int P, int NR, bool f64, const SolverArgs& a, void* cs,
                                           int64_t cstride, int grid, cudaStream_t s) {
-    SIGK_DISPATCH_P(fwd_cm_launch, f64, a, cs, cstride, grid, s)
+    SIGK_DISPATCH_PNR(fwd_cm_launch, f64, a, cs, cstride, grid, s)
     return cudaErrorInvalidValue;
 }
 
-static int bwd_info_dispatch(int P, int D, KernelInfo* info) {
-    SIGK_DISPATCH_P(bwd_info, D, info)
+static int bwd_info_dispatch(int P, int NR, int D, KernelInfo* info) {
+    SIGK_DISPATCH_PNR(bwd_info, D, info)
     return -1;
 }
 
-static cudaError_t bwd_launch_dispatch(int P, int D, const BwdArgs& a, int grid, cudaStream_t s) {
-    SIGK_DISPATCH_P(bwd_launch, D, a, grid, s)
+static cudaError_t bwd_launch_dispatch(int P, int NR, int D, const BwdArgs& a, int grid,
+                                       cudaStream_t s) {
+    SIGK_DISPATCH_PNR(bwd_launch, D, a, grid, s)
     return cudaErrorInvalidValue;
 }
 
@@ -178,8 +200,8 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         return fail(SIGK_ERR_UNSUPPORTED, "the backward runs in FP32 only (no SIGK_FLAG_FP64)");
     if (L->cm && train)
         return fail(SIGK_ERR_UNSUPPORTED, "the backward supports d <= 16 in this build");
-    const int qinfo = L->cm ? fwd_cm_info_dispatch(o.order, L->f64, &L->info)
-                            : fwd_info_dispatch(o.order, D, train ? 1 : 0, &L->info);
+    const int qinfo = L->cm ? fwd_cm_info_dispatch(o.order, o.rings, L->f64, &L->info)
+                            : fwd_info_dispatch(o.order, o.rings, D, train ? 1 : 0, &L->info);
     if (qinfo != 0 || L->info.blocks_per_sm <= 0)
         return fail(SIGK_ERR_CUDA, "kernel occupancy query failed");
     int dev = 0, sms = 0;
@@ -245,7 +267,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         off = align256(off + L->elem * (size_t)L->nwarps * L->cstride);
     }
     if (train) {
-        if (bwd_info_dispatch(o.order, D, &L->binfo) != 0 || L->binfo.blocks_per_sm <= 0)
+        if (bwd_info_dispatch(o.order, o.rings, D, &L->binfo) != 0 || L->binfo.blocks_per_sm <= 0)
             return fail(SIGK_ERR_CUDA, "backward occupancy query failed");
         L->bgrid = sms * L->binfo.blocks_per_sm;
         if (o.grid_ctas > 0 && o.grid_ctas < L->bgrid) L->bgrid = o.grid_ctas;
@@ -776,6 +798,7 @@ static void choose_order(const double* st, int64_t n, double tol, int* P_out, in
     P += (P & 1);
     if (P > kMaxP) P = kMaxP;
     if (nr > (P < kMaxRings ? P : kMaxRings)) nr = P < kMaxRings ? P : kMaxRings;
+    nr += (nr & 1);  // compiled ring counts are even
     *P_out = P;
     *nr_out = nr;
 }
@@ -919,9 +942,9 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     }
     if (L.n_pairs > 0) {
         if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_start, stream);
-        e = L.cm ? fwd_cm_launch_dispatch(o.order, L.f64, sa, base + L.cscratch, L.cstride,
+        e = L.cm ? fwd_cm_launch_dispatch(o.order, o.rings, L.f64, sa, base + L.cscratch, L.cstride,
                                           L.grid, stream)
-                 : fwd_launch_dispatch(o.order, dim_bucket(d), train ? 1 : 0, sa, L.grid, stream);
+                 : fwd_launch_dispatch(o.order, o.rings, dim_bucket(d), train ? 1 : 0, sa, L.grid, stream);
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
         if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_stop, stream);
     }
@@ -950,7 +973,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         ba.status = &hdr->status;
         ba.counters = hdr->counters;
         if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
-        e = bwd_launch_dispatch(o.order, dim_bucket(d), ba, L.bgrid, stream);
+        e = bwd_launch_dispatch(o.order, o.rings, dim_bucket(d), ba, L.bgrid, stream);
         if (e != cudaSuccess) return cuda_fail(e, "backward launch");
         if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_stop, stream);
     }
@@ -1133,7 +1156,7 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     Opts o;
     if (!resolve_opts(opts_in, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
     o.order = kMaxP;  // layout for the largest order (the planner's seam stride)
-    o.rings = 1;
+    o.rings = 2;
     Layout L;
     if ((st = make_layout(op, n_x, n_y, d, o, &L)) != SIGK_OK) return st;
     if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;

@@ -62,7 +62,7 @@ constexpr int fwd_min_blocks(int P, int D, int R) {
     return R == 1 ? 4 : (R == 2 ? (P <= 8 ? 4 : 3) : (P <= 4 ? 4 : 3));
 }
 
-template <int P, int D, int R>
+template <int P, int D, int R, int NR>
 __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(SolverArgs A) {
     constexpr int S = P + 4;
     constexpr int DS = DyStride<D>::value;
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                     float c = 0.0f;
 #pragma unroll
                     for (int e = 0; e < D; ++e) c = fmaf(dx[k][e], dy[e], c);
-                    tile_update<P>(c, a[k], a1lo[k], hi, lo, b, b1lo, A.nr);
+                    tile_update<P>(c, a[k], a1lo[k], hi, lo, b, b1lo, NR);
                 }
                 // renormalise when the corner value grows past 2^64
                 if (fabsf(hi) > 1.8446744e19f) {

@@ -42,7 +42,7 @@ __device__ __forceinline__ double inc_at_d(const float* z, int64_t row, int d, i
     return (double)z[(row + 1) * d + e] - (double)z[row * d + e];
 }
 
-template <int P, typename T>
+template <int P, typename T, int NR>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
     fwd_cm_kernel(SolverArgs A, T* cscratch, int64_t cstride) {
     constexpr bool F32 = sizeof(T) == 4;
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                 }
                 const T c = cring[(j & 63) * 32 + lane];
                 if constexpr (F32) {
-                    tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, A.nr);
+                    tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, NR);
                     if (fabsf(hi) > 1.8446744e19f) {  // 2^64
                         const float sc = 5.421011e-20f;  // 2^-64
                         a1lo *= sc;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                         E += 64;
                     }
                 } else {
-                    tile_update_f64<P>(c, a, hi, b, A.nr);
+                    tile_update_f64<P>(c, a, hi, b, NR);
                     if (fabs(hi) > 0x1p512) {
                         const double sc = 0x1p-512;
 #pragma unroll

@@ -1,6 +1,8 @@
-// sigk_fwd_inst.cu -- instantiates, for one edge degree P (compiled once per P
-// with -DSIGK_P=<P>) and D in {4, 8, 16}: the inference forward solver, the
-// one-row-per-lane training forward, and the backward (adjoint) kernel.
+// sigk_fwd_inst.cu -- instantiates, for one edge degree P and ring count NR
+// (compiled once per pair with -DSIGK_P=<P> -DSIGK_NR=<NR>) and D in
+// {4, 8, 16}: the inference forward solver, the one-row-per-lane training
+// forward and the backward (adjoint) kernel; and the two-phase solver in FP32
+// and FP64.
 #include "sigk_bwd.cuh"
 #include "sigk_fwd.cuh"
 #include "sigk_fwd_cm.cuh"
@@ -9,6 +11,10 @@
 #ifndef SIGK_P
 #error "compile with -DSIGK_P=<edge degree>"
 #endif
+#ifndef SIGK_NR
+#error "compile with -DSIGK_NR=<ring count>"
+#endif
+static_assert(SIGK_NR >= 1 && SIGK_NR <= SIGK_P && SIGK_NR <= sigk::kMaxRings, "bad ring count");
 
 namespace sigk {
 
@@ -26,120 +32,109 @@ static int occupancy(K kern, int threads, int smem, int R, KernelInfo* info) {
     return 0;
 }
 
-template <int P, int D, int R>
+template <int D, int R>
 static int fwd_info_impl(KernelInfo* info) {
-    const int smem = 4 * FwdSmem<P, D>::per_warp * (int)sizeof(float);
-    return occupancy(fwd_kernel<P, D, R>, 128, smem, R, info);
+    const int smem = 4 * FwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
+    return occupancy(fwd_kernel<SIGK_P, D, R, SIGK_NR>, 128, smem, R, info);
 }
 
-template <int P, int D, int R>
+template <int D, int R>
 static cudaError_t fwd_launch_impl(const SolverArgs& a, int grid, cudaStream_t s) {
-    const int smem = 4 * FwdSmem<P, D>::per_warp * (int)sizeof(float);
-    auto kern = fwd_kernel<P, D, R>;
+    const int smem = 4 * FwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
+    auto kern = fwd_kernel<SIGK_P, D, R, SIGK_NR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int P, int D>
+template <int D>
 static int bwd_info_impl(KernelInfo* info) {
-    const int smem = 4 * BwdSmem<P, D>::per_warp * (int)sizeof(float);
-    return occupancy(bwd_kernel<P, D>, 128, smem, 1, info);
+    const int smem = 4 * BwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
+    return occupancy(bwd_kernel<SIGK_P, D, SIGK_NR>, 128, smem, 1, info);
 }
 
-template <int P, int D>
+template <int D>
 static cudaError_t bwd_launch_impl(const BwdArgs& a, int grid, cudaStream_t s) {
-    const int smem = 4 * BwdSmem<P, D>::per_warp * (int)sizeof(float);
-    auto kern = bwd_kernel<P, D>;
+    const int smem = 4 * BwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
+    auto kern = bwd_kernel<SIGK_P, D, SIGK_NR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 128, smem, s>>>(a);
     return cudaGetLastError();
-}
-
-#define SIGK_DISPATCH_D(FN, ...)            \
-    switch (D) {                            \
-        case 4: return FN<SIGK_P, 4>(__VA_ARGS__);   \
-        case 8: return FN<SIGK_P, 8>(__VA_ARGS__);   \
-        case 16: return FN<SIGK_P, 16>(__VA_ARGS__); \
-        default: break;                     \
-    }
-
-template <>
-int fwd_info<SIGK_P>(int D, int R, KernelInfo* info) {
-    if (R == 1) {
-        switch (D) {
-            case 4: return fwd_info_impl<SIGK_P, 4, 1>(info);
-            case 8: return fwd_info_impl<SIGK_P, 8, 1>(info);
-            case 16: return fwd_info_impl<SIGK_P, 16, 1>(info);
-            default: return -1;
-        }
-    }
-    switch (D) {
-        case 4: return fwd_info_impl<SIGK_P, 4, rows_per_lane(SIGK_P, 4)>(info);
-        case 8: return fwd_info_impl<SIGK_P, 8, rows_per_lane(SIGK_P, 8)>(info);
-        case 16: return fwd_info_impl<SIGK_P, 16, rows_per_lane(SIGK_P, 16)>(info);
-        default: return -1;
-    }
-}
-
-template <>
-cudaError_t fwd_launch<SIGK_P>(int D, int R, const SolverArgs& a, int grid, cudaStream_t s) {
-    if (R == 1) {
-        switch (D) {
-            case 4: return fwd_launch_impl<SIGK_P, 4, 1>(a, grid, s);
-            case 8: return fwd_launch_impl<SIGK_P, 8, 1>(a, grid, s);
-            case 16: return fwd_launch_impl<SIGK_P, 16, 1>(a, grid, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
-    switch (D) {
-        case 4: return fwd_launch_impl<SIGK_P, 4, rows_per_lane(SIGK_P, 4)>(a, grid, s);
-        case 8: return fwd_launch_impl<SIGK_P, 8, rows_per_lane(SIGK_P, 8)>(a, grid, s);
-        case 16: return fwd_launch_impl<SIGK_P, 16, rows_per_lane(SIGK_P, 16)>(a, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 template <typename T>
 static int fwd_cm_info_impl(KernelInfo* info) {
-    return occupancy(fwd_cm_kernel<SIGK_P, T>, 128, CmSmem<SIGK_P, T>::bytes, 1, info);
+    return occupancy(fwd_cm_kernel<SIGK_P, T, SIGK_NR>, 128, CmSmem<SIGK_P, T>::bytes, 1, info);
 }
 
 template <typename T>
 static cudaError_t fwd_cm_launch_impl(const SolverArgs& a, void* cscratch, int64_t cstride,
                                       int grid, cudaStream_t s) {
     const int smem = CmSmem<SIGK_P, T>::bytes;
-    auto kern = fwd_cm_kernel<SIGK_P, T>;
+    auto kern = fwd_cm_kernel<SIGK_P, T, SIGK_NR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 128, smem, s>>>(a, static_cast<T*>(cscratch), cstride);
     return cudaGetLastError();
 }
 
+constexpr int kR4 = rows_per_lane(SIGK_P, 4);
+constexpr int kR8 = rows_per_lane(SIGK_P, 8);
+constexpr int kR16 = rows_per_lane(SIGK_P, 16);
+
 template <>
-int fwd_cm_info<SIGK_P>(bool f64, KernelInfo* info) {
+int fwd_info<SIGK_P, SIGK_NR>(int D, int R, KernelInfo* info) {
+    switch (D) {
+        case 4: return R == 1 ? fwd_info_impl<4, 1>(info) : fwd_info_impl<4, kR4>(info);
+        case 8: return R == 1 ? fwd_info_impl<8, 1>(info) : fwd_info_impl<8, kR8>(info);
+        case 16: return R == 1 ? fwd_info_impl<16, 1>(info) : fwd_info_impl<16, kR16>(info);
+        default: return -1;
+    }
+}
+
+template <>
+cudaError_t fwd_launch<SIGK_P, SIGK_NR>(int D, int R, const SolverArgs& a, int grid, cudaStream_t s) {
+    switch (D) {
+        case 4: return R == 1 ? fwd_launch_impl<4, 1>(a, grid, s) : fwd_launch_impl<4, kR4>(a, grid, s);
+        case 8: return R == 1 ? fwd_launch_impl<8, 1>(a, grid, s) : fwd_launch_impl<8, kR8>(a, grid, s);
+        case 16:
+            return R == 1 ? fwd_launch_impl<16, 1>(a, grid, s) : fwd_launch_impl<16, kR16>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+int fwd_cm_info<SIGK_P, SIGK_NR>(bool f64, KernelInfo* info) {
     return f64 ? fwd_cm_info_impl<double>(info) : fwd_cm_info_impl<float>(info);
 }
 
 template <>
-cudaError_t fwd_cm_launch<SIGK_P>(bool f64, const SolverArgs& a, void* cscratch, int64_t cstride,
-                                  int grid, cudaStream_t s) {
+cudaError_t fwd_cm_launch<SIGK_P, SIGK_NR>(bool f64, const SolverArgs& a, void* cscratch,
+                                           int64_t cstride, int grid, cudaStream_t s) {
     return f64 ? fwd_cm_launch_impl<double>(a, cscratch, cstride, grid, s)
                : fwd_cm_launch_impl<float>(a, cscratch, cstride, grid, s);
 }
 
 template <>
-int bwd_info<SIGK_P>(int D, KernelInfo* info) {
-    SIGK_DISPATCH_D(bwd_info_impl, info)
-    return -1;
+int bwd_info<SIGK_P, SIGK_NR>(int D, KernelInfo* info) {
+    switch (D) {
+        case 4: return bwd_info_impl<4>(info);
+        case 8: return bwd_info_impl<8>(info);
+        case 16: return bwd_info_impl<16>(info);
+        default: return -1;
+    }
 }
 
 template <>
-cudaError_t bwd_launch<SIGK_P>(int D, const BwdArgs& a, int grid, cudaStream_t s) {
-    SIGK_DISPATCH_D(bwd_launch_impl, a, grid, s)
-    return cudaErrorInvalidValue;
+cudaError_t bwd_launch<SIGK_P, SIGK_NR>(int D, const BwdArgs& a, int grid, cudaStream_t s) {
+    switch (D) {
+        case 4: return bwd_launch_impl<4>(a, grid, s);
+        case 8: return bwd_launch_impl<8>(a, grid, s);
+        case 16: return bwd_launch_impl<16>(a, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace sigk

@@ -17,20 +17,25 @@ struct KernelInfo {
 // footprint (R*(P + D) state floats) would push occupancy too low.
 constexpr int rows_per_lane(int P, int D) { return (P + D) <= 16 ? 4 : 2; }
 
+// Entry points of the kernel translation units, one unit per (edge degree P,
+// ring count NR); NR is a compile-time constant of every solver kernel, so
+// the truncated ring sums carry no run-time predicates.
+//
 // R = 0: the inference rows-per-lane rows_per_lane(P, D); R = 1: one row per
 // lane (the training forward, whose strips the backward kernel replays).
-template <int P> int fwd_info(int D, int R, KernelInfo* info);
-template <int P> cudaError_t fwd_launch(int D, int R, const SolverArgs& a, int grid, cudaStream_t s);
+template <int P, int NR> int fwd_info(int D, int R, KernelInfo* info);
+template <int P, int NR>
+cudaError_t fwd_launch(int D, int R, const SolverArgs& a, int grid, cudaStream_t s);
 
 // Two-phase kernel (strip coefficients first, then the sweep): d > 16 in
 // FP32, or any d in FP64 (f64 = true).  cscratch holds float or double strips.
-template <int P> int fwd_cm_info(bool f64, KernelInfo* info);
-template <int P>
+template <int P, int NR> int fwd_cm_info(bool f64, KernelInfo* info);
+template <int P, int NR>
 cudaError_t fwd_cm_launch(bool f64, const SolverArgs& a, void* cscratch, int64_t cstride, int grid,
                           cudaStream_t s);
 
 struct BwdArgs;
-template <int P> int bwd_info(int D, KernelInfo* info);
-template <int P> cudaError_t bwd_launch(int D, const BwdArgs& a, int grid, cudaStream_t s);
+template <int P, int NR> int bwd_info(int D, KernelInfo* info);
+template <int P, int NR> cudaError_t bwd_launch(int D, const BwdArgs& a, int grid, cudaStream_t s);
 
 }  // namespace sigk
