@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     float* rbuf1 = sin_ + 32 * S;                       // second record block
     float* ain = rbuf1 + 32 * S;                        // adjoint seam-in block
     float* aout = ain + 32 * SA;                        // adjoint seam-out block
-    float* colacc = aout + 32 * SA;                     // 64 x D column gradient
+    float* colacc = aout + 32 * SA;                     // column gradient [D][64]
     uint64_t* bars = reinterpret_cast<uint64_t*>(colacc + 64 * D);  // record-load mbarriers
     float* rec = A.rec + (size_t)gwarp * A.rec_stride;
     const int n_items = A.sched.hdr[2];
@@ -419,11 +419,13 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     for (int q = 1; q <= P; ++q) Bb[q] *= sc;
                 }
                 const float g = cbar * wsc;
-                float* ca = colacc + (jr & 63) * D;
+                // [D][64] layout: the 32 lanes (consecutive columns) hit 32
+                // consecutive words, free of bank conflicts
+                float* ca = colacc + (jr & 63);
 #pragma unroll
                 for (int e = 0; e < D; ++e) {
                     gx[e] = fmaf(g, dy[e], gx[e]);
-                    ca[e] = fmaf(g, dx[e], ca[e]);
+                    ca[e * 64] = fmaf(g, dx[e], ca[e * 64]);
                 }
                 oB0 = B0;
 #pragma unroll
@@ -444,8 +446,8 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 const int nb = jj - start + 1;
                 if (pd.gyr) {
                     for (int idx = lane; idx < nb * D; idx += 32) {
-                        const int col = idx / D, e = idx % D;
-                        float* cell = colacc + ((start + col) & 63) * D + e;
+                        const int col = idx % nb, e = idx / nb;
+                        float* cell = colacc + e * 64 + ((start + col) & 63);
                         const float v = *cell;
                         *cell = 0.0f;
                         if (e < A.d && v != 0.0f) {
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     }
                 } else {
                     for (int idx = lane; idx < nb * D; idx += 32)
-                        colacc[((start + idx / D) & 63) * D + idx % D] = 0.0f;
+                        colacc[(idx / nb) * 64 + ((start + idx % nb) & 63)] = 0.0f;
                 }
                 if (has_aout) {
                     if (start + nb > A.wcols) {
