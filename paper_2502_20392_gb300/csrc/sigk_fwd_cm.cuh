@@ -42,6 +42,197 @@ __device__ __forceinline__ double inc_at_d(const float* z, int64_t row, int d, i
     return (double)z[(row + 1) * d + e] - (double)z[row * d + e];
 }
 
+// The wavefront sweep of one 32-row strip with one row per lane, c read
+// from the strip scratch `cst` ([L2][32], column-major) through the shared
+// ring `cring`.  In the seam protocol the strip is `item`, fed by `prev` and
+// feeding `next` (-1: none); the caller has already made sure that slot
+// item % nslot is free.  Returns false when a bounded wait failed.
+template <int P, typename T, int NR>
+__device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc& pd, int lo_p,
+                                            int s, int item, int prev, int next, const T* cst,
+                                            T* cring, T* sin_, T* sout, T* seam,
+                                            unsigned long long& tiles_done,
+                                            unsigned long long& lane_tiles) {
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int S = P + 4;
+    const int lane = threadIdx.x & 31;
+    const int L1 = pd.L1, L2 = pd.L2;
+    const bool has_in = prev >= 0;
+    const bool has_out = next >= 0;
+    const int slot_in = has_in ? prev % A.nslot : 0;
+    const int slot_out = item % A.nslot;
+    const int i0 = s * 32;
+    bool ok = true;
+    T a[P + 1];
+    float a1lo = 0.0f;  // FP32 only: compensation of the first-order terms
+#pragma unroll
+    for (int p = 0; p <= P; ++p) a[p] = T(0);
+    int E = 0;
+    T ohi = T(1), ob[P + 1];
+    float olo = 0.0f, ob1lo = 0.0f;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) ob[q] = T(0);
+    int oE = 0;
+    const int pw_in = slot_in;
+    const int pw_out = slot_out;
+    constexpr int NV = 32 * (int)sizeof(T) / 16;  // 16-byte vectors per strip column
+    const int Tn = L2 + 31;
+    const bool has_row = i0 + lane < L1;
+    for (int t = 0; t < Tn && ok; ++t) {
+        if ((t & 31) == 0 && t < L2) {
+            const int nb = min(32, L2 - t);
+            // coefficients of columns [t, t+nb) into the ring (contiguous)
+            const int4* src = reinterpret_cast<const int4*>(cst + (size_t)t * 32);
+            for (int idx = lane; idx < nb * NV; idx += 32) {
+                const int col = idx / NV, q = idx % NV;
+                reinterpret_cast<int4*>(cring + ((t + col) & 63) * 32)[q] = src[idx];
+            }
+            if (has_in) {
+                const unsigned long long need =
+                    ((unsigned long long)prev << 32) | (unsigned)(t + nb);
+                bool okl = true;
+                if (lane == 0) okl = wait_ge_u64(&A.prod[pw_in], need, A.status);
+                ok = __shfl_sync(kFull, okl, 0);
+                if (ok) {
+                    const T* src2 = seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
+                    for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src2 + idx);
+                    __syncwarp();
+                    if (lane == 0)
+                        st_release_u64(&A.cons[slot_in],
+                                       ((unsigned long long)item << 32) | (unsigned)(t + nb));
+                }
+            }
+            __syncwarp();
+            if (!ok) break;
+        }
+        T hi = __shfl_up_sync(kFull, ohi, 1);
+        float lo = 0.0f, b1lo = 0.0f;
+        if constexpr (F32) {
+            lo = __shfl_up_sync(kFull, olo, 1);
+            b1lo = __shfl_up_sync(kFull, ob1lo, 1);
+        }
+        T b[P + 1];
+        b[0] = T(0);
+#pragma unroll
+        for (int q = 1; q <= P; ++q) b[q] = __shfl_up_sync(kFull, ob[q], 1);
+        int F = __shfl_up_sync(kFull, oE, 1);
+        if (lane == 0) {
+            if (has_in && t < L2) {
+                const T* e_ = sin_ + (t & 31) * S;
+                hi = e_[0];
+                if constexpr (F32) {
+                    lo = e_[1];
+                    b1lo = e_[2];
+                }
+#pragma unroll
+                for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
+                if constexpr (F32) F = __float_as_int(e_[P + 3]);
+                else F = (int)e_[P + 3];
+            } else {
+                hi = T(1); lo = 0.0f; b1lo = 0.0f; F = 0;
+#pragma unroll
+                for (int q = 1; q <= P; ++q) b[q] = T(0);
+            }
+        }
+        const int j = t - lane;
+        if (j >= 0 && j < L2) {
+            if (F != E) {
+                if (F > E) {
+                    const T sc = F32 ? (T)exp2_nonpos(E - F) : (T)exp2_nonpos_d(E - F);
+                    a1lo *= (float)sc;
+#pragma unroll
+                    for (int p = 1; p <= P; ++p) a[p] *= sc;
+                    E = F;
+                } else {
+                    const T sc = F32 ? (T)exp2_nonpos(F - E) : (T)exp2_nonpos_d(F - E);
+                    hi *= sc; lo *= (float)sc; b1lo *= (float)sc;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] *= sc;
+                }
+            }
+            const T c = cring[(j & 63) * 32 + lane];
+            if constexpr (F32) {
+                tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, NR);
+                if (fabsf(hi) > 1.8446744e19f) {  // 2^64
+                    const float sc = 5.421011e-20f;  // 2^-64
+                    a1lo *= sc;
+#pragma unroll
+                    for (int p = 1; p <= P; ++p) a[p] *= sc;
+                    hi *= sc; lo *= sc; b1lo *= sc;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] *= sc;
+                    E += 64;
+                }
+            } else {
+                tile_update_f64<P>(c, a, hi, b, NR);
+                if (fabs(hi) > 0x1p512) {
+                    const double sc = 0x1p-512;
+#pragma unroll
+                    for (int p = 1; p <= P; ++p) a[p] *= sc;
+                    hi *= sc;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) b[q] *= sc;
+                    E += 512;
+                }
+            }
+            ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
+#pragma unroll
+            for (int q = 1; q <= P; ++q) ob[q] = b[q];
+            tiles_done += has_row ? 1ull : 0ull;
+            lane_tiles += 1;
+            if (lane == 31) {
+                if (has_out) {
+                    T* e_ = sout + (j & 31) * S;
+                    e_[0] = hi;
+                    e_[1] = (T)lo;
+                    e_[2] = (T)b1lo;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) e_[2 + q] = b[q];
+                    if constexpr (F32) e_[P + 3] = __int_as_float(E);
+                    else e_[P + 3] = (double)E;
+                } else if (j == L2 - 1) {
+                    double k = (double)hi + (double)lo + (double)b1lo;
+                    double fq = 1.0;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) {
+                        fq *= (double)q;
+                        k += (double)b[q] / fq;
+                    }
+                    k = ldexp(k, E);
+                    if (!isfinite(k)) atomicCAS(A.status, 0, kErrNonfinite);
+                    if (pd.out0 >= 0) A.out[pd.out0] = k;
+                    if (pd.out1 >= 0) A.out[pd.out1] = k;
+                    if (A.pair_exp) A.pair_exp[lo_p] = E;
+                }
+            }
+        }
+        const int jj = t - 31;
+        if (has_out && jj >= 0 && jj < L2 && (((jj & 31) == 31) || jj == L2 - 1)) {
+            __syncwarp();
+            const int start = jj & ~31;
+            const int nb = jj - start + 1;
+            if (start + nb > A.wcols) {
+                const unsigned long long need = ((unsigned long long)next << 32) |
+                                                (unsigned)(start + nb - A.wcols);
+                bool okl = true;
+                if (lane == 0) okl = wait_ge_u64(&A.cons[slot_out], need, A.status);
+                ok = __shfl_sync(kFull, okl, 0);
+            }
+            if (ok) {
+                T* dst = seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
+                for (int idx = lane; idx < nb * S; idx += 32) __stcg(dst + idx, sout[idx]);
+                __threadfence();
+                __syncwarp();
+                if (lane == 0)
+                    st_release_u64(&A.prod[pw_out],
+                                   ((unsigned long long)item << 32) | (unsigned)(start + nb));
+            }
+            __syncwarp();
+        }
+    }
+    return ok;
+}
+
 template <int P, typename T, int NR>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
     fwd_cm_kernel(SolverArgs A, T* cscratch, int64_t cstride) {
@@ -78,8 +269,6 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         const int L1 = pd.L1, L2 = pd.L2;
         const bool has_in = ir.prev >= 0;
         const bool has_out = ir.next >= 0;
-        const int slot_in = has_in ? ir.prev % A.nslot : 0;
-        const int slot_out = item % A.nslot;
         const int i0 = s * 32;
         bool ok = true;
 
@@ -165,178 +354,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         __syncwarp();
 
         // ---- phase 2: the wavefront sweep (one row per lane) -------------------
-        T a[P + 1];
-        float a1lo = 0.0f;  // FP32 only: compensation of the first-order terms
-#pragma unroll
-        for (int p = 0; p <= P; ++p) a[p] = T(0);
-        int E = 0;
-        T ohi = T(1), ob[P + 1];
-        float olo = 0.0f, ob1lo = 0.0f;
-#pragma unroll
-        for (int q = 0; q <= P; ++q) ob[q] = T(0);
-        int oE = 0;
-        const bool train = F32 && A.store != nullptr;
-        T* st_pair = train ? reinterpret_cast<T*>(A.store) + A.store_off[lo_p] : nullptr;
-        const int pw_in = train ? ir.prev : slot_in;
-        const int pw_out = train ? item : slot_out;
-        if (has_out && !train) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
-        constexpr int NV = 32 * (int)sizeof(T) / 16;  // 16-byte vectors per strip column
-        const int Tn = L2 + 31;
-        const bool has_row = i0 + lane < L1;
-        for (int t = 0; t < Tn && ok; ++t) {
-            if ((t & 31) == 0 && t < L2) {
-                const int nb = min(32, L2 - t);
-                // coefficients of columns [t, t+nb) into the ring (contiguous)
-                const int4* src = reinterpret_cast<const int4*>(cst + (size_t)t * 32);
-                for (int idx = lane; idx < nb * NV; idx += 32) {
-                    const int col = idx / NV, q = idx % NV;
-                    reinterpret_cast<int4*>(cring + ((t + col) & 63) * 32)[q] = src[idx];
-                }
-                if (has_in) {
-                    const unsigned long long need =
-                        ((unsigned long long)ir.prev << 32) | (unsigned)(t + nb);
-                    bool okl = true;
-                    if (lane == 0) okl = wait_ge_u64(&A.prod[pw_in], need, A.status);
-                    ok = __shfl_sync(kFull, okl, 0);
-                    if (ok) {
-                        const T* src2 = train ? st_pair + ((size_t)(s - 1) * L2 + t) * S
-                                              : seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
-                        for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src2 + idx);
-                        __syncwarp();
-                        if (lane == 0 && !train)
-                            st_release_u64(&A.cons[slot_in],
-                                           ((unsigned long long)item << 32) | (unsigned)(t + nb));
-                    }
-                }
-                __syncwarp();
-                if (!ok) break;
-            }
-            T hi = __shfl_up_sync(kFull, ohi, 1);
-            float lo = 0.0f, b1lo = 0.0f;
-            if constexpr (F32) {
-                lo = __shfl_up_sync(kFull, olo, 1);
-                b1lo = __shfl_up_sync(kFull, ob1lo, 1);
-            }
-            T b[P + 1];
-            b[0] = T(0);
-#pragma unroll
-            for (int q = 1; q <= P; ++q) b[q] = __shfl_up_sync(kFull, ob[q], 1);
-            int F = __shfl_up_sync(kFull, oE, 1);
-            if (lane == 0) {
-                if (has_in && t < L2) {
-                    const T* e_ = sin_ + (t & 31) * S;
-                    hi = e_[0];
-                    if constexpr (F32) {
-                        lo = e_[1];
-                        b1lo = e_[2];
-                    }
-#pragma unroll
-                    for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
-                    if constexpr (F32) F = __float_as_int(e_[P + 3]);
-                    else F = (int)e_[P + 3];
-                } else {
-                    hi = T(1); lo = 0.0f; b1lo = 0.0f; F = 0;
-#pragma unroll
-                    for (int q = 1; q <= P; ++q) b[q] = T(0);
-                }
-            }
-            const int j = t - lane;
-            if (j >= 0 && j < L2) {
-                if (F != E) {
-                    if (F > E) {
-                        const T sc = F32 ? (T)exp2_nonpos(E - F) : (T)exp2_nonpos_d(E - F);
-                        a1lo *= (float)sc;
-#pragma unroll
-                        for (int p = 1; p <= P; ++p) a[p] *= sc;
-                        E = F;
-                    } else {
-                        const T sc = F32 ? (T)exp2_nonpos(F - E) : (T)exp2_nonpos_d(F - E);
-                        hi *= sc; lo *= (float)sc; b1lo *= (float)sc;
-#pragma unroll
-                        for (int q = 1; q <= P; ++q) b[q] *= sc;
-                    }
-                }
-                const T c = cring[(j & 63) * 32 + lane];
-                if constexpr (F32) {
-                    tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, NR);
-                    if (fabsf(hi) > 1.8446744e19f) {  // 2^64
-                        const float sc = 5.421011e-20f;  // 2^-64
-                        a1lo *= sc;
-#pragma unroll
-                        for (int p = 1; p <= P; ++p) a[p] *= sc;
-                        hi *= sc; lo *= sc; b1lo *= sc;
-#pragma unroll
-                        for (int q = 1; q <= P; ++q) b[q] *= sc;
-                        E += 64;
-                    }
-                } else {
-                    tile_update_f64<P>(c, a, hi, b, NR);
-                    if (fabs(hi) > 0x1p512) {
-                        const double sc = 0x1p-512;
-#pragma unroll
-                        for (int p = 1; p <= P; ++p) a[p] *= sc;
-                        hi *= sc;
-#pragma unroll
-                        for (int q = 1; q <= P; ++q) b[q] *= sc;
-                        E += 512;
-                    }
-                }
-                ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
-#pragma unroll
-                for (int q = 1; q <= P; ++q) ob[q] = b[q];
-                tiles_done += has_row ? 1ull : 0ull;
-                lane_tiles += 1;
-                if (lane == 31) {
-                    if (has_out) {
-                        T* e_ = sout + (j & 31) * S;
-                        e_[0] = hi;
-                        e_[1] = (T)lo;
-                        e_[2] = (T)b1lo;
-#pragma unroll
-                        for (int q = 1; q <= P; ++q) e_[2 + q] = b[q];
-                        if constexpr (F32) e_[P + 3] = __int_as_float(E);
-                        else e_[P + 3] = (double)E;
-                    } else if (j == L2 - 1) {
-                        double k = (double)hi + (double)lo + (double)b1lo;
-                        double fq = 1.0;
-#pragma unroll
-                        for (int q = 1; q <= P; ++q) {
-                            fq *= (double)q;
-                            k += (double)b[q] / fq;
-                        }
-                        k = ldexp(k, E);
-                        if (!isfinite(k)) atomicCAS(A.status, 0, kErrNonfinite);
-                        if (pd.out0 >= 0) A.out[pd.out0] = k;
-                        if (pd.out1 >= 0) A.out[pd.out1] = k;
-                        if (A.pair_exp) A.pair_exp[lo_p] = E;
-                    }
-                }
-            }
-            const int jj = t - 31;
-            if (has_out && jj >= 0 && jj < L2 && (((jj & 31) == 31) || jj == L2 - 1)) {
-                __syncwarp();
-                const int start = jj & ~31;
-                const int nb = jj - start + 1;
-                if (!train && start + nb > A.wcols) {
-                    const unsigned long long need = ((unsigned long long)ir.next << 32) |
-                                                    (unsigned)(start + nb - A.wcols);
-                    bool okl = true;
-                    if (lane == 0) okl = wait_ge_u64(&A.cons[slot_out], need, A.status);
-                    ok = __shfl_sync(kFull, okl, 0);
-                }
-                if (ok) {
-                    T* dst = train ? st_pair + ((size_t)s * L2 + start) * S
-                                   : seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
-                    for (int idx = lane; idx < nb * S; idx += 32) __stcg(dst + idx, sout[idx]);
-                    __threadfence();
-                    __syncwarp();
-                    if (lane == 0)
-                        st_release_u64(&A.prod[pw_out],
-                                       ((unsigned long long)item << 32) | (unsigned)(start + nb));
-                }
-                __syncwarp();
-            }
-        }
+        if (has_out) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
+        if (ok)
+            ok = sweep_strip<P, T, NR>(A, pd, lo_p, s, item, has_in ? ir.prev : -1,
+                                       has_out ? ir.next : -1, cst, cring, sin_, sout, seam,
+                                       tiles_done, lane_tiles);
         __syncwarp();
         if (lane == 0) {
             __threadfence();
