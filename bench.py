@@ -150,7 +150,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 16 paths per Gram (for ncu captures; not a bench line)")
+    ap.add_argument("--sweep", default=None, choices=["roughness", "dimension", "length"],
+                    help="print one JSON line per point of a sweep instead of the bench line")
     args = ap.parse_args()
+    if args.sweep:
+        return run_sweep(args)
     if args.case == "small":
         global N_PATHS
         N_PATHS = 16
@@ -361,6 +365,74 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_sweep(args):
+    """Throughput over the sweeps that widen the tested range (one GPU, forward
+    solve with the plan's options; CUDA events around the solve, after
+    warm-up).  roughness: 4096 pairs of 2-D fBM paths of 51 points, H from 0.4
+    down to 0.005, FP32 and FP64; dimension: a Gram of 16 Brownian paths of
+    512 segments, d = 2 .. 8192; length: one 2-D Brownian self-kernel of
+    2^k + 1 points (k = 10 .. 19), with the workspace bytes (O(L))."""
+    import json
+
+    import numpy as np
+    import torch
+
+    from paper_2502_20392_gb300 import build, sigk, synth
+    build.build()
+    sigk.load()
+    dev = torch.device("cuda", 0)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def emit(**kw):
+        print(json.dumps(kw), flush=True)
+
+    if args.sweep == "roughness":
+        for H in (0.4, 0.2, 0.1, 0.05, 0.01, 0.005):
+            X, lx = synth.fbm(4096, 50, 2, H, seed=6000 + int(H * 1000))
+            Y, ly = synth.fbm(4096, 50, 2, H, seed=7000 + int(H * 1000))
+            a = [torch.from_numpy(v).to(dev) for v in (X, lx, Y, ly)]
+            for flags in (0, sigk.FLAG_FP64):
+                o = sigk.plan(sigk.OP_PAIRS, *a, tol=1e-5, opts=sigk.Opts(max_len=4096, flags=flags))
+                ws = sigk.Workspace()
+                ms = timed(lambda: sigk.pairs(*a, opts=o, ws=ws, check=False))
+                emit(sweep="roughness", hurst=H, precision="fp64" if flags else "fp32",
+                     metric="cells/s", value=4096 * 2500 / (ms * 1e-3), ms=ms,
+                     opts=dict(order=o.order, rings=o.rings, refine_c=o.refine_c, max_len=o.max_len))
+    elif args.sweep == "dimension":
+        for d in (2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 8192):
+            pts, lens = synth.brownian(16, 512, d, 1.0, seed=8000 + d)
+            X, L = torch.from_numpy(pts).to(dev), torch.from_numpy(lens).to(dev)
+            o = sigk.plan(sigk.OP_GRAM, X, L, None, None, tol=1e-6, opts=sigk.Opts(max_len=513))
+            ws = sigk.Workspace()
+            ms = timed(lambda: sigk.gram(X, L, opts=o, ws=ws, check=False))
+            cells = 136 * 512 * 512
+            emit(sweep="dimension", d=d, metric="cells/s", value=cells / (ms * 1e-3), ms=ms,
+                 kernel="register" if d <= 16 else "two-phase",
+                 opts=dict(order=o.order, rings=o.rings, refine_c=o.refine_c))
+    else:
+        for k in range(10, 20):
+            n = 2 ** k
+            pts, lens = synth.brownian(1, n, 2, 1.0, seed=9000 + k)
+            X, L = torch.from_numpy(pts).to(dev), torch.from_numpy(lens).to(dev)
+            o = sigk.Opts(order=8, rings=4, max_len=n + 1)
+            ws = sigk.Workspace()
+            ms = timed(lambda: sigk.pairs(X, L, X, L, opts=o, ws=ws, check=False), reps=1)
+            emit(sweep="length", points=n + 1, metric="cells/s", value=n * n / (ms * 1e-3), ms=ms,
+                 workspace_bytes=int(sigk.workspace_size(sigk.OP_PAIRS, 1, 1, 2, o)),
+                 opts=dict(order=8, rings=4))
+    return 0
 
 
 def run_reference(args, world, rank):

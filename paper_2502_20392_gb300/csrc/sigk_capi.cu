@@ -175,6 +175,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // largest seam ring (bytes) it may take.
 constexpr int kLevelCap = 4096;
 constexpr double kStripMajorBudget = 8.0 * 1024 * 1024 * 1024;
+constexpr int64_t kStripMajorMinPairs = 64;
 
 // Number of pair entries solved by an op.
 static int64_t pair_count(int op, int64_t n_x, int64_t n_y, int flags) {
@@ -223,7 +224,11 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     // so a slot is reused only after an item at least nwarps earlier is done.
     const int64_t wfull = (o.max_len + 31) & ~(int64_t)31;
     const int64_t nslot_sm = L->n_pairs + L->nwarps + 64;
-    if (o.flags & SIGK_FLAG_PAIR_MAJOR) allow_sm = false;
+    // strip-major needs many pairs (a producer is one level, i.e. the pairs
+    // with more strips, ahead of its consumer); with few pairs it only costs
+    // ring memory
+    if ((o.flags & SIGK_FLAG_PAIR_MAJOR) || pair_count(op, n_x, n_y, o.flags) < kStripMajorMinPairs)
+        allow_sm = false;
     L->strip_major = allow_sm && !train && nslot_sm <= (int64_t)INT32_MAX / 2 &&
                      (double)nslot_sm * (double)wfull * (double)L->stride * (double)L->elem <=
                          kStripMajorBudget;

@@ -278,8 +278,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         const double cscale = 1.0 / ((double)pd.sx * (double)pd.sy);
         for (int j0 = 0; j0 < L2; j0 += 32) {
             T acc[32];
+            float comp[32];  // FP32: compensation of the sum of chunk partials
 #pragma unroll
-            for (int r = 0; r < 32; ++r) acc[r] = T(0);
+            for (int r = 0; r < 32; ++r) {
+                acc[r] = T(0);
+                comp[r] = 0.0f;
+            }
             const int jl = j0 + lane;
             for (int k0 = 0; k0 < d; k0 += kCmKC) {
                 __syncwarp();
@@ -305,8 +309,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                 const int kn = min(kCmKC, d - k0);
                 if constexpr (F32) {
                     // two-level sum: a chunk's products are accumulated from
-                    // zero and then added to the total, which cuts the rounding
-                    // error of a 256-term dot about 2.5x against one running sum
+                    // zero, then added to the total with TwoSum compensation,
+                    // so the error is that of 32-term sums, whatever d (one
+                    // running sum of 256 products had ~2.5x, of 8192 ~10x more)
                     float part[32];
 #pragma unroll
                     for (int r = 0; r < 32; ++r) part[r] = 0.0f;
@@ -323,7 +328,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                         }
                     }
 #pragma unroll
-                    for (int r = 0; r < 32; ++r) acc[r] += part[r];
+                    for (int r = 0; r < 32; ++r) {
+                        const float t = acc[r] + part[r];
+                        const float bp = t - acc[r];
+                        comp[r] += (acc[r] - (t - bp)) + (part[r] - bp);
+                        acc[r] = t;
+                    }
                 } else {
                     for (int ee = 0; ee < kn; ++ee) {
                         const double y = dys[lane * (kCmKC + 1) + ee];
@@ -342,7 +352,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                     float4* dst = reinterpret_cast<float4*>(cst + (size_t)jl * 32);
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        dst[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+                        dst[q] = make_float4(acc[4 * q] + comp[4 * q], acc[4 * q + 1] + comp[4 * q + 1],
+                                             acc[4 * q + 2] + comp[4 * q + 2],
+                                             acc[4 * q + 3] + comp[4 * q + 3]);
                 } else {
                     double2* dst = reinterpret_cast<double2*>(cst + (size_t)jl * 32);
 #pragma unroll

@@ -20,6 +20,12 @@ Sec. 3; no dataset is used):
   (the closed form I0(2 sqrt(<X,Y>)) then holds for the rounded inputs).
 * ``ragged_pairs``: independent pairs with lengths U{lo..hi} segments and a
   per-path scale sigma_p ~ U(s_lo, s_hi), increments N(0, sigma_p^2 / L_p).
+* ``fbm``: fractional Brownian motion on [0, 1] with Hurst index H, every
+  coordinate independent, sampled exactly on the grid by circulant embedding
+  of the fractional Gaussian noise covariance (the Davies-Harte method):
+  gamma(k) = (|k+1|^{2H} - 2|k|^{2H} + |k-1|^{2H}) / 2 embedded in a
+  circulant of size 2n, whose FFT gives non-negative eigenvalues for every
+  H in (0, 1); increments are scaled by n^{-H}.
 
 Layout: a batch of paths is a packed row-major FP32 array of shape
 ``(sum(lengths), d)`` plus an int64 ``lengths`` vector counting POINTS per path
@@ -151,3 +157,35 @@ def workload_long_pair(n_seg: int = 1_000_000, d: int = 8, seed: int = 3001):
     rng = np.random.default_rng(seed)
     inc = (rng.standard_normal((2 * n_seg, d)) / np.sqrt(n_seg)).astype(np.float32)
     return np.ascontiguousarray(inc), np.array([n_seg, n_seg], dtype=np.int64)
+
+
+def fgn_autocov(n: int, hurst: float) -> np.ndarray:
+    """Autocovariance gamma(0..n-1) of unit fractional Gaussian noise."""
+    k = np.arange(n, dtype=np.float64)
+    h2 = 2.0 * hurst
+    return 0.5 * (np.abs(k + 1) ** h2 - 2.0 * np.abs(k) ** h2 + np.abs(k - 1) ** h2)
+
+
+def fbm(n_paths: int, n_seg: int, d: int, hurst: float, seed: int = 0):
+    """Packed FP32 points and int64 point counts of fBM paths (Davies-Harte).
+
+    Each path has n_seg segments on [0, 1]; each coordinate is an independent
+    fBM with Hurst index ``hurst`` (increment variance n_seg^(-2H))."""
+    if not 0.0 < hurst < 1.0:
+        raise ValueError("hurst must be in (0, 1)")
+    rng = np.random.default_rng(seed)
+    n = int(n_seg)
+    g = fgn_autocov(n + 1, hurst)
+    circ = np.concatenate([g[:n + 1], g[n - 1:0:-1]])  # first row of the 2n circulant
+    lam = np.fft.fft(circ).real
+    lam = np.maximum(lam, 0.0)  # round-off only: exact eigenvalues are >= 0
+    m = circ.size
+    paths = []
+    for _ in range(n_paths):
+        inc = np.empty((n, d))
+        for e in range(d):
+            z = rng.standard_normal(m) + 1j * rng.standard_normal(m)
+            w = np.fft.fft(np.sqrt(lam / m) * z)
+            inc[:, e] = w.real[:n]
+        paths.append(_points_from_increments(inc * float(n) ** (-hurst)).astype(np.float32))
+    return pack(paths)
