@@ -31,6 +31,10 @@ L2_FLUSH_BYTES = 512 << 20
 ORACLE_SAMPLE_PAIRS = 16
 
 
+METRIC = ("fwd & fwd+bwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=16 "
+          "sigma in {1,4}")
+
+
 def tile_flops(P: int, nr: int, d: int) -> int:
     """FP32 operations per tile of the solver (FMA = 2), as executed: the
     increment inner product (2d), the ring powers, the Hankel sums of both
@@ -320,8 +324,7 @@ def main():
         e2e_ms = float(t.item())
 
     line = {
-        "metric": "fwd & fwd+bwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=16 "
-                  "sigma in {1,4}",
+        "metric": METRIC,
         "value": value,
         "fwd_only": {"value": cells * world / (fwd_ms * 1e-3), "unit": "cells/s",
                      "ms": fwd_ms, "note": "forward solver kernels of both Grams alone"}, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
@@ -453,12 +456,14 @@ def run_reference(args, world, rank):
     n_cells = len(SIGMAS) * per_step * N_SEG * N_SEG
     v = n_cells / statistics.mean(times)
     line = {"impl": "reference",
-            "metric": "fwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=16 sigma in {1,4}",
+            "metric": METRIC,
             "value": v, "unit": "cells/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Brownian, PCG64)",
             "config": {"workload": "gram_B64_L1024_d16_sigma1+4",
-                       "sample": f"{per_step} pairs per sigma per step"},
+                       "sample": f"{per_step} pairs per sigma per step",
+                       "step": "forward only: the FP64 oracle has no adjoint (its gradient is by "
+                               "finite differences), so every sampled cell is a forward cell"},
             "cpu_baseline": {"value": v, "unit": "cells/s", "cores": thr, "kind": "oracle",
                              "sample": f"{per_step} upper-triangle pairs per sigma per step, FP64 "
                                        f"tile series N=24, OpenMP over pairs"},
