@@ -52,12 +52,14 @@ struct BwdArgs {
 
 template <int P, int D>
 struct BwdSmem {
-    static constexpr int S = P + 4;   // record / forward seam entry
+    static constexpr int S = P + 4;   // forward seam entry
+    static constexpr int RS = rec_floats(P);  // record per lane
+    static constexpr int RB = 32 * (S > RS ? S : RS);  // one record block / seam-in block
     static constexpr int SA = P + 1;  // adjoint seam entry: corner, b1..bP
     static constexpr int DS = DyStride<D>::value;
     // dy ring, two record blocks (the first doubles as pass A's seam-in
     // block), adjoint seam in/out blocks, column gradients, two mbarriers
-    static constexpr int per_warp = 64 * DS + 2 * 32 * S + 2 * 32 * SA + 64 * D + 4;
+    static constexpr int per_warp = 64 * DS + 2 * RB + 2 * 32 * SA + 64 * D + 4;
 };
 
 __device__ __forceinline__ float exp2_nonneg(int n) {
@@ -109,8 +111,9 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     const int warp = threadIdx.x >> 5;
     const int gwarp = blockIdx.x * (blockDim.x >> 5) + warp;
     float* dyw = smem + warp * BwdSmem<P, D>::per_warp;  // 64-column ring of dy
+    constexpr int RS = BwdSmem<P, D>::RS;
     float* sin_ = dyw + 64 * DS;                        // forward seam-in block
-    float* rbuf1 = sin_ + 32 * S;                       // second record block
+    float* rbuf1 = sin_ + BwdSmem<P, D>::RB;            // second record block
     float* ain = rbuf1 + 32 * S;                        // adjoint seam-in block
     float* aout = ain + 32 * SA;                        // adjoint seam-out block
     float* colacc = aout + 32 * SA;                     // column gradient [D][64]
@@ -128,7 +131,11 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     }
     __syncwarp();
     unsigned nld = 0;
-    constexpr uint32_t kRecBytes = 32 * S * (uint32_t)sizeof(float);
+    constexpr uint32_t kRecBytes = 32 * RS * (uint32_t)sizeof(float);
+    // record fields: [0] hi, [1] b1lo, [1 + q] b_q, [P + 2] exponent word;
+    // groups of four wholly before the exponent are stored at the start of
+    // the step, the last group (with the exponent) at its end
+    constexpr int kFullGroups = (P + 2) / 4;
 
     for (;;) {
         int item = 0;
@@ -203,12 +210,17 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
             const int j = t - lane;
             if (j >= 0 && j < L2) {
                 // record of the incoming left edge, before alignment
-                float* r = rec + (size_t)t * S * 32 + lane;
-                r[0] = hi;
-                r[32] = lo;
-                r[64] = b1lo;
+                float rv[RS];
+                rv[0] = hi;
+                rv[1] = b1lo;
 #pragma unroll
-                for (int q = 1; q <= P; ++q) r[(2 + q) * 32] = b[q];
+                for (int q = 1; q <= P; ++q) rv[1 + q] = b[q];
+#pragma unroll
+                for (int q = P + 2; q < RS; ++q) rv[q] = 0.0f;
+                float4* r4 = reinterpret_cast<float4*>(rec + (size_t)t * RS * 32 + lane * RS);
+#pragma unroll
+                for (int g = 0; g < kFullGroups; ++g)
+                    r4[g] = make_float4(rv[4 * g], rv[4 * g + 1], rv[4 * g + 2], rv[4 * g + 3]);
                 const int Eb = E;
                 if (F != E) {
                     if (F > E) {
@@ -247,7 +259,9 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     E += 64;
                     bump = 1;
                 }
-                r[(P + 3) * 32] = __int_as_float(pack_exp(F, Eb, bump));
+                rv[P + 2] = __int_as_float(pack_exp(F, Eb, bump));
+                r4[kFullGroups] = make_float4(rv[4 * kFullGroups], rv[4 * kFullGroups + 1],
+                                              rv[4 * kFullGroups + 2], rv[4 * kFullGroups + 3]);
                 ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
 #pragma unroll
                 for (int q = 1; q <= P; ++q) ob[q] = b[q];
@@ -285,7 +299,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         unsigned issued = 0, waited = 0;
         auto rbuf = [&](unsigned n) { return (n & 1) ? rbuf1 : sin_; };
         // pass-A step of reverse step tp: every active lane reads t = L2 + 30 - tp
-        auto rec_block = [&](int tp) { return rec + (size_t)(L2 + 30 - tp) * S * 32; };
+        auto rec_block = [&](int tp) { return rec + (size_t)(L2 + 30 - tp) * RS * 32; };
         if (ok) {
             const unsigned first = T < 2 ? (unsigned)T : 2u;
             if (lane == 0)
@@ -332,13 +346,19 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     ok = false;
                     break;
                 }
-                const float* r = rbuf(n) + lane;
-                rhi = r[0];
-                rb1lo = r[64];
+                const float4* r4 = reinterpret_cast<const float4*>(rbuf(n) + lane * RS);
+                float rv[RS];
+#pragma unroll
+                for (int g = 0; g < RS / 4; ++g) {
+                    const float4 v = r4[g];
+                    rv[4 * g] = v.x; rv[4 * g + 1] = v.y; rv[4 * g + 2] = v.z; rv[4 * g + 3] = v.w;
+                }
+                rhi = rv[0];
+                rb1lo = rv[1];
                 rb[0] = 0.0f;
 #pragma unroll
-                for (int q = 1; q <= P; ++q) rb[q] = r[(2 + q) * 32];
-                rexp = __float_as_int(r[(P + 3) * 32]);
+                for (int q = 1; q <= P; ++q) rb[q] = rv[1 + q];
+                rexp = __float_as_int(rv[P + 2]);
                 __syncwarp();
                 if (tp + 2 < T) {
                     if (lane == 0) bulk_load(rbuf(n + 2), rec_block(tp + 2), kRecBytes, &bars[n & 1]);

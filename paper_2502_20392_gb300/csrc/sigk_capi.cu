@@ -292,7 +292,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         // forward seams of every strip boundary: (strips - 1) x swept columns
         const int64_t strips = (o.max_len + 31) / 32;
         L->store_floats = L->n_pairs * (strips > 1 ? strips - 1 : 0) * o.max_len * L->stride;
-        L->rec_stride = (o.max_len + 31) * (int64_t)L->stride * 32;
+        L->rec_stride = (o.max_len + 31) * (int64_t)rec_floats(o.order) * 32;
         L->store = off; off = align256(off + sizeof(float) * (size_t)L->store_floats);
         L->store_off = off; off = align256(off + sizeof(int64_t) * (size_t)L->n_pairs);
         L->pair_exp = off; off = align256(off + sizeof(int32_t) * (size_t)L->n_pairs);

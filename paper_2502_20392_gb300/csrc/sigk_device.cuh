@@ -88,6 +88,11 @@ struct ItemRef {
     int next;   // item that consumes this strip's outgoing seam, or -1
 };
 
+// Floats per lane in an adjoint record (pass A -> pass B): the incoming left
+// edge (hi, b1lo, b1..bP) and the exponent word, padded to a multiple of 4 so
+// a lane's record moves as 16-byte vectors.
+__host__ __device__ constexpr int rec_floats(int P) { return (P + 3 + 3) / 4 * 4; }
+
 // Largest i in [0, n) with v[i] <= x (v non-decreasing, v[0] <= x).
 __device__ __forceinline__ int upper_index(const int32_t* v, int n, int x) {
     int lo = 0, hi = n - 1;
