@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     constexpr int RS = BwdSmem<P, D>::RS;
     float* sin_ = dyw + 64 * DS;                        // forward seam-in block
     float* rbuf1 = sin_ + BwdSmem<P, D>::RB;            // second record block
-    float* ain = rbuf1 + 32 * S;                        // adjoint seam-in block
+    float* ain = rbuf1 + BwdSmem<P, D>::RB;             // adjoint seam-in block
     float* aout = ain + 32 * SA;                        // adjoint seam-out block
     float* colacc = aout + 32 * SA;                     // column gradient [D][64]
     uint64_t* bars = reinterpret_cast<uint64_t*>(colacc + 64 * D);  // record-load mbarriers

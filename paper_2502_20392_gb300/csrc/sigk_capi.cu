@@ -6,6 +6,7 @@
 // host synchronisation and no host lengths are needed), the persistent
 // solver, and the FP64 reductions (Gram mirror, MMD^2).  The library never
 // allocates device memory.
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -165,6 +166,8 @@ struct Layout {
     int64_t cstride;
     int64_t n_pairs, n_paths_x, n_paths_y;
     int nslot, wcols, grid, nwarps, rows_per_strip, stride;
+    int fwd_shift;       // training: forward items are 2^fwd_shift table strips
+    size_t item_start2, lvl2;
     int64_t nwords;
     KernelInfo info;
 };
@@ -202,7 +205,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     if (L->cm && train)
         return fail(SIGK_ERR_UNSUPPORTED, "the backward supports d <= 16 in this build");
     const int qinfo = L->cm ? fwd_cm_info_dispatch(o.order, o.rings, L->f64, &L->info)
-                            : fwd_info_dispatch(o.order, o.rings, D, train ? 1 : 0, &L->info);
+                            : fwd_info_dispatch(o.order, o.rings, D, 0, &L->info);
     if (qinfo != 0 || L->info.blocks_per_sm <= 0)
         return fail(SIGK_ERR_CUDA, "kernel occupancy query failed");
     int dev = 0, sms = 0;
@@ -212,7 +215,12 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     const int full_grid = sms * L->info.blocks_per_sm;
     L->grid = o.grid_ctas > 0 ? (o.grid_ctas < full_grid ? o.grid_ctas : full_grid) : full_grid;
     L->nwarps = L->grid * (L->info.threads / 32);
-    L->rows_per_strip = 32 * L->info.rows_per_lane;
+    // the pair table counts strips of 32 * R rows; in training it counts
+    // 32-row strips (the adjoint's unit) and the forward takes R of them
+    L->rows_per_strip = train ? 32 : 32 * L->info.rows_per_lane;
+    L->fwd_shift = 0;
+    if (train)
+        for (int r = L->info.rows_per_lane; r > 1; r >>= 1) ++L->fwd_shift;
     L->stride = o.order + 4;
     L->n_pairs = pair_count(op, n_x, n_y, o.flags);
     // Seam ring, pair-major: nslot > concurrent warps; wcols large enough that
@@ -258,6 +266,8 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->pairs = off; off = align256(off + sizeof(PairDesc) * (size_t)L->n_pairs);
     L->item_start = off; off = align256(off + sizeof(int32_t) * (size_t)(L->n_pairs + 1));
     L->order = off; off = align256(off + sizeof(int32_t) * (size_t)(L->n_pairs + 1));
+    L->item_start2 = off; off = align256(off + sizeof(int32_t) * (size_t)(L->n_pairs + 1));
+    L->lvl2 = off; off = align256(off + sizeof(int32_t) * (size_t)(kLevelCap + 2));
     L->lvl = off; off = align256(off + sizeof(int32_t) * 2 * (size_t)(kLevelCap + 2));
     L->prod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
     L->cons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->nwords);
@@ -316,8 +326,12 @@ struct Header {
     int pad;
     unsigned long long counters[4];
     int sched[4];  // schedule: mode, n_levels, n_items (Schedule::hdr)
-    long long diag[3];  // first timed-out wait: address, target, value seen
+    int sched2[4];  // training forward's schedule (items of 2^fwd_shift strips)
+    int pad2[12];
+    long long diag[3];  // first timed-out wait: address, target, value seen (byte 128)
 };
+static_assert(offsetof(Header, diag) == 128, "record_timeout writes the diagnosis at byte 128");
+static_assert(sizeof(Header) <= 256, "the header occupies the first 256 bytes of the workspace");
 
 // ---------------------------------------------------------------------------
 // device-side planner: one CTA builds prefix offsets, the pair table and the
@@ -347,6 +361,9 @@ struct PlanArgs {
     int32_t* lvl;       // level starts [lvl_cap + 2], then a scratch of the same size
     int lvl_cap;        // largest strip count the level arrays hold
     int allow_sm;       // strip-major allowed (the seam ring holds whole strips)
+    int fwd_shift;      // training: the forward solves 2^fwd_shift strips per item
+    int32_t* item_start2;  // training forward's item starts [pairs + 1]
+    int32_t* lvl2;         // training forward's level starts
     unsigned long long* prod;
     unsigned long long* cons;
     long long* done;
@@ -401,6 +418,36 @@ __device__ void block_exclusive_scan(const int64_t* v, int64_t n, int64_t* out, 
         run += v[i];
     }
     if (t == kPlanThreads - 1) out[n] = sh[t];
+    __syncthreads();
+}
+
+// Exclusive prefix over n pairs (pair i = order[i], or i when order is
+// null) of their items, ceil(n_strips / 2^shift), into out[0..n]; one CTA.
+__device__ void block_prefix_items(const PairDesc* pairs, const int32_t* order, int64_t n,
+                                   int shift, int32_t* out, int64_t* sh) {
+    const int t = threadIdx.x;
+    const int64_t chunk = (n + kPlanThreads - 1) / kPlanThreads;
+    const int64_t b0 = t * chunk, b1 = (b0 + chunk < n) ? b0 + chunk : n;
+    auto units = [&](int64_t i) -> int64_t {
+        const int ns = pairs[order ? order[i] : i].n_strips;
+        return (ns + (1 << shift) - 1) >> shift;
+    };
+    int64_t sum = 0;
+    for (int64_t i = b0; i < b1; ++i) sum += units(i);
+    sh[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < kPlanThreads; o <<= 1) {
+        int64_t add = (t >= o) ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += add;
+        __syncthreads();
+    }
+    int64_t run = sh[t] - sum;
+    for (int64_t i = b0; i < b1; ++i) {
+        out[i] = (int32_t)run;
+        run += units(i);
+    }
+    if (t == kPlanThreads - 1) out[n] = (int32_t)sh[t];
     __syncthreads();
 }
 
@@ -616,32 +663,42 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
             if (n > 0) A.order[atomicAdd(&cur[n], 1)] = (int32_t)p;
         }
         __syncthreads();
-        if (A.hdr->sched[0] == 2) {
-            // item_start over the sorted pairs
-            const int64_t n = A.hdr->sched[1];
-            const int64_t chunk = (n + kPlanThreads - 1) / kPlanThreads;
-            const int64_t b0 = t * chunk, b1 = (b0 + chunk < n) ? b0 + chunk : n;
-            int64_t sum = 0;
-            for (int64_t i = b0; i < b1; ++i) sum += A.pairs[A.order[i]].n_strips;
-            sh[t] = sum;
-            __syncthreads();
-            for (int o = 1; o < kPlanThreads; o <<= 1) {
-                int64_t add = (t >= o) ? sh[t - o] : 0;
-                __syncthreads();
-                sh[t] += add;
-                __syncthreads();
-            }
-            int64_t run = sh[t] - sum;
-            for (int64_t i = b0; i < b1; ++i) {
-                A.item_start[i] = (int32_t)run;
-                run += A.pairs[A.order[i]].n_strips;
-            }
-            if (t == kPlanThreads - 1) A.item_start[n] = (int32_t)sh[t];
-        }
+        if (A.hdr->sched[0] == 2)  // item_start over the sorted pairs
+            block_prefix_items(A.pairs, A.order, A.hdr->sched[1], 0, A.item_start, sh);
     } else if (t == 0) {
         A.hdr->sched[0] = 0;
         A.hdr->sched[1] = 0;
         A.hdr->sched[2] = A.item_start[A.n_pairs];
+    }
+    __syncthreads();
+    // training: the forward's own schedule in items of 2^fwd_shift strips,
+    // same mode and pair order (the adjoint keeps the 32-row schedule)
+    if (A.train) {
+        const int sh2 = A.fwd_shift;
+        const int mode = A.hdr->sched[0];
+        if (mode == 1) {
+            if (t == 0) {
+                const int n2 = (ms + (1 << sh2) - 1) >> sh2;
+                int run = 0;
+                for (int l = 0; l < n2; ++l) {
+                    A.lvl2[l] = run;
+                    const int n = l << sh2;  // pairs with more than n strips
+                    run += A.lvl[n + 1] - A.lvl[n];
+                }
+                A.lvl2[n2] = run;
+                A.hdr->sched2[0] = 1;
+                A.hdr->sched2[1] = n2;
+                A.hdr->sched2[2] = run;
+            }
+        } else {
+            const int64_t n = mode == 2 ? A.hdr->sched[1] : A.n_pairs;
+            block_prefix_items(A.pairs, mode == 2 ? A.order : nullptr, n, sh2, A.item_start2, sh);
+            if (t == 0) {
+                A.hdr->sched2[0] = mode;
+                A.hdr->sched2[1] = mode == 2 ? A.hdr->sched[1] : 0;
+                A.hdr->sched2[2] = A.item_start2[n];
+            }
+        }
     }
     __syncthreads();
     // reset the seam synchronisation words and the work counter
@@ -895,6 +952,9 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     pa.lvl = (int32_t*)(base + L.lvl);
     pa.lvl_cap = kLevelCap;
     pa.allow_sm = L.strip_major ? 1 : 0;
+    pa.fwd_shift = L.fwd_shift;
+    pa.item_start2 = (int32_t*)(base + L.item_start2);
+    pa.lvl2 = (int32_t*)(base + L.lvl2);
     pa.prod = (unsigned long long*)(base + L.prod);
     pa.cons = (unsigned long long*)(base + L.cons);
     pa.done = (long long*)(base + L.done);
@@ -921,11 +981,20 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     SolverArgs sa;
     memset(&sa, 0, sizeof(sa));
     sa.pairs = pa.pairs;
-    sa.sched.hdr = hdr->sched;
-    sa.sched.item_start = pa.item_start;
-    sa.sched.order = pa.order;
-    sa.sched.level_start = pa.lvl;
-    sa.sched.n_pairs = (int32_t)L.n_pairs;
+    Schedule table_sched;  // 32*R-row strips (inference) or 32-row strips (adjoint)
+    table_sched.hdr = hdr->sched;
+    table_sched.item_start = pa.item_start;
+    table_sched.order = pa.order;
+    table_sched.level_start = pa.lvl;
+    table_sched.n_pairs = (int32_t)L.n_pairs;
+    table_sched.shift = 0;
+    sa.sched = table_sched;
+    if (train) {  // the training forward's items are 2^fwd_shift table strips
+        sa.sched.hdr = hdr->sched2;
+        sa.sched.item_start = pa.item_start2;
+        sa.sched.level_start = pa.lvl2;
+        sa.sched.shift = L.fwd_shift;
+    }
     sa.n_pairs = (int32_t)L.n_pairs;
     sa.inc_mode = pa.inc_mode;
     sa.d = d;
@@ -949,7 +1018,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_start, stream);
         e = L.cm ? fwd_cm_launch_dispatch(o.order, o.rings, L.f64, sa, base + L.cscratch, L.cstride,
                                           L.grid, stream)
-                 : fwd_launch_dispatch(o.order, o.rings, dim_bucket(d), train ? 1 : 0, sa, L.grid, stream);
+                 : fwd_launch_dispatch(o.order, o.rings, dim_bucket(d), 0, sa, L.grid, stream);
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
         if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_stop, stream);
     }
@@ -957,7 +1026,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         BwdArgs ba;
         memset(&ba, 0, sizeof(ba));
         ba.pairs = pa.pairs;
-        ba.sched = sa.sched;
+        ba.sched = table_sched;
         ba.n_pairs = (int32_t)L.n_pairs;
         ba.inc_mode = pa.inc_mode;
         ba.d = d;
@@ -1131,6 +1200,7 @@ static cudaError_t launch_stats(const PlanArgs& pa, double* stats, size_t stats_
     if ((e = cudaMemsetAsync(&pa.hdr->item_counter, 0, sizeof(int), s)) != cudaSuccess) return e;
     StatArgs sa;
     sa.pairs = pa.pairs;
+    sa.sched.shift = 0;
     sa.sched.hdr = pa.hdr->sched;
     sa.sched.item_start = pa.item_start;
     sa.sched.order = pa.order;
@@ -1198,6 +1268,9 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     pa.lvl = (int32_t*)(base + L.lvl);
     pa.lvl_cap = kLevelCap;
     pa.allow_sm = L.strip_major ? 1 : 0;
+    pa.fwd_shift = L.fwd_shift;
+    pa.item_start2 = (int32_t*)(base + L.item_start2);
+    pa.lvl2 = (int32_t*)(base + L.lvl2);
     pa.prod = (unsigned long long*)(base + L.prod);
     pa.cons = (unsigned long long*)(base + L.cons);
     pa.done = (long long*)(base + L.done);

@@ -73,12 +73,17 @@ struct PairDesc {
 //     so a consumer rarely waits.  Used when the strip counts are even.
 //   mode 2, pair-major over order[]: item_start holds the prefix sums in that
 //     order, so the pairs with the longest chains of strips start first.
+//
+// A schedule may count work in units of 2^shift strips (the training forward
+// solves 32*R rows per item while the table counts 32-row strips): a pair
+// with n strips has ceil(n / 2^shift) items.
 struct Schedule {
     const int* hdr;                // mode, n_levels / sorted pairs, n_items
-    const int32_t* item_start;     // modes 0, 2: [pairs + 1] prefix sums of n_strips
+    const int32_t* item_start;     // modes 0, 2: [pairs + 1] prefix sums of the items per pair
     const int32_t* order;          // modes 1, 2: pairs by decreasing strip count
     const int32_t* level_start;    // mode 1: [n_levels + 1]
     int32_t n_pairs;
+    int32_t shift;                 // items are 2^shift strips
 };
 
 struct ItemRef {
@@ -121,7 +126,8 @@ __device__ __forceinline__ ItemRef decode_item(const Schedule& S, const PairDesc
         r.pair = p;
         r.k = item - S.item_start[q];
         r.prev = r.k > 0 ? item - 1 : -1;
-        r.next = r.k + 1 < pairs[p].n_strips ? item + 1 : -1;
+        const int units = (pairs[p].n_strips + (1 << S.shift) - 1) >> S.shift;
+        r.next = r.k + 1 < units ? item + 1 : -1;
     }
     return r;
 }
@@ -180,11 +186,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // First time-out of a launch: the status word, then (for diagnosis) the
 // waited-on address, the target and the value last seen, as three 64-bit
-// words at byte 64 of the status word's 256-byte header.
+// words at byte 128 of the status word's 256-byte header.
 __device__ __forceinline__ void record_timeout(int* status, const void* p, long long target,
                                                long long seen) {
     if (atomicCAS(status, 0, kErrTimeout) == 0) {
-        long long* diag = reinterpret_cast<long long*>(status + 16);
+        long long* diag = reinterpret_cast<long long*>(status + 32);
         diag[0] = (long long)(uintptr_t)p;
         diag[1] = target;
         diag[2] = seen;

@@ -94,6 +94,16 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
         const int i0 = s * 32 * R;
         const bool train = A.store != nullptr;
         float* st_pair = train ? A.store + A.store_off[lo_p] : nullptr;
+        // training: the store keeps the seam after every 32-row strip (the
+        // adjoint's checkpoints).  This item covers 32-row strips s*R ..
+        // s*R + R - 1; lane l = 32m/R - 1 ends strip s*R + m - 1, so lanes
+        // 32/R - 1, 2*32/R - 1, ... write the seams inside the item directly,
+        // lane 31 the item's last one through the seam-out block.
+        const int n32 = pd.n_strips;  // table strips (32 rows) in training mode
+        const int mid_m = (lane + 1) * R / 32;  // m for a mid-item seam lane, else 0
+        const bool mid_writer = train && R > 1 && lane != 31 && ((lane + 1) * R) % 32 == 0 &&
+                                s * R + mid_m < n32;
+        float* mid_dst = mid_writer ? st_pair + (size_t)(s * R + mid_m - 1) * L2 * S : nullptr;
         bool ok = true;
 
         // row increments of this lane (zero past the end of the path)
@@ -144,7 +154,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                     ok = __shfl_sync(kFull, okl, 0);
                     if (ok) {
                         const float* src =
-                            train ? st_pair + ((size_t)(s - 1) * L2 + t) * S
+                            train ? st_pair + ((size_t)(s * R - 1) * L2 + t) * S
                                   : A.seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
                         for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src + idx);
                         __syncwarp();
@@ -234,6 +244,13 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                 for (int q = 1; q <= P; ++q) ob[q] = b[q];
                 tiles_done += (unsigned long long)max(0, min(R, L1 - (i0 + lane * R)));
                 lane_tiles += R;
+                if (mid_writer) {
+                    float* e_ = mid_dst + (size_t)j * S;
+                    e_[0] = hi; e_[1] = lo; e_[2] = b1lo;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) e_[2 + q] = b[q];
+                    e_[P + 3] = __int_as_float(E);
+                }
                 if (lane == 31) {
                     if (has_out) {
                         float* e_ = sout + (j & 31) * S;
@@ -271,7 +288,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                     ok = __shfl_sync(kFull, okl, 0);
                 }
                 if (ok) {
-                    float* dst = train ? st_pair + ((size_t)s * L2 + start) * S
+                    float* dst = train ? st_pair + ((size_t)(s * R + R - 1) * L2 + start) * S
                                        : A.seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
                     for (int idx = lane; idx < nb * S; idx += 32) __stcg(dst + idx, sout[idx]);
                     __threadfence();

@@ -99,7 +99,9 @@ def test_pairs_gradient_vs_fd(S, orc, d):
                                        err_msg=f"pair {p} side {which}")
 
 
-def test_gram_self_gradient_vs_fd(S, orc):
+@pytest.mark.parametrize("order,rings", [(12, 6), (6, 4), (10, 6)])
+def test_gram_self_gradient_vs_fd(S, orc, order, rings):
+    # orders 6 and 10: the adjoint's per-lane record is wider than a seam entry
     from paper_2502_20392_gb300 import synth
     pts, lens = synth.brownian(4, [40, 70, 33, 100], 8, 1.0, seed=91)
     paths = synth.split(pts, lens)
@@ -107,10 +109,11 @@ def test_gram_self_gradient_vs_fd(S, orc):
     W = rng.standard_normal((4, 4))  # not symmetric: both triangles weigh in
     gX, _, G = S.backward(S.OP_GRAM, torch.from_numpy(pts).to(dev()),
                           torch.from_numpy(lens).to(dev()), None, None, torch.from_numpy(W),
-                          S.Opts(**OPTS, max_len=128))
+                          S.Opts(order=order, rings=rings, max_len=128))
     gX = synth.split(gX.cpu().numpy(), lens)
     ref_G = orc.series_gram(incs(paths))
-    np.testing.assert_allclose(G.cpu().numpy(), ref_G, rtol=1e-5)
+    # order 6 truncates at ~1e-6 relative on these paths
+    np.testing.assert_allclose(G.cpu().numpy(), ref_G, rtol=1e-5 if order >= 10 else 1e-4)
     for a in (0, 3):
         def f(pp):
             return float((W * orc.series_gram(incs(pp))).sum())
