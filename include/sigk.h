@@ -56,7 +56,7 @@ typedef enum {
     SIGK_ERR_WORKSPACE = -4,  /* ws too small or misaligned */
     SIGK_ERR_CUDA = -5,       /* a CUDA runtime call failed (see sigk_last_error) */
     SIGK_ERR_TIMEOUT = -6,    /* a bounded inter-warp wait ran out on the device */
-    SIGK_ERR_UNSUPPORTED = -8 /* a combination this build does not provide */
+    SIGK_ERR_UNSUPPORTED = -8 /* a combination this library does not provide */
 } sigk_status;
 
 /* Operation codes for sigk_workspace_size / sigk_plan. */

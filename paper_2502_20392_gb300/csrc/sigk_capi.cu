@@ -195,7 +195,7 @@ static int64_t pair_count(int op, int64_t n_x, int64_t n_y, int flags) {
 static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Opts& o, Layout* L,
                                bool train = false, bool allow_sm = true) {
     const int D = dim_bucket(d);
-    if (D < 0) return fail(SIGK_ERR_UNSUPPORTED, "d must be in 1..8192 in this build");
+    if (D < 0) return fail(SIGK_ERR_UNSUPPORTED, "d must be in 1..8192");
     L->train = train;
     L->f64 = (o.flags & SIGK_FLAG_FP64) != 0;
     L->cm = (D == 0) || L->f64;
@@ -203,7 +203,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     if (L->f64 && train)
         return fail(SIGK_ERR_UNSUPPORTED, "the backward runs in FP32 only (no SIGK_FLAG_FP64)");
     if (L->cm && train)
-        return fail(SIGK_ERR_UNSUPPORTED, "the backward supports d <= 16 in this build");
+        return fail(SIGK_ERR_UNSUPPORTED, "the backward supports d <= 16");
     const int qinfo = L->cm ? fwd_cm_info_dispatch(o.order, o.rings, L->f64, &L->info)
                             : fwd_info_dispatch(o.order, o.rings, D, 0, &L->info);
     if (qinfo != 0 || L->info.blocks_per_sm <= 0)

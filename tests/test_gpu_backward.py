@@ -202,3 +202,48 @@ def test_backward_schedules_agree_bitwise(S):
     assert torch.equal(G1, G2)
     # gradients accumulate with float atomics: equal up to summation order
     torch.testing.assert_close(g1, g2, rtol=1e-5, atol=1e-6 * float(g1.abs().max()))
+
+
+def test_increments_mode_gradient_and_gram_xy(S, orc):
+    # FLAG_INCREMENTS: gradients are with respect to the increments; a Gram of
+    # X against a different Y also returns grad_Y
+    from paper_2502_20392_gb300 import synth
+    px, lxp = synth.brownian(3, [30, 55, 41], 4, 1.0, seed=95)
+    py, lyp = synth.brownian(2, [47, 36], 4, 1.0, seed=96)
+    xs, ys = synth.split(px, lxp), synth.split(py, lyp)
+    ix = [np.diff(p, axis=0).astype(np.float32) for p in xs]
+    iy = [np.diff(p, axis=0).astype(np.float32) for p in ys]
+    IX, lix = synth.pack(ix)  # increments mode: one row per segment, len counts rows
+    IY, liy = synth.pack(iy)
+    W = np.random.default_rng(9).standard_normal((3, 2))
+    o = S.Opts(order=12, rings=6, max_len=128, flags=S.FLAG_INCREMENTS)
+    gX, gY, G = S.backward(S.OP_GRAM, torch.from_numpy(IX).to(dev()), torch.from_numpy(lix).to(dev()),
+                           torch.from_numpy(IY).to(dev()), torch.from_numpy(liy).to(dev()),
+                           torch.from_numpy(W), o)
+    ref_G = np.array([[orc.series_pair(a.astype(np.float64), b.astype(np.float64)) for b in iy]
+                      for a in ix])
+    np.testing.assert_allclose(G.cpu().numpy(), ref_G, rtol=1e-5)
+    gX = synth.split(gX.cpu().numpy(), lix)
+    gY = synth.split(gY.cpu().numpy(), liy)
+    rng = np.random.default_rng(10)
+
+    def fd_inc(which, p, coords, h=1e-3):
+        out = []
+        for c in coords:
+            vals = []
+            for hh in (h, h / 2):
+                fs = []
+                for sgn in (1.0, -1.0):
+                    a = [v.astype(np.float64) for v in ix]
+                    b = [v.astype(np.float64) for v in iy]
+                    (a if which == 0 else b)[p].reshape(-1)[c] += sgn * hh
+                    Gp = np.array([[orc.series_pair(u, v) for v in b] for u in a])
+                    fs.append(float((W * Gp).sum()))
+                vals.append((fs[0] - fs[1]) / (2 * hh))
+            out.append((4 * vals[1] - vals[0]) / 3)
+        return np.array(out)
+
+    for which, grads, p in ((0, gX, 1), (1, gY, 0)):
+        coords = rng.choice(grads[p].size, size=8, replace=False)
+        ref = fd_inc(which, p, coords)
+        np.testing.assert_allclose(grads[p].reshape(-1)[coords], ref, atol=1e-4 * np.abs(ref).max())

@@ -151,7 +151,7 @@ def test_brute_force_three_ways(orc, seed):
     assert ks == pytest.approx(kf, rel=1e-8, abs=1e-9)
 
 
-def test_golden_survey_values(orc):
+def test_golden_chen_values(orc):
     # Values recorded in the golden fixture (written by tests/golden/make_golden.py
     # from the Chen brute force, which shares nothing with the series code).
     with open(os.path.join(GOLDEN, "chen_tiny.json")) as f:
