@@ -67,6 +67,22 @@ def adjoint_tile_flops(P: int, nr: int, d: int) -> int:
     return tile_flops(P, nr, d) + 2 * d + inv + adj + 4 * d
 
 
+def rank_workloads(rank: int, n_paths: int):
+    """The batches rank `rank` solves: the Gram workload with per-rank seeds
+    (independent problems per GPU: weak scaling, no data-path collective)."""
+    from paper_2502_20392_gb300 import synth
+    return [synth.workload_gram_1024(s, seed + 1000 * rank, n_paths=n_paths) for s, seed, _, _ in SIGMAS]
+
+
+def max_over_ranks(x: float, device, dist) -> float:
+    """Max of a per-rank time over the process group (the job's time is the
+    slowest rank's)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def pairs_of_gram(n):
     return n * (n + 1) // 2
 
@@ -186,8 +202,7 @@ def main():
     sigk.load()
 
     # each rank solves its own batch (independent problems: weak scaling)
-    host = [synth.workload_gram_1024(s, seed + 1000 * rank, n_paths=N_PATHS)
-            for s, seed, _, _ in SIGMAS]
+    host = rank_workloads(rank, N_PATHS)
     X = [torch.from_numpy(p).to(dev) for p, _ in host]
     L = [torch.from_numpy(l).to(dev) for _, l in host]
     opts = [sigk.Opts(order=P, rings=nr, max_len=N_SEG) for _, _, P, nr in SIGMAS]
@@ -245,9 +260,7 @@ def main():
     kern_ms = [[a.elapsed_time(b) for a, b in row] for row in kev]
     ms = sum(step_ms) / len(step_ms)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dev, dist)
 
     cells = cells_per_step()
     value = cells * world / (ms * 1e-3)
@@ -319,9 +332,7 @@ def main():
         sigk.sync_status(ws)
     e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(e_s, e_e))
     if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e2e_ms, dev, dist)
 
     line = {
         "metric": METRIC,
