@@ -170,7 +170,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default="full", choices=["full", "small"],
                     help="small: 16 paths per Gram (for ncu captures; not a bench line)")
-    ap.add_argument("--sweep", default=None, choices=["roughness", "dimension", "length"],
+    ap.add_argument("--sweep", default=None, choices=["roughness", "dimension", "length", "configs"],
                     help="print one JSON line per point of a sweep instead of the bench line")
     args = ap.parse_args()
     if args.sweep:
@@ -435,6 +435,8 @@ def run_sweep(args):
             emit(sweep="dimension", d=d, metric="cells/s", value=cells / (ms * 1e-3), ms=ms,
                  kernel="register" if d <= 16 else "two-phase",
                  opts=dict(order=o.order, rings=o.rings, refine_c=o.refine_c))
+    elif args.sweep == "configs":
+        run_configs(timed, emit, dev)
     else:
         for k in range(10, 20):
             n = 2 ** k
@@ -447,6 +449,87 @@ def run_sweep(args):
                  workspace_bytes=int(sigk.workspace_size(sigk.OP_PAIRS, 1, 1, 2, o)),
                  opts=dict(order=8, rings=4))
     return 0
+
+
+def run_configs(timed, emit, dev):
+    """Throughput (and the accuracy checks that are cheap on the host) for the
+    five workloads: a 256-segment pair (d=4), the Gram B=64 (both sigmas), a
+    pair of 10^6-segment paths (collinear, against I0(2 sqrt(<X,Y>)), and
+    Brownian), 512 ragged pairs with d=256 (FP32 and FP64), and the MMD of
+    2 x 32 paths of 2048 segments with its gradient."""
+    import math
+
+    import numpy as np
+    import torch
+    from scipy.special import i0
+
+    import oracle
+    from paper_2502_20392_gb300 import sigk, synth
+
+    def t(a):
+        return torch.from_numpy(a).to(dev)
+
+    # pair 256, d=4
+    pts, lens = synth.workload_pair_256()  # two packed paths: x, y
+    xs = synth.split(pts, lens)
+    X, lx = synth.pack(xs[:1])
+    Y, ly = synth.pack(xs[1:])
+    a = [t(v) for v in (X, lx, Y, ly)]
+    o = sigk.plan(sigk.OP_PAIRS, *a, tol=1e-6, opts=sigk.Opts(max_len=257))
+    ws = sigk.Workspace()
+    ms = timed(lambda: sigk.pairs(*a, opts=o, ws=ws, check=False))
+    k = sigk.pairs(*a, opts=o, ws=ws).item()
+    r = oracle.series_pair(np.diff(X.astype(np.float64), axis=0), np.diff(Y.astype(np.float64), axis=0))
+    emit(config="pair_L256_d4", metric="cells/s", value=256 * 256 / (ms * 1e-3), ms=ms,
+         rel_err_vs_oracle=abs(k - r) / abs(r))
+    # Gram B=64 L=1024 d=16, sigma 1 and 4 (forward)
+    for sg in (1.0, 4.0):
+        pts, lens = synth.workload_gram_1024(sg)
+        Xd, Ld = t(pts), t(lens)
+        o = sigk.plan(sigk.OP_GRAM, Xd, Ld, None, None, tol=1e-5, opts=sigk.Opts(max_len=1025))
+        ws = sigk.Workspace()
+        ms = timed(lambda: sigk.gram(Xd, Ld, opts=o, ws=ws, check=False))
+        emit(config=f"gram_B64_L1024_d16_sigma{sg:g}", metric="cells/s",
+             value=2080 * 1024 * 1024 / (ms * 1e-3), ms=ms, opts=dict(order=o.order, rings=o.rings))
+    # 10^6-segment pairs (increments), collinear against the closed form
+    inc, segs, u, tot = synth.collinear_increments(1_000_000, 8, seed=3002, n_paths=2)
+    Xd, Ld = t(inc), t(segs)
+    o = sigk.Opts(order=4, rings=2, flags=sigk.FLAG_INCREMENTS, max_len=1_000_000)
+    ws = sigk.Workspace()
+    n = 1_000_000
+    ms = timed(lambda: sigk.pairs(Xd[:n], Ld[:1], Xd[n:], Ld[1:], opts=o, ws=ws, check=False), reps=1)
+    k = sigk.pairs(Xd[:n], Ld[:1], Xd[n:], Ld[1:], opts=o, ws=ws).item()
+    ref = i0(2 * math.sqrt(float(u @ u) * tot[0] * tot[1]))
+    emit(config="long_pair_1e6_d8_collinear", metric="cells/s", value=1e12 / (ms * 1e-3), ms=ms,
+         rel_err_vs_closed_form=abs(k - ref) / ref, workspace_bytes=int(ws.buf.numel()))
+    inc, segs = synth.workload_long_pair()
+    Xd, Ld = t(inc), t(segs)
+    o = sigk.Opts(order=8, rings=4, flags=sigk.FLAG_INCREMENTS, max_len=1_000_000)
+    ws = sigk.Workspace()
+    ms = timed(lambda: sigk.pairs(Xd[:n], Ld[:1], Xd[n:], Ld[1:], opts=o, ws=ws, check=False), reps=1)
+    emit(config="long_pair_1e6_d8_brownian", metric="cells/s", value=1e12 / (ms * 1e-3), ms=ms,
+         workspace_bytes=int(ws.buf.numel()))
+    # 512 ragged pairs, d=256
+    (X, lx), (Y, ly) = synth.workload_ragged_512()
+    a = [t(v) for v in (X, lx, Y, ly)]
+    cells = float(((lx - 1) * (ly - 1)).sum())
+    for flags, name in ((0, "fp32"), (sigk.FLAG_FP64, "fp64")):
+        o = sigk.plan(sigk.OP_PAIRS, *a, tol=1e-5, opts=sigk.Opts(max_len=8193, flags=flags))
+        ws = sigk.Workspace()
+        ms = timed(lambda: sigk.pairs(*a, opts=o, ws=ws, check=False), reps=1)
+        emit(config=f"ragged_512_d256_{name}", metric="cells/s", value=cells / (ms * 1e-3), ms=ms,
+             opts=dict(order=o.order, rings=o.rings, refine_c=o.refine_c, max_len=o.max_len))
+    # MMD 2 x 32 x 2048, d=8: value, then value + gradient
+    (X, lx), (Y, ly) = synth.workload_mmd_2048()
+    a = [t(v) for v in (X, lx, Y, ly)]
+    o = sigk.Opts(order=6, rings=4, max_len=2048)
+    ws, bws = sigk.Workspace(), sigk.Workspace()
+    cells = 64 * 65 / 2 * 2048 * 2048
+    one = torch.ones(1, dtype=torch.float64)
+    ms_f = timed(lambda: sigk.mmd(*a, opts=o, ws=ws, check=False))
+    ms_b = timed(lambda: sigk.backward(sigk.OP_MMD, *a, one, o, ws=bws, check=False))
+    emit(config="mmd_2x32_L2048_d8", metric="cells/s", value=cells / (ms_f * 1e-3), ms=ms_f,
+         fwd_bwd={"value": cells / (ms_b * 1e-3), "ms": ms_b})
 
 
 def run_reference(args, world, rank):
