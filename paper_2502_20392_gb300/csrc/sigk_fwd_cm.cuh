@@ -42,6 +42,49 @@ __device__ __forceinline__ double inc_at_d(const float* z, int64_t row, int d, i
     return (double)z[(row + 1) * d + e] - (double)z[row * d + e];
 }
 
+// Increments of the 32 consecutive virtual rows v0 .. v0+31 of a path (each
+// segment refined into s pieces) at dimension e, one value per row into
+// dst[r * stride]; rows at or past Lv (virtual rows of the path) give 0.
+// Points: consecutive virtual rows share their end points, so each point is
+// loaded once (one new load per segment instead of two per row).
+__device__ __forceinline__ void stage_increments(float* dst, int stride, const float* z, int v0,
+                                                 int Lv, int d, int e, int inc_mode, int s) {
+    if (e >= d) {
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) dst[r * stride] = 0.0f;
+        return;
+    }
+    const float inv = 1.0f / (float)s;
+    if (inc_mode) {
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            const int v = v0 + r;
+            dst[r * stride] = v < Lv ? (s == 1 ? z[(int64_t)(v / s) * d + e]
+                                               : z[(int64_t)(v / s) * d + e] * inv)
+                                     : 0.0f;
+        }
+        return;
+    }
+    const int Lseg = Lv / s;  // segments of the unrefined path
+    int qc = v0 / s;
+    float p0 = 0.0f, p1 = 0.0f;
+    if (qc < Lseg) {
+        p0 = z[(int64_t)qc * d + e];
+        p1 = z[(int64_t)(qc + 1) * d + e];
+    }
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+        const int q = (v0 + r) / s;
+        if (q != qc) {  // the same for every lane: no divergence
+            qc = q;
+            p0 = p1;
+            p1 = q < Lseg ? z[(int64_t)(q + 1) * d + e] : p0;
+        }
+        const float inc = p1 - p0;
+        dst[r * stride] = q < Lseg ? (s == 1 ? inc : inc * inv) : 0.0f;
+    }
+}
+
 // The wavefront sweep of one 32-row strip with one row per lane, c read
 // from the strip scratch `cst` ([L2][32], column-major) through the shared
 // ring `cring`.  In the seam protocol the strip is `item`, fed by `prev` and
@@ -233,7 +276,10 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
     return ok;
 }
 
-template <int P, typename T, int NR>
+// COMP (FP32 only): add the chunk partials with TwoSum compensation.  Needed
+// for very long dot products (d beyond ~1000); it costs 32 registers, which
+// the shorter ones spend on keeping more loads in flight.
+template <int P, typename T, int NR, bool COMP>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
     fwd_cm_kernel(SolverArgs A, T* cscratch, int64_t cstride) {
     constexpr bool F32 = sizeof(T) == 4;
@@ -289,29 +335,30 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                 __syncwarp();
                 const int e = k0 + lane;
                 // dx chunk, transposed to [dim][row]; dy chunk [column][dim]
+                if constexpr (F32) {
+                    stage_increments(dxs + lane * 36, 1, pd.xr, i0, L1, d, e, A.inc_mode, pd.sx);
+                    stage_increments(dys + lane, kCmKC + 1, pd.yr, j0, L2, d, e, A.inc_mode, pd.sy);
+                } else {
 #pragma unroll 4
                 for (int r = 0; r < 32; ++r) {
                     const int row = i0 + r;
                     const int col = j0 + r;
-                    if constexpr (F32) {
-                        dxs[lane * 36 + r] =
-                            (row < L1 && e < d) ? inc_ref(pd.xr, row, d, e, A.inc_mode, pd.sx) : 0.0f;
-                        dys[r * (kCmKC + 1) + lane] =
-                            (col < L2 && e < d) ? inc_ref(pd.yr, col, d, e, A.inc_mode, pd.sy) : 0.0f;
-                    } else {
+                    {
                         dxs[lane * 36 + r] =
                             (row < L1 && e < d) ? inc_at_d(pd.xr, row / pd.sx, d, e, A.inc_mode) : 0.0;
                         dys[r * (kCmKC + 1) + lane] =
                             (col < L2 && e < d) ? inc_at_d(pd.yr, col / pd.sy, d, e, A.inc_mode) : 0.0;
                     }
                 }
+                }
                 __syncwarp();
                 const int kn = min(kCmKC, d - k0);
                 if constexpr (F32) {
                     // two-level sum: a chunk's products are accumulated from
-                    // zero, then added to the total with TwoSum compensation,
-                    // so the error is that of 32-term sums, whatever d (one
-                    // running sum of 256 products had ~2.5x, of 8192 ~10x more)
+                    // zero, then added to the total (with TwoSum compensation
+                    // under COMP, so the error is that of 32-term sums whatever
+                    // d; one running sum of 256 products had ~2.5x, of 8192
+                    // ~10x more error than the plain two-level sum)
                     float part[32];
 #pragma unroll
                     for (int r = 0; r < 32; ++r) part[r] = 0.0f;
@@ -329,10 +376,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
                     }
 #pragma unroll
                     for (int r = 0; r < 32; ++r) {
-                        const float t = acc[r] + part[r];
-                        const float bp = t - acc[r];
-                        comp[r] += (acc[r] - (t - bp)) + (part[r] - bp);
-                        acc[r] = t;
+                        if constexpr (COMP) {
+                            const float t = acc[r] + part[r];
+                            const float bp = t - acc[r];
+                            comp[r] += (acc[r] - (t - bp)) + (part[r] - bp);
+                            acc[r] = t;
+                        } else {
+                            acc[r] += part[r];
+                        }
                     }
                 } else {
                     for (int ee = 0; ee < kn; ++ee) {

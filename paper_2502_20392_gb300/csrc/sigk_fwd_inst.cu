@@ -64,16 +64,19 @@ static cudaError_t bwd_launch_impl(const BwdArgs& a, int grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename T>
+// compensated chunk sums in the FP32 two-phase kernel from this dimension on
+constexpr int kCompDim = 1024;
+
+template <typename T, bool COMP>
 static int fwd_cm_info_impl(KernelInfo* info) {
-    return occupancy(fwd_cm_kernel<SIGK_P, T, SIGK_NR>, 128, CmSmem<SIGK_P, T>::bytes, 1, info);
+    return occupancy(fwd_cm_kernel<SIGK_P, T, SIGK_NR, COMP>, 128, CmSmem<SIGK_P, T>::bytes, 1, info);
 }
 
-template <typename T>
+template <typename T, bool COMP>
 static cudaError_t fwd_cm_launch_impl(const SolverArgs& a, void* cscratch, int64_t cstride,
                                       int grid, cudaStream_t s) {
     const int smem = CmSmem<SIGK_P, T>::bytes;
-    auto kern = fwd_cm_kernel<SIGK_P, T, SIGK_NR>;
+    auto kern = fwd_cm_kernel<SIGK_P, T, SIGK_NR, COMP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 128, smem, s>>>(a, static_cast<T*>(cscratch), cstride);
@@ -106,16 +109,22 @@ cudaError_t fwd_launch<SIGK_P, SIGK_NR>(int D, int R, const SolverArgs& a, int g
     }
 }
 
+// (both FP32 variants share the launch shape: the occupancy is the lower one)
 template <>
 int fwd_cm_info<SIGK_P, SIGK_NR>(bool f64, KernelInfo* info) {
-    return f64 ? fwd_cm_info_impl<double>(info) : fwd_cm_info_impl<float>(info);
+    if (f64) return fwd_cm_info_impl<double, false>(info);
+    KernelInfo a, b;
+    if (fwd_cm_info_impl<float, false>(&a) != 0 || fwd_cm_info_impl<float, true>(&b) != 0) return -1;
+    *info = a.blocks_per_sm <= b.blocks_per_sm ? a : b;
+    return 0;
 }
 
 template <>
 cudaError_t fwd_cm_launch<SIGK_P, SIGK_NR>(bool f64, const SolverArgs& a, void* cscratch,
                                            int64_t cstride, int grid, cudaStream_t s) {
-    return f64 ? fwd_cm_launch_impl<double>(a, cscratch, cstride, grid, s)
-               : fwd_cm_launch_impl<float>(a, cscratch, cstride, grid, s);
+    if (f64) return fwd_cm_launch_impl<double, false>(a, cscratch, cstride, grid, s);
+    return a.d > kCompDim ? fwd_cm_launch_impl<float, true>(a, cscratch, cstride, grid, s)
+                          : fwd_cm_launch_impl<float, false>(a, cscratch, cstride, grid, s);
 }
 
 template <>
