@@ -102,8 +102,8 @@ enum {
  *            more fails with SIGK_ERR_LENGTH (reported by sigk_sync_status).
  *            0 = 8193.
  *   refine_c: 0 = off.  Otherwise every path p is refined: each of its
- *            segments is split into s_p equal collinear pieces, s_p =
- *            ceil(max_i |dz_i| / sqrt(refine_c)) (at most 64), so that every
+ *            segments is split into s_p equal collinear pieces, s_p = the
+ *            power of two >= max_i |dz_i| / sqrt(refine_c) (at most 64), so that every
  *            tile satisfies |c| <= refine_c by Cauchy-Schwarz.  Exact (the
  *            kernel is invariant under collinear insertion); it trades more
  *            tiles for tiles the series resolves in FP32 (large |c| needs

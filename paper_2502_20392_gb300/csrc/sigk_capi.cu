@@ -781,10 +781,12 @@ __global__ void refine_kernel(const float* Z, const int64_t* len, const int64_t*
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(kFull, mx, o));
         if (lane == 0) {
-            float f = ceilf(sqrtf(mx) / sqrtf(refine_c));
-            if (!(f >= 1.0f)) f = 1.0f;
-            if (f > 64.0f) f = 64.0f;
-            s_out[p] = (int32_t)f;
+            const float f = ceilf(sqrtf(mx) / sqrtf(refine_c));
+            // the next power of two: the scaling 1/s is exact, and the strip
+            // kernels stage a virtual row's segment with shifts
+            int32_t sp = 1;
+            while (sp < 64 && (float)sp < f) sp <<= 1;
+            s_out[p] = sp;
         }
     }
 }

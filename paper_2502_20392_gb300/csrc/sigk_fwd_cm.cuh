@@ -42,13 +42,65 @@ __device__ __forceinline__ double inc_at_d(const float* z, int64_t row, int d, i
     return (double)z[(row + 1) * d + e] - (double)z[row * d + e];
 }
 
+// stage_increments for s = 2^LS and v0 a multiple of 32: virtual row v0 + r
+// lies on segment (v0 >> LS) + (r >> LS), so all loads are independent and
+// issued back to back (ceil(32/s) + 1 points, or ceil(32/s) increments).
+template <int LS>
+__device__ __forceinline__ void stage_pow2(float* dst, int stride, const float* z, int v0, int Lv,
+                                           int d, int e, int inc_mode) {
+    constexpr int S = 1 << LS;
+    constexpr int NQ = (32 + S - 1) / S;   // segments under the 32 rows
+    constexpr int G = NQ < 16 ? NQ : 16;   // segments per batch of loads
+    const int q0 = v0 >> LS;
+    const int Lseg = Lv >> LS;
+#pragma unroll
+    for (int g0 = 0; g0 < NQ; g0 += G) {
+        float inc[G];
+        if (inc_mode) {
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int q = q0 + g0 + k;
+                inc[k] = q < Lseg ? z[(int64_t)q * d + e] : 0.0f;
+            }
+        } else {
+            float pt[G + 1];
+#pragma unroll
+            for (int k = 0; k <= G; ++k) {
+                const int q = q0 + g0 + k;
+                pt[k] = q <= Lseg ? z[(int64_t)q * d + e] : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) inc[k] = q0 + g0 + k < Lseg ? pt[k + 1] - pt[k] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+#pragma unroll
+            for (int u = 0; u < S && (g0 + k) * S + u < 32; ++u)
+                dst[((g0 + k) * S + u) * stride] = S == 1 ? inc[k] : inc[k] * (1.0f / S);
+        }
+    }
+}
+
 // Increments of the 32 consecutive virtual rows v0 .. v0+31 of a path (each
 // segment refined into s pieces) at dimension e, one value per row into
 // dst[r * stride]; rows at or past Lv (virtual rows of the path) give 0.
 // Points: consecutive virtual rows share their end points, so each point is
-// loaded once (one new load per segment instead of two per row).
+// loaded once (one new load per segment instead of two per row).  Values are
+// those of inc_ref: (z[q+1] - z[q]) * (1/s), or z[q] * (1/s).
 __device__ __forceinline__ void stage_increments(float* dst, int stride, const float* z, int v0,
                                                  int Lv, int d, int e, int inc_mode, int s) {
+    if (e < d && (v0 & 31) == 0) {
+        switch (s) {
+            case 1: stage_pow2<0>(dst, stride, z, v0, Lv, d, e, inc_mode); return;
+            case 2: stage_pow2<1>(dst, stride, z, v0, Lv, d, e, inc_mode); return;
+            case 4: stage_pow2<2>(dst, stride, z, v0, Lv, d, e, inc_mode); return;
+            case 8: stage_pow2<3>(dst, stride, z, v0, Lv, d, e, inc_mode); return;
+            case 16: stage_pow2<4>(dst, stride, z, v0, Lv, d, e, inc_mode); return;
+            case 32: stage_pow2<5>(dst, stride, z, v0, Lv, d, e, inc_mode); return;
+            case 64: stage_pow2<6>(dst, stride, z, v0, Lv, d, e, inc_mode); return;
+            default: break;
+        }
+    }
     if (e >= d) {
 #pragma unroll 8
         for (int r = 0; r < 32; ++r) dst[r * stride] = 0.0f;

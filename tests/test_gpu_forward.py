@@ -260,8 +260,8 @@ def test_fp64_solver_matches_oracle(S, orc, d):
     k = S.pairs(*to_dev(X, lx), *to_dev(Y, ly), opts=o).cpu().numpy()
     e = rel_err(k, ref, kxx, kyy)
     assert e.max() < 1e-9, (o, e)
-    # refinement factors up to 3 (the largest increment / sqrt(refine_c) is
-    # 2.5): the scaling 1/(sx*sy) is not a power of two
+    # refinement factors up to 4 (the largest increment / sqrt(refine_c) is
+    # 2.5, rounded up to a power of two)
     mx = max(np.linalg.norm(v, axis=1).max() for v in ix + iy)
     o3 = S.Opts(order=16, rings=8, refine_c=float((mx / 2.5) ** 2), max_len=20000,
                 flags=S.FLAG_FP64)
