@@ -469,6 +469,20 @@ def run_configs(timed, emit, dev):
     def t(a):
         return torch.from_numpy(a).to(dev)
 
+    def oracle_rate(xs, ys, N=24):
+        """FP64 oracle (series, OpenMP over pairs) on a bounded sample: cells/s."""
+        t0 = time.perf_counter()
+        oracle.series_pairs(xs, ys, N=N)
+        secs = time.perf_counter() - t0
+        cells = float(sum(len(x) * len(y) for x, y in zip(xs, ys)))
+        return {"value": cells / secs, "unit": "cells/s", "cores": oracle.num_threads(),
+                "kind": "oracle", "sample_cells": cells, "seconds": secs}
+
+    def incs(pts, lens):
+        return [np.diff(p.astype(np.float64), axis=0) for p in synth.split(pts, lens)]
+
+    oracle.build()
+
     # pair 256, d=4
     pts, lens = synth.workload_pair_256()  # two packed paths: x, y
     xs = synth.split(pts, lens)
@@ -480,8 +494,21 @@ def run_configs(timed, emit, dev):
     ms = timed(lambda: sigk.pairs(*a, opts=o, ws=ws, check=False))
     k = sigk.pairs(*a, opts=o, ws=ws).item()
     r = oracle.series_pair(np.diff(X.astype(np.float64), axis=0), np.diff(Y.astype(np.float64), axis=0))
+    # the same call captured in a CUDA graph (no host work per replay)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    sigk.pairs(*a, opts=o, out=out, ws=ws)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            sigk.pairs(*a, opts=o, out=out, ws=ws, check=False)
+    torch.cuda.current_stream().wait_stream(side)
+    ms_g = timed(graph.replay, reps=20)
     emit(config="pair_L256_d4", metric="cells/s", value=256 * 256 / (ms * 1e-3), ms=ms,
-         rel_err_vs_oracle=abs(k - r) / abs(r))
+         graph={"value": 256 * 256 / (ms_g * 1e-3), "ms": ms_g},
+         rel_err_vs_oracle=abs(k - r) / abs(r),
+         cpu_baseline=oracle_rate(incs(X, lx) * 32, incs(Y, ly) * 32))
     # Gram B=64 L=1024 d=16, sigma 1 and 4 (forward)
     for sg in (1.0, 4.0):
         pts, lens = synth.workload_gram_1024(sg)
@@ -489,8 +516,10 @@ def run_configs(timed, emit, dev):
         o = sigk.plan(sigk.OP_GRAM, Xd, Ld, None, None, tol=1e-5, opts=sigk.Opts(max_len=1025))
         ws = sigk.Workspace()
         ms = timed(lambda: sigk.gram(Xd, Ld, opts=o, ws=ws, check=False))
+        zs = incs(pts, lens)
         emit(config=f"gram_B64_L1024_d16_sigma{sg:g}", metric="cells/s",
-             value=2080 * 1024 * 1024 / (ms * 1e-3), ms=ms, opts=dict(order=o.order, rings=o.rings))
+             value=2080 * 1024 * 1024 / (ms * 1e-3), ms=ms, opts=dict(order=o.order, rings=o.rings),
+             cpu_baseline=oracle_rate([zs[0]] * 16, zs[:16]))
     # 10^6-segment pairs (increments), collinear against the closed form
     inc, segs, u, tot = synth.collinear_increments(1_000_000, 8, seed=3002, n_paths=2)
     Xd, Ld = t(inc), t(segs)
@@ -507,18 +536,24 @@ def run_configs(timed, emit, dev):
     o = sigk.Opts(order=8, rings=4, flags=sigk.FLAG_INCREMENTS, max_len=1_000_000)
     ws = sigk.Workspace()
     ms = timed(lambda: sigk.pairs(Xd[:n], Ld[:1], Xd[n:], Ld[1:], opts=o, ws=ws, check=False), reps=1)
+    pre = [inc[:3000].astype(np.float64), inc[n:n + 3000].astype(np.float64)]
     emit(config="long_pair_1e6_d8_brownian", metric="cells/s", value=1e12 / (ms * 1e-3), ms=ms,
-         workspace_bytes=int(ws.buf.numel()))
+         workspace_bytes=int(ws.buf.numel()),
+         cpu_baseline=dict(oracle_rate([pre[0]], [pre[1]], N=8), sample="3000-segment prefix pair (one thread: the oracle parallelises over pairs)"))
     # 512 ragged pairs, d=256
     (X, lx), (Y, ly) = synth.workload_ragged_512()
     a = [t(v) for v in (X, lx, Y, ly)]
     cells = float(((lx - 1) * (ly - 1)).sum())
+    short = [p for p in np.argsort((lx - 1) * (ly - 1))[:8]]
+    xs4, ys4 = incs(X, lx), incs(Y, ly)
+    cpu4 = oracle_rate([xs4[p] for p in short], [ys4[p] for p in short])
     for flags, name in ((0, "fp32"), (sigk.FLAG_FP64, "fp64")):
         o = sigk.plan(sigk.OP_PAIRS, *a, tol=1e-5, opts=sigk.Opts(max_len=8193, flags=flags))
         ws = sigk.Workspace()
         ms = timed(lambda: sigk.pairs(*a, opts=o, ws=ws, check=False), reps=1)
         emit(config=f"ragged_512_d256_{name}", metric="cells/s", value=cells / (ms * 1e-3), ms=ms,
-             opts=dict(order=o.order, rings=o.rings, refine_c=o.refine_c, max_len=o.max_len))
+             opts=dict(order=o.order, rings=o.rings, refine_c=o.refine_c, max_len=o.max_len),
+             cpu_baseline=dict(cpu4, sample="the 8 pairs of fewest cells"))
     # MMD 2 x 32 x 2048, d=8: value, then value + gradient
     (X, lx), (Y, ly) = synth.workload_mmd_2048()
     a = [t(v) for v in (X, lx, Y, ly)]
@@ -528,8 +563,10 @@ def run_configs(timed, emit, dev):
     one = torch.ones(1, dtype=torch.float64)
     ms_f = timed(lambda: sigk.mmd(*a, opts=o, ws=ws, check=False))
     ms_b = timed(lambda: sigk.backward(sigk.OP_MMD, *a, one, o, ws=bws, check=False))
+    zx, zy = incs(X, lx), incs(Y, ly)
     emit(config="mmd_2x32_L2048_d8", metric="cells/s", value=cells / (ms_f * 1e-3), ms=ms_f,
-         fwd_bwd={"value": cells / (ms_b * 1e-3), "ms": ms_b})
+         fwd_bwd={"value": cells / (ms_b * 1e-3), "ms": ms_b},
+         cpu_baseline=dict(oracle_rate(zx[:16], zy[:16], N=12), sample="16 cross pairs"))
 
 
 def run_reference(args, world, rank):
