@@ -50,10 +50,11 @@ def tile_flops(P: int, nr: int, d: int) -> int:
     return f + 2 * d
 
 
-def adjoint_tile_flops(P: int, nr: int, d: int) -> int:
-    """FP32 operations per tile of the adjoint kernel (FMA = 2): the forward
-    replay of pass A (tile_flops), and in pass B the increment dot, the
-    inverse bottom-edge update, the tile adjoint and the two gradient FMAs."""
+def adjoint_tile_flops(P: int, nr: int, d: int, replay: bool = True) -> int:
+    """FP32 operations per tile of the adjoint kernel (FMA = 2): in pass B the
+    increment dot, the inverse bottom-edge update, the tile adjoint and the
+    two gradient FMAs; with `replay`, also pass A's forward replay
+    (tile_flops), which is skipped when the forward stored the tile records."""
     nrm = min(P, 8)
     nr = min(nr, nrm)
     inv = 2 * (nr - 1) + sum(2 * (1 + 2 * (P - p)) for p in range(1, nr + 1))
@@ -64,7 +65,7 @@ def adjoint_tile_flops(P: int, nr: int, d: int) -> int:
     for s_ in range(1, P + 1):
         adj += 4 * min(nr, P - s_) + 2 + 4 * min(nr, P - s_)                   # conv^T, S, Hankel^T
     adj += 2 * nr
-    return tile_flops(P, nr, d) + 2 * d + inv + adj + 4 * d
+    return (tile_flops(P, nr, d) if replay else 0) + 2 * d + inv + adj + 4 * d
 
 
 def rank_workloads(rank: int, n_paths: int):
@@ -279,7 +280,9 @@ def main():
                      "flops_per_launch": flops, "achieved": round(ach, 3)})
     sg, _, P, nr = SIGMAS[BWD_SIGMA]
     kms = statistics.mean(r[len(SIGMAS)] for r in kern_ms)
-    flops = bcnt[2] * adjoint_tile_flops(P, nr, DIM)
+    # pass B over every tile, pass A over the replayed ones (none when the
+    # training forward stored the tile records)
+    flops = bcnt[2] * adjoint_tile_flops(P, nr, DIM, replay=False) + bcnt[3] * tile_flops(P, nr, DIM)
     roof.append({"sigma": sg, "order": P, "rings": nr, "kernel": "bwd_kernel (adjoint)",
                  "kernel_ms": round(kms, 4), "flops_per_launch": flops,
                  "achieved": round(flops / (kms * 1e-3) / 1e12, 3)})

@@ -76,13 +76,17 @@ enum {
                                   kernels -- whose FP32 result carries a
                                   rounding error above the tolerance.  FP64
                                   runs at 1/64 of the FP32 rate on this GPU. */
-    SIGK_FLAG_PAIR_MAJOR = 16  /* schedule each pair's strips as consecutive
+    SIGK_FLAG_PAIR_MAJOR = 16, /* schedule each pair's strips as consecutive
                                   work items (smaller seam ring) instead of the
                                   default strip-major order, where strip l of
                                   every pair is scheduled before strip l+1 of
                                   any, longest pairs first, whenever the ring
                                   for whole strips fits in 8 GiB.  Results are
                                   identical; only the schedule differs. */
+    SIGK_FLAG_REPLAY = 32      /* sigk_backward: never store the tile records;
+                                  the adjoint replays every strip from its
+                                  stored seam instead (smaller workspace, more
+                                  arithmetic).  Results are identical. */
 };
 
 /* Truncation and scheduling parameters.  NULL = defaults (order 8, rings 4,
@@ -150,17 +154,23 @@ sigk_status sigk_mmd(const float* X, const int64_t* len_x, int64_t m, const floa
 
 /* Workspace bytes for sigk_backward (same arguments as sigk_workspace_size).
  * Includes the forward seam store, which needs up to
- * n_pairs * (ceil(max_len/32) - 1) * max_len * (order + 3) floats. */
+ * n_pairs * (ceil(max_len/32) - 1) * max_len * (order + 4) floats, and,
+ * unless SIGK_FLAG_REPLAY is set, the store of tile records when it takes at
+ * most 128 GiB: n_pairs * ceil(max_len/32) * (max_len + 32) * 32 * R floats,
+ * R = 4 * floor((order + 6) / 4) (one record per tile: the tile's incoming
+ * left edge and its exponent decisions, written by the forward and read back
+ * by the adjoint). */
 size_t sigk_backward_workspace_size(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts);
 
 /* Gradients by the adjoint of the solver (reverse-mode differentiation of the
  * truncated FP32 scheme; the paper has no gradient -- this is the adjoint of
  * the tile map of Sec. 2.3 swept in reverse wavefront order).
  * The call runs a training forward that stores the right-edge seam of every
- * 32-row strip (checkpointed wavefront boundaries), then the adjoint kernel,
- * which replays each strip from its stored seam, rebuilds every tile's inputs
- * by inverting the tile's bottom-to-top update, and chains dk/dc_ij to the
- * increments on the fly.
+ * 32-row strip (checkpointed wavefront boundaries) and, when they fit the
+ * budget above, every tile's record; then the adjoint kernel, which replays
+ * each strip from its stored seam (only when the records were not stored),
+ * rebuilds every tile's inputs by inverting the tile's bottom-to-top update,
+ * and chains dk/dc_ij to the increments on the fly.
  *   op, X, len_x, n_x, Y, len_y, n_y, d: as in sigk_pairs / sigk_gram /
  *     sigk_mmd (SIGK_OP_GRAM with Y == NULL: Gram of X with itself).
  *   grad_out (device FP64): upstream gradient of the op's output --
@@ -227,8 +237,9 @@ sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream);
 
 /* Counters of the last call on this workspace (synchronises `stream`):
  * out[0] = tiles solved by the forward, out[1] = lane-tiles including strip
- * padding, out[2] = tiles solved by the adjoint kernel. */
-sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out3);
+ * padding, out[2] = tiles solved by the adjoint kernel, out[3] = tiles the
+ * adjoint kernel replayed (0 when the forward stored the tile records). */
+sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out4);
 
 /* Profiling hook: when both are non-NULL, later calls on this host thread
  * record the two CUDA events (cudaEvent_t) on the call's stream immediately

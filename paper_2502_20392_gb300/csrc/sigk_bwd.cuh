@@ -8,7 +8,10 @@
 // Pass A replays the strip's forward from its stored input seam and keeps, per
 // lane and column, the lane's incoming left edge and the exponent decisions
 // (a record of P+3 floats) in a per-warp scratch area; it ends with each
-// lane's bottom-edge state after the last column in registers.
+// lane's bottom-edge state after the last column in registers.  When the
+// records of every tile fit the device memory budget, the training forward
+// (one row per lane, the same arithmetic) writes them once for all strips,
+// with each lane's final state, and pass A is skipped.
 //
 // Pass B sweeps the columns in reverse with the mirrored skew (lane 31 first).
 // At each tile it rebuilds the tile's bottom-edge input by inverting the
@@ -37,8 +40,12 @@ struct BwdArgs {
     const int64_t* store_off;    // [n_pairs] float offsets into store
     const int32_t* pair_exp;     // [n_pairs] exponent of the final value
     const double* pair_w;        // [n_pairs] upstream weight of each pair
-    float* rec;                  // per-warp records
+    float* rec;                  // per-warp records (replay)
     int64_t rec_stride;          // floats per warp
+    // records stored by the training forward (SolverArgs::rec layout); with
+    // rec_off != nullptr pass A is skipped
+    const float* rec_store;
+    const int64_t* rec_off;
     int32_t nslot;               // adjoint seam ring
     int32_t wcols;
     float* aseam;
@@ -61,20 +68,6 @@ struct BwdSmem {
     // block), adjoint seam in/out blocks, column gradients, two mbarriers
     static constexpr int per_warp = 64 * DS + 2 * RB + 2 * 32 * SA + 64 * D + 4;
 };
-
-__device__ __forceinline__ float exp2_nonneg(int n) {
-    return __int_as_float((127 + (n > 127 ? 127 : n)) << 23);
-}
-
-// exponent word of a record: F/64 (15 bits) | E_before/64 (16 bits) | bump
-__device__ __forceinline__ int pack_exp(int F, int Eb, int bump) {
-    return ((F >> 6) << 17) | (((Eb >> 6) & 0xFFFF) << 1) | bump;
-}
-__device__ __forceinline__ void unpack_exp(int w, int& F, int& Eb, int& bump) {
-    bump = w & 1;
-    Eb = ((int)(short)((w >> 1) & 0xFFFF)) * 64;
-    F = (w >> 17) * 64;
-}
 
 // gradient v of virtual row `vrow` (refinement s) -> its segment vrow / s
 // (scaled 1/s), then points (+ at segment+1, - at segment) or increments
@@ -120,7 +113,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     uint64_t* bars = reinterpret_cast<uint64_t*>(colacc + 64 * D);  // record-load mbarriers
     float* rec = A.rec + (size_t)gwarp * A.rec_stride;
     const int n_items = A.sched.hdr[2];
-    unsigned long long tiles = 0;
+    unsigned long long tiles = 0, replayed = 0;
     // pass B reads the record block of one pass-A step per step, prefetched
     // two steps ahead by bulk copies into sin_ / rbuf1 (load n uses buffer
     // n & 1, barrier phase (n >> 1) & 1; n counts this warp's loads)
@@ -169,7 +162,24 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         for (int q = 0; q <= P; ++q) ob[q] = 0.0f;
         int oE = 0;
         const int T = L2 + 31;
-        for (int t = 0; t < T; ++t) {
+        // records stored by the training forward: no replay, the lane's final
+        // bottom-edge state is the strip's last block
+        const bool stored = A.rec_off != nullptr;
+        const float* rsrc = stored ? A.rec_store + A.rec_off[lo_p] + (int64_t)s * (L2 + 32) * 32 * RS
+                                   : rec;
+        if (stored) {
+            const float4* f4 = reinterpret_cast<const float4*>(rsrc + ((size_t)T * 32 + lane) * RS);
+            float fv[RS];
+#pragma unroll
+            for (int g = 0; g < RS / 4; ++g) {
+                const float4 v = f4[g];
+                fv[4 * g] = v.x; fv[4 * g + 1] = v.y; fv[4 * g + 2] = v.z; fv[4 * g + 3] = v.w;
+            }
+            a1lo = fv[0];
+#pragma unroll
+            for (int p = 1; p <= P; ++p) a[p] = fv[p];
+        }
+        for (int t = 0; t < T && !stored; ++t) {
             if ((t & 31) == 0 && t < L2) {
                 const int nb = min(32, L2 - t);
                 for (int idx = lane; idx < 32 * D; idx += 32) {
@@ -265,6 +275,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
 #pragma unroll
                 for (int q = 1; q <= P; ++q) ob[q] = b[q];
+                replayed += has_row ? 1ull : 0ull;
             }
         }
         __syncwarp();
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         unsigned issued = 0, waited = 0;
         auto rbuf = [&](unsigned n) { return (n & 1) ? rbuf1 : sin_; };
         // pass-A step of reverse step tp: every active lane reads t = L2 + 30 - tp
-        auto rec_block = [&](int tp) { return rec + (size_t)(L2 + 30 - tp) * RS * 32; };
+        auto rec_block = [&](int tp) { return rsrc + (size_t)(L2 + 30 - tp) * RS * 32; };
         if (ok) {
             const unsigned first = T < 2 ? (unsigned)T : 2u;
             if (lane == 0)
@@ -523,8 +534,14 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         if (!ok) break;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tiles += __shfl_down_sync(kFull, tiles, o);
-    if (lane == 0) atomicAdd(&A.counters[2], tiles);
+    for (int o = 16; o > 0; o >>= 1) {
+        tiles += __shfl_down_sync(kFull, tiles, o);
+        replayed += __shfl_down_sync(kFull, replayed, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.counters[2], tiles);
+        atomicAdd(&A.counters[3], replayed);
+    }
 }
 
 }  // namespace sigk

@@ -156,6 +156,9 @@ struct Layout {
     // backward sections (train == true)
     size_t store, store_off, pair_exp, pair_w, rec, bprod, bcons, bdone, aseam;
     int64_t store_floats, rec_stride;
+    bool stored_rec;     // the training forward stores every tile's record
+    size_t rstore, rec_off;
+    int64_t rstore_floats;
     int bnslot, bwcols, bgrid, bnwarps;
     KernelInfo binfo;
     bool train;
@@ -179,6 +182,10 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr int kLevelCap = 4096;
 constexpr double kStripMajorBudget = 8.0 * 1024 * 1024 * 1024;
 constexpr int64_t kStripMajorMinPairs = 64;
+// Largest store of tile records (bytes) the training forward may write for
+// the adjoint; above it (or with SIGK_FLAG_REPLAY) the adjoint replays each
+// strip from its seam instead.
+constexpr double kRecordBudget = 128.0 * 1024 * 1024 * 1024;
 
 // Number of pair entries solved by an op.
 static int64_t pair_count(int op, int64_t n_x, int64_t n_y, int flags) {
@@ -204,8 +211,20 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         return fail(SIGK_ERR_UNSUPPORTED, "the backward runs in FP32 only (no SIGK_FLAG_FP64)");
     if (L->cm && train)
         return fail(SIGK_ERR_UNSUPPORTED, "the backward supports d <= 16");
+    // stored tile records: (pair, 32-row strip) x (max_len + 32) blocks of
+    // 32 records; the training forward then runs with one row per lane
+    L->stored_rec = false;
+    L->rstore_floats = 0;
+    if (train && !(o.flags & SIGK_FLAG_REPLAY)) {
+        const double fl = (double)pair_count(op, n_x, n_y, o.flags) * (double)((o.max_len + 31) / 32) *
+                          (double)(o.max_len + 32) * 32.0 * (double)rec_floats(o.order);
+        if (fl * sizeof(float) <= kRecordBudget) {
+            L->stored_rec = true;
+            L->rstore_floats = (int64_t)fl;
+        }
+    }
     const int qinfo = L->cm ? fwd_cm_info_dispatch(o.order, o.rings, L->f64, &L->info)
-                            : fwd_info_dispatch(o.order, o.rings, D, 0, &L->info);
+                            : fwd_info_dispatch(o.order, o.rings, D, L->stored_rec ? 1 : 0, &L->info);
     if (qinfo != 0 || L->info.blocks_per_sm <= 0)
         return fail(SIGK_ERR_CUDA, "kernel occupancy query failed");
     int dev = 0, sms = 0;
@@ -307,7 +326,10 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         L->store_off = off; off = align256(off + sizeof(int64_t) * (size_t)L->n_pairs);
         L->pair_exp = off; off = align256(off + sizeof(int32_t) * (size_t)L->n_pairs);
         L->pair_w = off; off = align256(off + sizeof(double) * (size_t)L->n_pairs);
-        L->rec = off; off = align256(off + sizeof(float) * (size_t)L->bnwarps * L->rec_stride);
+        L->rec = off;
+        if (!L->stored_rec) off = align256(off + sizeof(float) * (size_t)L->bnwarps * L->rec_stride);
+        L->rec_off = off; off = align256(off + sizeof(int64_t) * (size_t)L->n_pairs);
+        L->rstore = off; off = align256(off + sizeof(float) * (size_t)L->rstore_floats);
         L->bprod = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->bnslot);
         L->bcons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->bnslot);
         L->bdone = off; off = align256(off + sizeof(long long) * (size_t)L->bnslot);
@@ -377,6 +399,9 @@ struct PlanArgs {
     int stride;         // seam entry floats (P + 4)
     int64_t store_cap;  // floats available for the forward seam store
     int64_t* store_off;
+    int64_t* rec_off;   // stored tile records: per-pair offsets (null: replay)
+    int64_t rec_cap;    // floats available for them
+    int rec_block;      // floats per block (32 records)
     double* pair_w;
     const double* grad_out;
     float* gX;
@@ -448,6 +473,33 @@ __device__ void block_prefix_items(const PairDesc* pairs, const int32_t* order, 
         run += units(i);
     }
     if (t == kPlanThreads - 1) out[n] = (int32_t)sh[t];
+    __syncthreads();
+}
+
+// Per-pair offsets out[i] = sum_{i' < i} sz(pairs[i']) by a block scan; sets
+// SIGK_ERR_WORKSPACE when the total exceeds cap.  One CTA of kPlanThreads.
+template <typename F>
+__device__ void pair_offsets(const PlanArgs& A, int64_t* sh, int64_t* out, int64_t cap, F sz) {
+    const int t = threadIdx.x;
+    const int64_t n = A.n_pairs;
+    const int64_t chunk = (n + kPlanThreads - 1) / kPlanThreads;
+    const int64_t b0 = t * chunk, b1 = (b0 + chunk < n) ? b0 + chunk : n;
+    int64_t s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += sz(A.pairs[i]);
+    sh[t] = s;
+    __syncthreads();
+    for (int o = 1; o < kPlanThreads; o <<= 1) {
+        int64_t add = (t >= o) ? sh[t - o] : 0;
+        __syncthreads();
+        sh[t] += add;
+        __syncthreads();
+    }
+    int64_t run = sh[t] - s;
+    for (int64_t i = b0; i < b1; ++i) {
+        out[i] = run;
+        run += sz(A.pairs[i]);
+    }
+    if (t == kPlanThreads - 1 && sh[t] > cap) atomicCAS(&A.hdr->status, 0, kErrWorkspace);
     __syncthreads();
 }
 
@@ -713,6 +765,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         A.hdr->counters[0] = 0;
         A.hdr->counters[1] = 0;
         A.hdr->counters[2] = 0;
+        A.hdr->counters[3] = 0;
     }
     if (!A.train) return;
     for (int i = t; i < A.bnslot; i += kPlanThreads) {
@@ -731,35 +784,20 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
     }
     // per-pair offsets of the forward seam store: (strips - 1) x L2 x stride
     __syncthreads();
-    {
-        const int64_t n = A.n_pairs;
-        const int64_t chunk = (n + kPlanThreads - 1) / kPlanThreads;
-        const int64_t b0 = t * chunk, b1 = (b0 + chunk < n) ? b0 + chunk : n;
-        auto sz = [&](int64_t i) -> int64_t {
-            const PairDesc& q = A.pairs[i];
-            return q.n_strips > 1 ? (int64_t)(q.n_strips - 1) * q.L2 * A.stride : 0;
-        };
-        int64_t s = 0;
-        for (int64_t i = b0; i < b1; ++i) s += sz(i);
-        sh[t] = s;
+    pair_offsets(A, sh, A.store_off, A.store_cap, [&](const PairDesc& q) -> int64_t {
+        return q.n_strips > 1 ? (int64_t)(q.n_strips - 1) * q.L2 * A.stride : 0;
+    });
+    // and of the stored tile records: strips x (L2 + 32) blocks
+    if (A.rec_off) {
         __syncthreads();
-        for (int o = 1; o < kPlanThreads; o <<= 1) {
-            int64_t add = (t >= o) ? sh[t - o] : 0;
-            __syncthreads();
-            sh[t] += add;
-            __syncthreads();
-        }
-        int64_t run = sh[t] - s;
-        for (int64_t i = b0; i < b1; ++i) {
-            A.store_off[i] = run;
-            run += sz(i);
-        }
-        if (t == kPlanThreads - 1 && sh[t] > A.store_cap) atomicCAS(&A.hdr->status, 0, kErrWorkspace);
+        pair_offsets(A, sh, A.rec_off, A.rec_cap, [&](const PairDesc& q) -> int64_t {
+            return (int64_t)q.n_strips * (q.L2 + 32) * A.rec_block;
+        });
     }
 }
 
-// Per-path refinement factors: s = ceil(max_i |dz_i| / sqrt(refine_c)),
-// clamped to [1, 64]; one warp per path.  The planner multiplies the path's
+// Per-path refinement factors: s = the power of two >= max_i |dz_i| /
+// sqrt(refine_c), clamped to [1, 64]; one warp per path.  The planner multiplies the path's
 // segment count by s and the kernels read segment v / s scaled by 1/s.
 __global__ void refine_kernel(const float* Z, const int64_t* len, const int64_t* offs, int64_t n,
                               int d, int inc_mode, float refine_c, int32_t* s_out) {
@@ -969,6 +1007,11 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         pa.stride = L.stride;
         pa.store_cap = L.store_floats;
         pa.store_off = (int64_t*)(base + L.store_off);
+        if (L.stored_rec) {
+            pa.rec_off = (int64_t*)(base + L.rec_off);
+            pa.rec_cap = L.rstore_floats;
+            pa.rec_block = 32 * rec_floats(o.order);
+        }
         pa.pair_w = (double*)(base + L.pair_w);
         pa.grad_out = tr->grad_out;
         pa.gX = tr->gX;
@@ -1015,12 +1058,17 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         sa.store = (float*)(base + L.store);
         sa.store_off = pa.store_off;
         sa.pair_exp = (int32_t*)(base + L.pair_exp);
+        if (L.stored_rec) {
+            sa.rec = (float*)(base + L.rstore);
+            sa.rec_off = pa.rec_off;
+        }
     }
     if (L.n_pairs > 0) {
         if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_start, stream);
         e = L.cm ? fwd_cm_launch_dispatch(o.order, o.rings, L.f64, sa, base + L.cscratch, L.cstride,
                                           L.grid, stream)
-                 : fwd_launch_dispatch(o.order, o.rings, dim_bucket(d), 0, sa, L.grid, stream);
+                 : fwd_launch_dispatch(o.order, o.rings, dim_bucket(d), L.stored_rec ? 1 : 0, sa,
+                                       L.grid, stream);
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
         if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_stop, stream);
     }
@@ -1039,6 +1087,10 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         ba.pair_w = pa.pair_w;
         ba.rec = (float*)(base + L.rec);
         ba.rec_stride = L.rec_stride;
+        if (L.stored_rec) {
+            ba.rec_store = sa.rec;
+            ba.rec_off = pa.rec_off;
+        }
         ba.nslot = L.bnslot;
         ba.wcols = L.bwcols;
         ba.aseam = (float*)(base + L.aseam);
@@ -1370,16 +1422,14 @@ sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream) {
     return SIGK_OK;
 }
 
-sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out3) {
-    if (!ws || ws_bytes < 256 || !out3) return fail(SIGK_ERR_ARG, "bad arguments");
+sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out4) {
+    if (!ws || ws_bytes < 256 || !out4) return fail(SIGK_ERR_ARG, "bad arguments");
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     Header h;
     e = cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "counter copy");
-    out3[0] = (double)h.counters[0];
-    out3[1] = (double)h.counters[1];
-    out3[2] = (double)h.counters[2];
+    for (int i = 0; i < 4; ++i) out4[i] = (double)h.counters[i];
     return SIGK_OK;
 }
 

@@ -155,6 +155,13 @@ struct SolverArgs {
     float* store;
     const int64_t* store_off;      // [n_pairs] float offsets into store
     int32_t* pair_exp;             // [n_pairs] or null
+    // training with stored tile records (one row per lane only): every tile's
+    // record as the adjoint reads it, per (pair, strip) (L2 + 32) blocks of
+    // 32 * rec_floats(P) floats -- block t holds the records of step t, block
+    // L2 + 31 each lane's bottom-edge state after the last column.  rec ==
+    // nullptr: the adjoint replays the strips instead.
+    float* rec;
+    const int64_t* rec_off;        // [n_pairs] float offsets into rec
 };
 
 // ---------------------------------------------------------------------------
@@ -303,6 +310,21 @@ __device__ __forceinline__ bool wait_slot_free(const Schedule& S, const PairDesc
 // 2^n as a float for n <= 0 (0 below the normal range).
 __device__ __forceinline__ float exp2_nonpos(int n) {
     return n < -126 ? 0.0f : __int_as_float((127 + n) << 23);
+}
+__device__ __forceinline__ float exp2_nonneg(int n) {
+    return __int_as_float((127 + (n > 127 ? 127 : n)) << 23);
+}
+
+// Exponent word of a tile record: F/64 (15 bits) | E_before/64 (16 bits) |
+// bump.  F is the incoming edge's exponent, E_before the lane's exponent
+// before the tile, bump = 1 when the tile's outputs were rescaled by 2^-64.
+__device__ __forceinline__ int pack_exp(int F, int Eb, int bump) {
+    return ((F >> 6) << 17) | (((Eb >> 6) & 0xFFFF) << 1) | bump;
+}
+__device__ __forceinline__ void unpack_exp(int w, int& F, int& Eb, int& bump) {
+    bump = w & 1;
+    Eb = ((int)(short)((w >> 1) & 0xFFFF)) * 64;
+    F = (w >> 17) * 64;
 }
 
 // ---------------------------------------------------------------------------

@@ -59,13 +59,18 @@ __device__ __forceinline__ float inc_ref(const float* z, int64_t v, int d, int e
 // CTAs per SM the register allocation must allow (128 threads each): the
 // largest count that ptxas meets without spilling for that instantiation.
 constexpr int fwd_min_blocks(int P, int D, int R) {
-    return R == 1 ? 4 : (R == 2 ? (P <= 8 ? 4 : 3) : (P <= 4 ? 4 : 3));
+    return R == 1 ? ((P >= 14 && D >= 16) ? 3 : 4) : (R == 2 ? (P <= 8 ? 4 : 3) : (P <= 4 ? 4 : 3));
 }
 
 template <int P, int D, int R, int NR>
 __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(SolverArgs A) {
     constexpr int S = P + 4;
     constexpr int DS = DyStride<D>::value;
+    constexpr int RS = rec_floats(P);
+    // record fields: [0] hi, [1] b1lo, [1 + q] b_q, [P + 2] exponent word;
+    // the groups of four wholly before the exponent are stored before the
+    // tile, the last group (with the exponent) after it
+    constexpr int kFullGroups = (P + 2) / 4;
     extern __shared__ float4 smem_f4[];
     float* smem = reinterpret_cast<float*>(smem_f4);
     const int lane = threadIdx.x & 31;
@@ -104,6 +109,10 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
         const bool mid_writer = train && R > 1 && lane != 31 && ((lane + 1) * R) % 32 == 0 &&
                                 s * R + mid_m < n32;
         float* mid_dst = mid_writer ? st_pair + (size_t)(s * R + mid_m - 1) * L2 * S : nullptr;
+        // stored tile records (training, one row per lane): this strip's blocks
+        float* rec_item = nullptr;
+        if constexpr (R == 1)
+            if (A.rec) rec_item = A.rec + A.rec_off[lo_p] + (int64_t)s * (L2 + 32) * 32 * RS;
         bool ok = true;
 
         // row increments of this lane (zero past the end of the path)
@@ -192,6 +201,28 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
             }
             const int j = t - lane;
             if (j >= 0 && j < L2) {
+                // record of the incoming left edge, before alignment (the
+                // adjoint rebuilds the tile's inputs from it)
+                float4* r4 = nullptr;
+                float rtail[4];
+                const int Eb = E;
+                if constexpr (R == 1) {
+                    if (rec_item) {
+                        float rv[RS];
+                        rv[0] = hi;
+                        rv[1] = b1lo;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) rv[1 + q] = b[q];
+#pragma unroll
+                        for (int q = P + 2; q < RS; ++q) rv[q] = 0.0f;
+                        r4 = reinterpret_cast<float4*>(rec_item + ((size_t)t * 32 + lane) * RS);
+#pragma unroll
+                        for (int g = 0; g < kFullGroups; ++g)
+                            r4[g] = make_float4(rv[4 * g], rv[4 * g + 1], rv[4 * g + 2], rv[4 * g + 3]);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) rtail[q] = rv[4 * kFullGroups + q];
+                    }
+                }
                 // align exponents of the incoming edge and the lane's states
                 if (F != E) {
                     if (F > E) {
@@ -226,7 +257,9 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                     tile_update<P>(c, a[k], a1lo[k], hi, lo, b, b1lo, NR);
                 }
                 // renormalise when the corner value grows past 2^64
+                int bump = 0;
                 if (fabsf(hi) > 1.8446744e19f) {
+                    bump = 1;
                     const float sc = 5.421011e-20f;  // 2^-64
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
@@ -238,6 +271,12 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
 #pragma unroll
                     for (int q = 1; q <= P; ++q) b[q] *= sc;
                     E += 64;
+                }
+                if constexpr (R == 1) {
+                    if (rec_item) {
+                        rtail[P + 2 - 4 * kFullGroups] = __int_as_float(pack_exp(F, Eb, bump));
+                        r4[kFullGroups] = make_float4(rtail[0], rtail[1], rtail[2], rtail[3]);
+                    }
                 }
                 ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
 #pragma unroll
@@ -298,6 +337,22 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                                        ((unsigned long long)item << 32) | (unsigned)(start + nb));
                 }
                 __syncwarp();
+            }
+        }
+        // stored records: each lane's bottom-edge state after the last column
+        // (where the adjoint's reverse sweep starts)
+        if constexpr (R == 1) {
+            if (rec_item && ok) {
+                float fv[RS];
+                fv[0] = a1lo[0];
+#pragma unroll
+                for (int p = 1; p <= P; ++p) fv[p] = a[0][p];
+#pragma unroll
+                for (int q = P + 1; q < RS; ++q) fv[q] = 0.0f;
+                float4* f4 = reinterpret_cast<float4*>(rec_item + ((size_t)(L2 + 31) * 32 + lane) * RS);
+#pragma unroll
+                for (int g = 0; g < RS / 4; ++g)
+                    f4[g] = make_float4(fv[4 * g], fv[4 * g + 1], fv[4 * g + 2], fv[4 * g + 3]);
             }
         }
         __syncwarp();

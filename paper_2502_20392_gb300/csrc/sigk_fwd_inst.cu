@@ -1,8 +1,8 @@
 // sigk_fwd_inst.cu -- instantiates, for one edge degree P and ring count NR
 // (compiled once per pair with -DSIGK_P=<P> -DSIGK_NR=<NR>) and D in
 // {4, 8, 16}: the forward solver (inference, and training with every 32-row
-// seam stored) and the backward (adjoint) kernel; and the two-phase solver in
-// FP32 and FP64.
+// seam stored; with one row per lane also every tile's record) and the
+// backward (adjoint) kernel; and the two-phase solver in FP32 and FP64.
 #include "sigk_bwd.cuh"
 #include "sigk_fwd.cuh"
 #include "sigk_fwd_cm.cuh"
@@ -87,24 +87,26 @@ constexpr int kR4 = rows_per_lane(SIGK_P, 4);
 constexpr int kR8 = rows_per_lane(SIGK_P, 8);
 constexpr int kR16 = rows_per_lane(SIGK_P, 16);
 
+// R = 0: rows_per_lane(P, D) rows per lane; R = 1: one row per lane (the
+// training forward that stores every tile's record for the adjoint)
 template <>
 int fwd_info<SIGK_P, SIGK_NR>(int D, int R, KernelInfo* info) {
-    if (R != 0) return -1;  // one rows-per-lane count per (P, D)
+    if (R != 0 && R != 1) return -1;
     switch (D) {
-        case 4: return fwd_info_impl<4, kR4>(info);
-        case 8: return fwd_info_impl<8, kR8>(info);
-        case 16: return fwd_info_impl<16, kR16>(info);
+        case 4: return R ? fwd_info_impl<4, 1>(info) : fwd_info_impl<4, kR4>(info);
+        case 8: return R ? fwd_info_impl<8, 1>(info) : fwd_info_impl<8, kR8>(info);
+        case 16: return R ? fwd_info_impl<16, 1>(info) : fwd_info_impl<16, kR16>(info);
         default: return -1;
     }
 }
 
 template <>
 cudaError_t fwd_launch<SIGK_P, SIGK_NR>(int D, int R, const SolverArgs& a, int grid, cudaStream_t s) {
-    if (R != 0) return cudaErrorInvalidValue;
+    if (R != 0 && R != 1) return cudaErrorInvalidValue;
     switch (D) {
-        case 4: return fwd_launch_impl<4, kR4>(a, grid, s);
-        case 8: return fwd_launch_impl<8, kR8>(a, grid, s);
-        case 16: return fwd_launch_impl<16, kR16>(a, grid, s);
+        case 4: return R ? fwd_launch_impl<4, 1>(a, grid, s) : fwd_launch_impl<4, kR4>(a, grid, s);
+        case 8: return R ? fwd_launch_impl<8, 1>(a, grid, s) : fwd_launch_impl<8, kR8>(a, grid, s);
+        case 16: return R ? fwd_launch_impl<16, 1>(a, grid, s) : fwd_launch_impl<16, kR16>(a, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

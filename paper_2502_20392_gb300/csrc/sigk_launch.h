@@ -21,8 +21,9 @@ constexpr int rows_per_lane(int P, int D) { return (P + D) <= 16 ? 4 : 2; }
 // ring count NR); NR is a compile-time constant of every solver kernel, so
 // the truncated ring sums carry no run-time predicates.
 //
-// R = 0: the rows-per-lane count rows_per_lane(P, D) (the only one compiled);
-// training uses it too and stores the seam after every 32-row strip.
+// R = 0: the rows-per-lane count rows_per_lane(P, D); training uses it too
+// and stores the seam after every 32-row strip.  R = 1: one row per lane, the
+// training forward that also stores every tile's record for the adjoint.
 template <int P, int NR> int fwd_info(int D, int R, KernelInfo* info);
 template <int P, int NR>
 cudaError_t fwd_launch(int D, int R, const SolverArgs& a, int grid, cudaStream_t s);

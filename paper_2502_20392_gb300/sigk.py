@@ -22,7 +22,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libsigk.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "sigk.h")
 
 OP_PAIRS, OP_GRAM, OP_MMD = 0, 1, 2
-FLAG_INCREMENTS, FLAG_GRAM_FULL, FLAG_MMD_BIASED, FLAG_FP64, FLAG_PAIR_MAJOR = 1, 2, 4, 8, 16
+FLAG_INCREMENTS, FLAG_GRAM_FULL, FLAG_MMD_BIASED, FLAG_FP64, FLAG_PAIR_MAJOR, FLAG_REPLAY = 1, 2, 4, 8, 16, 32
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_LENGTH", -3: "ERR_NONFINITE", -4: "ERR_WORKSPACE",
           -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -8: "ERR_UNSUPPORTED"}
 
@@ -165,7 +165,7 @@ def profile_events(start=None, stop=None):
 
 
 def counters(ws: Workspace):
-    out = (ctypes.c_double * 3)()
+    out = (ctypes.c_double * 4)()
     _check(load().sigk_counters(_ptr(ws.buf), ws.buf.numel(), _stream(), out))
     return list(out)
 

@@ -204,6 +204,34 @@ def test_backward_schedules_agree_bitwise(S):
     torch.testing.assert_close(g1, g2, rtol=1e-5, atol=1e-6 * float(g1.abs().max()))
 
 
+@pytest.mark.parametrize("d,order,rings,sigma", [(16, 8, 4, 2.0), (4, 12, 6, 1.0)])
+def test_stored_records_match_replay(S, d, order, rings, sigma):
+    # the training forward (one row per lane) stores every tile's record and
+    # the adjoint skips its replay; with SIGK_FLAG_REPLAY it replays each
+    # strip instead.  sigma = 2 drives the self-kernels past 2^64 (to 2.5e26,
+    # gradients still inside the FP32 range), so the records carry exponent
+    # alignments and renormalisations.
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(6, [420, 1, 77, 300, 33, 129], d, sigma, seed=97)
+    Xd, ld = torch.from_numpy(pts).to(dev()), torch.from_numpy(lens).to(dev())
+    W = torch.from_numpy(np.random.default_rng(11).standard_normal((6, 6)))
+    out = {}
+    for flags in (0, S.FLAG_REPLAY):
+        ws = S.Workspace()
+        o = S.Opts(order=order, rings=rings, max_len=512, flags=flags)
+        g, _, G = S.backward(S.OP_GRAM, Xd, ld, None, None, W, o, ws=ws)
+        out[flags] = (g, G, S.counters(ws))
+    (g0, G0, c0), (g1, G1, c1) = out[0], out[S.FLAG_REPLAY]
+    tiles = sum((a - 1) * (b - 1) for i, a in enumerate(lens) for b in lens[i:])
+    assert c0[2] == c1[2] == tiles
+    assert c0[3] == 0 and c1[3] == tiles
+    assert torch.isfinite(G0).all()
+    if sigma > 2:
+        assert float(G0.abs().max()) > 2.0 ** 64
+    torch.testing.assert_close(G0, G1, rtol=1e-6, atol=0)
+    torch.testing.assert_close(g0, g1, rtol=1e-5, atol=1e-6 * float(g1.abs().max()))
+
+
 def test_increments_mode_gradient_and_gram_xy(S, orc):
     # FLAG_INCREMENTS: gradients are with respect to the increments; a Gram of
     # X against a different Y also returns grad_Y
