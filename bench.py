@@ -215,17 +215,25 @@ def main():
     W = torch.from_numpy(np.random.default_rng(7).standard_normal((N_PATHS, N_PATHS))).to(dev)
     bws = sigk.Workspace()
 
-    def step(ev_pairs=None):
+    def step(ev_pairs=None, pts=X, lens=L):
+        # the Gram whose gradient is taken runs as a training forward (it keeps
+        # its seams and tile records for the adjoint, as an autograd forward
+        # does); the other as an inference forward; then the adjoint
+        state = None
         for k in range(len(SIGMAS)):
             if ev_pairs is not None:
                 sigk.profile_events(*ev_pairs[k])
-            sigk.gram(X[k], L[k], opts=opts[k], out=G[k], ws=wss[k], check=False)
+            if k == BWD_SIGMA:
+                _, state = sigk.forward_train(sigk.OP_GRAM, pts[k], lens[k], None, None, opts[k],
+                                              ws=bws, out=G[k], check=False)
+            else:
+                sigk.gram(pts[k], lens[k], opts=opts[k], out=G[k], ws=wss[k], check=False)
         if ev_pairs is not None:
             sigk.profile_events(*ev_pairs[len(SIGMAS)])
-        k = BWD_SIGMA
-        sigk.backward(sigk.OP_GRAM, X[k], L[k], None, None, W, opts[k], ws=bws, check=False)
+        gX, _ = sigk.adjoint(state, W, need_y=False, check=False)
         if ev_pairs is not None:
             sigk.profile_events(None, None)
+        return gX
 
     for _ in range(args.warmup):
         step()
@@ -267,8 +275,8 @@ def main():
     value = cells * world / (ms * 1e-3)
 
     # counters of the last launch of each sigma (tiles actually solved)
-    tiles = [sigk.counters(ws)[0] for ws in wss]
     bcnt = sigk.counters(bws)
+    tiles = [bcnt[0] if k == BWD_SIGMA else sigk.counters(wss[k])[0] for k in range(len(SIGMAS))]
 
     # roofline of the solver kernel (dominant: the sigma = 4, P = 16 launch)
     roof = []
@@ -277,6 +285,8 @@ def main():
         flops = tiles[k] * tile_flops(P, nr, DIM)
         ach = flops / (kms * 1e-3) / 1e12
         roof.append({"sigma": sg, "order": P, "rings": nr, "kernel_ms": round(kms, 4),
+                     "kernel": (f"fwd_kernel<P={P},D=16,R=1> (training: stores the tile records)"
+                                if k == BWD_SIGMA else f"fwd_kernel<P={P},D=16>"),
                      "flops_per_launch": flops, "achieved": round(ach, 3)})
     sg, _, P, nr = SIGMAS[BWD_SIGMA]
     kms = statistics.mean(r[len(SIGMAS)] for r in kern_ms)
@@ -323,11 +333,9 @@ def main():
         for k in range(len(SIGMAS)):
             d_pts[k].copy_(h_pts[k], non_blocking=True)
             d_len[k].copy_(h_len[k], non_blocking=True)
-            sigk.gram(d_pts[k], d_len[k], opts=opts[k], out=G[k], ws=wss[k], check=False)
+        gX = step(pts=d_pts, lens=d_len)
+        for k in range(len(SIGMAS)):
             h_out[k].copy_(G[k], non_blocking=True)
-        k = BWD_SIGMA
-        gX, _, _ = sigk.backward(sigk.OP_GRAM, d_pts[k], d_len[k], None, None, W, opts[k],
-                                 ws=bws, check=False)
         h_grad.copy_(gX, non_blocking=True)
         e_e[i].record()
     torch.cuda.synchronize()
@@ -349,10 +357,12 @@ def main():
                    "d": DIM, "sigmas": [s for s, *_ in SIGMAS],
                    "order_rings": [[P, nr] for _, _, P, nr in SIGMAS],
                    "unique_pairs_per_gram": pairs_of_gram(N_PATHS), "l2": "flushed between steps",
-                   "step": "forward Gram (sigma 1 and 4) + adjoint of the sigma=1 Gram "
+                   "step": "forward Gram (sigma 1 and 4; sigma 1 as the training forward "
+                           "that keeps the adjoint's state) + adjoint of the sigma=1 Gram "
                            "(upstream: fixed dense weights)",
                    "parallelism": f"independent batch per rank x{world}"},
-        "gpu_launches": (2 * len(SIGMAS) + 3) * args.steps,
+        # per step: planner + solver for each Gram, adjoint set-up + adjoint
+        "gpu_launches": (2 * len(SIGMAS) + 2) * args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": cells * world / (e2e_ms * 1e-3), "unit": "cells/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},

@@ -189,6 +189,25 @@ sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t 
                           double* value_out, void* ws, size_t ws_bytes, void* stream,
                           const sigk_opts* opts);
 
+/* The two halves of sigk_backward, for callers that keep the forward's state
+ * until the upstream gradient is known (an autograd forward, then its
+ * backward).  sigk_forward_train is the training forward of sigk_backward: it
+ * writes the op's output to value_out (as sigk_backward does) and leaves the
+ * stored seams and tile records in ws.  sigk_adjoint then runs the adjoint
+ * from that state: same op, n_x, n_y (0 for a Gram of X with itself), d and
+ * opts; ws, ws_bytes (sigk_backward_workspace_size), X, Y and their lengths
+ * unchanged since the forward.  grad_out, grad_X, grad_Y as in sigk_backward
+ * (gradients are overwritten).  sigk_adjoint may run again on the same state
+ * with another grad_out.  Errors on the device are reported by
+ * sigk_sync_status. */
+sigk_status sigk_forward_train(int op, const float* X, const int64_t* len_x, int64_t n_x,
+                               const float* Y, const int64_t* len_y, int64_t n_y, int d,
+                               double* value_out, void* ws, size_t ws_bytes, void* stream,
+                               const sigk_opts* opts);
+sigk_status sigk_adjoint(int op, int64_t n_x, int64_t n_y, int d, const double* grad_out,
+                         float* grad_X, float* grad_Y, void* ws, size_t ws_bytes, void* stream,
+                         const sigk_opts* opts);
+
 /* Same result as sigk_pairs, for callers that cannot allocate device memory
  * (code that runs where cudaMalloc is not allowed or not wanted: inside a
  * region governed by someone else's memory pool or allocator, or a runtime

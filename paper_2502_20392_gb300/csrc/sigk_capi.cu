@@ -503,6 +503,50 @@ __device__ void pair_offsets(const PlanArgs& A, int64_t* sh, int64_t* out, int64
     __syncthreads();
 }
 
+// Pair p of the op -> the paths (a, b) it couples and its output entries
+// o0, o1 (o1 >= 0: the mirrored entry of a symmetric Gram).  nz: paths of
+// the square matrix (MMD: both samples; Gram: n_x).
+__device__ void pair_index(const PlanArgs& A, bool self, int64_t p, int64_t& a, int64_t& b,
+                           int64_t& o0, int64_t& o1) {
+    const int64_t nx = A.n_x;
+    const int64_t nz = (A.op == SIGK_OP_MMD) ? A.n_x + A.n_y : (self ? nx : A.n_y);
+    const bool tri = (A.op == SIGK_OP_MMD) || (self && !(A.flags & SIGK_FLAG_GRAM_FULL));
+    o0 = -1;
+    o1 = -1;
+    if (A.op == SIGK_OP_PAIRS) {
+        a = p; b = p; o0 = p;
+    } else if (tri) {
+        // p -> (a, b), a <= b, row-major upper triangle of an nz x nz matrix
+        const int64_t n = nz;
+        double disc = (double)(2 * n + 1) * (double)(2 * n + 1) - 8.0 * (double)p;
+        int64_t aa = (int64_t)(((double)(2 * n + 1) - sqrt(disc)) * 0.5);
+        if (aa < 0) aa = 0;
+        while (aa > 0 && aa * n - aa * (aa - 1) / 2 > p) --aa;
+        while ((aa + 1) * n - (aa + 1) * aa / 2 <= p) ++aa;
+        a = aa;
+        b = p - (aa * n - aa * (aa - 1) / 2) + aa;
+        o0 = a * A.out_ld + b;
+        o1 = (a != b) ? b * A.out_ld + a : -1;
+    } else {
+        const int64_t ny = self ? nx : A.n_y;
+        a = p / ny; b = p % ny;
+        o0 = a * A.out_ld + b;
+    }
+}
+
+// Path z of the pair table's side: (from Y?, index within X or Y).  MMD
+// numbers X then Y; a Gram of X with itself takes both sides from X.
+__device__ __forceinline__ void pair_side(const PlanArgs& A, bool self, int64_t z, bool second,
+                                          bool* from_y, int64_t* idx) {
+    if (A.op == SIGK_OP_MMD) {
+        *from_y = z >= A.n_x;
+        *idx = z < A.n_x ? z : z - A.n_x;
+    } else {
+        *from_y = second && !(A.op == SIGK_OP_GRAM && self);
+        *idx = z;
+    }
+}
+
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
     __shared__ int64_t sh[kPlanThreads];
     __shared__ int bad;
@@ -526,86 +570,30 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
     if (!(A.phase & 2)) return;
     if (ld_volatile_s32(&A.hdr->status) != 0) return;
     const int RS = A.rows_per_strip;
-    const int64_t nx = A.n_x;
-    const int64_t nz = (A.op == SIGK_OP_MMD) ? A.n_x + A.n_y : (self ? nx : A.n_y);
-    // pair table
+    // pair table (the adjoint's upstream weights and gradient pointers are
+    // set later, by adjoint_prep_kernel)
     for (int64_t p = t; p < A.n_pairs; p += kPlanThreads) {
-        int64_t a, b;
-        int64_t o0 = -1, o1 = -1;
-        const bool tri = (A.op == SIGK_OP_MMD) || (self && !(A.flags & SIGK_FLAG_GRAM_FULL));
-        if (A.op == SIGK_OP_PAIRS) {
-            a = p; b = p; o0 = p;
-        } else if (tri) {
-            // p -> (a, b), a <= b, row-major upper triangle of an nz x nz matrix
-            const int64_t n = nz;
-            double disc = (double)(2 * n + 1) * (double)(2 * n + 1) - 8.0 * (double)p;
-            int64_t aa = (int64_t)(((double)(2 * n + 1) - sqrt(disc)) * 0.5);
-            if (aa < 0) aa = 0;
-            while (aa > 0 && aa * n - aa * (aa - 1) / 2 > p) --aa;
-            while ((aa + 1) * n - (aa + 1) * aa / 2 <= p) ++aa;
-            a = aa;
-            b = p - (aa * n - aa * (aa - 1) / 2) + aa;
-            o0 = a * A.out_ld + b;
-            o1 = (a != b) ? b * A.out_ld + a : -1;
-        } else {
-            const int64_t ny = self ? nx : A.n_y;
-            a = p / ny; b = p % ny;
-            o0 = a * A.out_ld + b;
-        }
+        int64_t a, b, o0, o1;
+        pair_index(A, self, p, a, b, o0, o1);
         // resolve path pointers and segment counts
         const float* pa;
         const float* pb;
         int64_t la, lb;
-        float* ga = nullptr;
-        float* gb = nullptr;
         int32_t ra = 1, rb = 1;
-        auto path = [&](int64_t z, bool from_y, const float** ptr, int64_t* segs, float** g,
-                        int32_t* rf) {
+        auto path = [&](int64_t z, bool second, const float** ptr, int64_t* segs, int32_t* rf) {
+            bool from_y;
+            int64_t i;
+            pair_side(A, self, z, second, &from_y, &i);
             const float* base = from_y ? A.Y : A.X;
             const int64_t* off = from_y ? A.oy : A.ox;
             const int64_t* len = from_y ? A.len_y : A.len_x;
             const int32_t* sf = from_y ? A.sY : A.sX;
-            float* gbase = from_y ? A.gY : A.gX;
-            *ptr = base + off[z] * A.d;
-            *rf = sf ? sf[z] : 1;
-            *segs = (A.inc_mode ? len[z] : len[z] - 1) * (int64_t)(*rf);
-            *g = gbase ? gbase + off[z] * A.d : nullptr;
+            *ptr = base + off[i] * A.d;
+            *rf = sf ? sf[i] : 1;
+            *segs = (A.inc_mode ? len[i] : len[i] - 1) * (int64_t)(*rf);
         };
-        if (A.op == SIGK_OP_MMD) {
-            path(a < nx ? a : a - nx, a >= nx, &pa, &la, &ga, &ra);
-            path(b < nx ? b : b - nx, b >= nx, &pb, &lb, &gb, &rb);
-        } else if (A.op == SIGK_OP_PAIRS) {
-            path(a, false, &pa, &la, &ga, &ra);
-            path(b, true, &pb, &lb, &gb, &rb);
-        } else {
-            path(a, false, &pa, &la, &ga, &ra);
-            path(b, !self, &pb, &lb, &gb, &rb);
-        }
-        if (A.train) {
-            // upstream weight of this pair's k value
-            double w = 0.0;
-            if (A.op == SIGK_OP_PAIRS) {
-                w = A.grad_out[p];
-            } else if (A.op == SIGK_OP_GRAM) {
-                w = A.grad_out[o0];
-                if (o1 >= 0) w += A.grad_out[o1];
-            } else {  // MMD^2 = mean k(x,x') + mean k(y,y') - 2 mean k(x,y)
-                const int64_t m = nx, n = A.n_y;
-                const bool unb = !(A.flags & SIGK_FLAG_MMD_BIASED);
-                double cf;
-                if (a < m && b < m) {
-                    cf = (a == b) ? (unb ? 0.0 : 1.0 / ((double)m * m))
-                                  : (unb ? 2.0 / ((double)m * (m - 1)) : 2.0 / ((double)m * m));
-                } else if (a >= m && b >= m) {
-                    cf = (a == b) ? (unb ? 0.0 : 1.0 / ((double)n * n))
-                                  : (unb ? 2.0 / ((double)n * (n - 1)) : 2.0 / ((double)n * n));
-                } else {
-                    cf = -2.0 / ((double)m * n);
-                }
-                w = A.grad_out[0] * cf;
-            }
-            A.pair_w[p] = w;
-        }
+        path(a, false, &pa, &la, &ra);
+        path(b, true, &pb, &lb, &rb);
         PairDesc pd;
         pd.out0 = o0;
         pd.out1 = o1;
@@ -619,8 +607,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         if ((swap ? la : lb) > A.max_len) atomicCAS(&A.hdr->status, 0, kErrLength);
         pd.xr = swap ? pb : pa;
         pd.yr = swap ? pa : pb;
-        pd.gxr = A.train ? (swap ? gb : ga) : nullptr;
-        pd.gyr = A.train ? (swap ? ga : gb) : nullptr;
+        pd.gxr = nullptr;
+        pd.gyr = nullptr;
         pd.sx = swap ? rb : ra;
         pd.sy = swap ? ra : rb;
         if (la > (int64_t)INT32_MAX || lb > (int64_t)INT32_MAX) atomicCAS(&A.hdr->status, 0, kErrLength);
@@ -768,20 +756,6 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         A.hdr->counters[3] = 0;
     }
     if (!A.train) return;
-    for (int i = t; i < A.bnslot; i += kPlanThreads) {
-        A.bprod[i] = 0ull;
-        A.bcons[i] = 0ull;
-        A.bdone[i] = -1ll;
-    }
-    // gradient outputs are accumulated with atomics: zero them
-    if (A.gX) {
-        const int64_t nxf = (int64_t)A.ox[A.n_x] * A.d;
-        for (int64_t i = t; i < nxf; i += kPlanThreads) A.gX[i] = 0.0f;
-    }
-    if (A.gY && !self) {
-        const int64_t nyf = (int64_t)A.oy[A.n_y] * A.d;
-        for (int64_t i = t; i < nyf; i += kPlanThreads) A.gY[i] = 0.0f;
-    }
     // per-pair offsets of the forward seam store: (strips - 1) x L2 x stride
     __syncthreads();
     pair_offsets(A, sh, A.store_off, A.store_cap, [&](const PairDesc& q) -> int64_t {
@@ -793,6 +767,73 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         pair_offsets(A, sh, A.rec_off, A.rec_cap, [&](const PairDesc& q) -> int64_t {
             return (int64_t)q.n_strips * (q.L2 + 32) * A.rec_block;
         });
+    }
+}
+
+// Adjoint set-up, run before every adjoint launch on a workspace that holds
+// a training forward: the upstream weight of every pair's k value (from
+// grad_out), the gradient pointers of the pair table, zeroed gradient outputs
+// (accumulated with atomics) and reset adjoint synchronisation words.  A
+// grid-stride kernel; block 0 resets the counters.
+__global__ void adjoint_prep_kernel(PlanArgs A) {
+    const bool self = (A.op == SIGK_OP_GRAM && A.n_y == 0);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        A.hdr->bwd_item_counter = 0;
+        A.hdr->counters[2] = 0;
+        A.hdr->counters[3] = 0;
+    }
+    for (int64_t p = tid; p < A.n_pairs; p += nth) {
+        int64_t a, b, o0, o1;
+        pair_index(A, self, p, a, b, o0, o1);
+        double w = 0.0;
+        if (A.op == SIGK_OP_PAIRS) {
+            w = A.grad_out[p];
+        } else if (A.op == SIGK_OP_GRAM) {
+            w = A.grad_out[o0];
+            if (o1 >= 0) w += A.grad_out[o1];
+        } else {  // MMD^2 = mean k(x,x') + mean k(y,y') - 2 mean k(x,y)
+            const int64_t m = A.n_x, n = A.n_y;
+            const bool unb = !(A.flags & SIGK_FLAG_MMD_BIASED);
+            double cf;
+            if (a < m && b < m) {
+                cf = (a == b) ? (unb ? 0.0 : 1.0 / ((double)m * m))
+                              : (unb ? 2.0 / ((double)m * (m - 1)) : 2.0 / ((double)m * m));
+            } else if (a >= m && b >= m) {
+                cf = (a == b) ? (unb ? 0.0 : 1.0 / ((double)n * n))
+                              : (unb ? 2.0 / ((double)n * (n - 1)) : 2.0 / ((double)n * n));
+            } else {
+                cf = -2.0 / ((double)m * n);
+            }
+            w = A.grad_out[0] * cf;
+        }
+        A.pair_w[p] = w;
+        auto grad = [&](int64_t z, bool second) -> float* {
+            bool from_y;
+            int64_t i;
+            pair_side(A, self, z, second, &from_y, &i);
+            float* g = from_y ? A.gY : A.gX;
+            return g ? g + (from_y ? A.oy : A.ox)[i] * A.d : nullptr;
+        };
+        float* ga = grad(a, false);
+        float* gb = grad(b, true);
+        PairDesc& pd = A.pairs[p];
+        pd.gxr = pd.swapped ? gb : ga;
+        pd.gyr = pd.swapped ? ga : gb;
+    }
+    if (A.gX) {
+        const int64_t nxf = (int64_t)A.ox[A.n_x] * A.d;
+        for (int64_t i = tid; i < nxf; i += nth) A.gX[i] = 0.0f;
+    }
+    if (A.gY && !self) {
+        const int64_t nyf = (int64_t)A.oy[A.n_y] * A.d;
+        for (int64_t i = tid; i < nyf; i += nth) A.gY[i] = 0.0f;
+    }
+    for (int64_t i = tid; i < A.bnslot; i += nth) {
+        A.bprod[i] = 0ull;
+        A.bcons[i] = 0ull;
+        A.bdone[i] = -1ll;
     }
 }
 
@@ -947,23 +988,16 @@ static cudaError_t launch_planner(PlanArgs pa, const Opts& o, const Layout& L, c
     return cudaGetLastError();
 }
 
-// Backward extras for run_solver (train mode).
-struct TrainArgs {
-    const double* grad_out;
-    float* gX;
-    float* gY;
-};
-
-// Common driver: plan + solve into `out` (k values or Gram).  With `tr`, the
-// forward runs in training mode (one row per lane, every strip seam stored)
-// and the adjoint kernel follows, accumulating gradients into tr->gX/gY.
+// Common driver: plan + solve into `out` (k values or Gram).  With `train`,
+// the forward runs in training mode: every 32-row strip's seam is stored and,
+// within the record budget, every tile's record (one row per lane); the
+// workspace then holds what launch_adjoint needs.
 static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int64_t n_x,
                               const float* Y, const int64_t* len_y, int64_t n_y, int d,
                               double* out, int64_t out_ld, void* ws, size_t ws_bytes,
                               cudaStream_t stream, const Opts& o, Layout* Lout,
-                              const TrainArgs* tr = nullptr, bool allow_sm = true) {
+                              bool train = false, bool allow_sm = true) {
     Layout L;
-    const bool train = tr != nullptr;
     sigk_status st = make_layout(op, n_x, n_y, d, o, &L, train, allow_sm);
     if (st != SIGK_OK) return st;
     if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
@@ -1012,14 +1046,6 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
             pa.rec_cap = L.rstore_floats;
             pa.rec_block = 32 * rec_floats(o.order);
         }
-        pa.pair_w = (double*)(base + L.pair_w);
-        pa.grad_out = tr->grad_out;
-        pa.gX = tr->gX;
-        pa.gY = tr->gY;
-        pa.bprod = (unsigned long long*)(base + L.bprod);
-        pa.bcons = (unsigned long long*)(base + L.bcons);
-        pa.bdone = (long long*)(base + L.bdone);
-        pa.bnslot = L.bnslot;
     }
     cudaError_t e = launch_planner(pa, o, L, base, stream);
     if (e != cudaSuccess) return cuda_fail(e, "planner launch");
@@ -1064,48 +1090,91 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         }
     }
     if (L.n_pairs > 0) {
-        if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_start, stream);
+        if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
         e = L.cm ? fwd_cm_launch_dispatch(o.order, o.rings, L.f64, sa, base + L.cscratch, L.cstride,
                                           L.grid, stream)
                  : fwd_launch_dispatch(o.order, o.rings, dim_bucket(d), L.stored_rec ? 1 : 0, sa,
                                        L.grid, stream);
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
-        if (g_ev_start && g_ev_stop && !train) cudaEventRecord(g_ev_stop, stream);
-    }
-    if (train && L.n_pairs > 0) {
-        BwdArgs ba;
-        memset(&ba, 0, sizeof(ba));
-        ba.pairs = pa.pairs;
-        ba.sched = table_sched;
-        ba.n_pairs = (int32_t)L.n_pairs;
-        ba.inc_mode = pa.inc_mode;
-        ba.d = d;
-        ba.nr = o.rings;
-        ba.store = sa.store;
-        ba.store_off = pa.store_off;
-        ba.pair_exp = sa.pair_exp;
-        ba.pair_w = pa.pair_w;
-        ba.rec = (float*)(base + L.rec);
-        ba.rec_stride = L.rec_stride;
-        if (L.stored_rec) {
-            ba.rec_store = sa.rec;
-            ba.rec_off = pa.rec_off;
-        }
-        ba.nslot = L.bnslot;
-        ba.wcols = L.bwcols;
-        ba.aseam = (float*)(base + L.aseam);
-        ba.prod = pa.bprod;
-        ba.cons = pa.bcons;
-        ba.done = pa.bdone;
-        ba.item_counter = &hdr->bwd_item_counter;
-        ba.status = &hdr->status;
-        ba.counters = hdr->counters;
-        if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
-        e = bwd_launch_dispatch(o.order, o.rings, dim_bucket(d), ba, L.bgrid, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "backward launch");
         if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_stop, stream);
     }
     if (Lout) *Lout = L;
+    return SIGK_OK;
+}
+
+// The adjoint after a training forward on the same workspace (run_solver with
+// train = true, same op, sizes and opts): adjoint_prep_kernel, then the
+// adjoint kernel.  gX / gY (or null) receive the gradients.
+static sigk_status launch_adjoint(int op, int64_t n_x, int64_t n_y, int d, const double* grad_out,
+                                  float* gX, float* gY, void* ws, size_t ws_bytes,
+                                  cudaStream_t stream, const Opts& o) {
+    Layout L;
+    sigk_status st = make_layout(op, n_x, n_y, d, o, &L, true);
+    if (st != SIGK_OK) return st;
+    if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
+    if (L.n_pairs == 0) return SIGK_OK;
+    char* base = (char*)ws;
+    Header* hdr = (Header*)(base + L.hdr);
+    PlanArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.op = op;
+    pa.flags = o.flags;
+    pa.d = d;
+    pa.n_x = n_x;
+    pa.n_y = n_y;
+    pa.n_pairs = L.n_pairs;
+    pa.out_ld = op == SIGK_OP_MMD ? n_x + n_y : (op == SIGK_OP_GRAM ? (n_y > 0 ? n_y : n_x) : 0);
+    pa.ox = (int64_t*)(base + L.ox);
+    pa.oy = (int64_t*)(base + L.oy);
+    pa.pairs = (PairDesc*)(base + L.pairs);
+    pa.hdr = hdr;
+    pa.pair_w = (double*)(base + L.pair_w);
+    pa.grad_out = grad_out;
+    pa.gX = gX;
+    pa.gY = gY;
+    pa.bprod = (unsigned long long*)(base + L.bprod);
+    pa.bcons = (unsigned long long*)(base + L.bcons);
+    pa.bdone = (long long*)(base + L.bdone);
+    pa.bnslot = L.bnslot;
+    adjoint_prep_kernel<<<L.bgrid, 256, 0, stream>>>(pa);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint set-up launch");
+    BwdArgs ba;
+    memset(&ba, 0, sizeof(ba));
+    ba.pairs = pa.pairs;
+    ba.sched.hdr = hdr->sched;
+    ba.sched.item_start = (int32_t*)(base + L.item_start);
+    ba.sched.order = (int32_t*)(base + L.order);
+    ba.sched.level_start = (int32_t*)(base + L.lvl);
+    ba.sched.n_pairs = (int32_t)L.n_pairs;
+    ba.sched.shift = 0;
+    ba.n_pairs = (int32_t)L.n_pairs;
+    ba.inc_mode = (o.flags & SIGK_FLAG_INCREMENTS) ? 1 : 0;
+    ba.d = d;
+    ba.nr = o.rings;
+    ba.store = (float*)(base + L.store);
+    ba.store_off = (int64_t*)(base + L.store_off);
+    ba.pair_exp = (int32_t*)(base + L.pair_exp);
+    ba.pair_w = pa.pair_w;
+    ba.rec = (float*)(base + L.rec);
+    ba.rec_stride = L.rec_stride;
+    if (L.stored_rec) {
+        ba.rec_store = (float*)(base + L.rstore);
+        ba.rec_off = (int64_t*)(base + L.rec_off);
+    }
+    ba.nslot = L.bnslot;
+    ba.wcols = L.bwcols;
+    ba.aseam = (float*)(base + L.aseam);
+    ba.prod = pa.bprod;
+    ba.cons = pa.bcons;
+    ba.done = pa.bdone;
+    ba.item_counter = &hdr->bwd_item_counter;
+    ba.status = &hdr->status;
+    ba.counters = hdr->counters;
+    if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
+    e = bwd_launch_dispatch(o.order, o.rings, dim_bucket(d), ba, L.bgrid, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+    if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_stop, stream);
     return SIGK_OK;
 }
 
@@ -1196,46 +1265,32 @@ size_t sigk_backward_workspace_size(int op, int64_t n_x, int64_t n_y, int d, con
     return L.total;
 }
 
-sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t n_x, const float* Y,
-                          const int64_t* len_y, int64_t n_y, int d, const double* grad_out,
-                          float* grad_X, float* grad_Y, double* value_out, void* ws,
-                          size_t ws_bytes, void* stream, const sigk_opts* opts) {
-    if (op < SIGK_OP_PAIRS || op > SIGK_OP_MMD) return fail(SIGK_ERR_ARG, "bad op");
-    if (!grad_out) return fail(SIGK_ERR_ARG, "grad_out is NULL");
-    if (op == SIGK_OP_GRAM && !Y) n_y = 0;
-    if (op == SIGK_OP_PAIRS) n_y = n_x;
-    sigk_status st = common_checks(n_x, n_y, d, grad_out);
-    if (st != SIGK_OK) return st;
-    if (n_x > 0 && (!X || !len_x)) return fail(SIGK_ERR_ARG, "null X input");
-    if (op != SIGK_OP_GRAM || Y) {
-        if (n_y > 0 && (!Y || !len_y)) return fail(SIGK_ERR_ARG, "null Y input");
-    }
-    Opts o;
-    if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
-    if (n_x == 0 || (op != SIGK_OP_GRAM && n_y == 0)) return SIGK_OK;
-    const int unbiased = (o.flags & SIGK_FLAG_MMD_BIASED) ? 0 : 1;
-    if (op == SIGK_OP_MMD && (n_x < 1 + unbiased || n_y < 1 + unbiased))
-        return fail(SIGK_ERR_ARG, "MMD needs at least 2 paths per sample (1 for the V-statistic)");
+// Shared by sigk_forward_train and sigk_backward: argument checks and the
+// training forward into value_out (or the workspace's Gram for MMD).
+static sigk_status forward_train(int op, const float* X, const int64_t* len_x, int64_t n_x,
+                                 const float* Y, const int64_t* len_y, int64_t n_y, int d,
+                                 double* value_out, void* ws, size_t ws_bytes, void* stream,
+                                 const Opts& o) {
+    sigk_status st;
     Layout L;
     if ((st = make_layout(op, n_x, n_y, d, o, &L, true)) != SIGK_OK) return st;
     if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;
-    TrainArgs tr{grad_out, grad_X, (op == SIGK_OP_GRAM && !Y) ? nullptr : grad_Y};
+    const int unbiased = (o.flags & SIGK_FLAG_MMD_BIASED) ? 0 : 1;
     double* vals = nullptr;
     int64_t ld = 0;
     if (op == SIGK_OP_MMD) {
         vals = (double*)((char*)ws + L.gram);
         ld = n_x + n_y;
     } else if (op == SIGK_OP_GRAM) {
-        if (!value_out) return fail(SIGK_ERR_ARG, "Gram backward needs value_out [n_x*n_y] as scratch");
+        if (!value_out) return fail(SIGK_ERR_ARG, "a Gram training forward needs value_out [n_x*n_y]");
         vals = value_out;
-        ld = Y ? n_y : n_x;
+        ld = n_y > 0 ? n_y : n_x;
     } else {
-        if (!value_out) return fail(SIGK_ERR_ARG, "pairs backward needs value_out [n_pairs] as scratch");
+        if (!value_out) return fail(SIGK_ERR_ARG, "a pairs training forward needs value_out [n_pairs]");
         vals = value_out;
     }
-    st = run_solver(op, X, len_x, n_x, (op == SIGK_OP_GRAM && !Y) ? nullptr : Y, len_y,
-                    (op == SIGK_OP_GRAM && !Y) ? 0 : n_y, d, vals, ld, ws, ws_bytes,
-                    (cudaStream_t)stream, o, nullptr, &tr);
+    st = run_solver(op, X, len_x, n_x, n_y > 0 || op != SIGK_OP_GRAM ? Y : nullptr, len_y, n_y, d,
+                    vals, ld, ws, ws_bytes, (cudaStream_t)stream, o, nullptr, true);
     if (st != SIGK_OK) return st;
     if (op == SIGK_OP_MMD && value_out) {
         mmd_reduce_kernel<<<1, 1024, 0, (cudaStream_t)stream>>>(vals, n_x, n_y, unbiased, value_out);
@@ -1243,6 +1298,75 @@ sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t 
         if (e != cudaSuccess) return cuda_fail(e, "mmd_reduce launch");
     }
     return SIGK_OK;
+}
+
+// Normalises (op, n_x, n_y, Y) and checks the arguments common to the
+// training calls; *skip = true when there is nothing to solve.
+static sigk_status train_checks(int op, const float* X, const int64_t* len_x, int64_t n_x,
+                                const float* Y, const int64_t* len_y, int64_t* n_y, int d,
+                                const sigk_opts* opts, Opts* o, bool* skip) {
+    *skip = false;
+    if (op < SIGK_OP_PAIRS || op > SIGK_OP_MMD) return fail(SIGK_ERR_ARG, "bad op");
+    if (op == SIGK_OP_GRAM && !Y) *n_y = 0;
+    if (op == SIGK_OP_PAIRS) *n_y = n_x;
+    sigk_status st = common_checks(n_x, *n_y, d, (const void*)1);
+    if (st != SIGK_OK) return st;
+    if (n_x > 0 && (!X || !len_x)) return fail(SIGK_ERR_ARG, "null X input");
+    if (op != SIGK_OP_GRAM || Y) {
+        if (*n_y > 0 && (!Y || !len_y)) return fail(SIGK_ERR_ARG, "null Y input");
+    }
+    if (!resolve_opts(opts, o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    if (n_x == 0 || (op != SIGK_OP_GRAM && *n_y == 0)) {
+        *skip = true;
+        return SIGK_OK;
+    }
+    const int unbiased = (o->flags & SIGK_FLAG_MMD_BIASED) ? 0 : 1;
+    if (op == SIGK_OP_MMD && (n_x < 1 + unbiased || *n_y < 1 + unbiased))
+        return fail(SIGK_ERR_ARG, "MMD needs at least 2 paths per sample (1 for the V-statistic)");
+    return SIGK_OK;
+}
+
+sigk_status sigk_forward_train(int op, const float* X, const int64_t* len_x, int64_t n_x,
+                               const float* Y, const int64_t* len_y, int64_t n_y, int d,
+                               double* value_out, void* ws, size_t ws_bytes, void* stream,
+                               const sigk_opts* opts) {
+    Opts o;
+    bool skip;
+    sigk_status st = train_checks(op, X, len_x, n_x, Y, len_y, &n_y, d, opts, &o, &skip);
+    if (st != SIGK_OK || skip) return st;
+    return forward_train(op, X, len_x, n_x, Y, len_y, n_y, d, value_out, ws, ws_bytes, stream, o);
+}
+
+sigk_status sigk_adjoint(int op, int64_t n_x, int64_t n_y, int d, const double* grad_out,
+                         float* grad_X, float* grad_Y, void* ws, size_t ws_bytes, void* stream,
+                         const sigk_opts* opts) {
+    if (op < SIGK_OP_PAIRS || op > SIGK_OP_MMD) return fail(SIGK_ERR_ARG, "bad op");
+    if (!grad_out) return fail(SIGK_ERR_ARG, "grad_out is NULL");
+    if (op == SIGK_OP_PAIRS) n_y = n_x;
+    sigk_status st = common_checks(n_x, n_y, d, grad_out);
+    if (st != SIGK_OK) return st;
+    Opts o;
+    if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    if (n_x == 0 || (op != SIGK_OP_GRAM && n_y == 0)) return SIGK_OK;
+    return launch_adjoint(op, n_x, n_y, d, grad_out, grad_X,
+                          (op == SIGK_OP_GRAM && n_y == 0) ? nullptr : grad_Y, ws, ws_bytes,
+                          (cudaStream_t)stream, o);
+}
+
+sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t n_x, const float* Y,
+                          const int64_t* len_y, int64_t n_y, int d, const double* grad_out,
+                          float* grad_X, float* grad_Y, double* value_out, void* ws,
+                          size_t ws_bytes, void* stream, const sigk_opts* opts) {
+    if (!grad_out) return fail(SIGK_ERR_ARG, "grad_out is NULL");
+    Opts o;
+    bool skip;
+    sigk_status st = train_checks(op, X, len_x, n_x, Y, len_y, &n_y, d, opts, &o, &skip);
+    if (st != SIGK_OK || skip) return st;
+    st = forward_train(op, X, len_x, n_x, Y, len_y, n_y, d, value_out, ws, ws_bytes, stream, o);
+    if (st != SIGK_OK) return st;
+    return launch_adjoint(op, n_x, n_y, d, grad_out, grad_X,
+                          (op == SIGK_OP_GRAM && n_y == 0) ? nullptr : grad_Y, ws, ws_bytes,
+                          (cudaStream_t)stream, o);
 }
 
 // Exact tile statistics of the pair table as planned (sigk_stats.cuh).
@@ -1521,7 +1645,7 @@ extern "C" sigk_status sigk_pairs_static(const float* X, const int64_t* len_x, c
     void* ws = nullptr;
     if ((st = static_ws_ptr(&ws)) != SIGK_OK) return st;
     return run_solver(SIGK_OP_PAIRS, X, len_x, n_pairs, Y, len_y, n_pairs, d, k_out, 0, ws,
-                      kStaticWsBytes, (cudaStream_t)stream, o, nullptr, nullptr, sm);
+                      kStaticWsBytes, (cudaStream_t)stream, o, nullptr, false, sm);
 }
 
 extern "C" sigk_status sigk_static_sync_status(void* stream) {

@@ -84,6 +84,8 @@ def load(path: str | None = None):
     lib.sigk_backward_workspace_size.argtypes = [i32, i64, i64, i32, op]
     lib.sigk_backward_workspace_size.restype = sz
     lib.sigk_backward.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, vp, vp, vp, vp, vp, sz, vp, op]
+    lib.sigk_forward_train.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, vp, vp, sz, vp, op]
+    lib.sigk_adjoint.argtypes = [i32, i64, i64, i32, vp, vp, vp, vp, sz, vp, op]
     lib.sigk_sync_status.argtypes = [vp, sz, vp]
     lib.sigk_counters.argtypes = [vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sigk_profile_events.argtypes = [vp, vp]
@@ -277,52 +279,121 @@ def backward(op: int, X, len_x, Y, len_y, grad_out, opts: Opts | None = None,
     return gX, gY, value
 
 
+class TrainState:
+    """What forward_train leaves for adjoint: the workspace (seams and tile
+    records of the training forward) and the inputs it refers to, which must
+    stay unchanged until the adjoint has run."""
+
+    def __init__(self, op, X, len_x, Y, len_y, n_x, n_y, d, opts, ws):
+        self.op, self.X, self.len_x, self.Y, self.len_y = op, X, len_x, Y, len_y
+        self.n_x, self.n_y, self.d, self.opts, self.ws = n_x, n_y, d, opts, ws
+
+
+def _train_shapes(op, X, len_x, Y, len_y):
+    X, len_x = _paths(X, len_x)
+    n_x, d = len_x.numel(), X.shape[1]
+    self_gram = op == OP_GRAM and Y is None
+    if Y is not None:
+        Y, len_y = _paths(Y, len_y)
+        n_y = len_y.numel()
+    else:
+        n_y = 0 if self_gram else n_x
+    if op == OP_PAIRS:
+        n_y = n_x
+        vshape = (n_x,)
+    elif op == OP_GRAM:
+        vshape = (n_x, n_y or n_x)
+    else:
+        vshape = (1,)
+    return X, len_x, Y, len_y, n_x, n_y, d, vshape
+
+
+def forward_train(op: int, X, len_x, Y, len_y, opts: Opts | None = None,
+                  ws: Workspace | None = None, out=None, check: bool = True):
+    """Training forward of pairs / gram / mmd: returns (value, state); the
+    state feeds adjoint() once the upstream gradient is known.  The state owns
+    its workspace (a fresh one unless `ws` is given)."""
+    opts = opts or Opts()
+    X, len_x, Y, len_y, n_x, n_y, d, vshape = _train_shapes(op, X, len_x, Y, len_y)
+    value = out if out is not None else torch.empty(vshape, dtype=torch.float64, device=X.device)
+    ws = ws if ws is not None else Workspace()
+    buf = ws.get(backward_workspace_size(op, n_x, n_y, d, opts), X.device)
+    o = opts.c()
+    _check(load().sigk_forward_train(op, _ptr(X), _ptr(len_x), n_x, _ptr(Y), _ptr(len_y), n_y, d,
+                                     _ptr(value), _ptr(buf), buf.numel(), _stream(),
+                                     ctypes.byref(o)))
+    if check:
+        sync_status(ws)
+    return value, TrainState(op, X, len_x, Y, len_y, n_x, n_y, d, opts, ws)
+
+
+def adjoint(state: TrainState, grad_out, need_x: bool = True, need_y: bool = True,
+            check: bool = True):
+    """Adjoint from a forward_train state: (grad_X, grad_Y) as in backward()."""
+    X, Y = state.X, state.Y
+    gout = grad_out.to(device=X.device, dtype=torch.float64).contiguous()
+    gX = torch.empty_like(X) if need_x else None
+    gY = torch.empty_like(Y) if (need_y and Y is not None and state.n_y > 0) else None
+    buf = state.ws.buf
+    o = state.opts.c()
+    _check(load().sigk_adjoint(state.op, state.n_x, state.n_y, state.d, _ptr(gout), _ptr(gX),
+                               _ptr(gY), _ptr(buf), buf.numel(), _stream(), ctypes.byref(o)))
+    if check:
+        sync_status(state.ws)
+    return gX, gY
+
+
+# The autograd functions run the training forward when an input needs a
+# gradient and keep its state (seams, tile records: the workspace) on the
+# context until backward, which then runs only the adjoint.
+
 class _PairsFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, Y, len_x, len_y, opts):
-        ctx.save_for_backward(X, Y, len_x, len_y)
         ctx.opts = opts
-        return pairs(X.detach(), len_x, Y.detach(), len_y, opts=opts)
+        if not (ctx.needs_input_grad[0] or ctx.needs_input_grad[1]):
+            return pairs(X.detach(), len_x, Y.detach(), len_y, opts=opts)
+        value, ctx.state = forward_train(OP_PAIRS, X.detach(), len_x, Y.detach(), len_y, opts)
+        return value
 
     @staticmethod
     def backward(ctx, g):
-        X, Y, len_x, len_y = ctx.saved_tensors
-        gX, gY, _ = backward(OP_PAIRS, X.detach(), len_x, Y.detach(), len_y, g, ctx.opts,
-                             need_x=ctx.needs_input_grad[0], need_y=ctx.needs_input_grad[1])
+        gX, gY = adjoint(ctx.state, g, need_x=ctx.needs_input_grad[0],
+                         need_y=ctx.needs_input_grad[1])
         return gX, gY, None, None, None
 
 
 class _GramFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, Y, len_x, len_y, opts):
-        ctx.save_for_backward(X, Y if Y is not None else X, len_x, len_y if len_y is not None else len_x)
         ctx.self_gram = Y is None
         ctx.opts = opts
-        return gram(X.detach(), len_x, None if Y is None else Y.detach(), len_y, opts=opts)
+        Yd = None if Y is None else Y.detach()
+        if not (ctx.needs_input_grad[0] or ctx.needs_input_grad[1]):
+            return gram(X.detach(), len_x, Yd, len_y, opts=opts)
+        value, ctx.state = forward_train(OP_GRAM, X.detach(), len_x, Yd, len_y, opts)
+        return value
 
     @staticmethod
     def backward(ctx, g):
-        X, Y, len_x, len_y = ctx.saved_tensors
-        if ctx.self_gram:
-            gX, _, _ = backward(OP_GRAM, X.detach(), len_x, None, None, g, ctx.opts)
-            return gX, None, None, None, None
-        gX, gY, _ = backward(OP_GRAM, X.detach(), len_x, Y.detach(), len_y, g, ctx.opts,
-                             need_x=ctx.needs_input_grad[0], need_y=ctx.needs_input_grad[1])
-        return gX, gY, None, None, None
+        gX, gY = adjoint(ctx.state, g, need_x=ctx.needs_input_grad[0],
+                         need_y=(not ctx.self_gram) and ctx.needs_input_grad[1])
+        return gX, (None if ctx.self_gram else gY), None, None, None
 
 
 class _MMDFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, X, Y, len_x, len_y, opts):
-        ctx.save_for_backward(X, Y, len_x, len_y)
         ctx.opts = opts
-        return mmd(X.detach(), len_x, Y.detach(), len_y, opts=opts)
+        if not (ctx.needs_input_grad[0] or ctx.needs_input_grad[1]):
+            return mmd(X.detach(), len_x, Y.detach(), len_y, opts=opts)
+        value, ctx.state = forward_train(OP_MMD, X.detach(), len_x, Y.detach(), len_y, opts)
+        return value
 
     @staticmethod
     def backward(ctx, g):
-        X, Y, len_x, len_y = ctx.saved_tensors
-        gX, gY, _ = backward(OP_MMD, X.detach(), len_x, Y.detach(), len_y, g, ctx.opts,
-                             need_x=ctx.needs_input_grad[0], need_y=ctx.needs_input_grad[1])
+        gX, gY = adjoint(ctx.state, g, need_x=ctx.needs_input_grad[0],
+                         need_y=ctx.needs_input_grad[1])
         return gX, gY, None, None, None
 
 

@@ -168,6 +168,38 @@ def test_autograd_matches_backward(S):
     assert torch.isfinite(gG).all()
 
 
+@pytest.mark.parametrize("op", ["pairs", "gram_xy", "gram_self", "mmd"])
+def test_forward_train_then_adjoint(S, op):
+    # the split entry points: sigk_forward_train leaves the seams and tile
+    # records in the workspace, sigk_adjoint runs from them (twice here, with
+    # different upstream gradients: no accumulation across calls)
+    from paper_2502_20392_gb300 import synth
+    px, lxp = synth.brownian(4, [70, 33, 1, 120], 8, 1.0, seed=101)
+    py, lyp = synth.brownian(4, [90, 12, 64, 40], 8, 1.0, seed=102)
+    X, lx = torch.from_numpy(px).to(dev()), torch.from_numpy(lxp).to(dev())
+    Y, ly = torch.from_numpy(py).to(dev()), torch.from_numpy(lyp).to(dev())
+    o = S.Opts(order=8, rings=4, max_len=160)
+    rng = np.random.default_rng(103)
+    code, args, gshape = {
+        "pairs": (S.OP_PAIRS, (X, lx, Y, ly), (4,)),
+        "gram_xy": (S.OP_GRAM, (X, lx, Y, ly), (4, 4)),
+        "gram_self": (S.OP_GRAM, (X, lx, None, None), (4, 4)),
+        "mmd": (S.OP_MMD, (X, lx, Y, ly), (1,)),
+    }[op]
+    g1 = torch.from_numpy(rng.standard_normal(gshape))
+    value, state = S.forward_train(code, *args, o)
+    aX, aY = S.adjoint(state, g1)
+    bX, bY = S.adjoint(state, 2.0 * g1)
+    rX, rY, rv = S.backward(code, *args, g1, o)
+    assert torch.equal(value, rv)
+    torch.testing.assert_close(aX, rX, rtol=1e-5, atol=1e-6 * float(rX.abs().max()))
+    torch.testing.assert_close(bX, 2.0 * aX, rtol=1e-5, atol=1e-6 * float(rX.abs().max()))
+    if op == "gram_self":
+        assert aY is None and rY is None
+    else:
+        torch.testing.assert_close(aY, rY, rtol=1e-5, atol=1e-6 * float(rY.abs().max()))
+
+
 def test_gradient_with_refinement(S, orc):
     # gradients of refined virtual segments are folded back to the segments
     from paper_2502_20392_gb300 import synth
