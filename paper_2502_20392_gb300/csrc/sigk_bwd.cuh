@@ -182,15 +182,10 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         for (int t = 0; t < T && !stored; ++t) {
             if ((t & 31) == 0 && t < L2) {
                 const int nb = min(32, L2 - t);
-                for (int idx = lane; idx < 32 * D; idx += 32) {
-                    const int col = idx / D, e = idx % D;
-                    float v = 0.0f;
-                    if (col < nb && e < A.d) v = inc_ref(pd.yr, t + col, A.d, e, A.inc_mode, pd.sy);
-                    dyw[((t + col) & 63) * DS + e] = v;
-                }
+                fill_dy<D, DS, false>(dyw, pd.yr, t, nb, L2, A.d, A.inc_mode, pd.sy, lane);
                 if (s > 0) {
                     const float* src = st_base + ((size_t)(s - 1) * L2 + t) * S;
-                    for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = src[idx];
+                    warp_copy_cg<S>(sin_, src, nb * S, lane);
                 }
                 __syncwarp();
             }
@@ -322,12 +317,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
             if ((tp & 31) == 0 && tp < L2) {
                 const int nb = min(32, L2 - tp);
                 // dy for reverse columns jr in [tp, tp+nb): j = L2-1-jr
-                for (int idx = lane; idx < 32 * D; idx += 32) {
-                    const int col = idx / D, e = idx % D;
-                    float v = 0.0f;
-                    if (col < nb && e < A.d) v = inc_ref(pd.yr, L2 - 1 - (tp + col), A.d, e, A.inc_mode, pd.sy);
-                    dyw[((tp + col) & 63) * DS + e] = v;
-                }
+                fill_dy<D, DS, true>(dyw, pd.yr, tp, nb, L2, A.d, A.inc_mode, pd.sy, lane);
                 if (has_ain) {
                     const unsigned long long need =
                         ((unsigned long long)ir.prev << 32) | (unsigned)(tp + nb);
@@ -336,7 +326,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     ok = __shfl_sync(kFull, okl, 0);
                     if (ok) {
                         const float* src = A.aseam + ((size_t)slot_in * A.wcols + (tp % A.wcols)) * SA;
-                        for (int idx = lane; idx < nb * SA; idx += 32) ain[idx] = __ldcg(src + idx);
+                        warp_copy_cg<SA>(ain, src, nb * SA, lane);
                         __syncwarp();
                         if (lane == 0)
                             st_release_u64(&A.cons[slot_in],

@@ -56,6 +56,64 @@ __device__ __forceinline__ float inc_ref(const float* z, int64_t v, int d, int e
     return inc_at(z, v / s, d, e, inc_mode) * (1.0f / (float)s);
 }
 
+// The next 32 columns of the swept path's increments into the 64-column
+// shared ring (slot (t0 + col) & 63, row stride DS): column t0 + col, or
+// L2 - 1 - (t0 + col) with REV (the adjoint's reverse sweep), nb <= 32 valid.
+// Every global load of a chunk is issued before its shared stores: a loop
+// that interleaves them waits for each load in turn (the two pointers may
+// alias as far as the compiler knows).
+template <int D, int DS, bool REV>
+__device__ __forceinline__ void fill_dy(float* dyw, const float* z, int t0, int nb, int L2, int d,
+                                        int inc_mode, int s, int lane) {
+    constexpr int CH = D < 8 ? D : 8;  // loads in flight per chunk and lane
+    const float rs = 1.0f / (float)s;
+#pragma unroll
+    for (int q0 = 0; q0 < D; q0 += CH) {
+        float v[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int idx = lane + 32 * (q0 + q);
+            const int col = idx / D, e = idx % D;
+            float x = 0.0f;
+            if (col < nb && e < d) {
+                const int64_t vr = REV ? (int64_t)(L2 - 1 - (t0 + col)) : (int64_t)(t0 + col);
+                const float* p = z + (s == 1 ? vr : vr / s) * d + e;
+                x = inc_mode ? __ldg(p) : __ldg(p + d) - __ldg(p);
+                if (s != 1) x *= rs;
+            }
+            v[q] = x;
+        }
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int idx = lane + 32 * (q0 + q);
+            const int col = idx / D, e = idx % D;
+            dyw[((t0 + col) & 63) * DS + e] = v[q];
+        }
+    }
+}
+
+// dst[i] = src[i] for i < n (n <= 32 * NQ) by a warp, L2-coherent loads
+// (the data was written by other warps), all loads of a chunk before its
+// stores (see fill_dy).
+template <int NQ>
+__device__ __forceinline__ void warp_copy_cg(float* dst, const float* src, int n, int lane) {
+    constexpr int CH = NQ < 8 ? NQ : 8;
+#pragma unroll
+    for (int q0 = 0; q0 < NQ; q0 += CH) {
+        float v[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int i = lane + 32 * (q0 + q);
+            v[q] = (q0 + q < NQ && i < n) ? __ldcg(src + i) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int i = lane + 32 * (q0 + q);
+            if (q0 + q < NQ && i < n) dst[i] = v[q];
+        }
+    }
+}
+
 // CTAs per SM the register allocation must allow (128 threads each): the
 // largest count that ptxas meets without spilling for that instantiation.
 constexpr int fwd_min_blocks(int P, int D, int R) {
@@ -149,12 +207,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
             if ((t & 31) == 0 && t < L2) {
                 // next 32 columns of dy into the ring
                 const int nb = min(32, L2 - t);
-                for (int idx = lane; idx < 32 * D; idx += 32) {
-                    const int col = idx / D, e = idx % D;
-                    float v = 0.0f;
-                    if (col < nb && e < A.d) v = inc_ref(pd.yr, t + col, A.d, e, A.inc_mode, pd.sy);
-                    dyw[((t + col) & 63) * DS + e] = v;
-                }
+                fill_dy<D, DS, false>(dyw, pd.yr, t, nb, L2, A.d, A.inc_mode, pd.sy, lane);
                 if (has_in) {
                     const unsigned long long need =
                         ((unsigned long long)ir.prev << 32) | (unsigned)(t + nb);
@@ -165,7 +218,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                         const float* src =
                             train ? st_pair + ((size_t)(s * R - 1) * L2 + t) * S
                                   : A.seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
-                        for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src + idx);
+                        warp_copy_cg<S>(sin_, src, nb * S, lane);
                         __syncwarp();
                         if (lane == 0 && !train)
                             st_release_u64(&A.cons[slot_in],
