@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     E += 64;
                     bump = 1;
                 }
-                rv[P + 2] = __int_as_float(pack_exp(F, Eb, bump));
+                rv[P + 2] = __int_as_float(pack_exp(F, Eb, bump, bump));
                 r4[kFullGroups] = make_float4(rv[4 * kFullGroups], rv[4 * kFullGroups + 1],
                                               rv[4 * kFullGroups + 2], rv[4 * kFullGroups + 3]);
                 ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
@@ -393,22 +393,29 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
 #pragma unroll
                 for (int q = 1; q <= P; ++q) b[q] = rb[q];
                 b[1] += rb1lo;  // first-order term as one float
-                int F, Eb, bump;
-                unpack_exp(rexp, F, Eb, bump);
-                const int Em = F > Eb ? F : Eb;
-                if (bump) {  // undo the renormalisation after this tile
-                    const float up = 1.8446744e19f, dn = 5.421011e-20f;
+                // exponent handling of this tile (none in the common case)
+                const bool plain = exp_plain(rexp);
+                int F = 0, Eb = 0, Em = 0;
+                if (!plain) {
+                    int abump, bbump;
+                    unpack_exp(rexp, F, Eb, abump, bbump);
+                    Em = F > Eb ? F : Eb;
+                    // undo the renormalisations after this tile
+                    if (abump) {  // of the bottom-edge state
 #pragma unroll
-                    for (int p = 1; p <= P; ++p) { a[p] *= up; Ab[p] *= dn; }
-                    B0 *= dn;
+                        for (int p = 1; p <= P; ++p) { a[p] *= 1.8446744e19f; Ab[p] *= 5.421011e-20f; }
+                    }
+                    if (bbump) {  // of the outgoing right edge
+                        B0 *= 5.421011e-20f;
 #pragma unroll
-                    for (int q = 1; q <= P; ++q) Bb[q] *= dn;
-                }
-                if (F < Em) {  // the incoming edge was scaled to the lane exponent
-                    const float sc = exp2_nonpos(F - Em);
-                    hi *= sc;
+                        for (int q = 1; q <= P; ++q) Bb[q] *= 5.421011e-20f;
+                    }
+                    if (F < Em) {  // the incoming edge was scaled to the lane exponent
+                        const float sc = exp2_nonpos(F - Em);
+                        hi *= sc;
 #pragma unroll
-                    for (int q = 1; q <= P; ++q) b[q] *= sc;
+                        for (int q = 1; q <= P; ++q) b[q] *= sc;
+                    }
                 }
                 const float4* rowp = reinterpret_cast<const float4*>(dyw + (jr & 63) * DS);
                 float dy[D];
@@ -425,19 +432,20 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 tile_inverse_a<P>(c, a, hi, b, NR, ain_, ha);
                 const float cbar = tile_adjoint<P>(c, ain_, hi, b, ha, Ab, B0, Bb, NR);
                 // undo the alignment of this step
-                if (Eb < Em) {
-                    const float dn = exp2_nonpos(Eb - Em), up = exp2_nonneg(Em - Eb);
 #pragma unroll
-                    for (int p = 1; p <= P; ++p) { a[p] = ain_[p] * up; Ab[p] *= dn; }
-                } else {
+                for (int p = 1; p <= P; ++p) a[p] = ain_[p];
+                if (!plain) {
+                    if (Eb < Em) {
+                        const float dn = exp2_nonpos(Eb - Em), up = exp2_nonneg(Em - Eb);
 #pragma unroll
-                    for (int p = 1; p <= P; ++p) a[p] = ain_[p];
-                }
-                if (F < Em) {
-                    const float sc = exp2_nonpos(F - Em);
-                    B0 *= sc;
+                        for (int p = 1; p <= P; ++p) { a[p] *= up; Ab[p] *= dn; }
+                    }
+                    if (F < Em) {
+                        const float sc = exp2_nonpos(F - Em);
+                        B0 *= sc;
 #pragma unroll
-                    for (int q = 1; q <= P; ++q) Bb[q] *= sc;
+                        for (int q = 1; q <= P; ++q) Bb[q] *= sc;
+                    }
                 }
                 const float g = cbar * wsc;
                 // [D][64] layout: the 32 lanes (consecutive columns) hit 32

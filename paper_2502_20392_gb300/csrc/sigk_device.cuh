@@ -315,16 +315,29 @@ __device__ __forceinline__ float exp2_nonneg(int n) {
     return __int_as_float((127 + (n > 127 ? 127 : n)) << 23);
 }
 
-// Exponent word of a tile record: F/64 (15 bits) | E_before/64 (16 bits) |
-// bump.  F is the incoming edge's exponent, E_before the lane's exponent
-// before the tile, bump = 1 when the tile's outputs were rescaled by 2^-64.
-__device__ __forceinline__ int pack_exp(int F, int Eb, int bump) {
-    return ((F >> 6) << 17) | (((Eb >> 6) & 0xFFFF) << 1) | bump;
+// Exponent word of a tile record: bbump (bit 31) | F/64 (14 bits) |
+// E_before/64 (16 bits) | abump (bit 0).  F is the exponent of the tile's
+// incoming left edge, E_before that of the row's bottom-edge state before the
+// tile (both non-negative multiples of 64), abump = 1 when the row's
+// bottom-edge state was rescaled by 2^-64 after the tile, bbump = 1 when the
+// tile's outgoing right edge was.  With one row per lane the two bumps
+// coincide; with several rows per lane only the last row's right edge leaves
+// the lane, and only it is rescaled.
+__device__ __forceinline__ int pack_exp(int F, int Eb, int abump, int bbump) {
+    return (int)(((unsigned)bbump << 31) | ((unsigned)((F >> 6) & 0x3FFF) << 17) |
+                 ((unsigned)((Eb >> 6) & 0xFFFF) << 1) | (unsigned)abump);
 }
-__device__ __forceinline__ void unpack_exp(int w, int& F, int& Eb, int& bump) {
-    bump = w & 1;
-    Eb = ((int)(short)((w >> 1) & 0xFFFF)) * 64;
-    F = (w >> 17) * 64;
+// True when the record's tile needed no exponent handling: the incoming edge
+// had the row's exponent and nothing was rescaled (the common case).
+__device__ __forceinline__ bool exp_plain(int w) {
+    const unsigned u = (unsigned)w;
+    return (u & 0x80000001u) == 0u && ((u >> 17) & 0x3FFFu) == ((u >> 1) & 0xFFFFu);
+}
+__device__ __forceinline__ void unpack_exp(int w, int& F, int& Eb, int& abump, int& bbump) {
+    abump = w & 1;
+    bbump = (int)((unsigned)w >> 31);
+    Eb = (int)(((unsigned)w >> 1) & 0xFFFF) * 64;
+    F = (int)(((unsigned)w >> 17) & 0x3FFF) * 64;
 }
 
 // ---------------------------------------------------------------------------

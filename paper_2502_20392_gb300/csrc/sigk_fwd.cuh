@@ -116,12 +116,14 @@ __device__ __forceinline__ void warp_copy_cg(float* dst, const float* src, int n
 
 // CTAs per SM the register allocation must allow (128 threads each): the
 // largest count that ptxas meets without spilling for that instantiation.
-constexpr int fwd_min_blocks(int P, int D, int R) {
-    return R == 1 ? ((P >= 14 && D >= 16) ? 3 : 4) : (R == 2 ? (P <= 8 ? 4 : 3) : (P <= 4 ? 4 : 3));
+constexpr int fwd_min_blocks(int P, int D, int R, bool REC) {
+    return REC ? (R == 1 && !(P >= 14 && D >= 16) ? 4 : 3)
+               : (R == 1 ? 4 : (R == 2 ? (P <= 8 ? 4 : 3) : (P <= 4 ? 4 : 3)));
 }
 
-template <int P, int D, int R, int NR>
-__global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(SolverArgs A) {
+// REC: training forward that also stores every tile's record (SolverArgs::rec).
+template <int P, int D, int R, int NR, bool REC = false>
+__global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(SolverArgs A) {
     constexpr int S = P + 4;
     constexpr int DS = DyStride<D>::value;
     constexpr int RS = rec_floats(P);
@@ -167,10 +169,10 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
         const bool mid_writer = train && R > 1 && lane != 31 && ((lane + 1) * R) % 32 == 0 &&
                                 s * R + mid_m < n32;
         float* mid_dst = mid_writer ? st_pair + (size_t)(s * R + mid_m - 1) * L2 * S : nullptr;
-        // stored tile records (training, one row per lane): this strip's blocks
+        // stored tile records: the blocks of the item's first 32-row strip
+        // (row lane*R + k lies in strip s*R + (lane*R + k) / 32)
         float* rec_item = nullptr;
-        if constexpr (R == 1)
-            if (A.rec) rec_item = A.rec + A.rec_off[lo_p] + (int64_t)s * (L2 + 32) * 32 * RS;
+        if constexpr (REC) rec_item = A.rec + A.rec_off[lo_p] + (int64_t)(s * R) * (L2 + 32) * 32 * RS;
         bool ok = true;
 
         // row increments of this lane (zero past the end of the path)
@@ -254,13 +256,21 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
             }
             const int j = t - lane;
             if (j >= 0 && j < L2) {
-                // record of the incoming left edge, before alignment (the
-                // adjoint rebuilds the tile's inputs from it)
-                float4* r4 = nullptr;
-                float rtail[4];
+                // records of the rows' incoming left edges (the adjoint rebuilds
+                // each tile's inputs from them): row k = 0 as received, before
+                // the alignment; row k > 0 the previous row's outgoing edge.
+                // The first groups are stored before the tile, the group with
+                // the exponent word after the step's renormalisation.
+                float4* r4[R];
+                float rtail[R][4];
+                int Frec[R];
                 const int Eb = E;
-                if constexpr (R == 1) {
-                    if (rec_item) {
+                auto rec_head = [&](int k, int Fv) {
+                    const int rw = lane * R + k;
+                    const int m = rw >> 5, rr = rw & 31;
+                    r4[k] = nullptr;
+                    Frec[k] = Fv;
+                    if (s * R + m < n32) {
                         float rv[RS];
                         rv[0] = hi;
                         rv[1] = b1lo;
@@ -268,14 +278,16 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                         for (int q = 1; q <= P; ++q) rv[1 + q] = b[q];
 #pragma unroll
                         for (int q = P + 2; q < RS; ++q) rv[q] = 0.0f;
-                        r4 = reinterpret_cast<float4*>(rec_item + ((size_t)t * 32 + lane) * RS);
+                        r4[k] = reinterpret_cast<float4*>(
+                            rec_item + (int64_t)m * (L2 + 32) * 32 * RS + ((int64_t)(j + rr) * 32 + rr) * RS);
 #pragma unroll
                         for (int g = 0; g < kFullGroups; ++g)
-                            r4[g] = make_float4(rv[4 * g], rv[4 * g + 1], rv[4 * g + 2], rv[4 * g + 3]);
+                            r4[k][g] = make_float4(rv[4 * g], rv[4 * g + 1], rv[4 * g + 2], rv[4 * g + 3]);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) rtail[q] = rv[4 * kFullGroups + q];
+                        for (int q = 0; q < 4; ++q) rtail[k][q] = rv[4 * kFullGroups + q];
                     }
-                }
+                };
+                if constexpr (REC) rec_head(0, F);
                 // align exponents of the incoming edge and the lane's states
                 if (F != E) {
                     if (F > E) {
@@ -304,6 +316,8 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                 }
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
+                    if constexpr (REC)
+                        if (k > 0) rec_head(k, E);
                     float c = 0.0f;
 #pragma unroll
                     for (int e = 0; e < D; ++e) c = fmaf(dx[k][e], dy[e], c);
@@ -325,10 +339,15 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                     for (int q = 1; q <= P; ++q) b[q] *= sc;
                     E += 64;
                 }
-                if constexpr (R == 1) {
-                    if (rec_item) {
-                        rtail[P + 2 - 4 * kFullGroups] = __int_as_float(pack_exp(F, Eb, bump));
-                        r4[kFullGroups] = make_float4(rtail[0], rtail[1], rtail[2], rtail[3]);
+                if constexpr (REC) {
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        if (r4[k]) {
+                            // only the last row's outgoing edge leaves the lane
+                            rtail[k][P + 2 - 4 * kFullGroups] =
+                                __int_as_float(pack_exp(Frec[k], Eb, bump, k == R - 1 ? bump : 0));
+                            r4[k][kFullGroups] = make_float4(rtail[k][0], rtail[k][1], rtail[k][2], rtail[k][3]);
+                        }
                     }
                 }
                 ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
@@ -392,20 +411,28 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R)) fwd_kernel(Solve
                 __syncwarp();
             }
         }
-        // stored records: each lane's bottom-edge state after the last column
-        // (where the adjoint's reverse sweep starts)
-        if constexpr (R == 1) {
-            if (rec_item && ok) {
-                float fv[RS];
-                fv[0] = a1lo[0];
+        // stored records: each row's bottom-edge state after the last column
+        // (where the adjoint's reverse sweep starts), block L2 + 31 of its strip
+        if constexpr (REC) {
+            if (ok) {
 #pragma unroll
-                for (int p = 1; p <= P; ++p) fv[p] = a[0][p];
+                for (int k = 0; k < R; ++k) {
+                    const int rw = lane * R + k;
+                    const int m = rw >> 5, rr = rw & 31;
+                    if (s * R + m < n32) {
+                        float fv[RS];
+                        fv[0] = a1lo[k];
 #pragma unroll
-                for (int q = P + 1; q < RS; ++q) fv[q] = 0.0f;
-                float4* f4 = reinterpret_cast<float4*>(rec_item + ((size_t)(L2 + 31) * 32 + lane) * RS);
+                        for (int p = 1; p <= P; ++p) fv[p] = a[k][p];
 #pragma unroll
-                for (int g = 0; g < RS / 4; ++g)
-                    f4[g] = make_float4(fv[4 * g], fv[4 * g + 1], fv[4 * g + 2], fv[4 * g + 3]);
+                        for (int q = P + 1; q < RS; ++q) fv[q] = 0.0f;
+                        float4* f4 = reinterpret_cast<float4*>(
+                            rec_item + (int64_t)m * (L2 + 32) * 32 * RS + ((int64_t)(L2 + 31) * 32 + rr) * RS);
+#pragma unroll
+                        for (int g = 0; g < RS / 4; ++g)
+                            f4[g] = make_float4(fv[4 * g], fv[4 * g + 1], fv[4 * g + 2], fv[4 * g + 3]);
+                    }
+                }
             }
         }
         __syncwarp();

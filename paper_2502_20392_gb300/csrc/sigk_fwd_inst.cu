@@ -1,8 +1,8 @@
 // sigk_fwd_inst.cu -- instantiates, for one edge degree P and ring count NR
 // (compiled once per pair with -DSIGK_P=<P> -DSIGK_NR=<NR>) and D in
 // {4, 8, 16}: the forward solver (inference, and training with every 32-row
-// seam stored; with one row per lane also every tile's record) and the
-// backward (adjoint) kernel; and the two-phase solver in FP32 and FP64.
+// seam stored, with or without every tile's record) and the backward
+// (adjoint) kernel; and the two-phase solver in FP32 and FP64.
 #include "sigk_bwd.cuh"
 #include "sigk_fwd.cuh"
 #include "sigk_fwd_cm.cuh"
@@ -32,16 +32,16 @@ static int occupancy(K kern, int threads, int smem, int R, KernelInfo* info) {
     return 0;
 }
 
-template <int D, int R>
+template <int D, int R, bool REC>
 static int fwd_info_impl(KernelInfo* info) {
     const int smem = 4 * FwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
-    return occupancy(fwd_kernel<SIGK_P, D, R, SIGK_NR>, 128, smem, R, info);
+    return occupancy(fwd_kernel<SIGK_P, D, R, SIGK_NR, REC>, 128, smem, R, info);
 }
 
-template <int D, int R>
+template <int D, int R, bool REC>
 static cudaError_t fwd_launch_impl(const SolverArgs& a, int grid, cudaStream_t s) {
     const int smem = 4 * FwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
-    auto kern = fwd_kernel<SIGK_P, D, R, SIGK_NR>;
+    auto kern = fwd_kernel<SIGK_P, D, R, SIGK_NR, REC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 128, smem, s>>>(a);
@@ -86,27 +86,39 @@ static cudaError_t fwd_cm_launch_impl(const SolverArgs& a, void* cscratch, int64
 constexpr int kR4 = rows_per_lane(SIGK_P, 4);
 constexpr int kR8 = rows_per_lane(SIGK_P, 8);
 constexpr int kR16 = rows_per_lane(SIGK_P, 16);
+constexpr int kQ4 = rec_rows_per_lane(SIGK_P, 4);
+constexpr int kQ8 = rec_rows_per_lane(SIGK_P, 8);
+constexpr int kQ16 = rec_rows_per_lane(SIGK_P, 16);
 
-// R = 0: rows_per_lane(P, D) rows per lane; R = 1: one row per lane (the
-// training forward that stores every tile's record for the adjoint)
+// variant 0: inference, or training with the strip seams stored
+// (rows_per_lane(P, D) rows per lane); variant 1: training that also stores
+// every tile's record for the adjoint (rec_rows_per_lane(P, D) rows).
 template <>
-int fwd_info<SIGK_P, SIGK_NR>(int D, int R, KernelInfo* info) {
-    if (R != 0 && R != 1) return -1;
+int fwd_info<SIGK_P, SIGK_NR>(int D, int variant, KernelInfo* info) {
+    if (variant != 0 && variant != 1) return -1;
     switch (D) {
-        case 4: return R ? fwd_info_impl<4, 1>(info) : fwd_info_impl<4, kR4>(info);
-        case 8: return R ? fwd_info_impl<8, 1>(info) : fwd_info_impl<8, kR8>(info);
-        case 16: return R ? fwd_info_impl<16, 1>(info) : fwd_info_impl<16, kR16>(info);
+        case 4: return variant ? fwd_info_impl<4, kQ4, true>(info) : fwd_info_impl<4, kR4, false>(info);
+        case 8: return variant ? fwd_info_impl<8, kQ8, true>(info) : fwd_info_impl<8, kR8, false>(info);
+        case 16:
+            return variant ? fwd_info_impl<16, kQ16, true>(info) : fwd_info_impl<16, kR16, false>(info);
         default: return -1;
     }
 }
 
 template <>
-cudaError_t fwd_launch<SIGK_P, SIGK_NR>(int D, int R, const SolverArgs& a, int grid, cudaStream_t s) {
-    if (R != 0 && R != 1) return cudaErrorInvalidValue;
+cudaError_t fwd_launch<SIGK_P, SIGK_NR>(int D, int variant, const SolverArgs& a, int grid,
+                                        cudaStream_t s) {
+    if (variant != 0 && variant != 1) return cudaErrorInvalidValue;
     switch (D) {
-        case 4: return R ? fwd_launch_impl<4, 1>(a, grid, s) : fwd_launch_impl<4, kR4>(a, grid, s);
-        case 8: return R ? fwd_launch_impl<8, 1>(a, grid, s) : fwd_launch_impl<8, kR8>(a, grid, s);
-        case 16: return R ? fwd_launch_impl<16, 1>(a, grid, s) : fwd_launch_impl<16, kR16>(a, grid, s);
+        case 4:
+            return variant ? fwd_launch_impl<4, kQ4, true>(a, grid, s)
+                           : fwd_launch_impl<4, kR4, false>(a, grid, s);
+        case 8:
+            return variant ? fwd_launch_impl<8, kQ8, true>(a, grid, s)
+                           : fwd_launch_impl<8, kR8, false>(a, grid, s);
+        case 16:
+            return variant ? fwd_launch_impl<16, kQ16, true>(a, grid, s)
+                           : fwd_launch_impl<16, kR16, false>(a, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -16,17 +16,24 @@ struct KernelInfo {
 // Rows per lane as a function of (P, D): fewer rows when the register
 // footprint (R*(P + D) state floats) would push occupancy too low.
 constexpr int rows_per_lane(int P, int D) { return (P + D) <= 16 ? 4 : 2; }
+// The same for the training forward that stores the tile records: one row
+// per lane, so that a step's 32 records are one contiguous block (with two
+// rows per lane every lane writes to other blocks, and the scattered 48-byte
+// stores made the Gram B=64, L=1024, d=16, P=8 training forward 63 ms
+// instead of 30 ms on GB300).  The kernel supports any R.
+constexpr int rec_rows_per_lane(int, int) { return 1; }
 
 // Entry points of the kernel translation units, one unit per (edge degree P,
 // ring count NR); NR is a compile-time constant of every solver kernel, so
 // the truncated ring sums carry no run-time predicates.
 //
-// R = 0: the rows-per-lane count rows_per_lane(P, D); training uses it too
-// and stores the seam after every 32-row strip.  R = 1: one row per lane, the
-// training forward that also stores every tile's record for the adjoint.
-template <int P, int NR> int fwd_info(int D, int R, KernelInfo* info);
+// variant 0: inference, or training (SolverArgs::store set: the seam after
+// every 32-row strip is stored), rows_per_lane(P, D) rows per lane; variant
+// 1: training that also stores every tile's record for the adjoint,
+// rec_rows_per_lane(P, D) rows per lane.
+template <int P, int NR> int fwd_info(int D, int variant, KernelInfo* info);
 template <int P, int NR>
-cudaError_t fwd_launch(int D, int R, const SolverArgs& a, int grid, cudaStream_t s);
+cudaError_t fwd_launch(int D, int variant, const SolverArgs& a, int grid, cudaStream_t s);
 
 // Two-phase kernel (strip coefficients first, then the sweep): d > 16 in
 // FP32, or any d in FP64 (f64 = true).  cscratch holds float or double strips.
