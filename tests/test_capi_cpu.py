@@ -40,6 +40,22 @@ def test_version_and_errors_without_gpu(lib):
     assert b"NULL" in lib.sigk_last_error() or b"null" in lib.sigk_last_error()
 
 
+def test_training_calls_validate_without_gpu(lib):
+    # the split training entry points reject bad arguments on the host
+    from paper_2502_20392_gb300 import sigk
+    o = sigk.Opts().c()
+    assert lib.sigk_adjoint(7, 4, 4, 4, None, None, None, None, 0, None, ctypes.byref(o)) == -1
+    assert lib.sigk_adjoint(0, 4, 4, 4, None, None, None, None, 0, None, ctypes.byref(o)) == -1
+    assert b"grad_out" in lib.sigk_last_error()
+    assert lib.sigk_forward_train(9, None, None, 4, None, None, 4, 4, None, None, 0, None,
+                                  ctypes.byref(o)) == -1
+    # a Gram training forward needs X
+    assert lib.sigk_forward_train(1, None, None, 4, None, None, 0, 4, None, None, 0, None,
+                                  ctypes.byref(o)) == -1
+    bad = sigk.Opts(order=99).c()
+    assert lib.sigk_backward_workspace_size(1, 4, 0, 4, ctypes.byref(bad)) == 0
+
+
 def test_no_cpu_fallback_in_product_path():
     # the product package must not import the oracle
     pkg = os.path.join(ROOT, "paper_2502_20392_gb300")
