@@ -197,9 +197,10 @@ sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t 
  * from that state: same op, n_x, n_y (0 for a Gram of X with itself), d and
  * opts; ws, ws_bytes (sigk_backward_workspace_size), X, Y and their lengths
  * unchanged since the forward.  grad_out, grad_X, grad_Y as in sigk_backward
- * (gradients are overwritten).  sigk_adjoint may run again on the same state
- * with another grad_out.  Errors on the device are reported by
- * sigk_sync_status. */
+ * (gradients are overwritten).  sigk_adjoint reads what the forward wrote
+ * on the device: give it the same stream, or one ordered after the forward.
+ * It may run again on the same state with another grad_out.  Errors on the
+ * device are reported by sigk_sync_status. */
 sigk_status sigk_forward_train(int op, const float* X, const int64_t* len_x, int64_t n_x,
                                const float* Y, const int64_t* len_y, int64_t n_y, int d,
                                double* value_out, void* ws, size_t ws_bytes, void* stream,
