@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     float* rbuf1 = sin_ + BwdSmem<P, D>::RB;            // second record block
     float* ain = rbuf1 + BwdSmem<P, D>::RB;             // adjoint seam-in block
     float* aout = ain + 32 * SA;                        // adjoint seam-out block
-    float* colacc = aout + 32 * SA;                     // column gradient [D][64]
+    float* colacc = aout + 32 * SA;  // column gradient, float4 [D/4][64]: (e, col) at ((e/4)*64+col)*4 + e%4
     uint64_t* bars = reinterpret_cast<uint64_t*>(colacc + 64 * D);  // record-load mbarriers
     float* rec = A.rec + (size_t)gwarp * A.rec_stride;
     const int n_items = A.sched.hdr[2];
@@ -448,14 +448,20 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     }
                 }
                 const float g = cbar * wsc;
-                // [D][64] layout: the 32 lanes (consecutive columns) hit 32
-                // consecutive words, free of bank conflicts
-                float* ca = colacc + (jr & 63);
+                // float4 [D/4][64] layout: the 32 lanes (consecutive columns)
+                // read and write 512 contiguous bytes, free of bank conflicts
+                float4* ca = reinterpret_cast<float4*>(colacc) + (jr & 63);
 #pragma unroll
-                for (int e = 0; e < D; ++e) {
-                    gx[e] = fmaf(g, dy[e], gx[e]);
-                    ca[e * 64] = fmaf(g, dx[e], ca[e * 64]);
+                for (int e4 = 0; e4 < D / 4; ++e4) {
+                    float4 v = ca[e4 * 64];
+                    v.x = fmaf(g, dx[4 * e4 + 0], v.x);
+                    v.y = fmaf(g, dx[4 * e4 + 1], v.y);
+                    v.z = fmaf(g, dx[4 * e4 + 2], v.z);
+                    v.w = fmaf(g, dx[4 * e4 + 3], v.w);
+                    ca[e4 * 64] = v;
                 }
+#pragma unroll
+                for (int e = 0; e < D; ++e) gx[e] = fmaf(g, dy[e], gx[e]);
                 oB0 = B0;
 #pragma unroll
                 for (int q = 1; q <= P; ++q) oBb[q] = Bb[q];
@@ -474,9 +480,10 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 const int start = jj & ~31;
                 const int nb = jj - start + 1;
                 if (pd.gyr) {
+                    // dimension fastest: a warp's atomics hit whole rows of dL/dy
                     for (int idx = lane; idx < nb * D; idx += 32) {
-                        const int col = idx % nb, e = idx / nb;
-                        float* cell = colacc + e * 64 + ((start + col) & 63);
+                        const int col = idx / D, e = idx % D;
+                        float* cell = colacc + ((e >> 2) * 64 + ((start + col) & 63)) * 4 + (e & 3);
                         const float v = *cell;
                         *cell = 0.0f;
                         if (e < A.d && v != 0.0f) {
@@ -492,7 +499,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     }
                 } else {
                     for (int idx = lane; idx < nb * D; idx += 32)
-                        colacc[(idx / nb) * 64 + ((start + idx % nb) & 63)] = 0.0f;
+                        colacc[(((idx / nb) >> 2) * 64 + ((start + idx % nb) & 63)) * 4 + ((idx / nb) & 3)] = 0.0f;
                 }
                 if (has_aout) {
                     if (start + nb > A.wcols) {
