@@ -62,7 +62,7 @@ struct BwdSmem {
     static constexpr int S = P + 4;   // forward seam entry
     static constexpr int RS = rec_floats(P);  // record per lane
     static constexpr int RB = 32 * (S > RS ? S : RS);  // one record block / seam-in block
-    static constexpr int SA = P + 1;  // adjoint seam entry: corner, b1..bP
+    static constexpr int SA = adj_seam_floats(P);  // adjoint seam entry: corner, b1..bP (padded)
     static constexpr int DS = DyStride<D>::value;
     // dy ring, two record blocks (the first doubles as pass A's seam-in
     // block), adjoint seam in/out blocks, column gradients, two mbarriers
@@ -96,7 +96,7 @@ constexpr int bwd_min_blocks(int P, int D) { return (P <= 8 && D <= 8) ? 4 : 3; 
 template <int P, int D, int NR>
 __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs A) {
     constexpr int S = P + 4;
-    constexpr int SA = P + 1;
+    constexpr int SA = adj_seam_floats(P);
     constexpr int DS = DyStride<D>::value;
     extern __shared__ float4 smem_f4[];
     float* smem = reinterpret_cast<float*>(smem_f4);
@@ -375,9 +375,21 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
             if (lane == 31) {
                 if (has_ain && tp < L2) {
                     const float* e_ = ain + (tp & 31) * SA;
-                    B0 = e_[0];
+                    if constexpr (SA % 4 == 0) {
+                        float v[SA];
 #pragma unroll
-                    for (int q = 1; q <= P; ++q) Bb[q] = e_[q];
+                        for (int g4 = 0; g4 < SA / 4; ++g4) {
+                            const float4 w = reinterpret_cast<const float4*>(e_)[g4];
+                            v[4 * g4] = w.x; v[4 * g4 + 1] = w.y; v[4 * g4 + 2] = w.z; v[4 * g4 + 3] = w.w;
+                        }
+                        B0 = v[0];
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) Bb[q] = v[q];
+                    } else {
+                        B0 = e_[0];
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) Bb[q] = e_[q];
+                    }
                 } else {
                     const bool seed = last_strip && tp == 0;  // k = b0 + sum_q bh_q / q!
                     B0 = seed ? 1.0f : 0.0f;
@@ -467,9 +479,22 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 for (int q = 1; q <= P; ++q) oBb[q] = Bb[q];
                 if (lane == 0 && has_aout) {
                     float* e_ = aout + (jr & 31) * SA;
-                    e_[0] = B0;
+                    if constexpr (SA % 4 == 0) {
+                        float v[SA];
+                        v[0] = B0;
 #pragma unroll
-                    for (int q = 1; q <= P; ++q) e_[q] = Bb[q];
+                        for (int q = 1; q <= P; ++q) v[q] = Bb[q];
+#pragma unroll
+                        for (int q = P + 1; q < SA; ++q) v[q] = 0.0f;
+#pragma unroll
+                        for (int g4 = 0; g4 < SA / 4; ++g4)
+                            reinterpret_cast<float4*>(e_)[g4] =
+                                make_float4(v[4 * g4], v[4 * g4 + 1], v[4 * g4 + 2], v[4 * g4 + 3]);
+                    } else {
+                        e_[0] = B0;
+#pragma unroll
+                        for (int q = 1; q <= P; ++q) e_[q] = Bb[q];
+                    }
                 }
                 tiles += has_row ? 1ull : 0ull;
             }

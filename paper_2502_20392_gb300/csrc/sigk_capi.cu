@@ -308,7 +308,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         L->bnwarps = L->bgrid * (L->binfo.threads / 32);
         const int64_t bnslot_sm = L->n_pairs + L->bnwarps + 64;
         L->strip_major = allow_sm && bnslot_sm <= (int64_t)INT32_MAX / 2 &&
-                         (double)bnslot_sm * (double)wfull * (double)(o.order + 1) * 4.0 <=
+                         (double)bnslot_sm * (double)wfull * (double)adj_seam_floats(o.order) * 4.0 <=
                              kStripMajorBudget;
         L->bnslot = L->strip_major ? (int)bnslot_sm : L->bnwarps + 64;
         int64_t bw = 2 * o.max_len / L->bnwarps + 64;
@@ -334,7 +334,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         L->bcons = off; off = align256(off + sizeof(unsigned long long) * (size_t)L->bnslot);
         L->bdone = off; off = align256(off + sizeof(long long) * (size_t)L->bnslot);
         L->aseam = off;
-        off = align256(off + sizeof(float) * (size_t)L->bnslot * L->bwcols * (o.order + 1));
+        off = align256(off + sizeof(float) * (size_t)L->bnslot * L->bwcols * adj_seam_floats(o.order));
     }
     L->total = off;
     return SIGK_OK;

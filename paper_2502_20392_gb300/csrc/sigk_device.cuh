@@ -98,6 +98,11 @@ struct ItemRef {
 // a lane's record moves as 16-byte vectors.
 __host__ __device__ constexpr int rec_floats(int P) { return (P + 3 + 3) / 4 * 4; }
 
+// Floats per column of the adjoint seam (corner adjoint, b1..bP adjoints):
+// padded to a multiple of 4 (128-bit shared loads and stores) up to P = 12;
+// at P >= 14 the padding would cost the adjoint its third CTA per SM.
+__host__ __device__ constexpr int adj_seam_floats(int P) { return P <= 12 ? (P + 4) / 4 * 4 : P + 1; }
+
 // Largest i in [0, n) with v[i] <= x (v non-decreasing, v[0] <= x).
 __device__ __forceinline__ int upper_index(const int32_t* v, int n, int x) {
     int lo = 0, hi = n - 1;
