@@ -10,8 +10,8 @@
 // (a record of P+3 floats) in a per-warp scratch area; it ends with each
 // lane's bottom-edge state after the last column in registers.  When the
 // records of every tile fit the device memory budget, the training forward
-// (one row per lane, the same arithmetic) writes them once for all strips,
-// with each lane's final state, and pass A is skipped.
+// (the same arithmetic) writes them once for all strips, with each row's
+// final state, and pass A is skipped.
 //
 // Pass B sweeps the columns in reverse with the mirrored skew (lane 31 first).
 // At each tile it rebuilds the tile's bottom-edge input by inverting the
@@ -42,10 +42,11 @@ struct BwdArgs {
     const double* pair_w;        // [n_pairs] upstream weight of each pair
     float* rec;                  // per-warp records (replay)
     int64_t rec_stride;          // floats per warp
-    // records stored by the training forward (SolverArgs::rec layout); with
-    // rec_off != nullptr pass A is skipped
+    // records stored by the training forward (SolverArgs::rec layout, items
+    // of rec_rows strips); with rec_off != nullptr pass A is skipped
     const float* rec_store;
     const int64_t* rec_off;
+    int32_t rec_rows;
     int32_t nslot;               // adjoint seam ring
     int32_t wcols;
     float* aseam;
@@ -65,8 +66,9 @@ struct BwdSmem {
     static constexpr int SA = adj_seam_floats(P);  // adjoint seam entry: corner, b1..bP (padded)
     static constexpr int DS = DyStride<D>::value;
     // dy ring, two record blocks (the first doubles as pass A's seam-in
-    // block), adjoint seam in/out blocks, column gradients, two mbarriers
-    static constexpr int per_warp = 64 * DS + 2 * RB + 2 * 32 * SA + 64 * D + 4;
+    // block), adjoint seam in/out blocks, column gradients (every part a
+    // multiple of 4 floats: 16-byte aligned)
+    static constexpr int per_warp = 64 * DS + 2 * RB + 2 * 32 * SA + 64 * D;
 };
 
 // gradient v of virtual row `vrow` (refinement s) -> its segment vrow / s
@@ -110,21 +112,12 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     float* ain = rbuf1 + BwdSmem<P, D>::RB;             // adjoint seam-in block
     float* aout = ain + 32 * SA;                        // adjoint seam-out block
     float* colacc = aout + 32 * SA;  // column gradient, float4 [D/4][64]: (e, col) at ((e/4)*64+col)*4 + e%4
-    uint64_t* bars = reinterpret_cast<uint64_t*>(colacc + 64 * D);  // record-load mbarriers
     float* rec = A.rec + (size_t)gwarp * A.rec_stride;
     const int n_items = A.sched.hdr[2];
     unsigned long long tiles = 0, replayed = 0;
-    // pass B reads the record block of one pass-A step per step, prefetched
-    // two steps ahead by bulk copies into sin_ / rbuf1 (load n uses buffer
-    // n & 1, barrier phase (n >> 1) & 1; n counts this warp's loads)
-    if (lane == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-    unsigned nld = 0;
-    constexpr uint32_t kRecBytes = 32 * RS * (uint32_t)sizeof(float);
+    // pass B reads every lane's record of one step per step, prefetched two
+    // steps ahead by each lane with cp.async into its slot of sin_ / rbuf1
+    // (step tp uses buffer tp & 1)
     // record fields: [0] hi, [1] b1lo, [1 + q] b_q, [P + 2] exponent word;
     // groups of four wholly before the exponent are stored at the start of
     // the step, the last group (with the exponent) at its end
@@ -162,13 +155,18 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         for (int q = 0; q <= P; ++q) ob[q] = 0.0f;
         int oE = 0;
         const int T = L2 + 31;
-        // records stored by the training forward: no replay, the lane's final
-        // bottom-edge state is the strip's last block
+        // records stored by the training forward (no replay) in regions of
+        // items of RR strips: this lane's row is row rw of item s / RR, its
+        // record for column j in block j + rw / RR; the final bottom-edge
+        // state is block L2 + 31.  Replayed records: the one-row layout of the
+        // warp's scratch.
         const bool stored = A.rec_off != nullptr;
-        const float* rsrc = stored ? A.rec_store + A.rec_off[lo_p] + (int64_t)s * (L2 + 32) * 32 * RS
-                                   : rec;
+        const int RR = stored ? A.rec_rows : 1;
+        const int rw = (s % RR) * 32 + lane;
+        const float* rbase = stored ? A.rec_store + A.rec_off[lo_p] + (int64_t)(s / RR) * (L2 + 32) * 32 * RR * RS
+                                    : rec;
         if (stored) {
-            const float4* f4 = reinterpret_cast<const float4*>(rsrc + ((size_t)T * 32 + lane) * RS);
+            const float4* f4 = reinterpret_cast<const float4*>(rbase + ((int64_t)T * 32 * RR + rw) * RS);
             float fv[RS];
 #pragma unroll
             for (int g = 0; g < RS / 4; ++g) {
@@ -296,22 +294,26 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
 #pragma unroll
         for (int q = 0; q <= P; ++q) oBb[q] = 0.0f;
         const int lp = 31 - lane;
-        // the records were written with generic stores: order them (and pass
-        // A's use of sin_) before the bulk copies read them
-        fence_proxy_async_global();
-        fence_proxy_async_smem();
+        // pass A's records and its use of sin_ come before pass B's copies
+        __threadfence_block();
         __syncwarp();
-        const unsigned base = nld;
-        unsigned issued = 0, waited = 0;
-        auto rbuf = [&](unsigned n) { return (n & 1) ? rbuf1 : sin_; };
-        // pass-A step of reverse step tp: every active lane reads t = L2 + 30 - tp
-        auto rec_block = [&](int tp) { return rsrc + (size_t)(L2 + 30 - tp) * RS * 32; };
+        auto rbuf = [&](int tpp) { return (tpp & 1) ? rbuf1 : sin_; };
+        // the record of reverse step tpp, if this lane has a tile there (column
+        // j = L2 + 30 - tpp - lane), into its slot of the step's buffer; one
+        // commit group per step
+        auto rec_fetch = [&](int tpp) {
+            const int j = L2 + 30 - tpp - lane;
+            if (j >= 0 && j < L2) {
+                const float* src = rbase + ((int64_t)(j + rw / RR) * 32 * RR + rw) * RS;
+                float* dst = rbuf(tpp) + lane * RS;
+#pragma unroll
+                for (int g = 0; g < RS / 4; ++g) cp_async16(dst + 4 * g, src + 4 * g);
+            }
+            cp_async_commit();
+        };
         if (ok) {
-            const unsigned first = T < 2 ? (unsigned)T : 2u;
-            if (lane == 0)
-                for (unsigned q = 0; q < first; ++q)
-                    bulk_load(rbuf(base + q), rec_block((int)q), kRecBytes, &bars[(base + q) & 1]);
-            issued = first;
+            rec_fetch(0);
+            rec_fetch(1);
         }
         for (int tp = 0; tp < T && ok; ++tp) {
             if ((tp & 31) == 0 && tp < L2) {
@@ -336,18 +338,12 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 __syncwarp();
                 if (!ok) break;
             }
-            // this step's record block
+            // this step's record (groups in flight: this step's and the next)
             float rhi, rb[P + 1], rb1lo;
             int rexp;
             {
-                const unsigned n = base + (unsigned)tp;
-                const bool got = mbar_wait(&bars[n & 1], (n >> 1) & 1, A.status);
-                waited = (unsigned)tp + 1;
-                if (!__all_sync(kFull, got)) {
-                    ok = false;
-                    break;
-                }
-                const float4* r4 = reinterpret_cast<const float4*>(rbuf(n) + lane * RS);
+                cp_async_wait<1>();
+                const float4* r4 = reinterpret_cast<const float4*>(rbuf(tp) + lane * RS);
                 float rv[RS];
 #pragma unroll
                 for (int g = 0; g < RS / 4; ++g) {
@@ -360,11 +356,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
 #pragma unroll
                 for (int q = 1; q <= P; ++q) rb[q] = rv[1 + q];
                 rexp = __float_as_int(rv[P + 2]);
-                __syncwarp();
-                if (tp + 2 < T) {
-                    if (lane == 0) bulk_load(rbuf(n + 2), rec_block(tp + 2), kRecBytes, &bars[n & 1]);
-                    issued = (unsigned)tp + 3;
-                }
+                rec_fetch(tp + 2);  // into the buffer just read (an empty group past the end)
             }
             // adjoint of the right edge: from lane+1, or seam / seed for lane 31
             float B0 = __shfl_down_sync(kFull, oB0, 1);
@@ -547,13 +539,9 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 __syncwarp();
             }
         }
-        // record loads still in flight after an early exit: wait for them so
-        // the barrier phases and buffers stay consistent
-        for (unsigned q = waited; q < issued; ++q) {
-            const unsigned n = base + q;
-            mbar_wait(&bars[n & 1], (n >> 1) & 1, A.status);
-        }
-        nld = base + issued;
+        // record copies still in flight (the last steps', or after an early
+        // exit) complete before the buffers are used again
+        cp_async_wait<0>();
         __syncwarp();
         if (has_row) add_inc_grad<D>(pd.gxr, row, A.d, A.inc_mode, pd.sx, gx);
         __syncwarp();

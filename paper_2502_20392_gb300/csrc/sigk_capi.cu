@@ -157,6 +157,7 @@ struct Layout {
     size_t store, store_off, pair_exp, pair_w, rec, bprod, bcons, bdone, aseam;
     int64_t store_floats, rec_stride;
     bool stored_rec;     // the training forward stores every tile's record
+    int rec_rows;        // its rows per lane (records are grouped per item of that many strips)
     size_t rstore, rec_off;
     int64_t rstore_floats;
     int bnslot, bwcols, bgrid, bnwarps;
@@ -214,12 +215,17 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     // stored tile records: (pair, 32-row strip) x (max_len + 32) blocks of
     // 32 records; the training forward then runs with one row per lane
     L->stored_rec = false;
+    L->rec_rows = 1;
     L->rstore_floats = 0;
     if (train && !(o.flags & SIGK_FLAG_REPLAY)) {
-        const double fl = (double)pair_count(op, n_x, n_y, o.flags) * (double)((o.max_len + 31) / 32) *
-                          (double)(o.max_len + 32) * 32.0 * (double)rec_floats(o.order);
+        // (pair, item of R strips) x (max_len + 32) blocks of 32 R records
+        const int R = rec_rows_per_lane(o.order, D);
+        const int64_t items = ((o.max_len + 31) / 32 + R - 1) / R;
+        const double fl = (double)pair_count(op, n_x, n_y, o.flags) * (double)items *
+                          (double)(o.max_len + 32) * 32.0 * R * (double)rec_floats(o.order);
         if (fl * sizeof(float) <= kRecordBudget) {
             L->stored_rec = true;
+            L->rec_rows = R;
             L->rstore_floats = (int64_t)fl;
         }
     }
@@ -401,7 +407,8 @@ struct PlanArgs {
     int64_t* store_off;
     int64_t* rec_off;   // stored tile records: per-pair offsets (null: replay)
     int64_t rec_cap;    // floats available for them
-    int rec_block;      // floats per block (32 records)
+    int rec_rows;       // rows per lane of the forward that writes them
+    int rec_block;      // floats per block (32 * rec_rows records)
     double* pair_w;
     const double* grad_out;
     float* gX;
@@ -761,11 +768,12 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
     pair_offsets(A, sh, A.store_off, A.store_cap, [&](const PairDesc& q) -> int64_t {
         return q.n_strips > 1 ? (int64_t)(q.n_strips - 1) * q.L2 * A.stride : 0;
     });
-    // and of the stored tile records: strips x (L2 + 32) blocks
+    // and of the stored tile records: items of rec_rows strips x (L2 + 32)
+    // blocks
     if (A.rec_off) {
         __syncthreads();
         pair_offsets(A, sh, A.rec_off, A.rec_cap, [&](const PairDesc& q) -> int64_t {
-            return (int64_t)q.n_strips * (q.L2 + 32) * A.rec_block;
+            return (int64_t)((q.n_strips + A.rec_rows - 1) / A.rec_rows) * (q.L2 + 32) * A.rec_block;
         });
     }
 }
@@ -1044,7 +1052,8 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         if (L.stored_rec) {
             pa.rec_off = (int64_t*)(base + L.rec_off);
             pa.rec_cap = L.rstore_floats;
-            pa.rec_block = 32 * rec_floats(o.order);
+            pa.rec_rows = L.rec_rows;
+            pa.rec_block = 32 * L.rec_rows * rec_floats(o.order);
         }
     }
     cudaError_t e = launch_planner(pa, o, L, base, stream);
@@ -1161,6 +1170,7 @@ static sigk_status launch_adjoint(int op, int64_t n_x, int64_t n_y, int d, const
     if (L.stored_rec) {
         ba.rec_store = (float*)(base + L.rstore);
         ba.rec_off = (int64_t*)(base + L.rec_off);
+        ba.rec_rows = L.rec_rows;
     }
     ba.nslot = L.bnslot;
     ba.wcols = L.bwcols;

@@ -160,10 +160,11 @@ struct SolverArgs {
     float* store;
     const int64_t* store_off;      // [n_pairs] float offsets into store
     int32_t* pair_exp;             // [n_pairs] or null
-    // training with stored tile records (one row per lane only): every tile's
-    // record as the adjoint reads it, per (pair, strip) (L2 + 32) blocks of
-    // 32 * rec_floats(P) floats -- block t holds the records of step t, block
-    // L2 + 31 each lane's bottom-edge state after the last column.  rec ==
+    // training with stored tile records: every tile's record as the adjoint
+    // reads it, per work item (pair, R strips of 32 rows) (L2 + 32) blocks of
+    // 32 * R records of rec_floats(P) floats -- block t holds the records of
+    // the item's rows at step t (row lane*R + k at column t - lane), block
+    // L2 + 31 the rows' bottom-edge states after the last column.  rec ==
     // nullptr: the adjoint replays the strips instead.
     float* rec;
     const int64_t* rec_off;        // [n_pairs] float offsets into rec
@@ -311,6 +312,17 @@ __device__ __forceinline__ bool wait_slot_free(const Schedule& S, const PairDesc
     }
     return __shfl_sync(kFull, ok, 0);
 }
+
+// Asynchronous 16-byte global -> shared copies of one thread (cp.async,
+// cached in L2 only), committed as a group; wait_group N waits until at most
+// N of this thread's groups are still in flight.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // 2^n as a float for n <= 0 (0 below the normal range).
 __device__ __forceinline__ float exp2_nonpos(int n) {

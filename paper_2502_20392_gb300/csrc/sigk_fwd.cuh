@@ -169,10 +169,11 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
         const bool mid_writer = train && R > 1 && lane != 31 && ((lane + 1) * R) % 32 == 0 &&
                                 s * R + mid_m < n32;
         float* mid_dst = mid_writer ? st_pair + (size_t)(s * R + mid_m - 1) * L2 * S : nullptr;
-        // stored tile records: the blocks of the item's first 32-row strip
-        // (row lane*R + k lies in strip s*R + (lane*R + k) / 32)
+        // stored tile records: this item's region, (L2 + 32) blocks of 32*R
+        // records; block t holds the records of step t in the order of the
+        // item's rows (row lane*R + k), block L2 + 31 the rows' final states
         float* rec_item = nullptr;
-        if constexpr (REC) rec_item = A.rec + A.rec_off[lo_p] + (int64_t)(s * R) * (L2 + 32) * 32 * RS;
+        if constexpr (REC) rec_item = A.rec + A.rec_off[lo_p] + (int64_t)s * (L2 + 32) * 32 * R * RS;
         bool ok = true;
 
         // row increments of this lane (zero past the end of the path)
@@ -266,26 +267,20 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                 int Frec[R];
                 const int Eb = E;
                 auto rec_head = [&](int k, int Fv) {
-                    const int rw = lane * R + k;
-                    const int m = rw >> 5, rr = rw & 31;
-                    r4[k] = nullptr;
+                    float rv[RS];
+                    rv[0] = hi;
+                    rv[1] = b1lo;
+#pragma unroll
+                    for (int q = 1; q <= P; ++q) rv[1 + q] = b[q];
+#pragma unroll
+                    for (int q = P + 2; q < RS; ++q) rv[q] = 0.0f;
+                    r4[k] = reinterpret_cast<float4*>(rec_item + ((int64_t)t * 32 * R + lane * R + k) * RS);
                     Frec[k] = Fv;
-                    if (s * R + m < n32) {
-                        float rv[RS];
-                        rv[0] = hi;
-                        rv[1] = b1lo;
 #pragma unroll
-                        for (int q = 1; q <= P; ++q) rv[1 + q] = b[q];
+                    for (int g = 0; g < kFullGroups; ++g)
+                        r4[k][g] = make_float4(rv[4 * g], rv[4 * g + 1], rv[4 * g + 2], rv[4 * g + 3]);
 #pragma unroll
-                        for (int q = P + 2; q < RS; ++q) rv[q] = 0.0f;
-                        r4[k] = reinterpret_cast<float4*>(
-                            rec_item + (int64_t)m * (L2 + 32) * 32 * RS + ((int64_t)(j + rr) * 32 + rr) * RS);
-#pragma unroll
-                        for (int g = 0; g < kFullGroups; ++g)
-                            r4[k][g] = make_float4(rv[4 * g], rv[4 * g + 1], rv[4 * g + 2], rv[4 * g + 3]);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) rtail[k][q] = rv[4 * kFullGroups + q];
-                    }
+                    for (int q = 0; q < 4; ++q) rtail[k][q] = rv[4 * kFullGroups + q];
                 };
                 if constexpr (REC) rec_head(0, F);
                 // align exponents of the incoming edge and the lane's states
@@ -342,12 +337,10 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                 if constexpr (REC) {
 #pragma unroll
                     for (int k = 0; k < R; ++k) {
-                        if (r4[k]) {
-                            // only the last row's outgoing edge leaves the lane
-                            rtail[k][P + 2 - 4 * kFullGroups] =
-                                __int_as_float(pack_exp(Frec[k], Eb, bump, k == R - 1 ? bump : 0));
-                            r4[k][kFullGroups] = make_float4(rtail[k][0], rtail[k][1], rtail[k][2], rtail[k][3]);
-                        }
+                        // only the last row's outgoing edge leaves the lane
+                        rtail[k][P + 2 - 4 * kFullGroups] =
+                            __int_as_float(pack_exp(Frec[k], Eb, bump, k == R - 1 ? bump : 0));
+                        r4[k][kFullGroups] = make_float4(rtail[k][0], rtail[k][1], rtail[k][2], rtail[k][3]);
                     }
                 }
                 ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
@@ -412,26 +405,22 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
             }
         }
         // stored records: each row's bottom-edge state after the last column
-        // (where the adjoint's reverse sweep starts), block L2 + 31 of its strip
+        // (where the adjoint's reverse sweep starts), block L2 + 31
         if constexpr (REC) {
             if (ok) {
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
-                    const int rw = lane * R + k;
-                    const int m = rw >> 5, rr = rw & 31;
-                    if (s * R + m < n32) {
-                        float fv[RS];
-                        fv[0] = a1lo[k];
+                    float fv[RS];
+                    fv[0] = a1lo[k];
 #pragma unroll
-                        for (int p = 1; p <= P; ++p) fv[p] = a[k][p];
+                    for (int p = 1; p <= P; ++p) fv[p] = a[k][p];
 #pragma unroll
-                        for (int q = P + 1; q < RS; ++q) fv[q] = 0.0f;
-                        float4* f4 = reinterpret_cast<float4*>(
-                            rec_item + (int64_t)m * (L2 + 32) * 32 * RS + ((int64_t)(L2 + 31) * 32 + rr) * RS);
+                    for (int q = P + 1; q < RS; ++q) fv[q] = 0.0f;
+                    float4* f4 = reinterpret_cast<float4*>(
+                        rec_item + ((int64_t)(L2 + 31) * 32 * R + lane * R + k) * RS);
 #pragma unroll
-                        for (int g = 0; g < RS / 4; ++g)
-                            f4[g] = make_float4(fv[4 * g], fv[4 * g + 1], fv[4 * g + 2], fv[4 * g + 3]);
-                    }
+                    for (int g = 0; g < RS / 4; ++g)
+                        f4[g] = make_float4(fv[4 * g], fv[4 * g + 1], fv[4 * g + 2], fv[4 * g + 3]);
                 }
             }
         }

@@ -16,12 +16,11 @@ struct KernelInfo {
 // Rows per lane as a function of (P, D): fewer rows when the register
 // footprint (R*(P + D) state floats) would push occupancy too low.
 constexpr int rows_per_lane(int P, int D) { return (P + D) <= 16 ? 4 : 2; }
-// The same for the training forward that stores the tile records: one row
-// per lane, so that a step's 32 records are one contiguous block (with two
-// rows per lane every lane writes to other blocks, and the scattered 48-byte
-// stores made the Gram B=64, L=1024, d=16, P=8 training forward 63 ms
-// instead of 30 ms on GB300).  The kernel supports any R.
-constexpr int rec_rows_per_lane(int, int) { return 1; }
+// The same for the training forward that stores the tile records (its
+// per-row record state adds registers): two rows while that fits without
+// spills, else one.  The records are laid out per work item and step, so a
+// step's 32 * R records are one contiguous block whatever R is.
+constexpr int rec_rows_per_lane(int P, int D) { return (P <= 10 && P + D <= 24) ? 2 : 1; }
 
 // Entry points of the kernel translation units, one unit per (edge degree P,
 // ring count NR); NR is a compile-time constant of every solver kernel, so
