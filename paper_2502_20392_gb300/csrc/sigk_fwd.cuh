@@ -33,11 +33,13 @@ struct DyStride {
     static constexpr int value = ((D / 4) % 2 == 1) ? D : D + 4;
 };
 
-template <int P, int D>
+template <int P, int D, int R = 1, bool REC = false>
 struct FwdSmem {
     static constexpr int S = P + 4;  // seam entry: hi, lo, b1lo, b1..bP, exponent
     static constexpr int DS = DyStride<D>::value;
-    static constexpr int per_warp = 64 * DS + 2 * kG * S;  // floats
+    // record-storing forward: two staging blocks of a step's 32 * R records
+    static constexpr int stage = REC ? 2 * 32 * R * rec_floats(P) : 0;
+    static constexpr int per_warp = 64 * DS + 2 * kG * S + stage;  // floats
 };
 
 // Increment of row `row` of path base z (points or increments), coordinate e.
@@ -135,9 +137,14 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
     float* smem = reinterpret_cast<float*>(smem_f4);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    float* dyw = smem + warp * FwdSmem<P, D>::per_warp;  // 64-column ring of dy
+    float* dyw = smem + warp * FwdSmem<P, D, R, REC>::per_warp;  // 64-column ring of dy
     float* sin_ = dyw + 64 * DS;                        // seam-in block
     float* sout = sin_ + kG * S;                        // seam-out block
+    // record-storing forward: a step's 32*R records are staged in shared
+    // memory (two blocks, step t uses t & 1) and stored by one bulk copy,
+    // which the seam flushes' fences do not wait for
+    float* stg = sout + kG * S;
+    constexpr int kStage = 32 * R * RS;  // floats per staged block
     const int n_items = A.sched.hdr[2];
     unsigned long long tiles_done = 0, lane_tiles = 0;
 
@@ -255,6 +262,11 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                     for (int q = 1; q <= P; ++q) b[q] = 0.0f;
                 }
             }
+            if constexpr (REC) {
+                // the bulk store of step t - 2 has read this step's staging block
+                if (lane == 0) bulk_wait_read<1>();
+                __syncwarp();
+            }
             const int j = t - lane;
             if (j >= 0 && j < L2) {
                 // records of the rows' incoming left edges (the adjoint rebuilds
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                     for (int q = 1; q <= P; ++q) rv[1 + q] = b[q];
 #pragma unroll
                     for (int q = P + 2; q < RS; ++q) rv[q] = 0.0f;
-                    r4[k] = reinterpret_cast<float4*>(rec_item + ((int64_t)t * 32 * R + lane * R + k) * RS);
+                    r4[k] = reinterpret_cast<float4*>(stg + (t & 1) * kStage + (lane * R + k) * RS);
                     Frec[k] = Fv;
 #pragma unroll
                     for (int g = 0; g < kFullGroups; ++g)
@@ -378,6 +390,16 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                     }
                 }
             }
+            if constexpr (REC) {
+                // the step's records, staged by every lane, leave in one bulk store
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_store(rec_item + (int64_t)t * kStage, stg + (t & 1) * kStage,
+                               kStage * (uint32_t)sizeof(float));
+                    bulk_commit();
+                }
+            }
             // flush a completed 32-column block of the outgoing seam
             const int jj = t - 31;
             if (has_out && jj >= 0 && jj < L2 && (((jj & 31) == 31) || jj == L2 - 1)) {
@@ -407,6 +429,9 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
         // stored records: each row's bottom-edge state after the last column
         // (where the adjoint's reverse sweep starts), block L2 + 31
         if constexpr (REC) {
+            // the staging blocks are free for the next item
+            if (lane == 0) bulk_wait_read<0>();
+            __syncwarp();
             if (ok) {
 #pragma unroll
                 for (int k = 0; k < R; ++k) {
@@ -430,6 +455,9 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
             st_release_s64(&A.done[item % A.nslot], (long long)item);
         }
         if (!ok) break;
+    }
+    if constexpr (REC) {
+        if (lane == 0) bulk_wait_all();  // the record stores are complete
     }
     // counters
 #pragma unroll

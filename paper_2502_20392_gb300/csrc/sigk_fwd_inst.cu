@@ -34,13 +34,13 @@ static int occupancy(K kern, int threads, int smem, int R, KernelInfo* info) {
 
 template <int D, int R, bool REC>
 static int fwd_info_impl(KernelInfo* info) {
-    const int smem = 4 * FwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
+    const int smem = 4 * FwdSmem<SIGK_P, D, R, REC>::per_warp * (int)sizeof(float);
     return occupancy(fwd_kernel<SIGK_P, D, R, SIGK_NR, REC>, 128, smem, R, info);
 }
 
 template <int D, int R, bool REC>
 static cudaError_t fwd_launch_impl(const SolverArgs& a, int grid, cudaStream_t s) {
-    const int smem = 4 * FwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
+    const int smem = 4 * FwdSmem<SIGK_P, D, R, REC>::per_warp * (int)sizeof(float);
     auto kern = fwd_kernel<SIGK_P, D, R, SIGK_NR, REC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
