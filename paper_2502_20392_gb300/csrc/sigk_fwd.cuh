@@ -119,7 +119,7 @@ __device__ __forceinline__ void warp_copy_cg(float* dst, const float* src, int n
 // CTAs per SM the register allocation must allow (128 threads each): the
 // largest count that ptxas meets without spilling for that instantiation.
 constexpr int fwd_min_blocks(int P, int D, int R, bool REC) {
-    return REC ? (R == 1 && !(P >= 14 && D >= 16) ? 4 : 3)
+    return REC ? ((R == 1 && !(P >= 14 && D >= 16)) || P <= 8 ? 4 : 3)
                : (R == 1 ? 4 : (R == 2 ? (P <= 8 ? 4 : 3) : (P <= 4 ? 4 : 3)));
 }
 
