@@ -118,10 +118,8 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
     // pass B reads every lane's record of one step per step, prefetched two
     // steps ahead by each lane with cp.async into its slot of sin_ / rbuf1
     // (step tp uses buffer tp & 1)
-    // record fields: [0] hi, [1] b1lo, [1 + q] b_q, [P + 2] exponent word;
-    // groups of four wholly before the exponent are stored at the start of
-    // the step, the last group (with the exponent) at its end
-    constexpr int kFullGroups = (P + 2) / 4;
+    // records: rec_put_head / rec_put_tail / rec_get (pairs of floats; the
+    // last pair, with the exponent word, is stored after the tile)
 
     for (;;) {
         int item = 0;
@@ -165,18 +163,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         const int rw = (s % RR) * 32 + lane;
         const float* rbase = stored ? A.rec_store + A.rec_off[lo_p] + (int64_t)(s / RR) * (L2 + 32) * 32 * RR * RS
                                     : rec;
-        if (stored) {
-            const float4* f4 = reinterpret_cast<const float4*>(rbase + ((int64_t)T * 32 * RR + rw) * RS);
-            float fv[RS];
-#pragma unroll
-            for (int g = 0; g < RS / 4; ++g) {
-                const float4 v = f4[g];
-                fv[4 * g] = v.x; fv[4 * g + 1] = v.y; fv[4 * g + 2] = v.z; fv[4 * g + 3] = v.w;
-            }
-            a1lo = fv[0];
-#pragma unroll
-            for (int p = 1; p <= P; ++p) a[p] = fv[p];
-        }
+        if (stored) rec_get_state<P>(rbase + ((int64_t)T * 32 * RR + rw) * RS, a1lo, a);
         for (int t = 0; t < T && !stored; ++t) {
             if ((t & 31) == 0 && t < L2) {
                 const int nb = min(32, L2 - t);
@@ -213,17 +200,9 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
             const int j = t - lane;
             if (j >= 0 && j < L2) {
                 // record of the incoming left edge, before alignment
-                float rv[RS];
-                rv[0] = hi;
-                rv[1] = b1lo;
-#pragma unroll
-                for (int q = 1; q <= P; ++q) rv[1 + q] = b[q];
-#pragma unroll
-                for (int q = P + 2; q < RS; ++q) rv[q] = 0.0f;
-                float4* r4 = reinterpret_cast<float4*>(rec + (size_t)t * RS * 32 + lane * RS);
-#pragma unroll
-                for (int g = 0; g < kFullGroups; ++g)
-                    r4[g] = make_float4(rv[4 * g], rv[4 * g + 1], rv[4 * g + 2], rv[4 * g + 3]);
+                float* rslot = rec + (size_t)t * RS * 32 + lane * RS;
+                rec_put_head<P>(rslot, hi, b1lo, b);
+                const float rbP = b[P];
                 const int Eb = E;
                 if (F != E) {
                     if (F > E) {
@@ -262,9 +241,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                     E += 64;
                     bump = 1;
                 }
-                rv[P + 2] = __int_as_float(pack_exp(F, Eb, bump, bump));
-                r4[kFullGroups] = make_float4(rv[4 * kFullGroups], rv[4 * kFullGroups + 1],
-                                              rv[4 * kFullGroups + 2], rv[4 * kFullGroups + 3]);
+                rec_put_tail<P>(rslot, rbP, pack_exp(F, Eb, bump, bump));
                 ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
 #pragma unroll
                 for (int q = 1; q <= P; ++q) ob[q] = b[q];
@@ -307,7 +284,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 const float* src = rbase + ((int64_t)(j + rw / RR) * 32 * RR + rw) * RS;
                 float* dst = rbuf(tpp) + lane * RS;
 #pragma unroll
-                for (int g = 0; g < RS / 4; ++g) cp_async16(dst + 4 * g, src + 4 * g);
+                for (int g = 0; g < RS / 2; ++g) cp_async8(dst + 2 * g, src + 2 * g);
             }
             cp_async_commit();
         };
@@ -339,23 +316,11 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 if (!ok) break;
             }
             // this step's record (groups in flight: this step's and the next)
-            float rhi, rb[P + 1], rb1lo;
+            float rhi, rb[P + 1];
             int rexp;
             {
                 cp_async_wait<1>();
-                const float4* r4 = reinterpret_cast<const float4*>(rbuf(tp) + lane * RS);
-                float rv[RS];
-#pragma unroll
-                for (int g = 0; g < RS / 4; ++g) {
-                    const float4 v = r4[g];
-                    rv[4 * g] = v.x; rv[4 * g + 1] = v.y; rv[4 * g + 2] = v.z; rv[4 * g + 3] = v.w;
-                }
-                rhi = rv[0];
-                rb1lo = rv[1];
-                rb[0] = 0.0f;
-#pragma unroll
-                for (int q = 1; q <= P; ++q) rb[q] = rv[1 + q];
-                rexp = __float_as_int(rv[P + 2]);
+                rec_get<P>(rbuf(tp) + lane * RS, rhi, rb, rexp);
                 rec_fetch(tp + 2);  // into the buffer just read (an empty group past the end)
             }
             // adjoint of the right edge: from lane+1, or seam / seed for lane 31
@@ -395,8 +360,7 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
                 float b[P + 1];
                 b[0] = 0.0f;
 #pragma unroll
-                for (int q = 1; q <= P; ++q) b[q] = rb[q];
-                b[1] += rb1lo;  // first-order term as one float
+                for (int q = 1; q <= P; ++q) b[q] = rb[q];  // b[1]: first-order term as one float
                 // exponent handling of this tile (none in the common case)
                 const bool plain = exp_plain(rexp);
                 int F = 0, Eb = 0, Em = 0;

@@ -93,10 +93,11 @@ struct ItemRef {
     int next;   // item that consumes this strip's outgoing seam, or -1
 };
 
-// Floats per lane in an adjoint record (pass A -> pass B): the incoming left
-// edge (hi, b1lo, b1..bP) and the exponent word, padded to a multiple of 4 so
-// a lane's record moves as 16-byte vectors.
-__host__ __device__ constexpr int rec_floats(int P) { return (P + 3 + 3) / 4 * 4; }
+// Floats in a tile record (written by the training forward or the adjoint's
+// replay, read by the reverse sweep): [0] the incoming corner (high part),
+// [1] b1 with its low part added, [q] b_q for q = 2..P, [P + 1] the exponent
+// word -- P + 2 floats for the even orders, moved as 8-byte pairs.
+__host__ __device__ constexpr int rec_floats(int P) { return (P + 3) / 2 * 2; }
 
 // Floats per column of the adjoint seam (corner adjoint, b1..bP adjoints):
 // padded to a multiple of 4 (128-bit shared loads and stores) up to P = 12;
@@ -169,6 +170,76 @@ struct SolverArgs {
     float* rec;
     const int64_t* rec_off;        // [n_pairs] float offsets into rec
 };
+
+// Tile records (layout above).  rec_put_head stores every pair but the last,
+// which holds the exponent word (known only after the tile); rec_put_tail
+// stores that pair (b_P as recorded, the exponent word).
+template <int P>
+__device__ __forceinline__ void rec_put_head(float* dst, float hi, float b1lo, const float (&b)[P + 1]) {
+    constexpr int RS = rec_floats(P);
+    float rv[RS];
+    rv[0] = hi;
+    rv[1] = b[1] + b1lo;
+#pragma unroll
+    for (int q = 2; q <= P; ++q) rv[q] = b[q];
+#pragma unroll
+    for (int q = P + 1; q < RS; ++q) rv[q] = 0.0f;
+    float2* d2 = reinterpret_cast<float2*>(dst);
+#pragma unroll
+    for (int g = 0; g < RS / 2 - 1; ++g) d2[g] = make_float2(rv[2 * g], rv[2 * g + 1]);
+}
+template <int P>
+__device__ __forceinline__ void rec_put_tail(float* dst, float bP, int expw) {
+    constexpr int RS = rec_floats(P);
+    static_assert(RS == P + 2, "the last pair is (b_P, exponent word)");
+    reinterpret_cast<float2*>(dst)[RS / 2 - 1] = make_float2(bP, __int_as_float(expw));
+}
+template <int P>
+__device__ __forceinline__ void rec_get(const float* src, float& hi, float (&b)[P + 1], int& expw) {
+    constexpr int RS = rec_floats(P);
+    float rv[RS];
+    const float2* s2 = reinterpret_cast<const float2*>(src);
+#pragma unroll
+    for (int g = 0; g < RS / 2; ++g) {
+        const float2 v = s2[g];
+        rv[2 * g] = v.x;
+        rv[2 * g + 1] = v.y;
+    }
+    hi = rv[0];
+    b[0] = 0.0f;
+#pragma unroll
+    for (int q = 1; q <= P; ++q) b[q] = rv[q];
+    expw = __float_as_int(rv[P + 1]);
+}
+// A row's final bottom-edge state (a1lo, a_1..a_P) in a record slot.
+template <int P>
+__device__ __forceinline__ void rec_put_state(float* dst, float a1lo, const float (&a)[P + 1]) {
+    constexpr int RS = rec_floats(P);
+    float fv[RS];
+    fv[0] = a1lo;
+#pragma unroll
+    for (int p = 1; p <= P; ++p) fv[p] = a[p];
+#pragma unroll
+    for (int q = P + 1; q < RS; ++q) fv[q] = 0.0f;
+    float2* d2 = reinterpret_cast<float2*>(dst);
+#pragma unroll
+    for (int g = 0; g < RS / 2; ++g) d2[g] = make_float2(fv[2 * g], fv[2 * g + 1]);
+}
+template <int P>
+__device__ __forceinline__ void rec_get_state(const float* src, float& a1lo, float (&a)[P + 1]) {
+    constexpr int RS = rec_floats(P);
+    float fv[RS];
+    const float2* s2 = reinterpret_cast<const float2*>(src);
+#pragma unroll
+    for (int g = 0; g < RS / 2; ++g) {
+        const float2 v = s2[g];
+        fv[2 * g] = v.x;
+        fv[2 * g + 1] = v.y;
+    }
+    a1lo = fv[0];
+#pragma unroll
+    for (int p = 1; p <= P; ++p) a[p] = fv[p];
+}
 
 // ---------------------------------------------------------------------------
 // memory-order helpers
@@ -318,6 +389,10 @@ __device__ __forceinline__ bool wait_slot_free(const Schedule& S, const PairDesc
 // N of this thread's groups are still in flight.
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }

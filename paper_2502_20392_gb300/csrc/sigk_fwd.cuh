@@ -129,10 +129,6 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
     constexpr int S = P + 4;
     constexpr int DS = DyStride<D>::value;
     constexpr int RS = rec_floats(P);
-    // record fields: [0] hi, [1] b1lo, [1 + q] b_q, [P + 2] exponent word;
-    // the groups of four wholly before the exponent are stored before the
-    // tile, the last group (with the exponent) after it
-    constexpr int kFullGroups = (P + 2) / 4;
     extern __shared__ float4 smem_f4[];
     float* smem = reinterpret_cast<float*>(smem_f4);
     const int lane = threadIdx.x & 31;
@@ -274,25 +270,15 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                 // the alignment; row k > 0 the previous row's outgoing edge.
                 // The first groups are stored before the tile, the group with
                 // the exponent word after the step's renormalisation.
-                float4* r4[R];
-                float rtail[R][4];
+                float* rslot[R];
+                float rbP[R];
                 int Frec[R];
                 const int Eb = E;
                 auto rec_head = [&](int k, int Fv) {
-                    float rv[RS];
-                    rv[0] = hi;
-                    rv[1] = b1lo;
-#pragma unroll
-                    for (int q = 1; q <= P; ++q) rv[1 + q] = b[q];
-#pragma unroll
-                    for (int q = P + 2; q < RS; ++q) rv[q] = 0.0f;
-                    r4[k] = reinterpret_cast<float4*>(stg + (t & 1) * kStage + (lane * R + k) * RS);
+                    rslot[k] = stg + (t & 1) * kStage + (lane * R + k) * RS;
+                    rec_put_head<P>(rslot[k], hi, b1lo, b);
+                    rbP[k] = b[P];
                     Frec[k] = Fv;
-#pragma unroll
-                    for (int g = 0; g < kFullGroups; ++g)
-                        r4[k][g] = make_float4(rv[4 * g], rv[4 * g + 1], rv[4 * g + 2], rv[4 * g + 3]);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) rtail[k][q] = rv[4 * kFullGroups + q];
                 };
                 if constexpr (REC) rec_head(0, F);
                 // align exponents of the incoming edge and the lane's states
@@ -348,12 +334,8 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                 }
                 if constexpr (REC) {
 #pragma unroll
-                    for (int k = 0; k < R; ++k) {
-                        // only the last row's outgoing edge leaves the lane
-                        rtail[k][P + 2 - 4 * kFullGroups] =
-                            __int_as_float(pack_exp(Frec[k], Eb, bump, k == R - 1 ? bump : 0));
-                        r4[k][kFullGroups] = make_float4(rtail[k][0], rtail[k][1], rtail[k][2], rtail[k][3]);
-                    }
+                    for (int k = 0; k < R; ++k)  // only the last row's outgoing edge leaves the lane
+                        rec_put_tail<P>(rslot[k], rbP[k], pack_exp(Frec[k], Eb, bump, k == R - 1 ? bump : 0));
                 }
                 ohi = hi; olo = lo; ob1lo = b1lo; oE = E;
 #pragma unroll
@@ -434,19 +416,8 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
             __syncwarp();
             if (ok) {
 #pragma unroll
-                for (int k = 0; k < R; ++k) {
-                    float fv[RS];
-                    fv[0] = a1lo[k];
-#pragma unroll
-                    for (int p = 1; p <= P; ++p) fv[p] = a[k][p];
-#pragma unroll
-                    for (int q = P + 1; q < RS; ++q) fv[q] = 0.0f;
-                    float4* f4 = reinterpret_cast<float4*>(
-                        rec_item + ((int64_t)(L2 + 31) * 32 * R + lane * R + k) * RS);
-#pragma unroll
-                    for (int g = 0; g < RS / 4; ++g)
-                        f4[g] = make_float4(fv[4 * g], fv[4 * g + 1], fv[4 * g + 2], fv[4 * g + 3]);
-                }
+                for (int k = 0; k < R; ++k)
+                    rec_put_state<P>(rec_item + ((int64_t)(L2 + 31) * 32 * R + lane * R + k) * RS, a1lo[k], a[k]);
             }
         }
         __syncwarp();
