@@ -285,7 +285,7 @@ def main():
         flops = tiles[k] * tile_flops(P, nr, DIM)
         ach = flops / (kms * 1e-3) / 1e12
         roof.append({"sigma": sg, "order": P, "rings": nr, "kernel_ms": round(kms, 4),
-                     "kernel": (f"fwd_kernel<P={P},D=16,R=1> (training: stores the tile records)"
+                     "kernel": (f"fwd_kernel<P={P},D=16> (training: stores the tile records)"
                                 if k == BWD_SIGMA else f"fwd_kernel<P={P},D=16>"),
                      "flops_per_launch": flops, "achieved": round(ach, 3)})
     sg, _, P, nr = SIGMAS[BWD_SIGMA]
