@@ -319,56 +319,14 @@ __device__ __forceinline__ bool wait_ge_s64(const long long* p, long long target
 }
 
 // ---------------------------------------------------------------------------
-// Bulk asynchronous copies (TMA, cp.async.bulk) global -> shared memory with
-// mbarrier completion, for prefetching contiguous blocks.  One mbarrier per
-// buffer, initialised with an arrival count of 1: the issuing lane arrives
-// with the expected byte count, the copy completes the transaction.
+// Asynchronous copies.  Shared-memory addresses for PTX operands:
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-// make initialised barriers visible to the async proxy
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// order this thread's earlier generic-proxy global writes before later
-// async-proxy (bulk copy) reads of the same memory
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
+// make this thread's generic-proxy writes to shared memory visible to the
+// async proxy (before a bulk store reads them)
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// one lane: expect `bytes` on `bar` and start the copy (16-byte aligned
-// addresses, bytes a multiple of 16)
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return done != 0;
-}
-// Bounded wait for phase `parity` of `bar` to complete (every lane calls it).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
-    if (mbar_test(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (int it = 0; it < kWaitMaxIter; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) break;
-    }
-    record_timeout(status, bar, (long long)parity, -1);
-    return false;
 }
 
 // Before item writes seam slot item % nslot: the slot's previous user u =
@@ -384,13 +342,9 @@ __device__ __forceinline__ bool wait_slot_free(const Schedule& S, const PairDesc
     return __shfl_sync(kFull, ok, 0);
 }
 
-// Asynchronous 16-byte global -> shared copies of one thread (cp.async,
-// cached in L2 only), committed as a group; wait_group N waits until at most
-// N of this thread's groups are still in flight.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
-                 : "memory");
-}
+// Asynchronous 8-byte global -> shared copies of one thread (cp.async),
+// committed as a group; wait_group N waits until at most N of this thread's
+// groups are still in flight.
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem_dst)), "l"(gsrc)
                  : "memory");
