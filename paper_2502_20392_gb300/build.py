@@ -28,11 +28,16 @@ def _sources():
 
 
 def _digest() -> str:
+    """Hash of the sources and flags, independent of where the repository
+    lives (paths relative to its root), so a figure recorded for one build
+    can be matched on another machine."""
+    root = os.path.dirname(HERE)
     h = hashlib.sha256()
     for f in _sources():
         with open(f, "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+            h.update(os.path.relpath(f, root).encode() + b"\0" + fh.read())
+    flags = [os.path.relpath(x, root) if x == INCLUDE else x for x in ARCH + FLAGS]
+    h.update(" ".join(flags).encode())
     return h.hexdigest()
 
 
