@@ -1,17 +1,16 @@
 // sigk_bwd.cuh -- reverse-mode (adjoint) sweep of the wavefront solver.
 //
-// Runs after a training forward that stored every strip's right-edge seam
-// (the checkpointed wavefront boundaries; strips of 32 rows, one row per
-// lane).  One work item = (pair, strip), strips of a pair in DECREASING order
-// (the schedule's k-th item of a pair is strip n_strips - 1 - k).
+// Runs after a training forward that stored the right-edge seam after every
+// 32-row strip (the checkpointed wavefront boundaries).  One work item =
+// (pair, strip of 32 rows, one row per lane), strips of a pair in DECREASING
+// order (the schedule's k-th item of a pair is strip n_strips - 1 - k).
 //
-// Pass A replays the strip's forward from its stored input seam and keeps, per
-// lane and column, the lane's incoming left edge and the exponent decisions
-// (a record of P+3 floats) in a per-warp scratch area; it ends with each
-// lane's bottom-edge state after the last column in registers.  When the
-// records of every tile fit the device memory budget, the training forward
-// (the same arithmetic) writes them once for all strips, with each row's
-// final state, and pass A is skipped.
+// Every tile's record -- the row's incoming left edge and the exponent
+// decisions, P + 2 floats -- comes either from the training forward, which
+// writes all of them (with each row's final bottom-edge state) when they fit
+// the device memory budget, or from pass A: a replay of the strip's forward
+// from its stored input seam into a per-warp scratch area, ending with each
+// lane's bottom-edge state after the last column in registers.
 //
 // Pass B sweeps the columns in reverse with the mirrored skew (lane 31 first).
 // At each tile it rebuilds the tile's bottom-edge input by inverting the
