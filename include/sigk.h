@@ -56,6 +56,9 @@ typedef enum {
     SIGK_ERR_WORKSPACE = -4,  /* ws too small or misaligned */
     SIGK_ERR_CUDA = -5,       /* a CUDA runtime call failed (see sigk_last_error) */
     SIGK_ERR_TIMEOUT = -6,    /* a bounded inter-warp wait ran out on the device */
+    SIGK_ERR_ACCURACY = -7,   /* sigk_plan: no order up to 16 meets the tolerance, even
+                                 at the finest refinement tried (*opts_out still holds
+                                 that finest plan) */
     SIGK_ERR_UNSUPPORTED = -8 /* a combination this library does not provide */
 } sigk_status;
 
@@ -245,7 +248,9 @@ sigk_status sigk_static_sync_status(void* stream);
  * sum|c|^(n+1)/((n+1)!)^2 <= tol/10.  If a tile has |c| > 1 or no order up
  * to 16 fits, it sets refine_c = 1, 1/4, ... and plans the refined problem.
  * Synchronises `stream`.  Writes into *opts_out (other fields copied from
- * opts_in when given; max_len raised to the longest swept path, refined). */
+ * opts_in when given; max_len raised to the longest swept path, refined).
+ * Returns SIGK_ERR_ACCURACY, with *opts_out written, when the rule is not met
+ * even at the finest refinement tried (or at the caller's refine_c). */
 sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
                       const float* Y, const int64_t* len_y, int64_t n_y, int d, double tol,
                       void* ws, size_t ws_bytes, void* stream, const sigk_opts* opts_in,

@@ -1534,6 +1534,9 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     opts_out->rings = nr;
     opts_out->refine_c = o.refine_c;
     opts_out->max_len = max_swept;  // the longest swept path as planned (refined)
+    if (max_c > 1.0 || !fits)
+        return fail(SIGK_ERR_ACCURACY,
+                    "the a-priori rule is not met at order 16 even at the finest refinement tried");
     return SIGK_OK;
 }
 

@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
+import warnings
 from dataclasses import dataclass
 
 import torch
@@ -24,7 +25,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sigk.h")
 OP_PAIRS, OP_GRAM, OP_MMD = 0, 1, 2
 FLAG_INCREMENTS, FLAG_GRAM_FULL, FLAG_MMD_BIASED, FLAG_FP64, FLAG_PAIR_MAJOR, FLAG_REPLAY = 1, 2, 4, 8, 16, 32
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_LENGTH", -3: "ERR_NONFINITE", -4: "ERR_WORKSPACE",
-          -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -8: "ERR_UNSUPPORTED"}
+          -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_ACCURACY", -8: "ERR_UNSUPPORTED"}
+ERR_ACCURACY = -7
 
 
 class SigkError(RuntimeError):
@@ -434,8 +436,13 @@ def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | 
     buf = ws.get(nb, X.device)
     o_in = opts.c()
     o_out = _Opts()
-    _check(load().sigk_plan(op, _ptr(X), _ptr(len_x), n_x, _ptr(Y), _ptr(len_y), n_y, d,
-                            float(tol), _ptr(buf), buf.numel(), _stream(), ctypes.byref(o_in),
-                            ctypes.byref(o_out)))
+    st = load().sigk_plan(op, _ptr(X), _ptr(len_x), n_x, _ptr(Y), _ptr(len_y), n_y, d,
+                          float(tol), _ptr(buf), buf.numel(), _stream(), ctypes.byref(o_in),
+                          ctypes.byref(o_out))
+    if st == ERR_ACCURACY:  # the finest plan is still returned
+        warnings.warn(f"sigk.plan: tolerance {tol:g} not certified by the a-priori rule "
+                      f"({load().sigk_last_error().decode()})", RuntimeWarning)
+    else:
+        _check(st)
     return Opts(o_out.order, o_out.rings, o_out.flags, o_out.grid_ctas, o_out.max_len,
                 o_out.refine_c)

@@ -163,6 +163,26 @@ def test_plan_meets_tolerance(S, orc, sigma):
         assert e.max() < max(t, 2e-6), (t, o, e.max())
 
 
+def test_plan_reports_unreachable_tolerance(S):
+    # a tolerance below what order 16 can certify even at the finest
+    # refinement: SIGK_ERR_ACCURACY, with the finest plan still returned
+    import warnings
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(2, [12, 9], 3, 3.0, seed=31)
+    X, L = to_dev(pts, lens)
+    with warnings.catch_warnings(record=True) as w:
+        warnings.simplefilter("always")
+        o = S.plan(S.OP_GRAM, X, L, tol=1e-300)
+    assert any(issubclass(x.category, RuntimeWarning) for x in w)
+    assert o.order == 16 and 0.0 < o.refine_c < 1.0
+    assert b"a-priori" in S.load().sigk_last_error()
+    # a reachable tolerance on the same paths plans without the warning
+    with warnings.catch_warnings(record=True) as w:
+        warnings.simplefilter("always")
+        S.plan(S.OP_GRAM, X, L, tol=1e-4)
+    assert not any("sigk.plan" in str(x.message) for x in w)
+
+
 def test_cuda_graph_capture_and_replay(S, orc):
     # the C-ABI launches no host synchronisation, allocation or copy, so a call
     # with a preallocated workspace can be captured and replayed on new inputs
