@@ -202,8 +202,11 @@ sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t 
  * unchanged since the forward.  grad_out, grad_X, grad_Y as in sigk_backward
  * (gradients are overwritten).  sigk_adjoint reads what the forward wrote
  * on the device: give it the same stream, or one ordered after the forward.
- * It may run again on the same state with another grad_out.  Errors on the
- * device are reported by sigk_sync_status. */
+ * It may run again on the same state with another grad_out.  The workspace
+ * carries a signature of the training forward (op, sizes, options, layout);
+ * if it does not hold a successful training forward of this call's
+ * arguments, sigk_adjoint touches nothing and sigk_sync_status reports
+ * SIGK_ERR_ARG.  Errors on the device are reported by sigk_sync_status. */
 sigk_status sigk_forward_train(int op, const float* X, const int64_t* len_x, int64_t n_x,
                                const float* Y, const int64_t* len_y, int64_t n_y, int d,
                                double* value_out, void* ws, size_t ws_bytes, void* stream,

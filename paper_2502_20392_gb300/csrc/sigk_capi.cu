@@ -355,7 +355,8 @@ struct Header {
     unsigned long long counters[4];
     int sched[4];  // schedule: mode, n_levels, n_items (Schedule::hdr)
     int sched2[4];  // training forward's schedule (items of 2^fwd_shift strips)
-    int pad2[12];
+    long long train_sig;  // signature of the training forward whose state the workspace holds (0: none)
+    int pad2[10];
     long long diag[3];  // first timed-out wait: address, target, value seen (byte 128)
 };
 static_assert(offsetof(Header, diag) == 128, "record_timeout writes the diagnosis at byte 128");
@@ -409,6 +410,7 @@ struct PlanArgs {
     int64_t rec_cap;    // floats available for them
     int rec_rows;       // rows per lane of the forward that writes them
     int rec_block;      // floats per block (32 * rec_rows records)
+    long long train_sig;  // training: signature recorded once the plan succeeded
     double* pair_w;
     const double* grad_out;
     float* gX;
@@ -564,6 +566,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         if (t == 0) {
             bad = 0;
             A.hdr->status = 0;  // errors are reported per call
+            A.hdr->train_sig = 0;  // no training state until this plan succeeds
         }
         __syncthreads();
         block_exclusive_scan(A.len_x, A.n_x, A.ox, sh, true, A.inc_mode, &bad);
@@ -776,6 +779,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
             return (int64_t)((q.n_strips + A.rec_rows - 1) / A.rec_rows) * (q.L2 + 32) * A.rec_block;
         });
     }
+    __syncthreads();
+    if (t == 0 && ld_volatile_s32(&A.hdr->status) == 0) A.hdr->train_sig = A.train_sig;
 }
 
 // Adjoint set-up, run before every adjoint launch on a workspace that holds
@@ -787,6 +792,13 @@ __global__ void adjoint_prep_kernel(PlanArgs A) {
     const bool self = (A.op == SIGK_OP_GRAM && A.n_y == 0);
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    // the workspace must hold a successful training forward of this call's
+    // op, sizes and options; otherwise touch nothing (the adjoint kernel then
+    // sees the error status and exits before reading the workspace)
+    if (A.train_sig == 0 || *(volatile long long*)&A.hdr->train_sig != A.train_sig) {
+        if (tid == 0) atomicCAS(&A.hdr->status, 0, kErrArg);
+        return;
+    }
     if (tid == 0) {
         A.hdr->bwd_item_counter = 0;
         A.hdr->counters[2] = 0;
@@ -996,6 +1008,25 @@ static cudaError_t launch_planner(PlanArgs pa, const Opts& o, const Layout& L, c
     return cudaGetLastError();
 }
 
+// Signature of a training call (op, sizes, options, layout): recorded by the
+// training forward's planner, checked by the adjoint's set-up kernel.
+static long long train_signature(int op, int64_t n_x, int64_t n_y, int d, const Opts& o,
+                                 const Layout& L) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the fields
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xFF;
+            h *= 1099511628211ull;
+        }
+    };
+    uint32_t rc;
+    memcpy(&rc, &o.refine_c, sizeof(rc));
+    mix((uint64_t)op); mix((uint64_t)n_x); mix((uint64_t)n_y); mix((uint64_t)d);
+    mix((uint64_t)o.order); mix((uint64_t)o.rings); mix((uint64_t)o.flags);
+    mix((uint64_t)o.max_len); mix((uint64_t)o.grid_ctas); mix((uint64_t)rc); mix((uint64_t)L.total);
+    return (long long)(h | 1ull);  // never 0
+}
+
 // Common driver: plan + solve into `out` (k values or Gram).  With `train`,
 // the forward runs in training mode: every 32-row strip's seam is stored and,
 // within the record budget, every tile's record (one row per lane); the
@@ -1049,6 +1080,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         pa.stride = L.stride;
         pa.store_cap = L.store_floats;
         pa.store_off = (int64_t*)(base + L.store_off);
+        pa.train_sig = train_signature(op, n_x, n_y, d, o, L);
         if (L.stored_rec) {
             pa.rec_off = (int64_t*)(base + L.rec_off);
             pa.rec_cap = L.rstore_floats;
@@ -1145,6 +1177,7 @@ static sigk_status launch_adjoint(int op, int64_t n_x, int64_t n_y, int d, const
     pa.bcons = (unsigned long long*)(base + L.bcons);
     pa.bdone = (long long*)(base + L.bdone);
     pa.bnslot = L.bnslot;
+    pa.train_sig = train_signature(op, n_x, n_y, d, o, L);
     adjoint_prep_kernel<<<L.bgrid, 256, 0, stream>>>(pa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "adjoint set-up launch");

@@ -200,6 +200,35 @@ def test_forward_train_then_adjoint(S, op):
         torch.testing.assert_close(aY, rY, rtol=1e-5, atol=1e-6 * float(rY.abs().max()))
 
 
+def test_adjoint_refuses_foreign_workspace(S):
+    # sigk_adjoint checks, on the device, that the workspace holds a
+    # successful training forward of the same op, sizes and options; if not
+    # it reports SIGK_ERR_ARG and touches nothing
+    from paper_2502_20392_gb300 import synth
+    pts, lens = synth.brownian(3, [40, 33, 50], 4, 1.0, seed=105)
+    X, L = torch.from_numpy(pts).to(dev()), torch.from_numpy(lens).to(dev())
+    o = S.Opts(order=8, rings=4, max_len=64)
+    g = torch.from_numpy(np.random.default_rng(106).standard_normal((3, 3)))
+    nbytes = S.backward_workspace_size(S.OP_GRAM, 3, 0, 4, o)
+    # the workspace holds an inference Gram
+    ws = S.Workspace()
+    ws.get(nbytes, X.device)
+    S.gram(X, L, opts=o, ws=ws)
+    with pytest.raises(S.SigkError):
+        S.adjoint(S.TrainState(S.OP_GRAM, X, L, None, None, 3, 0, 4, o, ws), g)
+    # the workspace holds the training forward of the first two paths
+    n2 = int(lens[0] + lens[1])
+    S.forward_train(S.OP_GRAM, X[:n2], L[:2], None, None, o, ws=ws)
+    with pytest.raises(S.SigkError):
+        S.adjoint(S.TrainState(S.OP_GRAM, X, L, None, None, 3, 0, 4, o, ws), g)
+    # the matching training forward on the same workspace
+    value, state = S.forward_train(S.OP_GRAM, X, L, None, None, o, ws=ws)
+    gX, _ = S.adjoint(state, g)
+    rX, _, rv = S.backward(S.OP_GRAM, X, L, None, None, g, o)
+    assert torch.equal(value, rv)
+    torch.testing.assert_close(gX, rX, rtol=1e-5, atol=1e-6 * float(rX.abs().max()))
+
+
 def test_gradient_with_refinement(S, orc):
     # gradients of refined virtual segments are folded back to the segments
     from paper_2502_20392_gb300 import synth
