@@ -1,0 +1,39 @@
+"""Host-side checks of bench.py: the flop model behind the roofline figures,
+and the reference arm's JSON line (it runs the FP64 oracle on the host)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_flop_model():
+    import bench
+    # per-tile FP32 operations (FMA = 2) of the solver and of the adjoint
+    assert bench.tile_flops(8, 4, 16) == 282
+    assert bench.tile_flops(16, 6, 16) == 738
+    assert bench.adjoint_tile_flops(8, 4, 16, replay=False) == 672
+    for P, nr, d in ((8, 4, 16), (12, 6, 4), (16, 8, 8)):
+        # the replayed pass adds exactly one forward tile
+        assert (bench.adjoint_tile_flops(P, nr, d) - bench.adjoint_tile_flops(P, nr, d, replay=False)
+                == bench.tile_flops(P, nr, d))
+    # rings beyond the order add nothing
+    assert bench.tile_flops(4, 8, 4) == bench.tile_flops(4, 4, 4)
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                       timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "dtype", "config", "e2e", "cpu_baseline"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
