@@ -35,10 +35,27 @@ METRIC = ("fwd & fwd+bwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=
           "sigma in {1,4}")
 
 
+def useful_tile_fma(P: int, nr: int, d: int) -> int:
+    """Algorithmic FMAs of one tile (the work model of the method, counted
+    from the truncation actually used, not the executed instructions): the
+    increment inner product (d), ring m = 1..n adding 2(P - m) + 1
+    multiply-adds into the two outgoing edges, and the 2P additions of the
+    exact transport (ring 0)."""
+    nr = min(nr, P, 8)
+    return d + sum(2 * (P - m) + 1 for m in range(1, nr + 1)) + 2 * P
+
+
+def useful_tile_flops(P: int, nr: int, d: int, adjoint: bool = False) -> int:
+    """2 flops per algorithmic FMA; the adjoint counts twice the forward's
+    work (recomputation is overhead, not useful work)."""
+    return (4 if adjoint else 2) * useful_tile_fma(P, nr, d)
+
+
 def tile_flops(P: int, nr: int, d: int) -> int:
-    """FP32 operations per tile of the solver (FMA = 2), as executed: the
+    """FP32 operations per tile of the solver kernel as executed (FMA = 2): the
     increment inner product (2d), the ring powers, the Hankel sums of both
-    edges, the edge evaluation, the convolutions and the float-float corner."""
+    edges, the edge evaluation, the convolutions, the float-float corner and
+    the compensated first-order terms."""
     nrm = min(P, 8)
     nr = min(nr, nrm)
     f = 2 * (nr - 1)
@@ -51,9 +68,9 @@ def tile_flops(P: int, nr: int, d: int) -> int:
 
 
 def adjoint_tile_flops(P: int, nr: int, d: int, replay: bool = True) -> int:
-    """FP32 operations per tile of the adjoint kernel (FMA = 2): in pass B the
-    increment dot, the inverse bottom-edge update, the tile adjoint and the
-    two gradient FMAs; with `replay`, also pass A's forward replay
+    """FP32 operations per tile of the adjoint kernel as executed (FMA = 2): in
+    pass B the increment dot, the inverse bottom-edge update, the tile adjoint
+    and the two gradient FMAs; with `replay`, also pass A's forward replay
     (tile_flops), which is skipped when the forward stored the tile records."""
     nrm = min(P, 8)
     nr = min(nr, nrm)
@@ -144,22 +161,86 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
-def oracle_sample(pts_lens, n_pairs):
-    """FP64 oracle on the first n_pairs upper-triangle pairs (a, b) of each
-    Gram; returns (values per sigma, seconds, threads)."""
+def sample_pairs(n_pairs, seed):
+    """n_pairs distinct upper-triangle entries (a, b), a <= b, of the Gram,
+    drawn uniformly over the whole matrix (seeded)."""
+    import numpy as np
+    tri = [(a, b) for a in range(N_PATHS) for b in range(a, N_PATHS)]
+    pick = np.random.default_rng(seed).choice(len(tri), size=min(n_pairs, len(tri)), replace=False)
+    return [tri[i] for i in sorted(pick)]
+
+
+def oracle_sample(pts_lens, n_pairs, seed=0):
+    """FP64 oracle on n_pairs random upper-triangle pairs (a, b) of each Gram;
+    returns (values per sigma, seconds, threads)."""
     import numpy as np
 
     import oracle
     from paper_2502_20392_gb300 import synth
     oracle.build()
     out, t0 = [], time.perf_counter()
-    for pts, lens in pts_lens:
+    for k, (pts, lens) in enumerate(pts_lens):
         inc = [np.diff(p.astype(np.float64), axis=0) for p in synth.split(pts, lens)]
-        idx = [(a, b) for a in range(N_PATHS) for b in range(a, N_PATHS)][:n_pairs]
+        idx = sample_pairs(n_pairs, seed + k)
         xs = [inc[a] for a, _ in idx]
         ys = [inc[b] for _, b in idx]
         out.append((idx, oracle.series_pairs(xs, ys)))
     return out, time.perf_counter() - t0, oracle.num_threads()
+
+
+def rel_err_entry(G, a, b, r):
+    """Relative error of Gram entry (a, b) against the reference r; a near-zero
+    cross entry (|r| below 1e-2 of sqrt(G_aa G_bb)) is measured on that
+    Cauchy-Schwarz scale."""
+    e = abs(G[a, b] - r) / max(abs(r), 1e-300)
+    cs_scale = (abs(G[a, a] * G[b, b])) ** 0.5
+    if abs(r) < 1e-2 * cs_scale:
+        e = min(e, abs(G[a, b] - r) / cs_scale)
+    return e
+
+
+def timed_loop(step, n_kernels, steps, flush):
+    """Runs `steps` timed steps, L2 flushed before each (outside the timed
+    span); CUDA events around each step and, through the library's profiling
+    hook, around each solver kernel (on the launching stream).  Returns
+    (per-step ms, per-step list of per-kernel ms)."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(n_kernels)] for _ in range(steps)]
+    for row in kev:  # torch creates an event on first record: do it before handing out handles
+        for a, b in row:
+            a.record()
+            b.record()
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record()
+        step(kev[i])
+        ends[i].record()
+    torch.cuda.synchronize()
+    return ([a.elapsed_time(b) for a, b in zip(starts, ends)],
+            [[a.elapsed_time(b) for a, b in row] for row in kev])
+
+
+def e2e_loop(step, h_in, d_in, outs, h_outs, steps, flush):
+    """End to end through the public API: pinned host inputs -> device, the
+    step, results -> pinned host, every step; CUDA events around it."""
+    import torch
+    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        e_s[i].record()
+        for h, d in zip(h_in, d_in):
+            d.copy_(h, non_blocking=True)
+        res = step(None, d_in)
+        for o, h in zip(outs(res), h_outs):
+            h.copy_(o, non_blocking=True)
+        e_e[i].record()
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in zip(e_s, e_e))
 
 
 def main():
@@ -169,13 +250,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="full", choices=["full", "small"],
-                    help="small: 16 paths per Gram (for ncu captures; not a bench line)")
+    ap.add_argument("--case", default="full", choices=["full", "small", "large_d"],
+                    help="small: 16 paths per Gram (for ncu captures; not a bench line); "
+                         "large_d: two launches of 64 ragged pairs with d = 256 (the two-phase "
+                         "kernel, for ncu captures)")
     ap.add_argument("--sweep", default=None, choices=["roughness", "dimension", "length", "configs"],
                     help="print one JSON line per point of a sweep instead of the bench line")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)
+    if args.case == "large_d":
+        return run_large_d()
     if args.case == "small":
         global N_PATHS
         N_PATHS = 16
@@ -191,7 +276,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2502_20392_gb300 import build, sigk, synth
+    from paper_2502_20392_gb300 import build, sigk
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -207,95 +292,108 @@ def main():
     X = [torch.from_numpy(p).to(dev) for p, _ in host]
     L = [torch.from_numpy(l).to(dev) for _, l in host]
     opts = [sigk.Opts(order=P, rings=nr, max_len=N_SEG) for _, _, P, nr in SIGMAS]
+    # training forward of the Gram whose gradient is taken: only the seams of
+    # the 32-row strips are kept (checkpointed wavefront boundaries); the
+    # adjoint recomputes each strip from its seam
+    _, _, Pb, nrb = SIGMAS[BWD_SIGMA]
+    bopts = sigk.Opts(order=Pb, rings=nrb, max_len=N_SEG, flags=sigk.FLAG_REPLAY)
     wss = [sigk.Workspace() for _ in SIGMAS]
+    bws = sigk.Workspace()
     G = [torch.empty((N_PATHS, N_PATHS), dtype=torch.float64, device=dev) for _ in SIGMAS]
+    Gb = torch.empty((N_PATHS, N_PATHS), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
     # upstream gradient of the Gram in the adjoint (a fixed dense weighting)
     W = torch.from_numpy(np.random.default_rng(7).standard_normal((N_PATHS, N_PATHS))).to(dev)
-    bws = sigk.Workspace()
 
-    def step(ev_pairs=None, pts=X, lens=L):
-        # the Gram whose gradient is taken runs as a training forward (it keeps
-        # its seams and tile records for the adjoint, as an autograd forward
-        # does); the other as an inference forward; then the adjoint
-        state = None
+    def fwd_step(ev=None, inp=None):
+        # forward: both Grams (inference)
+        inp = inp or (X + L)
         for k in range(len(SIGMAS)):
-            if ev_pairs is not None:
-                sigk.profile_events(*ev_pairs[k])
-            if k == BWD_SIGMA:
-                _, state = sigk.forward_train(sigk.OP_GRAM, pts[k], lens[k], None, None, opts[k],
-                                              ws=bws, out=G[k], check=False)
-            else:
-                sigk.gram(pts[k], lens[k], opts=opts[k], out=G[k], ws=wss[k], check=False)
-        if ev_pairs is not None:
-            sigk.profile_events(*ev_pairs[len(SIGMAS)])
-        gX, _ = sigk.adjoint(state, W, need_y=False, check=False)
-        if ev_pairs is not None:
+            if ev is not None:
+                sigk.profile_events(*ev[k])
+            sigk.gram(inp[k], inp[len(SIGMAS) + k], opts=opts[k], out=G[k], ws=wss[k], check=False)
+        if ev is not None:
             sigk.profile_events(None, None)
-        return gX
+        return G
+
+    def fb_step(ev=None, inp=None):
+        # forward + backward of the sigma = 1 Gram: training forward (keeps
+        # the strip seams), then the adjoint from that state
+        pts, lens = inp if inp else (X[BWD_SIGMA], L[BWD_SIGMA])
+        if ev is not None:
+            sigk.profile_events(*ev[0])
+        _, state = sigk.forward_train(sigk.OP_GRAM, pts, lens, None, None, bopts, ws=bws, out=Gb,
+                                      check=False)
+        if ev is not None:
+            sigk.profile_events(*ev[1])
+        gX, _ = sigk.adjoint(state, W, need_y=False, check=False)
+        if ev is not None:
+            sigk.profile_events(None, None)
+        return Gb, gX
 
     for _ in range(args.warmup):
-        step()
+        fwd_step()
+        fb_step()
     torch.cuda.synchronize()
-    for ws in wss:
+    for ws in wss + [bws]:
         sigk.sync_status(ws)
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in range(len(SIGMAS) + 1)] for _ in range(args.steps)]
-    for row in kev:  # torch creates an event on first record: do it before handing out handles
-        for a, b in row:
-            a.record()
-            b.record()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         t_wall = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(float(i))  # evict the inputs from L2 (outside the timed span)
-            starts[i].record()
-            step(kev[i])
-            ends[i].record()
-        torch.cuda.synchronize()
+        f_ms, f_kern = timed_loop(fwd_step, len(SIGMAS), args.steps, flush)
+        b_ms, b_kern = timed_loop(fb_step, 2, args.steps, flush)
         t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
     for ws in wss + [bws]:
         sigk.sync_status(ws)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    kern_ms = [[a.elapsed_time(b) for a, b in row] for row in kev]
-    ms = sum(step_ms) / len(step_ms)
+    ms = statistics.mean(f_ms)
+    ms_fb = statistics.mean(b_ms)
     if world > 1:
         ms = max_over_ranks(ms, dev, dist)
+        ms_fb = max_over_ranks(ms_fb, dev, dist)
 
-    cells = cells_per_step()
+    cells = cells_per_step()                        # both Grams' cells
+    cells_fb = pairs_of_gram(N_PATHS) * N_SEG * N_SEG  # the sigma = 1 Gram's cells
     value = cells * world / (ms * 1e-3)
 
-    # counters of the last launch of each sigma (tiles actually solved)
+    # per-kernel rooflines: useful work (the algorithmic model) and the
+    # executed operation count, both over the kernel's CUDA-event time
+    tiles = [sigk.counters(wss[k])[0] for k in range(len(SIGMAS))]
     bcnt = sigk.counters(bws)
-    tiles = [bcnt[0] if k == BWD_SIGMA else sigk.counters(wss[k])[0] for k in range(len(SIGMAS))]
-
-    # roofline of the solver kernel (dominant: the sigma = 4, P = 16 launch)
     roof = []
+
+    def entry(name, kms, useful, executed, sg, P, nr, extra=None):
+        e = {"kernel": name, "sigma": sg, "order": P, "rings": nr, "kernel_ms": round(kms, 4),
+             "useful_flops": useful, "achieved": round(useful / (kms * 1e-3) / 1e12, 3),
+             "frac": round(useful / (kms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 4),
+             "executed_flops": executed,
+             "executed_tflops": round(executed / (kms * 1e-3) / 1e12, 3)}
+        if extra:
+            e.update(extra)
+        roof.append(e)
+
     for k, (sg, _, P, nr) in enumerate(SIGMAS):
-        kms = statistics.mean(r[k] for r in kern_ms)
-        flops = tiles[k] * tile_flops(P, nr, DIM)
-        ach = flops / (kms * 1e-3) / 1e12
-        roof.append({"sigma": sg, "order": P, "rings": nr, "kernel_ms": round(kms, 4),
-                     "kernel": (f"fwd_kernel<P={P},D=16> (training: stores the tile records)"
-                                if k == BWD_SIGMA else f"fwd_kernel<P={P},D=16>"),
-                     "flops_per_launch": flops, "achieved": round(ach, 3)})
+        kms = statistics.mean(r[k] for r in f_kern)
+        # compulsory increment reads: each pair's two paths once (points, FP32)
+        inc_bytes = pairs_of_gram(N_PATHS) * 2 * (N_SEG + 1) * DIM * 4
+        entry(f"fwd_kernel<P={P},D=16> (inference)", kms, tiles[k] * useful_tile_flops(P, nr, DIM),
+              tiles[k] * tile_flops(P, nr, DIM), sg, P, nr,
+              {"increment_read_gbs": round(inc_bytes / (kms * 1e-3) / 1e9, 1)})
     sg, _, P, nr = SIGMAS[BWD_SIGMA]
-    kms = statistics.mean(r[len(SIGMAS)] for r in kern_ms)
-    # pass B over every tile, pass A over the replayed ones (none when the
-    # training forward stored the tile records)
-    flops = bcnt[2] * adjoint_tile_flops(P, nr, DIM, replay=False) + bcnt[3] * tile_flops(P, nr, DIM)
-    roof.append({"sigma": sg, "order": P, "rings": nr, "kernel": "bwd_kernel (adjoint)",
-                 "kernel_ms": round(kms, 4), "flops_per_launch": flops,
-                 "achieved": round(flops / (kms * 1e-3) / 1e12, 3)})
+    kms = statistics.mean(r[0] for r in b_kern)
+    entry(f"fwd_kernel<P={P},D=16> (training: keeps the strip seams)", kms,
+          bcnt[0] * useful_tile_flops(P, nr, DIM), bcnt[0] * tile_flops(P, nr, DIM), sg, P, nr)
+    kms = statistics.mean(r[1] for r in b_kern)
+    # pass B over every tile (useful: twice the forward's work); pass A's
+    # replay of the forward is recomputation (executed, not useful)
+    entry(f"bwd_kernel<P={P},D=16> (adjoint, recomputes each strip from its seam)", kms,
+          bcnt[2] * useful_tile_flops(P, nr, DIM, adjoint=True),
+          bcnt[2] * adjoint_tile_flops(P, nr, DIM, replay=False) + bcnt[3] * tile_flops(P, nr, DIM),
+          sg, P, nr, {"replayed_tiles": bcnt[3]})
     dom = max(range(len(roof)), key=lambda k: roof[k]["kernel_ms"])
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
@@ -304,65 +402,67 @@ def main():
             tj = json.load(f)
         with open(os.path.join(ROOT, "paper_2502_20392_gb300", "_build", "libsigk.sha256")) as f:
             digest = f.read().strip()
-        if tj.get("digest") == digest:
+        if tj.get("digest") == digest and tj.get("kernel") == roof[dom]["kernel"]:
             traffic = tj.get("bytes_per_launch")
     except (OSError, ValueError):
         traffic = None
     roofline = {"bound": "alu", "achieved": roof[dom]["achieved"], "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(roof[dom]["achieved"] / FP32_PEAK_TFLOPS, 4),
-                "traffic": traffic,
-                "kernel": roof[dom].get("kernel", f"fwd_kernel<P={roof[dom]['order']},D=16>"),
-                "per_launch": roof}
-    fwd_ms = sum(statistics.mean(r[k] for r in kern_ms) for k in range(len(SIGMAS)))
+                "unit": "TFLOP/s", "frac": roof[dom]["frac"], "traffic": traffic,
+                "kernel": roof[dom]["kernel"],
+                "work_model": "useful flops = 2 x (d + sum_{m=1..n} (2(P-m)+1) + 2P) per tile; "
+                              "adjoint 2x the forward; peak = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "executed_tflops": roof[dom]["executed_tflops"], "per_launch": roof}
 
-    # end-to-end through the public API: pinned host inputs -> device, both
-    # Gram calls, Gram matrices -> pinned host, every step
-    h_pts = [torch.from_numpy(p).pin_memory() for p, _ in host]
-    h_len = [torch.from_numpy(l).pin_memory() for _, l in host]
-    h_out = [torch.empty((N_PATHS, N_PATHS), dtype=torch.float64).pin_memory() for _ in SIGMAS]
-    d_pts = [torch.empty_like(x) for x in X]
-    d_len = [torch.empty_like(x) for x in L]
-    h_grad = torch.empty_like(h_pts[BWD_SIGMA]).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in h_pts + h_len)
-    d2h = sum(t.numel() * t.element_size() for t in h_out + [h_grad])
-    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        e_s[i].record()
-        for k in range(len(SIGMAS)):
-            d_pts[k].copy_(h_pts[k], non_blocking=True)
-            d_len[k].copy_(h_len[k], non_blocking=True)
-        gX = step(pts=d_pts, lens=d_len)
-        for k in range(len(SIGMAS)):
-            h_out[k].copy_(G[k], non_blocking=True)
-        h_grad.copy_(gX, non_blocking=True)
-        e_e[i].record()
-    torch.cuda.synchronize()
+    # end to end through the public API: pinned host inputs -> device, the
+    # calls, results -> pinned host, every step
+    h_in = [torch.from_numpy(p).pin_memory() for p, _ in host] + \
+           [torch.from_numpy(l).pin_memory() for _, l in host]
+    d_in = [torch.empty_like(x) for x in X] + [torch.empty_like(x) for x in L]
+    h_G = [torch.empty((N_PATHS, N_PATHS), dtype=torch.float64).pin_memory() for _ in SIGMAS]
+    e2e_ms = e2e_loop(fwd_step, h_in, d_in, lambda res: res, h_G, args.steps, flush)
+    h_inb = [h_in[BWD_SIGMA], h_in[len(SIGMAS) + BWD_SIGMA]]
+    d_inb = [d_in[BWD_SIGMA], d_in[len(SIGMAS) + BWD_SIGMA]]
+    h_Gb = torch.empty((N_PATHS, N_PATHS), dtype=torch.float64).pin_memory()
+    h_grad = torch.empty_like(h_inb[0]).pin_memory()
+    e2e_fb_ms = e2e_loop(fb_step, h_inb, d_inb, lambda res: res, [h_Gb, h_grad], args.steps, flush)
     for ws in wss + [bws]:
         sigk.sync_status(ws)
-    e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(e_s, e_e))
     if world > 1:
         e2e_ms = max_over_ranks(e2e_ms, dev, dist)
+        e2e_fb_ms = max_over_ranks(e2e_fb_ms, dev, dist)
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = sum(t.numel() * t.element_size() for t in h_G)
+    h2d_fb = sum(t.numel() * t.element_size() for t in h_inb)
+    d2h_fb = h_Gb.numel() * h_Gb.element_size() + h_grad.numel() * h_grad.element_size()
+    ws_fb = sigk.backward_workspace_size(sigk.OP_GRAM, N_PATHS, 0, DIM, bopts)
+    ws_rec = sigk.backward_workspace_size(
+        sigk.OP_GRAM, N_PATHS, 0, DIM, sigk.Opts(order=Pb, rings=nrb, max_len=N_SEG))
 
     line = {
         "metric": METRIC,
-        "value": value,
-        "fwd_only": {"value": cells * world / (fwd_ms * 1e-3), "unit": "cells/s",
-                     "ms": fwd_ms, "note": "forward solver kernels of both Grams alone"}, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (float-float corner, f64 reductions)",
         "data": "synthetic (seeded Brownian, PCG64)",
         "config": {"workload": "gram_B64_L1024_d16_sigma1+4", "paths": N_PATHS, "segments": N_SEG,
-                   "d": DIM, "sigmas": [s for s, *_ in SIGMAS],
-                   "order_rings": [[P, nr] for _, _, P, nr in SIGMAS],
+                   "d": DIM, "sigmas": [s_ for s_, *_ in SIGMAS],
+                   "order_rings": [[P_, nr_] for _, _, P_, nr_ in SIGMAS],
                    "unique_pairs_per_gram": pairs_of_gram(N_PATHS), "l2": "flushed between steps",
-                   "step": "forward Gram (sigma 1 and 4; sigma 1 as the training forward "
-                           "that keeps the adjoint's state) + adjoint of the sigma=1 Gram "
+                   "step": "forward: the Grams for sigma = 1 and sigma = 4 (inference); "
+                           "fwd_bwd: training forward + adjoint of the sigma = 1 Gram "
                            "(upstream: fixed dense weights)",
                    "parallelism": f"independent batch per rank x{world}"},
-        # per step: planner + solver for each Gram, adjoint set-up + adjoint
-        "gpu_launches": (2 * len(SIGMAS) + 2) * args.steps,
+        "fwd_bwd": {"value": cells_fb * world / (ms_fb * 1e-3), "unit": "cells/s", "ms_per_step": ms_fb,
+                    "cells_per_step": cells_fb,
+                    "note": "training forward keeps only the 32-row strip seams (checkpointed "
+                            "wavefront boundaries); the adjoint recomputes each strip from its seam",
+                    "workspace_bytes": ws_fb, "workspace_bytes_with_stored_tile_records": ws_rec,
+                    "e2e": {"value": cells_fb * world / (e2e_fb_ms * 1e-3), "unit": "cells/s",
+                            "h2d_bytes_per_step": h2d_fb, "d2h_bytes_per_step": d2h_fb,
+                            "ms_per_step": e2e_fb_ms}},
+        # per forward step: planner + solver per Gram; per fwd_bwd step:
+        # planner, training forward, adjoint set-up, adjoint
+        "gpu_launches": 2 * len(SIGMAS) * args.steps + 4 * args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": cells * world / (e2e_ms * 1e-3), "unit": "cells/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
@@ -372,26 +472,44 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         host_G = [g.cpu().numpy() for g in G]
-        vals, secs, thr = oracle_sample(host, ORACLE_SAMPLE_PAIRS)
-        errs = []
-        for (idx, ref), Gk in zip(vals, host_G):
-            for (a, b), r in zip(idx, ref):
-                e = abs(Gk[a, b] - r) / max(abs(r), 1e-300)
-                cs_scale = (abs(Gk[a, a] * Gk[b, b])) ** 0.5
-                if abs(r) < 1e-2 * cs_scale:  # near-zero cross entry: Cauchy-Schwarz scale
-                    e = min(e, abs(Gk[a, b] - r) / cs_scale)
-                errs.append(e)
+        vals, secs, thr = oracle_sample(host, ORACLE_SAMPLE_PAIRS, seed=11)
+        errs = [rel_err_entry(Gk, a, b, r) for (idx, ref), Gk in zip(vals, host_G)
+                for (a, b), r in zip(idx, ref)]
         n_cells = sum(len(idx) for idx, _ in vals) * N_SEG * N_SEG
         line["cpu_baseline"] = {"value": n_cells / secs, "unit": "cells/s", "cores": thr,
                                 "kind": "oracle",
-                                "sample": f"first {ORACLE_SAMPLE_PAIRS} upper-triangle pairs of each "
+                                "sample": f"{ORACLE_SAMPLE_PAIRS} random upper-triangle pairs of each "
                                           f"Gram ({n_cells:.3e} cells), FP64 tile series N=24, "
                                           f"OpenMP over pairs, {secs:.1f} s"}
         line["rel_err_vs_oracle_sample"] = max(errs)
+        gb = Gb.cpu().numpy()
+        line["fwd_bwd"]["rel_err_vs_oracle_sample"] = max(
+            rel_err_entry(gb, a, b, r) for (a, b), r in zip(*vals[BWD_SIGMA]))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_large_d():
+    """64 ragged pairs of 1500-2048 segments, d = 256, sigma in [0.5, 1.5]:
+    the two-phase kernel (increment Gram, then the sweep), one warm-up call
+    and one measured call.  The inputs exceed the 129 MB L2 while the device
+    footprint stays at a few GB (for profiler captures of that kernel)."""
+    import torch
+
+    from paper_2502_20392_gb300 import build, sigk, synth
+    build.build()
+    sigk.load()
+    (X, lx), (Y, ly) = synth.ragged_pairs(64, 1500, 2048, 256, 0.5, 1.5, seed=4401)
+    a = [torch.from_numpy(v).cuda() for v in (X, lx, Y, ly)]
+    o = sigk.Opts(order=12, rings=6, max_len=2048)
+    ws = sigk.Workspace()
+    for _ in range(2):
+        k = sigk.pairs(*a, opts=o, ws=ws)
+    torch.cuda.synchronize()
+    assert torch.isfinite(k).all()
+    return 0
 
 
 def run_sweep(args):
@@ -584,18 +702,22 @@ def run_configs(timed, emit, dev):
 
 def run_reference(args, world, rank):
     """Reference arm: the FP64 oracle, timed as it stands on the host cores, on
-    a bounded sample of the workload per step (rank 0 only)."""
+    a bounded sample of the workload per step (rank 0 only): per step and
+    sigma, as many random pairs of the Gram as the oracle has threads (it
+    parallelises over pairs), so that every host core works."""
     if rank != 0:
         return
+    import oracle
     from paper_2502_20392_gb300 import synth
-    host = [synth.workload_gram_1024(s, seed) for s, seed, _, _ in SIGMAS]
-    per_step = max(1, ORACLE_SAMPLE_PAIRS // 4)
-    for _ in range(args.warmup):
-        oracle_sample(host, 1)
+    oracle.build()
+    host = [synth.workload_gram_1024(s_, seed) for s_, seed, _, _ in SIGMAS]
+    per_step = max(ORACLE_SAMPLE_PAIRS, oracle.num_threads())
+    for w in range(args.warmup):
+        oracle_sample(host, 1, seed=1000 + w)
     times = []
     thr = 1
-    for _ in range(args.steps):
-        _, secs, thr = oracle_sample(host, per_step)
+    for i in range(args.steps):
+        _, secs, thr = oracle_sample(host, per_step, seed=2000 + i)
         times.append(secs)
     n_cells = len(SIGMAS) * per_step * N_SEG * N_SEG
     v = n_cells / statistics.mean(times)
@@ -605,12 +727,12 @@ def run_reference(args, world, rank):
             "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Brownian, PCG64)",
             "config": {"workload": "gram_B64_L1024_d16_sigma1+4",
-                       "sample": f"{per_step} pairs per sigma per step",
+                       "sample": f"{per_step} random pairs per sigma per step",
                        "step": "forward only: the FP64 oracle has no adjoint (its gradient is by "
                                "finite differences), so every sampled cell is a forward cell"},
             "cpu_baseline": {"value": v, "unit": "cells/s", "cores": thr, "kind": "oracle",
-                             "sample": f"{per_step} upper-triangle pairs per sigma per step, FP64 "
-                                       f"tile series N=24, OpenMP over pairs"},
+                             "sample": f"{per_step} random upper-triangle pairs per sigma per step, "
+                                       f"FP64 tile series N=24, OpenMP over pairs"},
             "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

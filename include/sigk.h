@@ -59,7 +59,10 @@ typedef enum {
     SIGK_ERR_ACCURACY = -7,   /* sigk_plan: no order up to 16 meets the tolerance, even
                                  at the finest refinement tried (*opts_out still holds
                                  that finest plan) */
-    SIGK_ERR_UNSUPPORTED = -8 /* a combination this library does not provide */
+    SIGK_ERR_UNSUPPORTED = -8, /* a combination this library does not provide */
+    SIGK_ERR_BOUNDS = -9      /* a device-side bounds check failed (only in a library
+                                 built with SIGK_DEBUG, which checks every work item's
+                                 buffer regions before touching them) */
 } sigk_status;
 
 /* Operation codes for sigk_workspace_size / sigk_plan. */
@@ -86,14 +89,23 @@ enum {
                                   any, longest pairs first, whenever the ring
                                   for whole strips fits in 8 GiB.  Results are
                                   identical; only the schedule differs. */
-    SIGK_FLAG_REPLAY = 32      /* sigk_backward: never store the tile records;
+    SIGK_FLAG_REPLAY = 32,     /* sigk_backward: never store the tile records;
                                   the adjoint replays every strip from its
                                   stored seam instead (smaller workspace, more
                                   arithmetic).  Results are identical. */
+    SIGK_FLAG_TEST_WITHHOLD_SEAM = 64  /* fault-injection hook for tests of the
+                                  bounded waits: in the inference forward of
+                                  sigk_pairs / sigk_gram / sigk_mmd (d <= 16),
+                                  the first work item of the schedule never
+                                  publishes its outgoing seam, so the strip that
+                                  consumes it waits until wait_ms runs out and
+                                  the call reports SIGK_ERR_TIMEOUT through
+                                  sigk_sync_status; its outputs are then
+                                  undefined.  No other effect. */
 };
 
 /* Truncation and scheduling parameters.  NULL = defaults (order 8, rings 4,
- * max_len 8193).
+ * max_len 8193, wait_ms 4000).
  *   order: degree P of the edge polynomials (the truncation order N of the
  *          coefficient matrices, App. A.7); supported 4..16, rounded up to an
  *          even value.
@@ -114,7 +126,12 @@ enum {
  *            tile satisfies |c| <= refine_c by Cauchy-Schwarz.  Exact (the
  *            kernel is invariant under collinear insertion); it trades more
  *            tiles for tiles the series resolves in FP32 (large |c| needs
- *            orders and rings beyond 16 and 8, and negative c cancels). */
+ *            orders and rings beyond 16 and 8, and negative c cancels).
+ *   wait_ms: budget of every bounded inter-warp wait on the device, in
+ *            milliseconds (0 = 4000; at most 600000).  A wait that runs out
+ *            records SIGK_ERR_TIMEOUT, with the waited address, target and last
+ *            value seen in the workspace header, and makes every warp of the
+ *            launch return. */
 typedef struct {
     int order;
     int rings;
@@ -122,6 +139,7 @@ typedef struct {
     int grid_ctas;
     int64_t max_len;
     float refine_c;
+    int wait_ms;
 } sigk_opts;
 
 /* Device workspace bytes needed by sigk_pairs/sigk_gram/sigk_mmd for the

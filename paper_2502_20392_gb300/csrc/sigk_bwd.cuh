@@ -55,6 +55,10 @@ struct BwdArgs {
     int* item_counter;
     int* status;
     unsigned long long* counters;
+    // extents, for the bounds checks of SIGK_DEBUG builds
+    int64_t store_cap;           // floats of store
+    int64_t rec_cap;             // floats of rec_store
+    int64_t rec_total;           // floats of the per-warp replay records
 };
 
 template <int P, int D>
@@ -136,6 +140,23 @@ __global__ void __launch_bounds__(128, bwd_min_blocks(P, D)) bwd_kernel(BwdArgs 
         const bool has_row = row < L1;
         const float* st_base = A.store + A.store_off[lo_p];
         bool ok = true;
+#ifdef SIGK_DEBUG
+        {
+            // the regions this item touches lie inside their buffers
+            const int RRd = A.rec_off != nullptr ? A.rec_rows : 1;
+            bool in = dbg_in(A.status, 21, lo_p, A.n_pairs - 1) &&
+                      dbg_in(A.status, 22, item % A.nslot, A.nslot - 1) &&
+                      dbg_in(A.status, 23, ir.prev >= 0 ? ir.prev % A.nslot : 0, A.nslot - 1) &&
+                      dbg_in(A.status, 24, s > 0 ? A.store_off[lo_p] + (int64_t)s * L2 * S : 0, A.store_cap);
+            if (in && A.rec_off != nullptr)
+                in = dbg_in(A.status, 25, A.rec_off[lo_p] + (int64_t)(s / RRd + 1) * (L2 + 32) * 32 * RRd * rec_floats(P),
+                            A.rec_cap);
+            if (in && A.rec_off == nullptr)
+                in = dbg_in(A.status, 26, (int64_t)(L2 + 31) * 32 * rec_floats(P), A.rec_stride) &&
+                     dbg_in(A.status, 27, (int64_t)(gwarp + 1) * A.rec_stride, A.rec_total);
+            if (!__all_sync(kFull, in)) break;
+        }
+#endif
 
         float dx[D];
 #pragma unroll

@@ -48,6 +48,7 @@ struct Opts {
     int grid_ctas;
     int64_t max_len;
     float refine_c;  // 0: no refinement
+    int wait_ms;     // bounded-wait budget
 };
 
 static bool resolve_opts(const sigk_opts* o, Opts* r) {
@@ -57,6 +58,7 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
     r->grid_ctas = 0;
     r->max_len = 8193;
     r->refine_c = 0.0f;
+    r->wait_ms = 4000;
     if (o) {
         if (o->order) r->order = o->order;
         if (o->rings) r->rings = o->rings;
@@ -64,7 +66,9 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
         r->grid_ctas = o->grid_ctas;
         if (o->max_len > 0) r->max_len = o->max_len;
         r->refine_c = o->refine_c;
+        if (o->wait_ms) r->wait_ms = o->wait_ms;
     }
+    if (r->wait_ms < 1 || r->wait_ms > 600000) return false;
     if (!(r->refine_c >= 0.0f) || r->refine_c > 1e30f) return false;
     if (r->order < 4 || r->order > kMaxP) return false;
     r->order += (r->order & 1);
@@ -358,8 +362,10 @@ struct Header {
     long long train_sig;  // signature of the training forward whose state the workspace holds (0: none)
     int pad2[10];
     long long diag[3];  // first timed-out wait: address, target, value seen (byte 128)
+    long long wait_ns;  // budget of the bounded waits of the current launch (byte 152)
 };
 static_assert(offsetof(Header, diag) == 128, "record_timeout writes the diagnosis at byte 128");
+static_assert(offsetof(Header, wait_ns) == kHdrWaitNs, "wait_budget reads the budget at kHdrWaitNs");
 static_assert(sizeof(Header) <= 256, "the header occupies the first 256 bytes of the workspace");
 
 // ---------------------------------------------------------------------------
@@ -402,6 +408,7 @@ struct PlanArgs {
     int64_t out_ld;     // leading dimension of the Gram output
     // training (backward) extras; train == 0 leaves them unused
     int phase;          // 1: prefix sums; 2: pair table, items, resets; 3: both
+    long long wait_ns;  // budget of the bounded waits (written to the header)
     int train;
     int stride;         // seam entry floats (P + 4)
     int64_t store_cap;  // floats available for the forward seam store
@@ -567,6 +574,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
             bad = 0;
             A.hdr->status = 0;  // errors are reported per call
             A.hdr->train_sig = 0;  // no training state until this plan succeeds
+            A.hdr->wait_ns = A.wait_ns;
         }
         __syncthreads();
         block_exclusive_scan(A.len_x, A.n_x, A.ox, sh, true, A.inc_mode, &bad);
@@ -803,6 +811,7 @@ __global__ void adjoint_prep_kernel(PlanArgs A) {
         A.hdr->bwd_item_counter = 0;
         A.hdr->counters[2] = 0;
         A.hdr->counters[3] = 0;
+        A.hdr->wait_ns = A.wait_ns;
     }
     for (int64_t p = tid; p < A.n_pairs; p += nth) {
         int64_t a, b, o0, o1;
@@ -1075,6 +1084,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     pa.hdr = hdr;
     pa.out = out;
     pa.out_ld = out_ld;
+    pa.wait_ns = (long long)o.wait_ms * 1000000ll;
     if (train) {
         pa.train = 1;
         pa.stride = L.stride;
@@ -1121,6 +1131,13 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     sa.status = &hdr->status;
     sa.counters = hdr->counters;
     sa.out = out;
+    sa.withhold_first_seam = (o.flags & SIGK_FLAG_TEST_WITHHOLD_SEAM) && !train ? 1 : 0;
+    sa.nwords = (int32_t)L.nwords;
+    sa.store_cap = train ? L.store_floats : 0;
+    sa.rec_cap = L.stored_rec ? L.rstore_floats : 0;
+    sa.out_cap = op == SIGK_OP_PAIRS ? L.n_pairs
+                                     : (op == SIGK_OP_MMD ? (n_x + n_y) * (n_x + n_y)
+                                                          : n_x * (n_y > 0 ? n_y : n_x));
     if (train) {
         sa.store = (float*)(base + L.store);
         sa.store_off = pa.store_off;
@@ -1178,6 +1195,7 @@ static sigk_status launch_adjoint(int op, int64_t n_x, int64_t n_y, int d, const
     pa.bdone = (long long*)(base + L.bdone);
     pa.bnslot = L.bnslot;
     pa.train_sig = train_signature(op, n_x, n_y, d, o, L);
+    pa.wait_ns = (long long)o.wait_ms * 1000000ll;
     adjoint_prep_kernel<<<L.bgrid, 256, 0, stream>>>(pa);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "adjoint set-up launch");
@@ -1214,6 +1232,9 @@ static sigk_status launch_adjoint(int op, int64_t n_x, int64_t n_y, int d, const
     ba.item_counter = &hdr->bwd_item_counter;
     ba.status = &hdr->status;
     ba.counters = hdr->counters;
+    ba.store_cap = L.store_floats;
+    ba.rec_cap = L.stored_rec ? L.rstore_floats : 0;
+    ba.rec_total = L.stored_rec ? 0 : (int64_t)L.bnwarps * L.rec_stride;
     if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
     e = bwd_launch_dispatch(o.order, o.rings, dim_bucket(d), ba, L.bgrid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch");
@@ -1499,6 +1520,7 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     pa.hdr = (Header*)(base + L.hdr);
     pa.out = scratch_out;
     pa.out_ld = 0;
+    pa.wait_ns = (long long)o.wait_ms * 1000000ll;
     float* statbase = nullptr;
     if (op != SIGK_OP_PAIRS) {
         // Gram-shaped ops write k at a*ld+b; give them a large enough scratch
@@ -1586,6 +1608,7 @@ sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream) {
         const char* msg = h.status == kErrTimeout ? "a bounded device wait timed out"
                           : h.status == kErrNonfinite ? "non-finite value met on the device"
                           : h.status == kErrLength ? "a path length is out of range"
+                          : h.status == kErrBounds ? "a device-side bounds check failed (debug build)"
                                                    : "device error";
         return fail((sigk_status)h.status, msg);
     }

@@ -44,7 +44,7 @@ static __constant__ float c_inv_fact[34] = {1.0f, 1.0f, 0.5f, 0.166666667f, 0.04
 
 enum : int {
     kOK = 0, kErrArg = -1, kErrLength = -2, kErrNonfinite = -3, kErrWorkspace = -4,
-    kErrCuda = -5, kErrTimeout = -6
+    kErrCuda = -5, kErrTimeout = -6, kErrBounds = -9
 };
 
 struct PairDesc {
@@ -169,6 +169,14 @@ struct SolverArgs {
     // nullptr: the adjoint replays the strips instead.
     float* rec;
     const int64_t* rec_off;        // [n_pairs] float offsets into rec
+    // fault-injection hook (tests of the bounded waits): the schedule's first
+    // item does not publish its outgoing seam
+    int32_t withhold_first_seam;
+    // extents of the buffers above, for the bounds checks of SIGK_DEBUG builds
+    int32_t nwords;                // progress words (prod, cons, done)
+    int64_t store_cap;             // floats of store
+    int64_t rec_cap;               // floats of rec
+    int64_t out_cap;               // entries of out
 };
 
 // Tile records (layout above).  rec_put_head stores every pair but the last,
@@ -281,22 +289,52 @@ __device__ __forceinline__ void record_timeout(int* status, const void* p, long 
     }
 }
 
-// Bounded wait until *p >= target.  Gives up after ~4 s of wall time (or a
-// hard iteration cap), or as soon as another warp has recorded an error; on
-// time-out it records kErrTimeout.  Returns true when the condition holds.
+// Bounds checks of the SIGK_DEBUG build: a region a work item is about to
+// touch must lie inside its buffer.  On a violation the first one is recorded
+// (status kErrBounds; diagnosis: check site, offending offset, limit) and the
+// caller skips the access; in other builds the check is compiled out.
+__device__ __forceinline__ bool dbg_in(int* status, int site, long long off, long long lim) {
+#ifdef SIGK_DEBUG
+    if (off >= 0 && off <= lim) return true;
+    if (atomicCAS(status, 0, kErrBounds) == 0) {
+        long long* diag = reinterpret_cast<long long*>(status + 32);
+        diag[0] = site;
+        diag[1] = off;
+        diag[2] = lim;
+    }
+    return false;
+#else
+    (void)status; (void)site; (void)off; (void)lim;
+    return true;
+#endif
+}
+
+// Bounded wait until *p >= target.  Gives up after the call's wait budget
+// (the 64-bit word kHdrWaitNs bytes after the status word, in nanoseconds of
+// %globaltimer; 0 means 4 s), or a hard iteration cap, or as soon as another
+// warp has recorded an error; on time-out it records kErrTimeout.  Returns
+// true when the condition holds.
 constexpr unsigned long long kWaitNs = 4000000000ull;
 constexpr int kWaitMaxIter = 1 << 24;
+constexpr int kHdrWaitNs = 152;  // byte offset of the budget from the status word
+
+__device__ __forceinline__ unsigned long long wait_budget(const int* status) {
+    const unsigned long long b =
+        *reinterpret_cast<const volatile unsigned long long*>(reinterpret_cast<const char*>(status) + kHdrWaitNs);
+    return b ? b : kWaitNs;
+}
 
 __device__ __forceinline__ bool wait_ge_u64(const unsigned long long* p,
                                             unsigned long long target, int* status) {
     if (ld_acquire_u64(p) >= target) return true;
     const unsigned long long t0 = global_ns();
+    const unsigned long long budget = wait_budget(status);
     for (int it = 0; it < kWaitMaxIter; ++it) {
         __nanosleep(it < 64 ? 32 : 256);
         if (ld_acquire_u64(p) >= target) return true;
         if ((it & 31) == 31) {
             if (ld_volatile_s32(status) != 0) return false;
-            if (global_ns() - t0 > kWaitNs) break;
+            if (global_ns() - t0 > budget) break;
         }
     }
     record_timeout(status, p, (long long)target, (long long)ld_acquire_u64(p));
@@ -306,12 +344,13 @@ __device__ __forceinline__ bool wait_ge_u64(const unsigned long long* p,
 __device__ __forceinline__ bool wait_ge_s64(const long long* p, long long target, int* status) {
     if (ld_acquire_s64(p) >= target) return true;
     const unsigned long long t0 = global_ns();
+    const unsigned long long budget = wait_budget(status);
     for (int it = 0; it < kWaitMaxIter; ++it) {
         __nanosleep(it < 64 ? 32 : 256);
         if (ld_acquire_s64(p) >= target) return true;
         if ((it & 31) == 31) {
             if (ld_volatile_s32(status) != 0) return false;
-            if (global_ns() - t0 > kWaitNs) break;
+            if (global_ns() - t0 > budget) break;
         }
     }
     record_timeout(status, p, target, ld_acquire_s64(p));

@@ -206,8 +206,25 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
         // the seams are not reused and a slot's word could be overtaken)
         const int pw_in = train ? ir.prev : slot_in;
         const int pw_out = train ? item : slot_out;
+#ifdef SIGK_DEBUG
+        // the regions this item touches lie inside their buffers
+        ok = dbg_in(A.status, 1, lo_p, A.n_pairs - 1) && dbg_in(A.status, 2, slot_out, A.nslot - 1) &&
+             dbg_in(A.status, 3, slot_in, A.nslot - 1) && dbg_in(A.status, 4, pw_out, A.nwords - 1) &&
+             dbg_in(A.status, 5, has_in ? pw_in : 0, A.nwords - 1) &&
+             dbg_in(A.status, 6, pd.out0, A.out_cap - 1) && dbg_in(A.status, 7, pd.out1 < 0 ? 0 : pd.out1, A.out_cap - 1);
+        if (ok && train) {
+            // seams of strips s*R - 1 (read) .. min(s*R + R - 1, n32 - 2) (written)
+            const int last = min(s * R + R - 1, n32 - 2);
+            const int64_t base = st_pair - A.store;
+            if (has_out || R > 1) ok = dbg_in(A.status, 8, base + (int64_t)(last + 1) * L2 * S, A.store_cap);
+            if (ok && has_in) ok = dbg_in(A.status, 9, base + (int64_t)(s * R) * L2 * S, A.store_cap);
+        }
+        if constexpr (REC)
+            if (ok) ok = dbg_in(A.status, 10, (rec_item - A.rec) + (int64_t)(L2 + 32) * 32 * R * RS, A.rec_cap);
+        ok = __all_sync(kFull, ok);
+#endif
         // the slot we write must have been read by its previous consumer
-        if (has_out && !train) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
+        if (ok && has_out && !train) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
         const int T = L2 + 31;
         for (int t = 0; t < T && ok; ++t) {
             if ((t & 31) == 0 && t < L2) {
@@ -401,7 +418,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                     for (int idx = lane; idx < nb * S; idx += 32) __stcg(dst + idx, sout[idx]);
                     __threadfence();
                     __syncwarp();
-                    if (lane == 0)
+                    if (lane == 0 && !(A.withhold_first_seam && item == 0))
                         st_release_u64(&A.prod[pw_out],
                                        ((unsigned long long)item << 32) | (unsigned)(start + nb));
                 }

@@ -369,6 +369,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         const bool has_out = ir.next >= 0;
         const int i0 = s * 32;
         bool ok = true;
+#ifdef SIGK_DEBUG
+        {
+            // the strip scratch, seam slots and outputs of this item lie inside
+            // their buffers
+            const bool in = dbg_in(A.status, 31, lo_p, A.n_pairs - 1) &&
+                            dbg_in(A.status, 32, (int64_t)L2 * 32, cstride) &&
+                            dbg_in(A.status, 33, item % A.nslot, A.nslot - 1) &&
+                            dbg_in(A.status, 34, pd.out0, A.out_cap - 1) &&
+                            dbg_in(A.status, 35, pd.out1 < 0 ? 0 : pd.out1, A.out_cap - 1);
+            if (!__all_sync(kFull, in)) break;
+        }
+#endif
 
         // ---- phase 1: c[i0 + r][j] for r < 32, all j, into the scratch strip ----
         // FP64: the increments are staged unscaled and the refinement factor

@@ -24,8 +24,10 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sigk.h")
 
 OP_PAIRS, OP_GRAM, OP_MMD = 0, 1, 2
 FLAG_INCREMENTS, FLAG_GRAM_FULL, FLAG_MMD_BIASED, FLAG_FP64, FLAG_PAIR_MAJOR, FLAG_REPLAY = 1, 2, 4, 8, 16, 32
+FLAG_TEST_WITHHOLD_SEAM = 64
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_LENGTH", -3: "ERR_NONFINITE", -4: "ERR_WORKSPACE",
-          -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_ACCURACY", -8: "ERR_UNSUPPORTED"}
+          -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_ACCURACY", -8: "ERR_UNSUPPORTED",
+          -9: "ERR_BOUNDS"}
 ERR_ACCURACY = -7
 
 
@@ -38,7 +40,7 @@ class SigkError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("rings", ctypes.c_int), ("flags", ctypes.c_int),
                 ("grid_ctas", ctypes.c_int), ("max_len", ctypes.c_int64),
-                ("refine_c", ctypes.c_float)]
+                ("refine_c", ctypes.c_float), ("wait_ms", ctypes.c_int)]
 
 
 @dataclass
@@ -49,10 +51,11 @@ class Opts:
     grid_ctas: int = 0
     max_len: int = 8193
     refine_c: float = 0.0
+    wait_ms: int = 0
 
     def c(self) -> _Opts:
         return _Opts(self.order, self.rings, self.flags, self.grid_ctas, self.max_len,
-                     self.refine_c)
+                     self.refine_c, self.wait_ms)
 
 
 _lib = None
@@ -67,11 +70,13 @@ def exported_functions() -> list[str]:
 
 
 def load(path: str | None = None):
-    """Load libsigk.so (built by paper_2502_20392_gb300.build)."""
+    """Load libsigk.so (built by paper_2502_20392_gb300.build); `path`, else
+    the SIGK_LIB environment variable, selects another build of it (e.g. the
+    bounds-checked one of build(debug=True))."""
     global _lib
     if _lib is not None:
         return _lib
-    path = path or _LIB_PATH
+    path = path or os.environ.get("SIGK_LIB") or _LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libsigk.so not built ({path}); run __graft_entry__.build()")
     lib = ctypes.CDLL(path)
@@ -427,7 +432,7 @@ def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | 
     else:
         n_y = 0 if op == OP_GRAM else n_x
     big = Opts(order=16, rings=1, flags=opts.flags, grid_ctas=opts.grid_ctas, max_len=opts.max_len,
-               refine_c=opts.refine_c)
+               refine_c=opts.refine_c, wait_ms=opts.wait_ms)
     nb = workspace_size(op, n_x, n_y if op != OP_PAIRS else n_x, d, big)
     npairs = n_x if op == OP_PAIRS else (n_x * (n_x + 1) // 2 if n_y == 0 else
                                          (n_x * n_y if op == OP_GRAM else (n_x + n_y) ** 2))
@@ -445,4 +450,4 @@ def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | 
     else:
         _check(st)
     return Opts(o_out.order, o_out.rings, o_out.flags, o_out.grid_ctas, o_out.max_len,
-                o_out.refine_c)
+                o_out.refine_c, o_out.wait_ms)

@@ -23,6 +23,26 @@ def test_flop_model():
     assert bench.tile_flops(4, 8, 4) == bench.tile_flops(4, 4, 4)
 
 
+def test_useful_work_model():
+    import bench
+    # algorithmic FMAs per tile: d + sum_{m=1..n} (2(P - m) + 1) + 2P, written
+    # out for the bench's two launches (P = 8, n = 4 and P = 16, n = 6, d = 16)
+    assert bench.useful_tile_fma(8, 4, 16) == 16 + (15 + 13 + 11 + 9) + 16 == 80
+    assert bench.useful_tile_fma(16, 6, 16) == 16 + (31 + 29 + 27 + 25 + 23 + 21) + 32 == 204
+    assert bench.useful_tile_flops(8, 4, 16) == 160
+    assert bench.useful_tile_flops(8, 4, 16, adjoint=True) == 320
+    # the executed count is never below the useful one
+    for P, nr, d in ((4, 2, 4), (8, 4, 16), (16, 6, 16), (14, 6, 256)):
+        assert bench.tile_flops(P, nr, d) >= bench.useful_tile_flops(P, nr, d)
+
+
+def test_accuracy_sample_spans_the_gram():
+    import bench
+    idx = bench.sample_pairs(16, 11)
+    assert len(set(idx)) == 16 and all(a <= b for a, b in idx)
+    assert len({a for a, _ in idx}) > 4  # not one row of the Gram
+
+
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                         "--steps", "1", "--warmup", "0"], capture_output=True, text=True,

@@ -65,3 +65,15 @@ def test_no_cpu_fallback_in_product_path():
                 with open(os.path.join(dirpath, f)) as fh:
                     src = fh.read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_wait_budget_is_validated_without_gpu(lib):
+    # the bounded-wait budget must lie in 1..600000 ms (0 selects 4000 ms);
+    # out-of-range budgets are rejected on the host before any CUDA call
+    from paper_2502_20392_gb300 import sigk
+    for bad in (-1, 600001):
+        o = sigk.Opts(wait_ms=bad).c()
+        assert lib.sigk_workspace_size(0, 4, 4, 4, ctypes.byref(o)) == 0
+        nz = ctypes.c_void_p(256)  # never dereferenced: the options are checked first
+        st = lib.sigk_pairs(nz, nz, nz, nz, 3, 4, nz, nz, 1 << 20, None, ctypes.byref(o))
+        assert st == -1 and b"sigk_opts" in lib.sigk_last_error()

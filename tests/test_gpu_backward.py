@@ -1,12 +1,14 @@
 """GPU parity of the adjoint (sigk_backward through the C-ABI, and the
 torch.autograd wrappers) against FP64 central finite differences of the oracle
 and the single-tile closed form.  Gradients are with respect to the points;
-the tolerance is 1e-4 relative to the largest gradient entry (the
-differentiation workload's tolerance)."""
+every checked coordinate must agree to 1e-4 relative (the differentiation
+workload's tolerance), except coordinates whose reference is below 1e-3 of the
+largest, which are held to 1e-7 of the largest in absolute terms."""
 import math
 
 import numpy as np
 import pytest
+from gradcheck import assert_grad_close
 from scipy.special import i1, j1
 
 pytestmark = pytest.mark.gpu
@@ -93,10 +95,8 @@ def test_pairs_gradient_vs_fd(S, orc, d):
             coords = rng.choice(g.size, size=min(12, g.size), replace=False)
             ref = fd_points(f, [xs[p], ys[p]], which, coords)
             got = g.reshape(-1)[coords]
-            scale = np.abs(ref).max()
             # the upstream weight w[p] is part of the computed gradient
-            np.testing.assert_allclose(got, ref * w[p], atol=1e-4 * scale * abs(w[p]),
-                                       err_msg=f"pair {p} side {which}")
+            assert_grad_close(got, ref * w[p])
 
 
 @pytest.mark.parametrize("order,rings", [(12, 6), (6, 4), (10, 6)])
@@ -112,14 +112,15 @@ def test_gram_self_gradient_vs_fd(S, orc, order, rings):
                           S.Opts(order=order, rings=rings, max_len=128))
     gX = synth.split(gX.cpu().numpy(), lens)
     ref_G = orc.series_gram(incs(paths))
-    # order 6 truncates at ~1e-6 relative on these paths
-    np.testing.assert_allclose(G.cpu().numpy(), ref_G, rtol=1e-5 if order >= 10 else 1e-4)
+    # order 6 truncates at 4.4e-7 relative on these paths (the oracle at
+    # N = 6 against N = 24), inside the 1e-5 tolerance
+    np.testing.assert_allclose(G.cpu().numpy(), ref_G, rtol=1e-5)
     for a in (0, 3):
         def f(pp):
             return float((W * orc.series_gram(incs(pp))).sum())
         coords = rng.choice(gX[a].size, size=10, replace=False)
         ref = fd_points(f, paths, a, coords)
-        np.testing.assert_allclose(gX[a].reshape(-1)[coords], ref, atol=1e-4 * np.abs(ref).max())
+        assert_grad_close(gX[a].reshape(-1)[coords], ref)
 
 
 def test_mmd_gradient_vs_fd(S, orc):
@@ -145,8 +146,7 @@ def test_mmd_gradient_vs_fd(S, orc):
         p = int(np.searchsorted(off, c, side="right") - 1)
         got.append(gX.reshape(-1)[c])
         ref.append(fd_points(f, xs + ys, p, [c - off[p]])[0])
-    got, ref = np.array(got), np.array(ref)
-    np.testing.assert_allclose(got, ref, atol=1e-4 * np.abs(ref).max())
+    assert_grad_close(np.array(got), np.array(ref))
 
 
 def test_autograd_matches_backward(S):
@@ -247,8 +247,8 @@ def test_gradient_with_refinement(S, orc):
         return orc.series_pair(*incs(pp), N=30)
     gx_ref = fd_points(f, xs, 0, range(xs[0].size))
     gy_ref = fd_points(f, xs, 1, range(xs[1].size))
-    np.testing.assert_allclose(gX.cpu().numpy().ravel(), gx_ref, atol=1e-4 * np.abs(gx_ref).max())
-    np.testing.assert_allclose(gY.cpu().numpy().ravel(), gy_ref, atol=1e-4 * np.abs(gy_ref).max())
+    assert_grad_close(gX.cpu().numpy().ravel(), gx_ref)
+    assert_grad_close(gY.cpu().numpy().ravel(), gy_ref)
 
 
 def test_backward_schedules_agree_bitwise(S):
@@ -335,4 +335,4 @@ def test_increments_mode_gradient_and_gram_xy(S, orc):
     for which, grads, p in ((0, gX, 1), (1, gY, 0)):
         coords = rng.choice(grads[p].size, size=8, replace=False)
         ref = fd_inc(which, p, coords)
-        np.testing.assert_allclose(grads[p].reshape(-1)[coords], ref, atol=1e-4 * np.abs(ref).max())
+        assert_grad_close(grads[p].reshape(-1)[coords], ref)

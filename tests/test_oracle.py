@@ -308,3 +308,85 @@ def test_statement_orientation_is_rejected(orc):
     k_chen = orc.chen_pair(dx, dy, 16)
     assert orc.series_pair(dx, dy) == pytest.approx(k_chen, rel=1e-12)
     assert abs(k_literal - k_chen) > 1e-2
+
+
+def _straight_batch(rng, n, d, lens_x, lens_y, scale=0.5):
+    """Ragged batch whose x_p are straight (collinear segments of varying
+    length along a fixed direction) and whose y_p are arbitrary: k(x_p, y_p) =
+    I0/J0 of <X_p, Y_p> with X_p, Y_p the total increments (straight-path
+    closed form), so every pair's value depends on which rows are its own."""
+    xs, ys = [], []
+    for p in range(n):
+        u = rng.standard_normal(d)
+        u /= np.linalg.norm(u)
+        r = rng.uniform(-0.2, 0.5, size=lens_x[p])
+        xs.append(r[:, None] * u[None, :])
+        ys.append(rng.standard_normal((lens_y[p], d)) * scale)
+    return xs, ys
+
+
+def test_series_pairs_ragged_packed_closed_form(orc):
+    # The batched pair routine on packed ragged inputs (one path of the batch
+    # has no segment): every value must be the straight-path closed form of
+    # its own pair.  A slip in the prefix offsets of either side would pair a
+    # path with a neighbour's rows and miss the closed form.
+    rng = np.random.default_rng(23)
+    lx = [3, 1, 7, 0, 5, 2]
+    ly = [4, 6, 1, 3, 0, 8]
+    xs, ys = _straight_batch(rng, 6, 3, lx, ly)
+    got = orc.series_pairs(xs, ys)
+    for p in range(6):
+        s = float(xs[p].sum(0) @ ys[p].sum(0)) if lx[p] and ly[p] else 0.0
+        assert got[p] == pytest.approx(bessel_k(s), rel=1e-13), p
+        assert got[p] == orc.series_pair(xs[p], ys[p])  # the same arithmetic per pair
+
+
+def test_series_gram_ragged_closed_form(orc):
+    # Gram of straight x_a (ragged) against arbitrary y_b (ragged): entry
+    # (a, b) is the closed form of <X_a, Y_b>; rows and columns may not mix.
+    rng = np.random.default_rng(29)
+    xs, _ = _straight_batch(rng, 4, 2, [2, 5, 1, 4], [1, 1, 1, 1])
+    ys = [rng.standard_normal((n, 2)) * 0.6 for n in (3, 1, 6)]
+    G = orc.series_gram(xs, ys)
+    for a in range(4):
+        for b in range(3):
+            s = float(xs[a].sum(0) @ ys[b].sum(0))
+            assert G[a, b] == pytest.approx(bessel_k(s), rel=1e-13), (a, b)
+
+
+def test_mmd_u_statistic_hand_expanded(orc):
+    # Two samples of two single-segment paths each: every kernel value is a
+    # Bessel closed form, and the unbiased MMD^2 with m = n = 2 expands by hand
+    # to k(x1,x2) + k(y1,y2) - (k(x1,y1) + k(x1,y2) + k(x2,y1) + k(x2,y2)) / 2
+    # (the diagonal terms drop out; each off-diagonal pair appears twice over
+    # m(m-1) = 2).  The biased form keeps the diagonals with weight 1/m^2.
+    x1, x2 = np.array([[0.7, -0.2]]), np.array([[0.1, 0.9]])
+    y1, y2 = np.array([[-0.4, 0.3]]), np.array([[1.1, 0.5]])
+
+    def k(a, b):
+        return bessel_k(float(a[0] @ b[0]))
+
+    cross = k(x1, y1) + k(x1, y2) + k(x2, y1) + k(x2, y2)
+    u = k(x1, x2) + k(y1, y2) - cross / 2
+    v = ((k(x1, x1) + 2 * k(x1, x2) + k(x2, x2)) / 4 + (k(y1, y1) + 2 * k(y1, y2) + k(y2, y2)) / 4
+         - cross / 2)
+    assert orc.mmd2([x1, x2], [y1, y2]) == pytest.approx(u, rel=1e-13)
+    assert orc.mmd2([x1, x2], [y1, y2], unbiased=False) == pytest.approx(v, rel=1e-13)
+
+
+def test_mmd_u_statistic_is_unbiased(orc):
+    # The U-statistic is an unbiased estimator of MMD^2, which is 0 when both
+    # samples come from one distribution: its mean over independent draws
+    # (single-segment paths, so each draw is cheap) is 0 within a few standard
+    # errors, while the V-statistic is biased upwards by the mean diagonal.
+    rng = np.random.default_rng(31)
+    us, vs = [], []
+    for _ in range(400):
+        xs = [rng.standard_normal((1, 2)) * 0.8 for _ in range(3)]
+        ys = [rng.standard_normal((1, 2)) * 0.8 for _ in range(3)]
+        us.append(orc.mmd2(xs, ys, N=16))
+        vs.append(orc.mmd2(xs, ys, N=16, unbiased=False))
+    us, vs = np.array(us), np.array(vs)
+    se = us.std(ddof=1) / math.sqrt(len(us))
+    assert abs(us.mean()) < 4 * se, (us.mean(), se)
+    assert vs.mean() > 10 * se
