@@ -163,11 +163,17 @@ class ClockSampler:
 
 def sample_pairs(n_pairs, seed):
     """n_pairs distinct upper-triangle entries (a, b), a <= b, of the Gram,
-    drawn uniformly over the whole matrix (seeded)."""
+    drawn uniformly over the whole matrix (seeded): a quarter of them on the
+    diagonal (the self-kernels, the largest values), the rest off it (cross
+    kernels, often a large cancellation measured on the Cauchy-Schwarz
+    scale)."""
     import numpy as np
-    tri = [(a, b) for a in range(N_PATHS) for b in range(a, N_PATHS)]
-    pick = np.random.default_rng(seed).choice(len(tri), size=min(n_pairs, len(tri)), replace=False)
-    return [tri[i] for i in sorted(pick)]
+    rng = np.random.default_rng(seed)
+    n_diag = min(n_pairs // 4, N_PATHS)
+    off = [(a, b) for a in range(N_PATHS) for b in range(a + 1, N_PATHS)]
+    pick = rng.choice(len(off), size=min(n_pairs - n_diag, len(off)), replace=False)
+    diag = rng.choice(N_PATHS, size=n_diag, replace=False)
+    return sorted([off[i] for i in pick] + [(int(a), int(a)) for a in diag])
 
 
 def oracle_sample(pts_lens, n_pairs, seed=0):
@@ -560,12 +566,17 @@ def run_sweep(args):
             pts, lens = synth.brownian(16, 512, d, 1.0, seed=8000 + d)
             X, L = torch.from_numpy(pts).to(dev), torch.from_numpy(lens).to(dev)
             o = sigk.plan(sigk.OP_GRAM, X, L, None, None, tol=1e-6, opts=sigk.Opts(max_len=513))
-            ws = sigk.Workspace()
-            ms = timed(lambda: sigk.gram(X, L, opts=o, ws=ws, check=False))
             cells = 136 * 512 * 512
-            emit(sweep="dimension", d=d, metric="cells/s", value=cells / (ms * 1e-3), ms=ms,
-                 kernel="register" if d <= 16 else "two-phase",
-                 opts=dict(order=o.order, rings=o.rings, refine_c=o.refine_c))
+            variants = [(0, "register" if d <= 16 else ("tensor-core" if d <= 1024 else "fma-gemm"))]
+            if 16 < d <= 1024:
+                variants.append((sigk.FLAG_NO_TENSOR, "fma-gemm"))
+            for flag, name in variants:
+                oo = sigk.Opts(order=o.order, rings=o.rings, refine_c=o.refine_c, max_len=o.max_len,
+                               flags=o.flags | flag)
+                ws = sigk.Workspace()
+                ms = timed(lambda: sigk.gram(X, L, opts=oo, ws=ws, check=False))
+                emit(sweep="dimension", d=d, metric="cells/s", value=cells / (ms * 1e-3), ms=ms,
+                     kernel=name, opts=dict(order=o.order, rings=o.rings, refine_c=o.refine_c))
     elif args.sweep == "configs":
         run_configs(timed, emit, dev)
     else:

@@ -93,6 +93,12 @@ enum {
                                   the adjoint replays every strip from its
                                   stored seam instead (smaller workspace, more
                                   arithmetic).  Results are identical. */
+    SIGK_FLAG_NO_TENSOR = 128, /* d > 16: form the increment Gram with FP32 FMA
+                                  (a register-blocked micro-GEMM, FP32 accuracy)
+                                  instead of the tensor cores (exact 8-bit digit
+                                  products accumulated on tcgen05, float-float
+                                  accuracy; used for 16 < d <= 1024).  For
+                                  comparisons. */
     SIGK_FLAG_TEST_WITHHOLD_SEAM = 64  /* fault-injection hook for tests of the
                                   bounded waits: in the inference forward of
                                   sigk_pairs / sigk_gram / sigk_mmd (d <= 16),
@@ -278,7 +284,11 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
                       sigk_opts* opts_out);
 
 /* Waits for `stream`, then returns and clears the device status recorded in
- * ws by earlier calls (SIGK_OK, SIGK_ERR_TIMEOUT or SIGK_ERR_NONFINITE). */
+ * ws by earlier calls: SIGK_OK; SIGK_ERR_TIMEOUT, SIGK_ERR_LENGTH or
+ * SIGK_ERR_BOUNDS, after which the call's outputs are undefined (the launch
+ * stopped); or SIGK_ERR_NONFINITE, when some output is NaN or infinite (from
+ * non-finite input data, or beyond the exponent range), in which case every
+ * other output is valid. */
 sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream);
 
 /* Counters of the last call on this workspace (synchronises `stream`):

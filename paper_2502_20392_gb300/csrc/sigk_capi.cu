@@ -21,6 +21,7 @@
 #include "sigk_bwd.cuh"
 #include "sigk_stats.cuh"
 #include "sigk_device.cuh"
+#include "sigk_fwd_tc.cuh"
 #include "sigk_launch.h"
 
 namespace sigk {
@@ -140,6 +141,16 @@ static cudaError_t fwd_cm_launch_dispatch(int P, int NR, bool f64, const SolverA
     return cudaErrorInvalidValue;
 }
 
+static int fwd_tc_info_dispatch(int P, int NR, KernelInfo* info) {
+    SIGK_DISPATCH_PNR(fwd_tc_info, info)
+    return -1;
+}
+
+static cudaError_t fwd_tc_launch_dispatch(int P, int NR, const TcArgs& a, int grid, cudaStream_t s) {
+    SIGK_DISPATCH_PNR(fwd_tc_launch, a, grid, s)
+    return cudaErrorInvalidValue;
+}
+
 static int bwd_info_dispatch(int P, int NR, int D, KernelInfo* info) {
     SIGK_DISPATCH_PNR(bwd_info, D, info)
     return -1;
@@ -169,6 +180,12 @@ struct Layout {
     bool train;
     bool cm;             // two-phase kernel (d > 16, or FP64)
     bool f64;            // FP64 solve (SIGK_FLAG_FP64)
+    bool tc;             // tensor-core increment Gram (d > 16, FP32, d <= kTcMaxDim)
+    int d_pad;           // its digit rows: d rounded up to 16
+    int64_t n_slots;     // paths of the call (digit cache slots)
+    size_t ycache, yexp, ablk, aexp, cst;  // its sections
+    int64_t cst_stride;
+    int strip_quantum;   // the pair table's strips per work unit (tc: 4)
     size_t elem;         // bytes per seam / strip element (4 or 8)
     size_t cscratch;     // its per-warp coefficient strips
     int64_t cstride;
@@ -233,7 +250,11 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
             L->rstore_floats = (int64_t)fl;
         }
     }
-    const int qinfo = L->cm ? fwd_cm_info_dispatch(o.order, o.rings, L->f64, &L->info)
+    L->tc = L->cm && !L->f64 && !train && d <= kTcMaxDim && !(o.flags & SIGK_FLAG_NO_TENSOR);
+    L->d_pad = (d + kTcK - 1) / kTcK * kTcK;
+    L->strip_quantum = L->tc ? 4 : 1;
+    const int qinfo = L->tc ? fwd_tc_info_dispatch(o.order, o.rings, &L->info)
+                      : L->cm ? fwd_cm_info_dispatch(o.order, o.rings, L->f64, &L->info)
                             : fwd_info_dispatch(o.order, o.rings, D, L->stored_rec ? 1 : 0, &L->info);
     if (qinfo != 0 || L->info.blocks_per_sm <= 0)
         return fail(SIGK_ERR_CUDA, "kernel occupancy query failed");
@@ -244,6 +265,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     const int full_grid = sms * L->info.blocks_per_sm;
     L->grid = o.grid_ctas > 0 ? (o.grid_ctas < full_grid ? o.grid_ctas : full_grid) : full_grid;
     L->nwarps = L->grid * (L->info.threads / 32);
+    if (L->tc) allow_sm = false;  // blocks of four consecutive strips: pair-major schedules only
     // the pair table counts strips of 32 * R rows; in training it counts
     // 32-row strips (the adjoint's unit) and the forward takes R of them
     L->rows_per_strip = train ? 32 : 32 * L->info.rows_per_lane;
@@ -306,7 +328,20 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     if (op == SIGK_OP_MMD) off = align256(off + sizeof(double) * (size_t)(n_x + n_y) * (n_x + n_y));
     L->cstride = 0;
     L->cscratch = off;
-    if (L->cm) {  // one [max_len][32] coefficient strip per warp
+    L->n_slots = n_x + L->n_paths_y;
+    L->cst_stride = 0;
+    L->ycache = L->yexp = L->ablk = L->aexp = L->cst = off;
+    if (L->tc) {
+        // digits of every path's first max_len segments, exponents; per CTA
+        // the digits of a block's rows and the skewed (c, clo) of its strips
+        L->ycache = off;
+        off = align256(off + sizeof(uint16_t) * (size_t)L->n_slots * o.max_len * kTcDigits * L->d_pad);
+        L->yexp = off; off = align256(off + sizeof(int32_t) * (size_t)L->n_slots * o.max_len);
+        L->ablk = off; off = align256(off + sizeof(uint16_t) * (size_t)L->grid * kTcDigits * kTcRows * L->d_pad);
+        L->aexp = off; off = align256(off + sizeof(int32_t) * (size_t)L->grid * kTcRows);
+        L->cst_stride = (o.max_len + 32 + kTcPF) * 32;
+        L->cst = off; off = align256(off + sizeof(float2) * (size_t)L->grid * 4 * L->cst_stride);
+    } else if (L->cm) {  // one [max_len][32] coefficient strip per warp
         L->cstride = 32 * ((o.max_len + 31) & ~(int64_t)31);
         off = align256(off + L->elem * (size_t)L->nwarps * L->cstride);
     }
@@ -355,7 +390,7 @@ struct Header {
     int status;
     int item_counter;
     int bwd_item_counter;
-    int pad;
+    int nonfinite;      // a non-finite output was met (record_nonfinite writes status + 3)
     unsigned long long counters[4];
     int sched[4];  // schedule: mode, n_levels, n_items (Schedule::hdr)
     int sched2[4];  // training forward's schedule (items of 2^fwd_shift strips)
@@ -366,6 +401,7 @@ struct Header {
 };
 static_assert(offsetof(Header, diag) == 128, "record_timeout writes the diagnosis at byte 128");
 static_assert(offsetof(Header, wait_ns) == kHdrWaitNs, "wait_budget reads the budget at kHdrWaitNs");
+static_assert(offsetof(Header, nonfinite) == 3 * sizeof(int), "record_nonfinite writes status + 3");
 static_assert(sizeof(Header) <= 256, "the header occupies the first 256 bytes of the workspace");
 
 // ---------------------------------------------------------------------------
@@ -385,6 +421,7 @@ struct PlanArgs {
     int64_t n_y;        // 0: Gram of X with itself
     int64_t max_len;
     int rows_per_strip;
+    int strip_quantum;  // strip counts are rounded up to a multiple of this (>= 1)
     int64_t n_pairs;
     int64_t* ox;
     int64_t* oy;
@@ -573,6 +610,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         if (t == 0) {
             bad = 0;
             A.hdr->status = 0;  // errors are reported per call
+            A.hdr->nonfinite = 0;
             A.hdr->train_sig = 0;  // no training state until this plan succeeds
             A.hdr->wait_ns = A.wait_ns;
         }
@@ -598,10 +636,12 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         const float* pb;
         int64_t la, lb;
         int32_t ra = 1, rb = 1;
+        int32_t slot_a = 0, slot_b = 0;
         auto path = [&](int64_t z, bool second, const float** ptr, int64_t* segs, int32_t* rf) {
             bool from_y;
             int64_t i;
             pair_side(A, self, z, second, &from_y, &i);
+            (second ? slot_b : slot_a) = (int32_t)(from_y ? A.n_x + i : i);
             const float* base = from_y ? A.Y : A.X;
             const int64_t* off = from_y ? A.oy : A.ox;
             const int64_t* len = from_y ? A.len_y : A.len_x;
@@ -617,8 +657,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         pd.out1 = o1;
         // orientation: rows = the path that minimises padded work
         // ceil(rows/RS)*RS*(cols + 31), subject to cols <= max_len
-        const int64_t cost_ab = ((la + RS - 1) / RS) * RS * (lb + 31);
-        const int64_t cost_ba = ((lb + RS - 1) / RS) * RS * (la + 31);
+        const int64_t RQ = (int64_t)RS * (A.strip_quantum > 1 ? A.strip_quantum : 1);
+        const int64_t cost_ab = ((la + RQ - 1) / RQ) * RQ * (lb + 31);
+        const int64_t cost_ba = ((lb + RQ - 1) / RQ) * RQ * (la + 31);
         bool swap = cost_ba < cost_ab;
         if (swap && la > A.max_len) swap = false;
         if (!swap && lb > A.max_len) swap = true;
@@ -629,6 +670,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         pd.gyr = nullptr;
         pd.sx = swap ? rb : ra;
         pd.sy = swap ? ra : rb;
+        pd.xslot = swap ? slot_b : slot_a;
+        pd.yslot = swap ? slot_a : slot_b;
         if (la > (int64_t)INT32_MAX || lb > (int64_t)INT32_MAX) atomicCAS(&A.hdr->status, 0, kErrLength);
         pd.L1 = (int32_t)(swap ? lb : la);
         pd.L2 = (int32_t)(swap ? la : lb);
@@ -638,7 +681,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
             if (o0 >= 0) A.out[o0] = 1.0;  // a one-point path: k = 1
             if (o1 >= 0) A.out[o1] = 1.0;
         } else {
-            pd.n_strips = (pd.L1 + RS - 1) / RS;
+            const int q = A.strip_quantum > 1 ? A.strip_quantum : 1;
+            pd.n_strips = ((pd.L1 + RS - 1) / RS + q - 1) / q * q;
         }
         A.pairs[p] = pd;
     }
@@ -1065,6 +1109,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     pa.n_y = n_y;
     pa.max_len = o.max_len;
     pa.rows_per_strip = L.rows_per_strip;
+    pa.strip_quantum = L.strip_quantum;
     pa.n_pairs = L.n_pairs;
     pa.ox = (int64_t*)(base + L.ox);
     pa.oy = (int64_t*)(base + L.oy);
@@ -1147,12 +1192,53 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
             sa.rec_off = pa.rec_off;
         }
     }
+    if (L.n_pairs > 0 && L.tc) {
+        // digits of every path's first max_len segments (the swept sides)
+        SliceArgs sl;
+        sl.X = X;
+        sl.Y = (op == SIGK_OP_GRAM && n_y == 0) ? nullptr : Y;
+        sl.ox = pa.ox;
+        sl.oy = pa.oy;
+        sl.len_x = len_x;
+        sl.len_y = len_y;
+        sl.n_x = n_x;
+        sl.n_slots = L.n_slots;
+        sl.d = d;
+        sl.d_pad = L.d_pad;
+        sl.inc_mode = pa.inc_mode;
+        sl.max_len = o.max_len;
+        sl.cache = (uint16_t*)(base + L.ycache);
+        sl.exps = (int32_t*)(base + L.yexp);
+        const int64_t rows = L.n_slots * o.max_len;
+        const int64_t blocks = (rows + 7) / 8;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+        slice_paths_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, stream>>>(sl);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "digit pre-pass launch");
+    }
     if (L.n_pairs > 0) {
         if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
-        e = L.cm ? fwd_cm_launch_dispatch(o.order, o.rings, L.f64, sa, base + L.cscratch, L.cstride,
-                                          L.grid, stream)
-                 : fwd_launch_dispatch(o.order, o.rings, dim_bucket(d), L.stored_rec ? 1 : 0, sa,
-                                       L.grid, stream);
+        if (L.tc) {
+            TcArgs ta;
+            ta.A = sa;
+            ta.ycache = (const uint16_t*)(base + L.ycache);
+            ta.yexp = (const int32_t*)(base + L.yexp);
+            ta.max_len = o.max_len;
+            ta.d_pad = L.d_pad;
+            ta.ablk = (uint16_t*)(base + L.ablk);
+            ta.aexp = (int32_t*)(base + L.aexp);
+            ta.cst = (float2*)(base + L.cst);
+            ta.cst_stride = L.cst_stride;
+            ta.block_counter = &hdr->item_counter;
+            e = fwd_tc_launch_dispatch(o.order, o.rings, ta, L.grid, stream);
+        } else {
+            e = L.cm ? fwd_cm_launch_dispatch(o.order, o.rings, L.f64, sa, base + L.cscratch, L.cstride,
+                                              L.grid, stream)
+                     : fwd_launch_dispatch(o.order, o.rings, dim_bucket(d), L.stored_rec ? 1 : 0, sa,
+                                           L.grid, stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
         if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_stop, stream);
     }
@@ -1501,6 +1587,7 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     pa.n_y = (op == SIGK_OP_GRAM && !Y) ? 0 : n_y;
     pa.max_len = (int64_t)INT32_MAX;  // no swept-length limit while planning
     pa.rows_per_strip = L.rows_per_strip;
+    pa.strip_quantum = 1;
     pa.n_pairs = L.n_pairs;
     pa.ox = (int64_t*)(base + L.ox);
     pa.oy = (int64_t*)(base + L.oy);
@@ -1602,9 +1689,15 @@ sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream) {
     Header h;
     e = cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "status copy");
-    if (h.status != 0) {
+    if (h.status == 0 && h.nonfinite != 0) {
         int zero = 0;
-        cudaMemcpy(ws, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy((char*)ws + offsetof(Header, nonfinite), &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(SIGK_ERR_NONFINITE, "non-finite value met on the device (the other outputs are valid)");
+    }
+    if (h.status != 0) {
+        int zero[4] = {0, 0, 0, 0};
+        cudaMemcpy(ws, &zero[0], sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy((char*)ws + offsetof(Header, nonfinite), &zero[3], sizeof(int), cudaMemcpyHostToDevice);
         const char* msg = h.status == kErrTimeout ? "a bounded device wait timed out"
                           : h.status == kErrNonfinite ? "non-finite value met on the device"
                           : h.status == kErrLength ? "a path length is out of range"

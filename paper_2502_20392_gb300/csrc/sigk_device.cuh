@@ -56,6 +56,8 @@ struct PairDesc {
     int32_t swapped;   // 1 if the row path is the caller's y
     int32_t sx;        // refinement of the row path: each segment in sx pieces
     int32_t sy;        // refinement of the swept path
+    int32_t xslot;     // index of the row path among the call's paths (X, then Y)
+    int32_t yslot;     // index of the swept path among the call's paths
     int64_t out0;      // output index, or -1
     int64_t out1;      // mirrored output index, or -1
     float* gxr;        // gradient rows of the row path (backward), or null
@@ -276,6 +278,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// A non-finite result (NaN or Inf in the data, or beyond the range of the
+// power-of-two exponent) is recorded in the word after the three work
+// counters of the header (status + 3), not in the status word: it is an
+// error of that output alone, and the launch carries on with every other
+// pair (the status word stops the launch).
+__device__ __forceinline__ void record_nonfinite(int* status) { atomicExch(status + 3, 1); }
+
 // First time-out of a launch: the status word, then (for diagnosis) the
 // waited-on address, the target and the value last seen, as three 64-bit
 // words at byte 128 of the status word's 256-byte header.
@@ -446,9 +455,20 @@ __device__ __forceinline__ void unpack_exp(int w, int& F, int& Eb, int& abump, i
 // ---------------------------------------------------------------------------
 // One tile.  a[1..P]: scaled bottom edge (overwritten by the top edge);
 // (hi, lo), b[1..P]: scaled left edge (overwritten by the right edge).
-template <int P>
+//
+// CLO: the coefficient is the unevaluated float-float pair c + clo (an
+// increment Gram computed beyond FP32 precision).  Rounding c to one float
+// perturbs every tile by a relative 2^-24, and over the millions of tiles of
+// a long, strongly coupled pair these perturbations reach the 1e-5 level of
+// k (CPU emulation of this sweep: 1.1e-5 with the FP32 dot products, 3e-6
+// with c correctly rounded, 8e-7 with the pair).  The low part enters where
+// the result is first order in c: the m = 1 ring of every edge coefficient
+// (clo * a_{p-1}) and the first-order coefficients, whose product c * ha_1 is
+// then formed exactly (TwoProduct) before the compensated accumulation.
+template <int P, bool CLO = false>
 __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a1lo, float& hi,
-                                            float& lo, float (&b)[P + 1], float& b1lo, int nr) {
+                                            float& lo, float (&b)[P + 1], float& b1lo, int nr,
+                                            float clo = 0.0f) {
     constexpr int NRM = P < kMaxRings ? P : kMaxRings;
     float cp[NRM + 1], ch[NRM + 1];
     cp[1] = c;
@@ -488,6 +508,7 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
         for (int m = 1; m < p && m <= NRM; ++m)
             if (m <= nr) v = fmaf(ch[m], a[p - m], v);
         if (p <= NRM && p <= nr) v = fmaf(cp[p], ha[p], v);
+        if constexpr (CLO) v = fmaf(clo, a[p - 1], v);
         a[p] = v;
     }
     // right edge
@@ -498,6 +519,7 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
         for (int m = 1; m < q && m <= NRM; ++m)
             if (m <= nr) v = fmaf(ch[m], b[q - m], v);
         if (q <= NRM && q <= nr) v = fmaf(cp[q], hb[q], v);
+        if constexpr (CLO) v = fmaf(clo, b[q - 1], v);
         b[q] = v;
     }
     // first-order coefficients: compensated (TwoSum) accumulation.  Along a
@@ -510,8 +532,12 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
         const float da = cp[1] * ha[1], db = cp[1] * hb[1];
         const float sa = a[1] + da, sb = b[1] + db;
         const float ta = sa - a[1], tb = sb - b[1];
-        const float la = a1lo + ((a[1] - (sa - ta)) + (da - ta));
-        const float lb = b1lo + ((b[1] - (sb - tb)) + (db - tb));
+        float la = a1lo + ((a[1] - (sa - ta)) + (da - ta));
+        float lb = b1lo + ((b[1] - (sb - tb)) + (db - tb));
+        if constexpr (CLO) {  // exact product error of c * ha_1, and the low part of c
+            la += fmaf(clo, ha[1], fmaf(c, ha[1], -da));
+            lb += fmaf(clo, hb[1], fmaf(c, hb[1], -db));
+        }
         a[1] = sa + la;
         b[1] = sb + lb;
         a1lo = la - (a[1] - sa);

@@ -294,7 +294,7 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
                         k += (double)b[q] / fq;
                     }
                     k = ldexp(k, E);
-                    if (!isfinite(k)) atomicCAS(A.status, 0, kErrNonfinite);
+                    if (!isfinite(k)) record_nonfinite(A.status);
                     if (pd.out0 >= 0) A.out[pd.out0] = k;
                     if (pd.out1 >= 0) A.out[pd.out1] = k;
                     if (A.pair_exp) A.pair_exp[lo_p] = E;

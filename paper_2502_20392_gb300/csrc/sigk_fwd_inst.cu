@@ -2,10 +2,12 @@
 // (compiled once per pair with -DSIGK_P=<P> -DSIGK_NR=<NR>) and D in
 // {4, 8, 16}: the forward solver (inference, and training with every 32-row
 // seam stored, with or without every tile's record) and the backward
-// (adjoint) kernel; and the two-phase solver in FP32 and FP64.
+// (adjoint) kernel; the two-phase solver in FP32 and FP64; and the
+// tensor-core solver for large d.
 #include "sigk_bwd.cuh"
 #include "sigk_fwd.cuh"
 #include "sigk_fwd_cm.cuh"
+#include "sigk_fwd_tc.cuh"
 #include "sigk_launch.h"
 
 #ifndef SIGK_P
@@ -159,6 +161,24 @@ cudaError_t bwd_launch<SIGK_P, SIGK_NR>(int D, const BwdArgs& a, int grid, cudaS
         case 16: return bwd_launch_impl<16>(a, grid, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <>
+int fwd_tc_info<SIGK_P, SIGK_NR>(KernelInfo* info) {
+    const int r = occupancy(fwd_tc_kernel<SIGK_P, SIGK_NR>, 128, TcSmem<SIGK_P>::bytes, 1, info);
+    // at most four CTAs per SM hold TMEM at a time (4 x 128 columns)
+    if (r == 0 && info->blocks_per_sm > 4) info->blocks_per_sm = 4;
+    return r;
+}
+
+template <>
+cudaError_t fwd_tc_launch<SIGK_P, SIGK_NR>(const TcArgs& a, int grid, cudaStream_t s) {
+    const int smem = TcSmem<SIGK_P>::bytes;
+    auto kern = fwd_tc_kernel<SIGK_P, SIGK_NR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 128, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace sigk

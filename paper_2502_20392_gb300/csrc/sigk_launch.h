@@ -41,6 +41,12 @@ template <int P, int NR>
 cudaError_t fwd_cm_launch(bool f64, const SolverArgs& a, void* cscratch, int64_t cstride, int grid,
                           cudaStream_t s);
 
+// Tensor-core solver for large d (increment Gram on tcgen05, float-float
+// coefficients, FP32 sweep); one CTA per 128-row block.
+struct TcArgs;
+template <int P, int NR> int fwd_tc_info(KernelInfo* info);
+template <int P, int NR> cudaError_t fwd_tc_launch(const TcArgs& a, int grid, cudaStream_t s);
+
 struct BwdArgs;
 template <int P, int NR> int bwd_info(int D, KernelInfo* info);
 template <int P, int NR> cudaError_t bwd_launch(int D, const BwdArgs& a, int grid, cudaStream_t s);

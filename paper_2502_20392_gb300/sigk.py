@@ -25,6 +25,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "sigk.h")
 OP_PAIRS, OP_GRAM, OP_MMD = 0, 1, 2
 FLAG_INCREMENTS, FLAG_GRAM_FULL, FLAG_MMD_BIASED, FLAG_FP64, FLAG_PAIR_MAJOR, FLAG_REPLAY = 1, 2, 4, 8, 16, 32
 FLAG_TEST_WITHHOLD_SEAM = 64
+FLAG_NO_TENSOR = 128
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_LENGTH", -3: "ERR_NONFINITE", -4: "ERR_WORKSPACE",
           -5: "ERR_CUDA", -6: "ERR_TIMEOUT", -7: "ERR_ACCURACY", -8: "ERR_UNSUPPORTED",
           -9: "ERR_BOUNDS"}
