@@ -110,6 +110,7 @@ def cells_per_step():
 
 
 BWD_SIGMA = 0  # index into SIGMAS of the Gram whose adjoint is part of the step
+RING_TOL = 1e-5 / (10 * N_SEG * N_SEG)
 
 
 class ClockSampler:
@@ -262,11 +263,13 @@ def main():
                          "kernel, for ncu captures)")
     ap.add_argument("--sweep", default=None, choices=["roughness", "dimension", "length", "configs"],
                     help="print one JSON line per point of a sweep instead of the bench line")
+    ap.add_argument("--no-tensor", action="store_true",
+                    help="large_d: the FMA micro-GEMM for the increment Gram instead of the tensor cores")
     args = ap.parse_args()
     if args.sweep:
         return run_sweep(args)
     if args.case == "large_d":
-        return run_large_d()
+        return run_large_d(args.no_tensor)
     if args.case == "small":
         global N_PATHS
         N_PATHS = 16
@@ -297,7 +300,9 @@ def main():
     host = rank_workloads(rank, N_PATHS)
     X = [torch.from_numpy(p).to(dev) for p, _ in host]
     L = [torch.from_numpy(l).to(dev) for _, l in host]
-    opts = [sigk.Opts(order=P, rings=nr, max_len=N_SEG) for _, _, P, nr in SIGMAS]
+    # the forward Grams choose the ring count per tile: the first dropped ring
+    # of every tile within an equal share, tol / (10 L^2), of the tolerance 1e-5
+    opts = [sigk.Opts(order=P, rings=nr, max_len=N_SEG, ring_tol=RING_TOL) for _, _, P, nr in SIGMAS]
     # training forward of the Gram whose gradient is taken: only the seams of
     # the 32-row strips are kept (checkpointed wavefront boundaries); the
     # adjoint recomputes each strip from its seam
@@ -369,6 +374,7 @@ def main():
     # per-kernel rooflines: useful work (the algorithmic model) and the
     # executed operation count, both over the kernel's CUDA-event time
     tiles = [sigk.counters(wss[k])[0] for k in range(len(SIGMAS))]
+    hists = [sigk.ring_histogram(wss[k]) for k in range(len(SIGMAS))]
     bcnt = sigk.counters(bws)
     roof = []
 
@@ -386,9 +392,16 @@ def main():
         kms = statistics.mean(r[k] for r in f_kern)
         # compulsory increment reads: each pair's two paths once (points, FP32)
         inc_bytes = pairs_of_gram(N_PATHS) * 2 * (N_SEG + 1) * DIM * 4
-        entry(f"fwd_kernel<P={P},D=16> (inference)", kms, tiles[k] * useful_tile_flops(P, nr, DIM),
-              tiles[k] * tile_flops(P, nr, DIM), sg, P, nr,
-              {"increment_read_gbs": round(inc_bytes / (kms * 1e-3) / 1e9, 1)})
+        # work from the ring counts the tiles actually used
+        h = hists[k] if sum(hists[k]) > 0 else [0, 0, 0, 0]
+        if sum(h) > 0:
+            useful = sum(h[q] * useful_tile_flops(P, 2 * q + 2, DIM) for q in range(4))
+            executed = sum(h[q] * tile_flops(P, 2 * q + 2, DIM) for q in range(4))
+        else:
+            useful, executed = tiles[k] * useful_tile_flops(P, nr, DIM), tiles[k] * tile_flops(P, nr, DIM)
+        entry(f"fwd_kernel<P={P},D=16> (inference)", kms, useful, executed, sg, P, nr,
+              {"increment_read_gbs": round(inc_bytes / (kms * 1e-3) / 1e9, 1),
+               "tiles_by_rings_2_4_6_8": h})
     sg, _, P, nr = SIGMAS[BWD_SIGMA]
     kms = statistics.mean(r[0] for r in b_kern)
     entry(f"fwd_kernel<P={P},D=16> (training: keeps the strip seams)", kms,
@@ -453,6 +466,7 @@ def main():
         "config": {"workload": "gram_B64_L1024_d16_sigma1+4", "paths": N_PATHS, "segments": N_SEG,
                    "d": DIM, "sigmas": [s_ for s_, *_ in SIGMAS],
                    "order_rings": [[P_, nr_] for _, _, P_, nr_ in SIGMAS],
+                   "ring_tol": RING_TOL,
                    "unique_pairs_per_gram": pairs_of_gram(N_PATHS), "l2": "flushed between steps",
                    "step": "forward: the Grams for sigma = 1 and sigma = 4 (inference); "
                            "fwd_bwd: training forward + adjoint of the sigma = 1 Gram "
@@ -497,11 +511,12 @@ def main():
         dist.destroy_process_group()
 
 
-def run_large_d():
+def run_large_d(no_tensor=False):
     """64 ragged pairs of 1500-2048 segments, d = 256, sigma in [0.5, 1.5]:
-    the two-phase kernel (increment Gram, then the sweep), one warm-up call
-    and one measured call.  The inputs exceed the 129 MB L2 while the device
-    footprint stays at a few GB (for profiler captures of that kernel)."""
+    the large-d solver (increment Gram on the tensor cores, or with
+    no_tensor the FMA micro-GEMM; then the sweep), one warm-up call and one
+    measured call.  The inputs exceed the 129 MB L2 while the device footprint
+    stays at a few GB (for profiler captures of that kernel)."""
     import torch
 
     from paper_2502_20392_gb300 import build, sigk, synth
@@ -509,10 +524,15 @@ def run_large_d():
     sigk.load()
     (X, lx), (Y, ly) = synth.ragged_pairs(64, 1500, 2048, 256, 0.5, 1.5, seed=4401)
     a = [torch.from_numpy(v).cuda() for v in (X, lx, Y, ly)]
-    o = sigk.Opts(order=12, rings=6, max_len=2048)
+    o = sigk.Opts(order=12, rings=6, max_len=2048, flags=sigk.FLAG_NO_TENSOR if no_tensor else 0)
     ws = sigk.Workspace()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     for _ in range(2):
+        ev[0].record()
         k = sigk.pairs(*a, opts=o, ws=ws)
+        ev[1].record()
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "large_d", "no_tensor": no_tensor, "ms": ev[0].elapsed_time(ev[1])}))
     torch.cuda.synchronize()
     assert torch.isfinite(k).all()
     return 0

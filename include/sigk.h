@@ -137,7 +137,18 @@ enum {
  *            milliseconds (0 = 4000; at most 600000).  A wait that runs out
  *            records SIGK_ERR_TIMEOUT, with the waited address, target and last
  *            value seen in the workspace header, and makes every warp of the
- *            launch return. */
+ *            launch return.
+ *   ring_tol: 0 = every tile keeps `rings` Neumann iterations.  Otherwise the
+ *            forward ops (sigk_pairs, sigk_gram, sigk_mmd; not the training
+ *            forward, whose adjoint differentiates the fixed count) choose the
+ *            count per tile, as the local Neumann iteration of App. B stops
+ *            when the next term is negligible: a tile with coefficient c needs
+ *            the smallest even n <= rings with |c|^(n+1) / ((n+1)!)^2 <=
+ *            ring_tol (the first dropped ring, relative to the edge data), and
+ *            the tiles a warp solves in one step use the largest count among
+ *            them.  sigk_plan sets it to tol / (10 L1 L2) of the largest pair,
+ *            an equal share of its ring-sum rule.  sigk_ring_histogram reports
+ *            the counts used. */
 typedef struct {
     int order;
     int rings;
@@ -146,6 +157,7 @@ typedef struct {
     int64_t max_len;
     float refine_c;
     int wait_ms;
+    float ring_tol;
 } sigk_opts;
 
 /* Device workspace bytes needed by sigk_pairs/sigk_gram/sigk_mmd for the
@@ -296,6 +308,11 @@ sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream);
  * padding, out[2] = tiles solved by the adjoint kernel, out[3] = tiles the
  * adjoint kernel replayed (0 when the forward stored the tile records). */
 sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out4);
+
+/* Tiles solved by the last forward on this workspace with 2, 4, 6 and 8
+ * Neumann rings (out4[0..3]; synchronises `stream`); all zero unless
+ * opts->ring_tol was set. */
+sigk_status sigk_ring_histogram(void* ws, size_t ws_bytes, void* stream, double* out4);
 
 /* Profiling hook: when both are non-NULL, later calls on this host thread
  * record the two CUDA events (cudaEvent_t) on the call's stream immediately

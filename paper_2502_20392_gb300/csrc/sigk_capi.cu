@@ -50,6 +50,7 @@ struct Opts {
     int64_t max_len;
     float refine_c;  // 0: no refinement
     int wait_ms;     // bounded-wait budget
+    float ring_tol;  // per-tile ring count (0: fixed)
 };
 
 static bool resolve_opts(const sigk_opts* o, Opts* r) {
@@ -60,6 +61,7 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
     r->max_len = 8193;
     r->refine_c = 0.0f;
     r->wait_ms = 4000;
+    r->ring_tol = 0.0f;
     if (o) {
         if (o->order) r->order = o->order;
         if (o->rings) r->rings = o->rings;
@@ -68,7 +70,9 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
         if (o->max_len > 0) r->max_len = o->max_len;
         r->refine_c = o->refine_c;
         if (o->wait_ms) r->wait_ms = o->wait_ms;
+        r->ring_tol = o->ring_tol;
     }
+    if (!(r->ring_tol >= 0.0f) || r->ring_tol > 1.0f) return false;
     if (r->wait_ms < 1 || r->wait_ms > 600000) return false;
     if (!(r->refine_c >= 0.0f) || r->refine_c > 1e30f) return false;
     if (r->order < 4 || r->order > kMaxP) return false;
@@ -395,7 +399,8 @@ struct Header {
     int sched[4];  // schedule: mode, n_levels, n_items (Schedule::hdr)
     int sched2[4];  // training forward's schedule (items of 2^fwd_shift strips)
     long long train_sig;  // signature of the training forward whose state the workspace holds (0: none)
-    int pad2[10];
+    unsigned ring_hist[4];  // tiles solved with 2, 4, 6, 8 rings (adaptive forwards)
+    int pad2[6];
     long long diag[3];  // first timed-out wait: address, target, value seen (byte 128)
     long long wait_ns;  // budget of the bounded waits of the current launch (byte 152)
 };
@@ -816,6 +821,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(PlanArgs A) {
         A.hdr->counters[1] = 0;
         A.hdr->counters[2] = 0;
         A.hdr->counters[3] = 0;
+        for (int q = 0; q < 4; ++q) A.hdr->ring_hist[q] = 0u;
     }
     if (!A.train) return;
     // per-pair offsets of the forward seam store: (strips - 1) x L2 x stride
@@ -1177,6 +1183,16 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     sa.counters = hdr->counters;
     sa.out = out;
     sa.withhold_first_seam = (o.flags & SIGK_FLAG_TEST_WITHHOLD_SEAM) && !train ? 1 : 0;
+    // per-tile ring counts (inference only): |c| <= theta_n keeps the first
+    // dropped ring |c|^(n+1)/((n+1)!)^2 within ring_tol
+    sa.ring_adaptive = (o.ring_tol > 0.0f && !train && !L.f64 && !(L.cm && !L.tc)) ? 1 : 0;
+    sa.ring_hist = hdr->ring_hist;
+    for (int q = 0; q < 3; ++q) {
+        const int n = 2 * q + 2;
+        double f = 1.0;
+        for (int k = 2; k <= n + 1; ++k) f *= k;
+        sa.ring_theta[q] = (float)pow((double)o.ring_tol * f * f, 1.0 / (n + 1));
+    }
     sa.nwords = (int32_t)L.nwords;
     sa.store_cap = train ? L.store_floats : 0;
     sa.rec_cap = L.stored_rec ? L.rstore_floats : 0;
@@ -1675,6 +1691,16 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     opts_out->order = P;
     opts_out->rings = nr;
     opts_out->refine_c = o.refine_c;
+    {
+        // per-tile ring tolerance: an equal share of the ring-sum rule of the
+        // largest pair (tol / 10 over its L1 L2 tiles)
+        double cells = 1.0;
+        for (int64_t p = 0; p < L.n_pairs; ++p) {
+            const double* st = hs.data() + p * kStatFields;
+            if (st[0] * st[1] > cells) cells = st[0] * st[1];
+        }
+        opts_out->ring_tol = (float)(0.1 * tol / cells);
+    }
     opts_out->max_len = max_swept;  // the longest swept path as planned (refined)
     if (max_c > 1.0 || !fits)
         return fail(SIGK_ERR_ACCURACY,
@@ -1705,6 +1731,17 @@ sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream) {
                                                    : "device error";
         return fail((sigk_status)h.status, msg);
     }
+    return SIGK_OK;
+}
+
+sigk_status sigk_ring_histogram(void* ws, size_t ws_bytes, void* stream, double* out4) {
+    if (!ws || ws_bytes < 256 || !out4) return fail(SIGK_ERR_ARG, "bad arguments");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    Header h;
+    e = cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "histogram copy");
+    for (int i = 0; i < 4; ++i) out4[i] = (double)h.ring_hist[i];
     return SIGK_OK;
 }
 

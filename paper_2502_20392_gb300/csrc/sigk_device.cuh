@@ -174,6 +174,13 @@ struct SolverArgs {
     // fault-injection hook (tests of the bounded waits): the schedule's first
     // item does not publish its outgoing seam
     int32_t withhold_first_seam;
+    // per-tile ring count (inference forwards; 0 = the fixed count NR): a
+    // tile whose |c| is at most ring_theta[k] needs at most 2k + 2 rings (its
+    // first dropped ring |c|^(n+1)/((n+1)!)^2 stays below the ring tolerance);
+    // a warp uses the largest count any of its tiles of the step needs
+    int32_t ring_adaptive;
+    float ring_theta[3];
+    unsigned* ring_hist;           // [4] tiles solved with 2, 4, 6, 8 rings (adaptive launches)
     // extents of the buffers above, for the bounds checks of SIGK_DEBUG builds
     int32_t nwords;                // progress words (prod, cons, done)
     int64_t store_cap;             // floats of store
@@ -450,6 +457,12 @@ __device__ __forceinline__ void unpack_exp(int w, int& F, int& Eb, int& abump, i
     bbump = (int)((unsigned)w >> 31);
     Eb = (int)(((unsigned)w >> 1) & 0xFFFF) * 64;
     F = (int)(((unsigned)w >> 17) & 0x3FFF) * 64;
+}
+
+// Rings a tile with coefficient magnitude ac needs (2, 4, 6 or 8) under the
+// launch's thresholds (SolverArgs::ring_theta).
+__device__ __forceinline__ int rings_needed(float ac, const float (&th)[3]) {
+    return ac <= th[0] ? 2 : (ac <= th[1] ? 4 : (ac <= th[2] ? 6 : 8));
 }
 
 // ---------------------------------------------------------------------------

@@ -37,6 +37,7 @@
 // of one overlaps the FMA sweep of the others.  The L1 x L2 coefficient
 // matrix is never stored: only one block's strips per CTA exist at a time.
 #pragma once
+#include <type_traits>
 #include "sigk_device.cuh"
 #include "sigk_fwd.cuh"
 
@@ -237,7 +238,7 @@ __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDe
                                                int s, int item, int prev, int next, const float2* cw,
                                                float* sin_, float* sout,
                                                unsigned long long& tiles_done,
-                                               unsigned long long& lane_tiles) {
+                                               unsigned long long& lane_tiles, unsigned (&rhist)[4]) {
     constexpr int S = P + 4;
     const int lane = threadIdx.x & 31;
     const int L1 = pd.L1, L2 = pd.L2;
@@ -305,6 +306,16 @@ __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDe
             }
         }
         const int j = t - lane;
+        // the warp's ring count for this step (the largest its tiles need)
+        int nw = NR;
+        if (A.ring_adaptive) {
+            const int nl = (j >= 0 && j < L2) ? rings_needed(fabsf(cc.x), A.ring_theta) : 0;
+            nw = min((int)__reduce_max_sync(kFull, (unsigned)nl), NR);
+            if (j >= 0 && j < L2 && has_row) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) rhist[q] += ((nw >> 1) - 1 == q) ? 1u : 0u;
+            }
+        }
         if (j >= 0 && j < L2) {
             if (F != E) {
                 if (F > E) {
@@ -321,7 +332,13 @@ __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDe
                 }
             }
             // rows past the end of the path have zero digits: c = clo = 0
-            tile_update<P, true>(cc.x, a, a1lo, hi, lo, b, b1lo, NR, cc.y);
+            auto tile = [&](auto nrc) {
+                tile_update<P, true>(cc.x, a, a1lo, hi, lo, b, b1lo, decltype(nrc)::value, cc.y);
+            };
+            if (nw == NR) tile(std::integral_constant<int, NR>{});
+            else if (nw <= 2) tile(std::integral_constant<int, 2>{});
+            else if (NR > 4 && nw == 4) tile(std::integral_constant<int, (NR > 4 ? 4 : NR)>{});
+            else tile(std::integral_constant<int, (NR > 6 ? 6 : NR)>{});
             if (fabsf(hi) > 1.8446744e19f) {  // 2^64
                 const float sc = 5.421011e-20f;  // 2^-64
                 a1lo *= sc;
@@ -423,6 +440,7 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = tmem_base_s;
+    unsigned rhist[4] = {0u, 0u, 0u, 0u};  // tiles by ring count (adaptive launches)
     uint32_t step = 0;         // MMA steps of this CTA so far (stage = step & 1)
     int64_t issued = -1;       // last step whose MMAs were committed (CTA-uniform)
     int64_t waited = -1;       // last step whose completion was observed
@@ -584,7 +602,7 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
             if (ir.next >= 0) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
             if (ok)
                 ok = sweep_strip_tc<P, NR>(A, pd, lo_p, s, item, ir.prev, ir.next, cw, seam_w,
-                                           seam_w + kG * S, tiles_done, lane_tiles);
+                                           seam_w + kG * S, tiles_done, lane_tiles, rhist);
         }
         __syncwarp();
         if (lane == 0) {
@@ -609,6 +627,15 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
     if (lane == 0) {
         atomicAdd(&A.counters[0], tiles_done);
         atomicAdd(&A.counters[1], lane_tiles);
+    }
+    if (A.ring_adaptive) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            unsigned v = rhist[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+            if (lane == 0 && v) atomicAdd(&A.ring_hist[q], v);
+        }
     }
 }
 

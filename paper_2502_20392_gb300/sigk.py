@@ -41,7 +41,7 @@ class SigkError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("rings", ctypes.c_int), ("flags", ctypes.c_int),
                 ("grid_ctas", ctypes.c_int), ("max_len", ctypes.c_int64),
-                ("refine_c", ctypes.c_float), ("wait_ms", ctypes.c_int)]
+                ("refine_c", ctypes.c_float), ("wait_ms", ctypes.c_int), ("ring_tol", ctypes.c_float)]
 
 
 @dataclass
@@ -53,10 +53,11 @@ class Opts:
     max_len: int = 8193
     refine_c: float = 0.0
     wait_ms: int = 0
+    ring_tol: float = 0.0
 
     def c(self) -> _Opts:
         return _Opts(self.order, self.rings, self.flags, self.grid_ctas, self.max_len,
-                     self.refine_c, self.wait_ms)
+                     self.refine_c, self.wait_ms, self.ring_tol)
 
 
 _lib = None
@@ -96,12 +97,13 @@ def load(path: str | None = None):
     lib.sigk_adjoint.argtypes = [i32, i64, i64, i32, vp, vp, vp, vp, sz, vp, op]
     lib.sigk_sync_status.argtypes = [vp, sz, vp]
     lib.sigk_counters.argtypes = [vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.sigk_ring_histogram.argtypes = [vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sigk_profile_events.argtypes = [vp, vp]
     lib.sigk_profile_events.restype = None
     lib.sigk_last_error.restype = ctypes.c_char_p
     lib.sigk_version.restype = ctypes.c_char_p
     for name in ("sigk_pairs", "sigk_gram", "sigk_mmd", "sigk_plan", "sigk_sync_status",
-                 "sigk_counters", "sigk_backward"):
+                 "sigk_counters", "sigk_ring_histogram", "sigk_backward"):
         getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -177,6 +179,14 @@ def profile_events(start=None, stop=None):
 def counters(ws: Workspace):
     out = (ctypes.c_double * 4)()
     _check(load().sigk_counters(_ptr(ws.buf), ws.buf.numel(), _stream(), out))
+    return list(out)
+
+
+def ring_histogram(ws: Workspace):
+    """Tiles of the last forward on ws solved with 2, 4, 6, 8 rings (adaptive
+    ring counts only)."""
+    out = (ctypes.c_double * 4)()
+    _check(load().sigk_ring_histogram(_ptr(ws.buf), ws.buf.numel(), _stream(), out))
     return list(out)
 
 
@@ -451,4 +461,4 @@ def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | 
     else:
         _check(st)
     return Opts(o_out.order, o_out.rings, o_out.flags, o_out.grid_ctas, o_out.max_len,
-                o_out.refine_c, o_out.wait_ms)
+                o_out.refine_c, o_out.wait_ms, o_out.ring_tol)
