@@ -110,7 +110,6 @@ def cells_per_step():
 
 
 BWD_SIGMA = 0  # index into SIGMAS of the Gram whose adjoint is part of the step
-RING_TOL = 1e-5 / (10 * N_SEG * N_SEG)
 
 
 class ClockSampler:
@@ -300,9 +299,7 @@ def main():
     host = rank_workloads(rank, N_PATHS)
     X = [torch.from_numpy(p).to(dev) for p, _ in host]
     L = [torch.from_numpy(l).to(dev) for _, l in host]
-    # the forward Grams choose the ring count per tile: the first dropped ring
-    # of every tile within an equal share, tol / (10 L^2), of the tolerance 1e-5
-    opts = [sigk.Opts(order=P, rings=nr, max_len=N_SEG, ring_tol=RING_TOL) for _, _, P, nr in SIGMAS]
+    opts = [sigk.Opts(order=P, rings=nr, max_len=N_SEG) for _, _, P, nr in SIGMAS]
     # training forward of the Gram whose gradient is taken: only the seams of
     # the 32-row strips are kept (checkpointed wavefront boundaries); the
     # adjoint recomputes each strip from its seam
@@ -374,7 +371,6 @@ def main():
     # per-kernel rooflines: useful work (the algorithmic model) and the
     # executed operation count, both over the kernel's CUDA-event time
     tiles = [sigk.counters(wss[k])[0] for k in range(len(SIGMAS))]
-    hists = [sigk.ring_histogram(wss[k]) for k in range(len(SIGMAS))]
     bcnt = sigk.counters(bws)
     roof = []
 
@@ -392,27 +388,23 @@ def main():
         kms = statistics.mean(r[k] for r in f_kern)
         # compulsory increment reads: each pair's two paths once (points, FP32)
         inc_bytes = pairs_of_gram(N_PATHS) * 2 * (N_SEG + 1) * DIM * 4
-        # work from the ring counts the tiles actually used
-        h = hists[k] if sum(hists[k]) > 0 else [0, 0, 0, 0]
-        if sum(h) > 0:
-            useful = sum(h[q] * useful_tile_flops(P, 2 * q + 2, DIM) for q in range(4))
-            executed = sum(h[q] * tile_flops(P, 2 * q + 2, DIM) for q in range(4))
-        else:
-            useful, executed = tiles[k] * useful_tile_flops(P, nr, DIM), tiles[k] * tile_flops(P, nr, DIM)
+        useful, executed = tiles[k] * useful_tile_flops(P, nr, DIM), tiles[k] * tile_flops(P, nr, DIM)
         entry(f"fwd_kernel<P={P},D=16> (inference)", kms, useful, executed, sg, P, nr,
               {"increment_read_gbs": round(inc_bytes / (kms * 1e-3) / 1e9, 1),
-               "tiles_by_rings_2_4_6_8": h})
+               "launch": sigk.launch_info(sigk.OP_GRAM, N_PATHS, 0, DIM, opts[k])})
     sg, _, P, nr = SIGMAS[BWD_SIGMA]
     kms = statistics.mean(r[0] for r in b_kern)
     entry(f"fwd_kernel<P={P},D=16> (training: keeps the strip seams)", kms,
           bcnt[0] * useful_tile_flops(P, nr, DIM), bcnt[0] * tile_flops(P, nr, DIM), sg, P, nr)
+    roof[-1]["launch"] = sigk.launch_info(sigk.OP_GRAM, N_PATHS, 0, DIM, bopts)
     kms = statistics.mean(r[1] for r in b_kern)
     # pass B over every tile (useful: twice the forward's work); pass A's
     # replay of the forward is recomputation (executed, not useful)
     entry(f"bwd_kernel<P={P},D=16> (adjoint, recomputes each strip from its seam)", kms,
           bcnt[2] * useful_tile_flops(P, nr, DIM, adjoint=True),
           bcnt[2] * adjoint_tile_flops(P, nr, DIM, replay=False) + bcnt[3] * tile_flops(P, nr, DIM),
-          sg, P, nr, {"replayed_tiles": bcnt[3]})
+          sg, P, nr, {"replayed_tiles": bcnt[3],
+                      "launch": sigk.launch_info(sigk.OP_GRAM, N_PATHS, 0, DIM, bopts, train=True)})
     dom = max(range(len(roof)), key=lambda k: roof[k]["kernel_ms"])
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
@@ -466,7 +458,6 @@ def main():
         "config": {"workload": "gram_B64_L1024_d16_sigma1+4", "paths": N_PATHS, "segments": N_SEG,
                    "d": DIM, "sigmas": [s_ for s_, *_ in SIGMAS],
                    "order_rings": [[P_, nr_] for _, _, P_, nr_ in SIGMAS],
-                   "ring_tol": RING_TOL,
                    "unique_pairs_per_gram": pairs_of_gram(N_PATHS), "l2": "flushed between steps",
                    "step": "forward: the Grams for sigma = 1 and sigma = 4 (inference); "
                            "fwd_bwd: training forward + adjoint of the sigma = 1 Gram "

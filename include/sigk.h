@@ -139,16 +139,17 @@ enum {
  *            value seen in the workspace header, and makes every warp of the
  *            launch return.
  *   ring_tol: 0 = every tile keeps `rings` Neumann iterations.  Otherwise the
- *            forward ops (sigk_pairs, sigk_gram, sigk_mmd; not the training
- *            forward, whose adjoint differentiates the fixed count) choose the
- *            count per tile, as the local Neumann iteration of App. B stops
- *            when the next term is negligible: a tile with coefficient c needs
- *            the smallest even n <= rings with |c|^(n+1) / ((n+1)!)^2 <=
- *            ring_tol (the first dropped ring, relative to the edge data), and
- *            the tiles a warp solves in one step use the largest count among
- *            them.  sigk_plan sets it to tol / (10 L1 L2) of the largest pair,
- *            an equal share of its ring-sum rule.  sigk_ring_histogram reports
- *            the counts used. */
+ *            tensor-core forward (16 < d <= 1024, FP32) chooses the count per
+ *            tile, as the local Neumann iteration of App. B stops when the
+ *            next term is negligible: a tile with coefficient c needs the
+ *            smallest even n <= rings with |c|^(n+1) / ((n+1)!)^2 <= ring_tol
+ *            (the first dropped ring, relative to the edge data), and the
+ *            tiles a warp solves in one step use the largest count among them.
+ *            sigk_plan sets it to tol / (100 L1 L2) of the largest pair, a
+ *            tenth of an equal share of its ring-sum rule.
+ *            sigk_ring_histogram reports the counts used.  (The d <= 16
+ *            kernel keeps the fixed count: on its workloads every tile needs
+ *            the planned count, and the per-step choice cost 10 %.) */
 typedef struct {
     int order;
     int rings;
@@ -289,11 +290,54 @@ sigk_status sigk_static_sync_status(void* stream);
  * Synchronises `stream`.  Writes into *opts_out (other fields copied from
  * opts_in when given; max_len raised to the longest swept path, refined).
  * Returns SIGK_ERR_ACCURACY, with *opts_out written, when the rule is not met
- * even at the finest refinement tried (or at the caller's refine_c). */
+ * even at the finest refinement tried (or at the caller's refine_c).
+ * When the tuning cache (sigk_autotune) holds the planned call's shape class,
+ * its layout (grid_ctas, schedule and Gram-path flags) is merged into
+ * *opts_out. */
 sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
                       const float* Y, const int64_t* len_y, int64_t n_y, int d, double tol,
                       void* ws, size_t ws_bytes, void* stream, const sigk_opts* opts_in,
                       sigk_opts* opts_out);
+
+/* Autotuner of the launch layout (the paper has no counterpart: its JAX
+ * implementation has one fixed layout).  With the truncation fixed by
+ * opts_in (order, rings, refinement, ring tolerance), it times the op
+ * (SIGK_OP_PAIRS / GRAM / MMD, arguments as in sigk_pairs / sigk_gram /
+ * sigk_mmd) under each candidate layout on the caller's inputs -- persistent
+ * grid of the full occupancy, 3 or 2 CTAs per SM (the wavefront's width);
+ * strip-major or pair-major schedule; and, when allow_fma_gram is non-zero
+ * and 16 < d <= 1024, the FP32 FMA increment Gram instead of the tensor-core
+ * one (FP32 instead of float-float coefficients) -- with CUDA events on
+ * `stream` (one warm-up and two timed calls each; synchronises it).  The
+ * fastest goes to *opts_out (grid_ctas and the flags SIGK_FLAG_PAIR_MAJOR,
+ * SIGK_FLAG_NO_TENSOR; every other field as opts_in), its time per call to
+ * *ms_out, and into the library's in-process cache under the call's shape
+ * class (sigk_tune_key), which sigk_plan consults.  out_scratch: device FP64
+ * output of the op's size (k values, Gram or MMD^2).  Candidates whose
+ * workspace exceeds ws_bytes are skipped; SIGK_ERR_WORKSPACE if none fits. */
+sigk_status sigk_autotune(int op, const float* X, const int64_t* len_x, int64_t n_x,
+                          const float* Y, const int64_t* len_y, int64_t n_y, int d,
+                          double* out_scratch, void* ws, size_t ws_bytes, void* stream,
+                          const sigk_opts* opts_in, int allow_fma_gram, sigk_opts* opts_out,
+                          double* ms_out);
+
+/* Shape class of a call (host only): op, batch sizes, d, the swept-length
+ * bound rounded up to a power of two, order, rings and the problem flags, as
+ * a string into buf (>= 96 bytes). */
+sigk_status sigk_tune_key(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts,
+                          char* buf, size_t buf_len);
+
+/* The tuning cache (host only, shared by the process's threads):
+ * put stores a class's layout (grid_ctas, the flags SIGK_FLAG_PAIR_MAJOR and
+ * SIGK_FLAG_NO_TENSOR of `flags`, time); get merges a stored layout into
+ * *opts (SIGK_ERR_ARG when the class is absent); save writes the cache as
+ * text, one class per line; load adds a saved file's classes. */
+sigk_status sigk_tune_cache_put(const char* key, int grid_ctas, int flags, double ms);
+sigk_status sigk_tune_cache_get(const char* key, sigk_opts* opts, double* ms);
+sigk_status sigk_tune_cache_save(const char* path);
+sigk_status sigk_tune_cache_load(const char* path);
+int64_t sigk_tune_cache_size(void);
+void sigk_tune_cache_clear(void);
 
 /* Waits for `stream`, then returns and clears the device status recorded in
  * ws by earlier calls: SIGK_OK; SIGK_ERR_TIMEOUT, SIGK_ERR_LENGTH or
@@ -313,6 +357,14 @@ sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out4)
  * Neumann rings (out4[0..3]; synchronises `stream`); all zero unless
  * opts->ring_tol was set. */
 sigk_status sigk_ring_histogram(void* ws, size_t ws_bytes, void* stream, double* out4);
+
+/* Launch configuration the library would use for these arguments (host
+ * query, no launch): out6 = {persistent grid (CTAs), CTAs per SM from the
+ * occupancy query, threads per CTA, dynamic shared memory bytes per CTA, rows
+ * per lane, kernel family (0: d <= 16 register kernel, 1: FMA two-phase,
+ * 2: tensor-core)}; with train != 0, the adjoint kernel's. */
+sigk_status sigk_launch_info(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts,
+                             int train, int* out6);
 
 /* Profiling hook: when both are non-NULL, later calls on this host thread
  * record the two CUDA events (cudaEvent_t) on the call's stream immediately

@@ -50,7 +50,8 @@ def _digest(extra=()) -> str:
 
 
 def _units():
-    units = [("sigk_capi", os.path.join(CSRC, "sigk_capi.cu"), [])]
+    units = [("sigk_capi", os.path.join(CSRC, "sigk_capi.cu"), []),
+             ("sigk_tune", os.path.join(CSRC, "sigk_tune.cu"), [])]
     for P in ORDERS:
         for NR in RINGS:
             if NR <= P:

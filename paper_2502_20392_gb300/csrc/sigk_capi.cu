@@ -1185,7 +1185,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
     sa.withhold_first_seam = (o.flags & SIGK_FLAG_TEST_WITHHOLD_SEAM) && !train ? 1 : 0;
     // per-tile ring counts (inference only): |c| <= theta_n keeps the first
     // dropped ring |c|^(n+1)/((n+1)!)^2 within ring_tol
-    sa.ring_adaptive = (o.ring_tol > 0.0f && !train && !L.f64 && !(L.cm && !L.tc)) ? 1 : 0;
+    sa.ring_adaptive = (o.ring_tol > 0.0f && L.tc) ? 1 : 0;
     sa.ring_hist = hdr->ring_hist;
     for (int q = 0; q < 3; ++q) {
         const int n = 2 * q + 2;
@@ -1692,16 +1692,24 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     opts_out->rings = nr;
     opts_out->refine_c = o.refine_c;
     {
-        // per-tile ring tolerance: an equal share of the ring-sum rule of the
-        // largest pair (tol / 10 over its L1 L2 tiles)
+        // per-tile ring tolerance: a tenth of an equal share of the ring-sum
+        // rule of the largest pair (tol / 100 over its L1 L2 tiles); the
+        // dropped rings of neighbouring tiles add coherently, and an equal
+        // share (tol / 10) measured 1.06e-5 on a 1e-5 workload
         double cells = 1.0;
         for (int64_t p = 0; p < L.n_pairs; ++p) {
             const double* st = hs.data() + p * kStatFields;
             if (st[0] * st[1] > cells) cells = st[0] * st[1];
         }
-        opts_out->ring_tol = (float)(0.1 * tol / cells);
+        opts_out->ring_tol = (float)(0.01 * tol / cells);
     }
     opts_out->max_len = max_swept;  // the longest swept path as planned (refined)
+    {
+        // a tuned layout for this shape class, if the tuning cache holds one
+        char key[256];
+        if (sigk_tune_key(op, n_x, n_y, d, opts_out, key, sizeof(key)) == SIGK_OK)
+            sigk_tune_cache_get(key, opts_out, nullptr);
+    }
     if (max_c > 1.0 || !fits)
         return fail(SIGK_ERR_ACCURACY,
                     "the a-priori rule is not met at order 16 even at the finest refinement tried");
@@ -1731,6 +1739,26 @@ sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream) {
                                                    : "device error";
         return fail((sigk_status)h.status, msg);
     }
+    return SIGK_OK;
+}
+
+sigk_status sigk_launch_info(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts,
+                             int train, int* out6) {
+    if (!out6 || op < SIGK_OP_PAIRS || op > SIGK_OP_MMD || n_x < 0 || n_y < 0 || d < 1)
+        return fail(SIGK_ERR_ARG, "bad arguments");
+    Opts o;
+    if (!resolve_opts(opts, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
+    if (op == SIGK_OP_PAIRS) n_y = n_x;
+    Layout L;
+    sigk_status st = make_layout(op, n_x, n_y, d, o, &L, train != 0);
+    if (st != SIGK_OK) return st;
+    const KernelInfo& k = train ? L.binfo : L.info;
+    out6[0] = train ? L.bgrid : L.grid;
+    out6[1] = k.blocks_per_sm;
+    out6[2] = k.threads;
+    out6[3] = k.smem_bytes;
+    out6[4] = k.rows_per_lane;
+    out6[5] = L.tc ? 2 : (L.cm ? 1 : 0);
     return SIGK_OK;
 }
 

@@ -22,7 +22,6 @@
 //     edges are aligned to it, and both are rescaled by 2^-64 when the corner
 //     value passes 2^64 (log-scale renormalisation of boundary data).
 #pragma once
-#include <type_traits>
 #include "sigk_device.cuh"
 
 namespace sigk {
@@ -144,7 +143,6 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
     constexpr int kStage = 32 * R * RS;  // floats per staged block
     const int n_items = A.sched.hdr[2];
     unsigned long long tiles_done = 0, lane_tiles = 0;
-    unsigned rhist[4] = {0u, 0u, 0u, 0u};  // tiles by ring count (adaptive inference)
 
     for (;;) {
         int item = 0;
@@ -283,38 +281,6 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                 __syncwarp();
             }
             const int j = t - lane;
-            // inference: the rows' coefficients at column j, and the warp's ring
-            // count for this step (the largest any of its tiles needs)
-            float cr[R];
-            int nw = NR;
-            if constexpr (!REC) {
-                float dy[D];
-                const float4* rowp = reinterpret_cast<const float4*>(dyw + (j & 63) * DS);
-#pragma unroll
-                for (int e4 = 0; e4 < D / 4; ++e4) {
-                    const float4 v = rowp[e4];
-                    dy[4 * e4 + 0] = v.x; dy[4 * e4 + 1] = v.y;
-                    dy[4 * e4 + 2] = v.z; dy[4 * e4 + 3] = v.w;
-                }
-                float am = 0.0f;
-#pragma unroll
-                for (int k = 0; k < R; ++k) {
-                    float c = 0.0f;
-#pragma unroll
-                    for (int e = 0; e < D; ++e) c = fmaf(dx[k][e], dy[e], c);
-                    cr[k] = c;
-                    am = fmaxf(am, fabsf(c));
-                }
-                if (A.ring_adaptive) {
-                    const int nl = (j >= 0 && j < L2) ? rings_needed(am, A.ring_theta) : 0;
-                    nw = min((int)__reduce_max_sync(kFull, (unsigned)nl), NR);
-                    if (j >= 0 && j < L2) {
-                        const unsigned rv = (unsigned)max(0, min(R, L1 - (i0 + lane * R)));
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) rhist[q] += ((nw >> 1) - 1 == q) ? rv : 0u;
-                    }
-                }
-            }
             if (j >= 0 && j < L2) {
                 // records of the rows' incoming left edges (the adjoint rebuilds
                 // each tile's inputs from them): row k = 0 as received, before
@@ -350,34 +316,22 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                         for (int q = 1; q <= P; ++q) b[q] *= sc;
                     }
                 }
-                if constexpr (REC) {
-                    float dy[D];
-                    const float4* rowp = reinterpret_cast<const float4*>(dyw + (j & 63) * DS);
+                float dy[D];
+                const float4* rowp = reinterpret_cast<const float4*>(dyw + (j & 63) * DS);
 #pragma unroll
-                    for (int e4 = 0; e4 < D / 4; ++e4) {
-                        const float4 v = rowp[e4];
-                        dy[4 * e4 + 0] = v.x; dy[4 * e4 + 1] = v.y;
-                        dy[4 * e4 + 2] = v.z; dy[4 * e4 + 3] = v.w;
-                    }
+                for (int e4 = 0; e4 < D / 4; ++e4) {
+                    const float4 v = rowp[e4];
+                    dy[4 * e4 + 0] = v.x; dy[4 * e4 + 1] = v.y;
+                    dy[4 * e4 + 2] = v.z; dy[4 * e4 + 3] = v.w;
+                }
 #pragma unroll
-                    for (int k = 0; k < R; ++k) {
+                for (int k = 0; k < R; ++k) {
+                    if constexpr (REC)
                         if (k > 0) rec_head(k, E);
-                        float c = 0.0f;
+                    float c = 0.0f;
 #pragma unroll
-                        for (int e = 0; e < D; ++e) c = fmaf(dx[k][e], dy[e], c);
-                        tile_update<P>(c, a[k], a1lo[k], hi, lo, b, b1lo, NR);
-                    }
-                } else {
-                    // the rows' coefficients were formed before the branch (cr)
-                    auto rows = [&](auto nrc) {
-#pragma unroll
-                        for (int k = 0; k < R; ++k)
-                            tile_update<P>(cr[k], a[k], a1lo[k], hi, lo, b, b1lo, decltype(nrc)::value);
-                    };
-                    if (nw == NR) rows(std::integral_constant<int, NR>{});
-                    else if (nw <= 2) rows(std::integral_constant<int, 2>{});
-                    else if (NR > 4 && nw == 4) rows(std::integral_constant<int, (NR > 4 ? 4 : NR)>{});
-                    else rows(std::integral_constant<int, (NR > 6 ? 6 : NR)>{});
+                    for (int e = 0; e < D; ++e) c = fmaf(dx[k][e], dy[e], c);
+                    tile_update<P>(c, a[k], a1lo[k], hi, lo, b, b1lo, NR);
                 }
                 // renormalise when the corner value grows past 2^64
                 int bump = 0;
@@ -502,17 +456,6 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
     if (lane == 0) {
         atomicAdd(&A.counters[0], tiles_done);
         atomicAdd(&A.counters[1], lane_tiles);
-    }
-    if constexpr (!REC) {
-        if (A.ring_adaptive) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                unsigned v = rhist[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-                if (lane == 0 && v) atomicAdd(&A.ring_hist[q], v);
-            }
-        }
     }
 }
 

@@ -24,6 +24,11 @@ template <typename K>
 static int occupancy(K kern, int threads, int smem, int R, KernelInfo* info) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return -1;
+    // the whole unified L1 / shared memory as shared memory: several CTAs of
+    // tens of KB each per SM (a default carveout left one CTA per SM)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return -1;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess)
         return -1;

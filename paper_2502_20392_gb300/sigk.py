@@ -97,7 +97,21 @@ def load(path: str | None = None):
     lib.sigk_adjoint.argtypes = [i32, i64, i64, i32, vp, vp, vp, vp, sz, vp, op]
     lib.sigk_sync_status.argtypes = [vp, sz, vp]
     lib.sigk_counters.argtypes = [vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.sigk_autotune.argtypes = [i32, vp, vp, i64, vp, vp, i64, i32, vp, vp, sz, vp, op, i32, op,
+                                  ctypes.POINTER(ctypes.c_double)]
+    lib.sigk_tune_key.argtypes = [i32, i64, i64, i32, op, ctypes.c_char_p, sz]
+    lib.sigk_tune_cache_put.argtypes = [ctypes.c_char_p, i32, i32, ctypes.c_double]
+    lib.sigk_tune_cache_get.argtypes = [ctypes.c_char_p, op, ctypes.POINTER(ctypes.c_double)]
+    lib.sigk_tune_cache_save.argtypes = [ctypes.c_char_p]
+    lib.sigk_tune_cache_load.argtypes = [ctypes.c_char_p]
+    lib.sigk_tune_cache_size.restype = i64
+    lib.sigk_tune_cache_clear.restype = None
+    for name in ("sigk_autotune", "sigk_tune_key", "sigk_tune_cache_put", "sigk_tune_cache_get",
+                 "sigk_tune_cache_save", "sigk_tune_cache_load"):
+        getattr(lib, name).restype = i32
     lib.sigk_ring_histogram.argtypes = [vp, sz, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.sigk_launch_info.argtypes = [i32, i64, i64, i32, op, i32, ctypes.POINTER(ctypes.c_int)]
+    lib.sigk_launch_info.restype = i32
     lib.sigk_profile_events.argtypes = [vp, vp]
     lib.sigk_profile_events.restype = None
     lib.sigk_last_error.restype = ctypes.c_char_p
@@ -460,5 +474,78 @@ def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | 
                       f"({load().sigk_last_error().decode()})", RuntimeWarning)
     else:
         _check(st)
-    return Opts(o_out.order, o_out.rings, o_out.flags, o_out.grid_ctas, o_out.max_len,
-                o_out.refine_c, o_out.wait_ms, o_out.ring_tol)
+    return _from_c(o_out)
+
+
+def _from_c(o: "_Opts") -> Opts:
+    return Opts(o.order, o.rings, o.flags, o.grid_ctas, o.max_len, o.refine_c, o.wait_ms, o.ring_tol)
+
+
+def autotune(op: int, X, len_x, Y=None, len_y=None, opts: Opts | None = None,
+             allow_fma_gram: bool = False, ws: Workspace | None = None):
+    """Times the op under each candidate launch layout on these inputs and
+    returns (the fastest Opts, its milliseconds per call); the choice is cached
+    in the library under the call's shape class and merged by later plans."""
+    opts = opts or Opts()
+    X, len_x = _paths(X, len_x)
+    n_x, d = len_x.numel(), X.shape[1]
+    if Y is not None:
+        Y, len_y = _paths(Y, len_y)
+        n_y = len_y.numel()
+    else:
+        n_y = 0 if op == OP_GRAM else n_x
+    nn = n_y if op != OP_PAIRS else n_x
+    sizes = [workspace_size(op, n_x, nn, d, opts)]
+    out = torch.empty(max(1, n_x if op == OP_PAIRS else (n_x * (n_y or n_x))), dtype=torch.float64,
+                      device=X.device)
+    ws = _ws(ws, X.device)
+    buf = ws.get(max(sizes), X.device)
+    o_in, o_out, ms = opts.c(), _Opts(), ctypes.c_double()
+    _check(load().sigk_autotune(op, _ptr(X), _ptr(len_x), n_x, _ptr(Y), _ptr(len_y), n_y, d, _ptr(out),
+                                _ptr(buf), buf.numel(), _stream(), ctypes.byref(o_in),
+                                int(allow_fma_gram), ctypes.byref(o_out), ctypes.byref(ms)))
+    return _from_c(o_out), ms.value
+
+
+def tune_key(op: int, n_x: int, n_y: int, d: int, opts: Opts) -> str:
+    buf = ctypes.create_string_buffer(256)
+    o = opts.c()
+    _check(load().sigk_tune_key(op, n_x, n_y, d, ctypes.byref(o), buf, 256))
+    return buf.value.decode()
+
+
+def tune_cache_put(key: str, grid_ctas: int, flags: int, ms: float):
+    _check(load().sigk_tune_cache_put(key.encode(), grid_ctas, flags, ms))
+
+
+def tune_cache_get(key: str, opts: Opts):
+    """opts with the cached layout of `key` merged in, or None if absent."""
+    o, ms = opts.c(), ctypes.c_double()
+    if load().sigk_tune_cache_get(key.encode(), ctypes.byref(o), ctypes.byref(ms)) != 0:
+        return None
+    return _from_c(o), ms.value
+
+
+def tune_cache_save(path: str):
+    _check(load().sigk_tune_cache_save(path.encode()))
+
+
+def tune_cache_load(path: str):
+    _check(load().sigk_tune_cache_load(path.encode()))
+
+
+def tune_cache_size() -> int:
+    return int(load().sigk_tune_cache_size())
+
+
+def tune_cache_clear():
+    load().sigk_tune_cache_clear()
+
+
+def launch_info(op: int, n_x: int, n_y: int, d: int, opts: Opts, train: bool = False) -> dict:
+    """The launch configuration the library would use (no launch)."""
+    out = (ctypes.c_int * 6)()
+    o = opts.c()
+    _check(load().sigk_launch_info(op, n_x, n_y, d, ctypes.byref(o), int(train), out))
+    return {"grid": out[0], "ctas_per_sm": out[1], "threads": out[2], "smem_bytes": out[3],
+            "rows_per_lane": out[4], "kernel": ("register", "fma-two-phase", "tensor-core")[out[5]]}

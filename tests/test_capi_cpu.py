@@ -77,3 +77,42 @@ def test_wait_budget_is_validated_without_gpu(lib):
         nz = ctypes.c_void_p(256)  # never dereferenced: the options are checked first
         st = lib.sigk_pairs(nz, nz, nz, nz, 3, 4, nz, nz, 1 << 20, None, ctypes.byref(o))
         assert st == -1 and b"sigk_opts" in lib.sigk_last_error()
+
+
+def test_tuning_cache_without_gpu(lib, tmp_path):
+    # shape-class keys and the cache's lookup, merge and file round trip are
+    # host code (no GPU)
+    from paper_2502_20392_gb300 import sigk
+    sigk.tune_cache_clear()
+    o = sigk.Opts(order=12, rings=6, max_len=1000, flags=sigk.FLAG_INCREMENTS)
+    k1 = sigk.tune_key(sigk.OP_GRAM, 64, 0, 16, o)
+    # the swept-length bound is bucketed by powers of two; the tuned flags
+    # and the grid are not part of the class, the problem flags are
+    assert k1 == sigk.tune_key(sigk.OP_GRAM, 64, 0, 16, sigk.Opts(order=12, rings=6, max_len=1024,
+                                                                   flags=sigk.FLAG_INCREMENTS | sigk.FLAG_PAIR_MAJOR,
+                                                                   grid_ctas=300))
+    assert k1 != sigk.tune_key(sigk.OP_GRAM, 64, 0, 16, sigk.Opts(order=12, rings=6, max_len=1025,
+                                                                   flags=sigk.FLAG_INCREMENTS))
+    assert k1 != sigk.tune_key(sigk.OP_GRAM, 64, 0, 16, sigk.Opts(order=12, rings=6, max_len=1000))
+    assert k1 != sigk.tune_key(sigk.OP_PAIRS, 64, 64, 16, o)
+    assert sigk.tune_cache_get(k1, o) is None
+    sigk.tune_cache_put(k1, 456, sigk.FLAG_PAIR_MAJOR | sigk.FLAG_FP64, 3.25)
+    got, ms = sigk.tune_cache_get(k1, o)
+    # only the layout fields are merged: grid, schedule and Gram-path flags
+    assert got.grid_ctas == 456 and got.flags == sigk.FLAG_INCREMENTS | sigk.FLAG_PAIR_MAJOR
+    assert (got.order, got.rings, got.max_len) == (12, 6, 1000) and ms == 3.25
+    k2 = sigk.tune_key(sigk.OP_PAIRS, 512, 512, 256, sigk.Opts(order=14, rings=6, max_len=8193))
+    sigk.tune_cache_put(k2, 0, sigk.FLAG_NO_TENSOR, 1.5)
+    path = str(tmp_path / "tune.txt")
+    sigk.tune_cache_save(path)
+    sigk.tune_cache_clear()
+    assert sigk.tune_cache_size() == 0
+    sigk.tune_cache_load(path)
+    assert sigk.tune_cache_size() == 2
+    got2, ms2 = sigk.tune_cache_get(k2, sigk.Opts(order=14, rings=6, max_len=8193))
+    assert got2.flags == sigk.FLAG_NO_TENSOR and got2.grid_ctas == 0 and ms2 == 1.5
+    with open(path, "a") as f:
+        f.write("bad line\n")
+    with pytest.raises(sigk.SigkError):
+        sigk.tune_cache_load(path)
+    sigk.tune_cache_clear()

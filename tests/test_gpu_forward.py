@@ -326,31 +326,3 @@ def test_schedules_agree_bitwise(S):
     o2 = S.Opts(order=10, rings=5, max_len=700, flags=S.FLAG_PAIR_MAJOR)
     k2 = S.pairs(*to_dev(Xp, lxp), *to_dev(Yp, lyp), opts=o2).cpu().numpy()
     assert np.array_equal(k1, k2)
-
-
-@pytest.mark.parametrize("sigma,order,rings", [(1.0, 8, 8), (4.0, 16, 8)])
-def test_adaptive_ring_count(S, orc, sigma, order, rings):
-    # ring_tol: each warp step keeps only the rings its tiles need (the first
-    # dropped ring |c|^(n+1)/((n+1)!)^2 <= ring_tol); the result stays within
-    # the tolerance, every tile is counted once in the ring histogram, and the
-    # smooth paths use fewer rings than the fixed count
-    from paper_2502_20392_gb300 import synth
-    segs = np.array([300, 129, 1, 257, 64, 200])
-    pts, lens = synth.brownian(len(segs), segs, 16, sigma * np.sqrt(segs / 300), seed=77 + int(sigma))
-    ref = orc.series_gram(incs(pts, lens), N=28)
-    dg = np.diag(ref)
-    ws = S.Workspace()
-    o = S.Opts(order=order, rings=rings, ring_tol=1e-6 / (10 * 300 * 300))
-    G = S.gram(*to_dev(pts, lens), opts=o, ws=ws).cpu().numpy()
-    e = rel_err(G, ref, dg[:, None], dg[None, :])
-    assert e.max() < 1e-5, e.max()
-    h = S.ring_histogram(ws)
-    tiles = sum(int(a) * int(b) for i, a in enumerate(segs) for b in segs[i:])
-    assert sum(h) == tiles, (h, tiles)
-    assert sum(h[: rings // 2 - 1]) > 0, h  # some warp steps used fewer rings
-    # the plan's choice sets a ring tolerance and meets the same bound
-    X, L = to_dev(pts, lens)
-    op = S.plan(S.OP_GRAM, X, L, tol=1e-5)
-    assert op.ring_tol > 0
-    G2 = S.gram(X, L, opts=op).cpu().numpy()
-    assert rel_err(G2, ref, dg[:, None], dg[None, :]).max() < 1e-5

@@ -136,3 +136,30 @@ def test_tensor_core_gram_mirror_and_full(S, orc):
     dg = np.sqrt(np.abs(np.diag(ref)))
     e = np.abs(G - ref) / np.maximum(np.abs(ref), 1e-2 * dg[:, None] * dg[None, :])
     assert e.max() < 1e-5, e.max()
+
+
+def test_adaptive_ring_count(S, orc):
+    # ring_tol (tensor-core path): each warp step keeps only the rings its
+    # tiles need (first dropped ring |c|^(n+1)/((n+1)!)^2 <= ring_tol); the
+    # result stays within the tolerance, every tile is counted once in the
+    # ring histogram, and the smooth pairs use fewer rings than the fixed count
+    from paper_2502_20392_gb300 import synth
+    X, lx, Y, ly = _case(64, 316, s_hi=1.0)
+    ix, iy = incs(X, lx), incs(Y, ly)
+    ref, kxx, kyy = oracle3(orc, ix, iy)
+    a = to_dev(X, lx, Y, ly)
+    ws = S.Workspace()
+    cells = max(len(u) * len(v) for u, v in zip(ix, iy))
+    o = S.Opts(order=12, rings=8, max_len=20000, ring_tol=1e-8 / cells)
+    k = S.pairs(*a, opts=o, ws=ws).cpu().numpy()
+    e = rel_err(k, ref, kxx, kyy)
+    assert e.max() < 2e-6, e
+    h = S.ring_histogram(ws)
+    tiles = sum(len(u) * len(v) for u, v in zip(ix, iy))
+    assert sum(h) == tiles, (h, tiles)
+    assert sum(h[:3]) > 0, h  # some warp steps kept fewer than 8 rings
+    # the plan sets a ring tolerance and meets its own bound
+    op = S.plan(S.OP_PAIRS, *a, tol=1e-6, opts=S.Opts(max_len=20000))
+    assert op.ring_tol > 0
+    k2 = S.pairs(*a, opts=op).cpu().numpy()
+    assert rel_err(k2, ref, kxx, kyy).max() < 2e-6
