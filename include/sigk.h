@@ -161,28 +161,37 @@ typedef struct {
     float ring_tol;
 } sigk_opts;
 
-/* Device workspace bytes needed by sigk_pairs/sigk_gram/sigk_mmd for the
+/* [The one-strip memory of the wavefront sweep, App. C.1 and the O(l P)
+ * memory statement of the complexity discussion, Sec. 3.]
+ * Device workspace bytes needed by sigk_pairs/sigk_gram/sigk_mmd for the
  * given batch sizes (n_x, n_y = number of paths; for SIGK_OP_PAIRS n_x = n_y =
  * number of pairs; for SIGK_OP_GRAM pass n_y = 0 for a Gram of X with itself).
  * Depends on the lengths only through opts->max_len.  Returns 0 on bad
  * arguments. */
 size_t sigk_workspace_size(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts);
 
-/* k_out[p] = k(x_p, y_p) for n_pairs independent pairs (ragged lengths).
+/* [k(x,y) = K(1,1): Sec. 2.1, Definition "Signature Kernel"; solved tile by
+ * tile with the tile-centred expansion, Sec. 2.3 / App. A.6; swept in
+ * anti-diagonal order, App. C.1.]
+ * k_out[p] = k(x_p, y_p) for n_pairs independent pairs (ragged lengths).
  * X, len_x describe the x_p, Y, len_y the y_p (each a batch of n_pairs
  * paths).  k_out: device FP64[n_pairs]. */
 sigk_status sigk_pairs(const float* X, const int64_t* len_x, const float* Y,
                        const int64_t* len_y, int64_t n_pairs, int d, double* k_out,
                        void* ws, size_t ws_bytes, void* stream, const sigk_opts* opts);
 
-/* Gram matrix G[a*n_y + b] = k(x_a, y_b), row-major device FP64[n_x*n_y].
+/* [The Gram matrix of App. A.7 (Proposition on the truncated Gram matrix)
+ * and of the kernel experiments of Sec. 3.]
+ * Gram matrix G[a*n_y + b] = k(x_a, y_b), row-major device FP64[n_x*n_y].
  * Y == NULL (and n_y ignored) means Y = X: G is n_x x n_x; unless
  * SIGK_FLAG_GRAM_FULL, only a <= b is computed and mirrored. */
 sigk_status sigk_gram(const float* X, const int64_t* len_x, int64_t n_x, const float* Y,
                       const int64_t* len_y, int64_t n_y, int d, double* G, void* ws,
                       size_t ws_bytes, void* stream, const sigk_opts* opts);
 
-/* Signature-kernel MMD^2 between samples X (m paths) and Y (n paths):
+/* [The paper has no MMD: a reduction of the Gram blocks of Sec. 2.1's
+ * kernel, computed in FP64.]
+ * Signature-kernel MMD^2 between samples X (m paths) and Y (n paths):
  * mean_{a!=b} k(x_a,x_b) + mean_{a!=b} k(y_a,y_b) - 2 mean k(x_a,y_b)
  * (U-statistic; SIGK_FLAG_MMD_BIASED: V-statistic with all terms), reduced in
  * FP64 on the device.  mmd2_out: device FP64[1]; gram_out (optional, device
@@ -192,7 +201,9 @@ sigk_status sigk_mmd(const float* X, const int64_t* len_x, int64_t m, const floa
                      double* gram_out, void* ws, size_t ws_bytes, void* stream,
                      const sigk_opts* opts);
 
-/* Workspace bytes for sigk_backward (same arguments as sigk_workspace_size).
+/* [The checkpointed wavefront boundaries of the adjoint; no counterpart in
+ * the paper.]
+ * Workspace bytes for sigk_backward (same arguments as sigk_workspace_size).
  * Includes the forward seam store, which needs up to
  * n_pairs * (ceil(max_len/32) - 1) * max_len * (order + 4) floats, and,
  * unless SIGK_FLAG_REPLAY is set, the store of tile records when it takes at
@@ -229,7 +240,8 @@ sigk_status sigk_backward(int op, const float* X, const int64_t* len_x, int64_t 
                           double* value_out, void* ws, size_t ws_bytes, void* stream,
                           const sigk_opts* opts);
 
-/* The two halves of sigk_backward, for callers that keep the forward's state
+/* [Adjoint of the tile map of Sec. 2.3, as sigk_backward.]
+ * The two halves of sigk_backward, for callers that keep the forward's state
  * until the upstream gradient is known (an autograd forward, then its
  * backward).  sigk_forward_train is the training forward of sigk_backward: it
  * writes the op's output to value_out (as sigk_backward does) and leaves the
@@ -274,7 +286,8 @@ sigk_status sigk_pairs_static(const float* X, const int64_t* len_x, const float*
                               const int64_t* len_y, int64_t n_pairs, int d, double* k_out,
                               void* stream, const sigk_opts* opts);
 
-/* sigk_sync_status for the static scratch of sigk_pairs_static. */
+/* [No counterpart in the paper.]  sigk_sync_status for the static scratch of
+ * sigk_pairs_static. */
 sigk_status sigk_static_sync_status(void* stream);
 
 /* A-priori truncation choice (App. C.3: order search from the largest
@@ -321,13 +334,15 @@ sigk_status sigk_autotune(int op, const float* X, const int64_t* len_x, int64_t 
                           const sigk_opts* opts_in, int allow_fma_gram, sigk_opts* opts_out,
                           double* ms_out);
 
-/* Shape class of a call (host only): op, batch sizes, d, the swept-length
+/* [No counterpart in the paper.]
+ * Shape class of a call (host only): op, batch sizes, d, the swept-length
  * bound rounded up to a power of two, order, rings and the problem flags, as
  * a string into buf (>= 96 bytes). */
 sigk_status sigk_tune_key(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts,
                           char* buf, size_t buf_len);
 
-/* The tuning cache (host only, shared by the process's threads):
+/* [No counterpart in the paper.]
+ * The tuning cache (host only, shared by the process's threads):
  * put stores a class's layout (grid_ctas, the flags SIGK_FLAG_PAIR_MAJOR and
  * SIGK_FLAG_NO_TENSOR of `flags`, time); get merges a stored layout into
  * *opts (SIGK_ERR_ARG when the class is absent); save writes the cache as
@@ -339,7 +354,9 @@ sigk_status sigk_tune_cache_load(const char* path);
 int64_t sigk_tune_cache_size(void);
 void sigk_tune_cache_clear(void);
 
-/* Waits for `stream`, then returns and clears the device status recorded in
+/* [No counterpart in the paper: the bounded waits of the persistent
+ * wavefront.]
+ * Waits for `stream`, then returns and clears the device status recorded in
  * ws by earlier calls: SIGK_OK; SIGK_ERR_TIMEOUT, SIGK_ERR_LENGTH or
  * SIGK_ERR_BOUNDS, after which the call's outputs are undefined (the launch
  * stopped); or SIGK_ERR_NONFINITE, when some output is NaN or infinite (from
@@ -347,18 +364,21 @@ void sigk_tune_cache_clear(void);
  * other output is valid. */
 sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream);
 
-/* Counters of the last call on this workspace (synchronises `stream`):
+/* [Tiles of the App. C.1 sweep, for the work accounting.]
+ * Counters of the last call on this workspace (synchronises `stream`):
  * out[0] = tiles solved by the forward, out[1] = lane-tiles including strip
  * padding, out[2] = tiles solved by the adjoint kernel, out[3] = tiles the
  * adjoint kernel replayed (0 when the forward stored the tile records). */
 sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out4);
 
-/* Tiles solved by the last forward on this workspace with 2, 4, 6 and 8
+/* [The per-tile Neumann iteration counts of App. B.]
+ * Tiles solved by the last forward on this workspace with 2, 4, 6 and 8
  * Neumann rings (out4[0..3]; synchronises `stream`); all zero unless
  * opts->ring_tol was set. */
 sigk_status sigk_ring_histogram(void* ws, size_t ws_bytes, void* stream, double* out4);
 
-/* Launch configuration the library would use for these arguments (host
+/* [No counterpart in the paper.]
+ * Launch configuration the library would use for these arguments (host
  * query, no launch): out6 = {persistent grid (CTAs), CTAs per SM from the
  * occupancy query, threads per CTA, dynamic shared memory bytes per CTA, rows
  * per lane, kernel family (0: d <= 16 register kernel, 1: FMA two-phase,
@@ -366,16 +386,18 @@ sigk_status sigk_ring_histogram(void* ws, size_t ws_bytes, void* stream, double*
 sigk_status sigk_launch_info(int op, int64_t n_x, int64_t n_y, int d, const sigk_opts* opts,
                              int train, int* out6);
 
-/* Profiling hook: when both are non-NULL, later calls on this host thread
+/* [No counterpart in the paper.]
+ * Profiling hook: when both are non-NULL, later calls on this host thread
  * record the two CUDA events (cudaEvent_t) on the call's stream immediately
  * before and after the solver kernel launch, so that a caller can time the
  * solver alone.  Pass NULL, NULL to stop. */
 void sigk_profile_events(void* ev_start, void* ev_stop);
 
-/* Thread-local message for the last error returned on this host thread. */
+/* [No counterpart in the paper.]  Thread-local message for the last error
+ * returned on this host thread. */
 const char* sigk_last_error(void);
 
-/* Library version string. */
+/* [No counterpart in the paper.]  Library version string. */
 const char* sigk_version(void);
 
 #ifdef __cplusplus

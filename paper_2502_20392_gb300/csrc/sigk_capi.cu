@@ -341,10 +341,11 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         L->ycache = off;
         off = align256(off + sizeof(uint16_t) * (size_t)L->n_slots * o.max_len * kTcDigits * L->d_pad);
         L->yexp = off; off = align256(off + sizeof(int32_t) * (size_t)L->n_slots * o.max_len);
-        L->ablk = off; off = align256(off + sizeof(uint16_t) * (size_t)L->grid * kTcDigits * kTcRows * L->d_pad);
-        L->aexp = off; off = align256(off + sizeof(int32_t) * (size_t)L->grid * kTcRows);
+        const size_t workers = (size_t)L->grid * kTcGroups;  // block workers (4-warp groups)
+        L->ablk = off; off = align256(off + sizeof(uint16_t) * workers * kTcDigits * kTcRows * L->d_pad);
+        L->aexp = off; off = align256(off + sizeof(int32_t) * workers * kTcRows);
         L->cst_stride = (o.max_len + 32 + kTcPF) * 32;
-        L->cst = off; off = align256(off + sizeof(float2) * (size_t)L->grid * 4 * L->cst_stride);
+        L->cst = off; off = align256(off + sizeof(float2) * workers * 4 * L->cst_stride);
     } else if (L->cm) {  // one [max_len][32] coefficient strip per warp
         L->cstride = 32 * ((o.max_len + 31) & ~(int64_t)31);
         off = align256(off + L->elem * (size_t)L->nwarps * L->cstride);

@@ -170,9 +170,9 @@ cudaError_t bwd_launch<SIGK_P, SIGK_NR>(int D, const BwdArgs& a, int grid, cudaS
 
 template <>
 int fwd_tc_info<SIGK_P, SIGK_NR>(KernelInfo* info) {
-    const int r = occupancy(fwd_tc_kernel<SIGK_P, SIGK_NR>, 128, TcSmem<SIGK_P>::bytes, 1, info);
-    // at most four CTAs per SM hold TMEM at a time (4 x 128 columns)
-    if (r == 0 && info->blocks_per_sm > 4) info->blocks_per_sm = 4;
+    const int r = occupancy(fwd_tc_kernel<SIGK_P, SIGK_NR>, kTcGroups * 128, TcSmem<SIGK_P>::bytes, 1, info);
+    // one CTA per SM holds the whole TMEM (kTcGroups x 128 columns)
+    if (r == 0 && info->blocks_per_sm > 1) info->blocks_per_sm = 1;
     return r;
 }
 
@@ -182,7 +182,7 @@ cudaError_t fwd_tc_launch<SIGK_P, SIGK_NR>(const TcArgs& a, int grid, cudaStream
     auto kern = fwd_tc_kernel<SIGK_P, SIGK_NR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, 128, smem, s>>>(a);
+    kern<<<grid, kTcGroups * 128, smem, s>>>(a);
     return cudaGetLastError();
 }
 

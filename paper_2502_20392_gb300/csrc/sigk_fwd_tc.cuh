@@ -20,8 +20,8 @@
 //
 // Work unit: a block of 128 rows = four 32-row strips of one pair (the pair
 // table counts 32-row strips, padded to a multiple of four; the schedule is
-// pair-major, so the four strips are consecutive work items).  One CTA owns a
-// block:
+// pair-major, so the four strips are consecutive work items).  A group of
+// four warps owns a block (four groups per CTA, one CTA per SM):
 //   phase 1  the block's rows are cut into digits in a per-CTA global area;
 //            for every 32-column chunk of the swept path, the CTA stages the
 //            digit tiles (16 dimensions per step, two stages, cp.async) in the
@@ -33,8 +33,8 @@
 //   phase 2  warp w sweeps strip w of the block (the wavefront sweep of
 //            sigk_fwd_cm.cuh with one row per lane), seams between strips and
 //            blocks through the global seam ring as in every other solver.
-// Different CTAs of an SM are in different phases, so the tensor-core phase
-// of one overlaps the FMA sweep of the others.  The L1 x L2 coefficient
+// The groups of a CTA are in different phases, so the tensor-core phase of
+// one overlaps the FMA sweep of the others.  The L1 x L2 coefficient
 // matrix is never stored: only one block's strips per CTA exist at a time.
 #pragma once
 #include <type_traits>
@@ -49,6 +49,26 @@ constexpr int kTcK = 16;           // contraction per MMA (BF16)
 constexpr int kTcDigits = 4;       // 8-bit digits per operand
 constexpr int kTcMaxDim = 1024;    // exact accumulation of the leading group
 constexpr int kTcPF = 2;           // sweep: coefficient loads in flight per lane
+// A CTA of this kernel holds TMEM, and the occupancy calculation then allows
+// one CTA per SM whatever its shared memory (measured on this GPU: a kernel
+// that contains tcgen05.alloc gets 1 CTA per SM at 16 KB of shared memory, the
+// same kernel without it 13).  So one CTA per SM runs kTcGroups independent
+// 4-warp groups, each a block worker with its own quarter of TMEM.
+constexpr int kTcGroups = 4;
+
+// Barriers of one 128-thread group (named barrier 1 + gr; barrier 0 is
+// __syncthreads).
+__device__ __forceinline__ void group_sync(int gr) {
+    asm volatile("bar.sync %0, 128;" ::"r"(gr + 1) : "memory");
+}
+__device__ __forceinline__ bool group_and(int gr, bool v) {
+    int r;
+    asm volatile("{\n.reg .pred p, q;\nsetp.ne.s32 p, %1, 0;\nbar.red.and.pred q, %2, 128, p;\nselp.s32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((int)v), "r"(gr + 1)
+                 : "memory");
+    return r != 0;
+}
 
 // Dynamic shared memory of the tensor-core kernel (bytes).  Phase 1: two
 // stages of the digit tiles (A: 4 digits x 128 rows x 16 dims, B: 4 digits x
@@ -62,9 +82,10 @@ struct TcSmem {
     static constexpr int stage = kTcDigits * (a_tile + b_tile);  // 20 KB
     static constexpr int phase1 = 2 * stage;
     static constexpr int phase2 = 4 * 2 * kG * (P + 4) * 4;
-    static constexpr int body = (phase1 > phase2 ? phase1 : phase2) + 1024;  // + 1 KB alignment slack
-    static constexpr int bytes = body < 48 * 1024 ? 48 * 1024 : body;
-    static_assert(bytes <= 54 * 1024, "four CTAs per SM");
+    // per group, 1 KB aligned (tcgen05 operand tiles)
+    static constexpr int group = ((phase1 > phase2 ? phase1 : phase2) + 1023) / 1024 * 1024;
+    static constexpr int bytes = kTcGroups * group + 1024;  // + 1 KB alignment slack
+    static_assert(bytes <= 227 * 1024, "one CTA of kTcGroups groups per SM");
 };
 
 struct TcArgs {
@@ -405,29 +426,40 @@ __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDe
 // ---------------------------------------------------------------------------
 
 template <int P, int NR>
-__global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
+__global__ void __launch_bounds__(kTcGroups * 128, 1) fwd_tc_kernel(TcArgs T) {
     const SolverArgs& A = T.A;
     constexpr int S = P + 4;
     using Sm = TcSmem<P>;
     extern __shared__ float4 smem_tc_raw[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar_g[kTcGroups][2];
     __shared__ uint32_t tmem_base_s;
-    __shared__ int blk_s, st_s, stop_s;
-    __shared__ int32_t yexp_s[2][kTcN];  // column exponents of the chunk (double buffered)
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ int blk_g[kTcGroups], st_g[kTcGroups], stop_g[kTcGroups];
+    __shared__ int32_t yexp_g[kTcGroups][2][kTcN];  // column exponents of the chunk (double buffered)
+    // group gr = warps 4 gr .. 4 gr + 3: an independent block worker with its
+    // own shared memory, TMEM columns [128 gr, 128 gr + 128), mbarriers and
+    // named barrier 1 + gr; warp w % 4 of a group reaches TMEM lanes 32 (w % 4)
+    const int gr = threadIdx.x >> 7;
+    const int tid = threadIdx.x & 127, lane = tid & 31, warp = tid >> 5;
+    const int wid = (int)(blockIdx.x * kTcGroups + gr);  // worker index: per-worker scratch
+    uint64_t* mbar = mbar_g[gr];
+    int& blk_s = blk_g[gr];
+    int& st_s = st_g[gr];
+    int& stop_s = stop_g[gr];
+    int32_t (*yexp_s)[kTcN] = yexp_g[gr];
     const int d = A.d, d_pad = T.d_pad;
     const int KS = d_pad / kTcK;
-    uint16_t* ablk = T.ablk + (int64_t)blockIdx.x * kTcDigits * kTcRows * d_pad;
-    int32_t* aexp = T.aexp + (int64_t)blockIdx.x * kTcRows;
-    float2* cblk = T.cst + (int64_t)blockIdx.x * 4 * T.cst_stride;
+    uint16_t* ablk = T.ablk + (int64_t)wid * kTcDigits * kTcRows * d_pad;
+    int32_t* aexp = T.aexp + (int64_t)wid * kTcRows;
+    float2* cblk = T.cst + (int64_t)wid * 4 * T.cst_stride;
     // operand tiles 1 KB aligned (the dynamic area is 1 KB larger than needed)
     unsigned char* st0 = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_tc_raw) + 1023) & ~(uintptr_t)1023);
+        (reinterpret_cast<uintptr_t>(smem_tc_raw) + 1023) & ~(uintptr_t)1023) + gr * Sm::group;
     float* seam_w = reinterpret_cast<float*>(st0) + warp * 2 * kG * S;  // phase 2 (aliases phase 1)
     unsigned long long tiles_done = 0, lane_tiles = 0;
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tmem_base_s)));
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                     "r"(128 * kTcGroups));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -439,7 +471,7 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tbase = tmem_base_s;
+    const uint32_t tbase = tmem_base_s + 128 * gr;
     unsigned rhist[4] = {0u, 0u, 0u, 0u};  // tiles by ring count (adaptive launches)
     uint32_t step = 0;         // MMA steps of this CTA so far (stage = step & 1)
     int64_t issued = -1;       // last step whose MMAs were committed (CTA-uniform)
@@ -451,9 +483,9 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
             blk_s = atomicAdd(T.block_counter, 1);
             st_s = ld_volatile_s32(A.status);
         }
-        __syncthreads();
+        group_sync(gr);
         const int blk = blk_s, st = st_s;
-        __syncthreads();  // read before thread 0 can overwrite them
+        group_sync(gr);  // read before thread 0 can overwrite them
         if (blk >= n_blocks || st != 0) break;
         const int item = 4 * blk + warp;
         const ItemRef ir = decode_item(A.sched, A.pairs, item);
@@ -470,7 +502,7 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
              dbg_in(A.status, 47, (int64_t)(L2 + pd.sy - 1) / pd.sy, T.max_len) &&
              dbg_in(A.status, 48, (int64_t)(s & 3), warp) && dbg_in(A.status, 49, (int64_t)warp, s & 3);
 #endif
-        ok = __syncthreads_and(ok);
+        ok = group_and(gr, ok);
 
         // ---- phase 1a: digits of the block's 128 rows (32 per warp) -----------
         if (ok) {
@@ -483,7 +515,7 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
                 if (lane == 0) aexp[r] = ex;
             }
         }
-        __syncthreads();
+        group_sync(gr);
         // ---- phase 1b: the coefficients, 32 columns at a time --------------------
         // step n of the block: chunk n / KS, dimensions 16 (n % KS); its digit
         // tiles are copied one step ahead into stage (step + n) & 1
@@ -529,7 +561,7 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
             asm volatile("cp.async.wait_group 1;" ::: "memory");  // step n's tiles have landed
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
-            ok = __syncthreads_and(ok);
+            ok = group_and(gr, ok);
             if (!ok) break;
             const int kk = n % KS;
             if (tid == 0) {
@@ -552,7 +584,7 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
             if (kk == KS - 1) {
                 // the chunk's MMAs are done (the last commit covers all before it)
                 if (!mbar_wait(&mbar[g & 1], (g >> 1) & 1, A.status)) ok = false;
-                ok = __syncthreads_and(ok);
+                ok = group_and(gr, ok);
                 if (!ok) break;
                 waited = g;
                 tc_fence_after();
@@ -591,13 +623,13 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
                     }
                 }
                 tc_fence_before();
-                __syncthreads();  // TMEM is free for the next chunk
+                group_sync(gr);  // TMEM is free for the next chunk
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         step += nst;  // (after an early exit the loop below ends the kernel)
         // ---- phase 2: warp w sweeps strip w of the block -------------------------
-        __syncthreads();
+        group_sync(gr);
         if (ok) {
             if (ir.next >= 0) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
             if (ok)
@@ -610,15 +642,16 @@ __global__ void __launch_bounds__(128, 4) fwd_tc_kernel(TcArgs T) {
             st_release_s64(&A.done[item % A.nslot], (long long)item);
         }
         if (!ok && lane == 0) atomicExch(&stop_s, 1);
-        __syncthreads();
+        group_sync(gr);
         if (stop_s) break;
     }
     // in-flight MMAs (after an early exit) complete before TMEM is freed
     if (issued > waited) mbar_wait(&mbar[issued & 1], (uint32_t)(issued >> 1) & 1, A.status);
     tc_fence_before();
-    __syncthreads();
+    __syncthreads();  // every group is done with TMEM
     tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tbase));
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(128 * kTcGroups));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         tiles_done += __shfl_down_sync(kFull, tiles_done, o);
