@@ -26,7 +26,7 @@
  * SIGK_FLAG_INCREMENTS a row is a segment increment and len[p] counts
  * segments (>= 0).  d is shared by all paths of a call, 1 <= d <= 8192
  * (d <= 16 keeps the increments in registers; larger d computes each strip's
- * coefficients first, see the kernel notes; sigk_backward: d <= 16).
+ * coefficients first, see the kernel notes; sigk_backward: d <= 1024).
  *
  * Precision.  Inputs are FP32.  The series arithmetic is FP32 with a
  * float-float corner value and a per-edge power-of-two exponent; results are
@@ -217,11 +217,13 @@ size_t sigk_backward_workspace_size(int op, int64_t n_x, int64_t n_y, int d, con
  * truncated FP32 scheme; the paper has no gradient -- this is the adjoint of
  * the tile map of Sec. 2.3 swept in reverse wavefront order).
  * The call runs a training forward that stores the right-edge seam of every
- * 32-row strip (checkpointed wavefront boundaries) and, when they fit the
- * budget above, every tile's record; then the adjoint kernel, which replays
- * each strip from its stored seam (only when the records were not stored),
- * rebuilds every tile's inputs by inverting the tile's bottom-to-top update,
- * and chains dk/dc_ij to the increments on the fly.
+ * 32-row strip (checkpointed wavefront boundaries) and, for d <= 16 when they
+ * fit the budget above, every tile's record; then the adjoint kernel, which
+ * per strip forms the strip's coefficients, replays the strip from its stored
+ * seam (only when the records were not stored), sweeps it in reverse --
+ * rebuilding every tile's inputs by inverting the tile's bottom-to-top update
+ * -- and chains dk/dc_ij to the increments with two contractions over the
+ * strip.  d <= 1024 (FP32 coefficients).
  *   op, X, len_x, n_x, Y, len_y, n_y, d: as in sigk_pairs / sigk_gram /
  *     sigk_mmd (SIGK_OP_GRAM with Y == NULL: Gram of X with itself).
  *   grad_out (device FP64): upstream gradient of the op's output --

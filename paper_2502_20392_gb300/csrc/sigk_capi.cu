@@ -155,14 +155,14 @@ static cudaError_t fwd_tc_launch_dispatch(int P, int NR, const TcArgs& a, int gr
     return cudaErrorInvalidValue;
 }
 
-static int bwd_info_dispatch(int P, int NR, int D, KernelInfo* info) {
-    SIGK_DISPATCH_PNR(bwd_info, D, info)
+static int bwd2_info_dispatch(int P, int NR, KernelInfo* info) {
+    SIGK_DISPATCH_PNR(bwd2_info, info)
     return -1;
 }
 
-static cudaError_t bwd_launch_dispatch(int P, int NR, int D, const BwdArgs& a, int grid,
-                                       cudaStream_t s) {
-    SIGK_DISPATCH_PNR(bwd_launch, D, a, grid, s)
+static cudaError_t bwd2_launch_dispatch(int P, int NR, const BwdArgs& a, float* cs, int64_t cstride,
+                                        int grid, cudaStream_t s) {
+    SIGK_DISPATCH_PNR(bwd2_launch, a, cs, cstride, grid, s)
     return cudaErrorInvalidValue;
 }
 
@@ -173,7 +173,8 @@ struct Layout {
     size_t hdr, ox, oy, sx, sy, pairs, item_start, order, lvl, prod, cons, done, seam, gram, total;
     bool strip_major;    // the ring in use can hold whole strips: strip-major allowed
     // backward sections (train == true)
-    size_t store, store_off, pair_exp, pair_w, rec, bprod, bcons, bdone, aseam;
+    size_t store, store_off, pair_exp, pair_w, rec, bprod, bcons, bdone, aseam, bcs;
+    int64_t bcstride;
     int64_t store_floats, rec_stride;
     bool stored_rec;     // the training forward stores every tile's record
     int rec_rows;        // its rows per lane (records are grouped per item of that many strips)
@@ -235,15 +236,16 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->elem = L->f64 ? sizeof(double) : sizeof(float);
     if (L->f64 && train)
         return fail(SIGK_ERR_UNSUPPORTED, "the backward runs in FP32 only (no SIGK_FLAG_FP64)");
-    if (L->cm && train)
-        return fail(SIGK_ERR_UNSUPPORTED, "the backward supports d <= 16");
+    if (L->cm && train && d > kTcMaxDim)
+        return fail(SIGK_ERR_UNSUPPORTED, "the backward supports d <= 1024");
     // stored tile records: (pair, 32-row strip) x (max_len + 32) blocks of
     // 32 records; the training forward then runs with one row per lane
     L->stored_rec = false;
     L->rec_rows = 1;
     L->rstore_floats = 0;
-    if (train && !(o.flags & SIGK_FLAG_REPLAY)) {
+    if (train && !(o.flags & SIGK_FLAG_REPLAY) && !L->cm) {
         // (pair, item of R strips) x (max_len + 32) blocks of 32 R records
+        // (d > 16: the two-phase training forward keeps the seams only)
         const int R = rec_rows_per_lane(o.order, D);
         const int64_t items = ((o.max_len + 31) / 32 + R - 1) / R;
         const double fl = (double)pair_count(op, n_x, n_y, o.flags) * (double)items *
@@ -351,7 +353,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         off = align256(off + L->elem * (size_t)L->nwarps * L->cstride);
     }
     if (train) {
-        if (bwd_info_dispatch(o.order, o.rings, D, &L->binfo) != 0 || L->binfo.blocks_per_sm <= 0)
+        if (bwd2_info_dispatch(o.order, o.rings, &L->binfo) != 0 || L->binfo.blocks_per_sm <= 0)
             return fail(SIGK_ERR_CUDA, "backward occupancy query failed");
         L->bgrid = sms * L->binfo.blocks_per_sm;
         if (o.grid_ctas > 0 && o.grid_ctas < L->bgrid) L->bgrid = o.grid_ctas;
@@ -385,6 +387,10 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         L->bdone = off; off = align256(off + sizeof(long long) * (size_t)L->bnslot);
         L->aseam = off;
         off = align256(off + sizeof(float) * (size_t)L->bnslot * L->bwcols * adj_seam_floats(o.order));
+        // per adjoint warp: its strip's coefficients, then g, skewed
+        L->bcstride = (o.max_len + 34) * 32;
+        L->bcs = off;
+        off = align256(off + sizeof(float) * (size_t)L->bnwarps * L->bcstride);
     }
     L->total = off;
     return SIGK_OK;
@@ -1339,7 +1345,7 @@ static sigk_status launch_adjoint(int op, int64_t n_x, int64_t n_y, int d, const
     ba.rec_cap = L.stored_rec ? L.rstore_floats : 0;
     ba.rec_total = L.stored_rec ? 0 : (int64_t)L.bnwarps * L.rec_stride;
     if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_start, stream);
-    e = bwd_launch_dispatch(o.order, o.rings, dim_bucket(d), ba, L.bgrid, stream);
+    e = bwd2_launch_dispatch(o.order, o.rings, ba, (float*)(base + L.bcs), L.bcstride, L.bgrid, stream);
     if (e != cudaSuccess) return cuda_fail(e, "backward launch");
     if (g_ev_start && g_ev_stop) cudaEventRecord(g_ev_stop, stream);
     return SIGK_OK;

@@ -168,8 +168,13 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
 #pragma unroll
     for (int q = 0; q <= P; ++q) ob[q] = T(0);
     int oE = 0;
-    const int pw_in = slot_in;
-    const int pw_out = slot_out;
+    // training forward (FP32; A.store set): every strip's right-edge seam goes
+    // to the per-pair store (the adjoint's checkpoints) instead of the ring,
+    // with one progress word per item
+    const bool train = F32 && A.store != nullptr;
+    float* st_pair = train ? A.store + A.store_off[lo_p] : nullptr;
+    const int pw_in = train ? prev : slot_in;
+    const int pw_out = train ? item : slot_out;
     constexpr int NV = 32 * (int)sizeof(T) / 16;  // 16-byte vectors per strip column
     const int Tn = L2 + 31;
     const bool has_row = i0 + lane < L1;
@@ -189,10 +194,11 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
                 if (lane == 0) okl = wait_ge_u64(&A.prod[pw_in], need, A.status);
                 ok = __shfl_sync(kFull, okl, 0);
                 if (ok) {
-                    const T* src2 = seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
+                    const T* src2 = train ? reinterpret_cast<const T*>(st_pair + ((size_t)(s - 1) * L2 + t) * S)
+                                          : seam + ((size_t)slot_in * A.wcols + (t % A.wcols)) * S;
                     for (int idx = lane; idx < nb * S; idx += 32) sin_[idx] = __ldcg(src2 + idx);
                     __syncwarp();
-                    if (lane == 0)
+                    if (lane == 0 && !train)
                         st_release_u64(&A.cons[slot_in],
                                        ((unsigned long long)item << 32) | (unsigned)(t + nb));
                 }
@@ -306,7 +312,7 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
             __syncwarp();
             const int start = jj & ~31;
             const int nb = jj - start + 1;
-            if (start + nb > A.wcols) {
+            if (!train && start + nb > A.wcols) {
                 const unsigned long long need = ((unsigned long long)next << 32) |
                                                 (unsigned)(start + nb - A.wcols);
                 bool okl = true;
@@ -314,7 +320,8 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
                 ok = __shfl_sync(kFull, okl, 0);
             }
             if (ok) {
-                T* dst = seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
+                T* dst = train ? reinterpret_cast<T*>(st_pair + ((size_t)s * L2 + start) * S)
+                               : seam + ((size_t)slot_out * A.wcols + (start % A.wcols)) * S;
                 for (int idx = lane; idx < nb * S; idx += 32) __stcg(dst + idx, sout[idx]);
                 __threadfence();
                 __syncwarp();
@@ -481,7 +488,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
         __syncwarp();
 
         // ---- phase 2: the wavefront sweep (one row per lane) -------------------
-        if (has_out) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
+        // (training: the seams are not reused, no slot to wait for)
+        if (has_out && A.store == nullptr) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
         if (ok)
             ok = sweep_strip<P, T, NR>(A, pd, lo_p, s, item, has_in ? ir.prev : -1,
                                        has_out ? ir.next : -1, cst, cring, sin_, sout, seam,

@@ -5,6 +5,7 @@
 // (adjoint) kernel; the two-phase solver in FP32 and FP64; and the
 // tensor-core solver for large d.
 #include "sigk_bwd.cuh"
+#include "sigk_bwd2.cuh"
 #include "sigk_fwd.cuh"
 #include "sigk_fwd_cm.cuh"
 #include "sigk_fwd_tc.cuh"
@@ -49,22 +50,6 @@ template <int D, int R, bool REC>
 static cudaError_t fwd_launch_impl(const SolverArgs& a, int grid, cudaStream_t s) {
     const int smem = 4 * FwdSmem<SIGK_P, D, R, REC>::per_warp * (int)sizeof(float);
     auto kern = fwd_kernel<SIGK_P, D, R, SIGK_NR, REC>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, 128, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int D>
-static int bwd_info_impl(KernelInfo* info) {
-    const int smem = 4 * BwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
-    return occupancy(bwd_kernel<SIGK_P, D, SIGK_NR>, 128, smem, 1, info);
-}
-
-template <int D>
-static cudaError_t bwd_launch_impl(const BwdArgs& a, int grid, cudaStream_t s) {
-    const int smem = 4 * BwdSmem<SIGK_P, D>::per_warp * (int)sizeof(float);
-    auto kern = bwd_kernel<SIGK_P, D, SIGK_NR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, 128, smem, s>>>(a);
@@ -149,23 +134,20 @@ cudaError_t fwd_cm_launch<SIGK_P, SIGK_NR>(bool f64, const SolverArgs& a, void* 
 }
 
 template <>
-int bwd_info<SIGK_P, SIGK_NR>(int D, KernelInfo* info) {
-    switch (D) {
-        case 4: return bwd_info_impl<4>(info);
-        case 8: return bwd_info_impl<8>(info);
-        case 16: return bwd_info_impl<16>(info);
-        default: return -1;
-    }
+int bwd2_info<SIGK_P, SIGK_NR>(KernelInfo* info) {
+    const int smem = 4 * Bwd2Smem<SIGK_P>::per_warp * (int)sizeof(float);
+    return occupancy(bwd2_kernel<SIGK_P, SIGK_NR>, 128, smem, 1, info);
 }
 
 template <>
-cudaError_t bwd_launch<SIGK_P, SIGK_NR>(int D, const BwdArgs& a, int grid, cudaStream_t s) {
-    switch (D) {
-        case 4: return bwd_launch_impl<4>(a, grid, s);
-        case 8: return bwd_launch_impl<8>(a, grid, s);
-        case 16: return bwd_launch_impl<16>(a, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t bwd2_launch<SIGK_P, SIGK_NR>(const BwdArgs& a, float* cs, int64_t cstride, int grid,
+                                         cudaStream_t s) {
+    const int smem = 4 * Bwd2Smem<SIGK_P>::per_warp * (int)sizeof(float);
+    auto kern = bwd2_kernel<SIGK_P, SIGK_NR>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 128, smem, s>>>(a, cs, cstride);
+    return cudaGetLastError();
 }
 
 template <>

@@ -47,8 +47,11 @@ struct TcArgs;
 template <int P, int NR> int fwd_tc_info(KernelInfo* info);
 template <int P, int NR> cudaError_t fwd_tc_launch(const TcArgs& a, int grid, cudaStream_t s);
 
+// The adjoint kernel (any d): phase 0 coefficients, replay, reverse sweep,
+// contraction to the increments; cs: per-warp strip areas of cstride floats.
 struct BwdArgs;
-template <int P, int NR> int bwd_info(int D, KernelInfo* info);
-template <int P, int NR> cudaError_t bwd_launch(int D, const BwdArgs& a, int grid, cudaStream_t s);
+template <int P, int NR> int bwd2_info(KernelInfo* info);
+template <int P, int NR>
+cudaError_t bwd2_launch(const BwdArgs& a, float* cs, int64_t cstride, int grid, cudaStream_t s);
 
 }  // namespace sigk

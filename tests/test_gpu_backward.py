@@ -315,3 +315,61 @@ def test_increments_mode_gradient_and_gram_xy(S, orc):
         coords = rng.choice(grads[p].size, size=8, replace=False)
         ref, scale = increment_gradient_terms(terms, inc, coords)
         assert_grad_close(grads[p].reshape(-1)[coords], ref, scale)
+
+
+@pytest.mark.parametrize("d,seed", [(64, 121), (256, 122)])
+def test_large_dimension_gradient_vs_fd(S, orc, d, seed):
+    # d > 16: the training forward is the two-phase kernel (FMA increment
+    # Gram, seams kept), the adjoint replays each strip and chains to the
+    # increments with the contraction; gradients w.r.t. the increments of a
+    # Gram of X against Y
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.ragged_pairs(3, 30, 110, d, 0.5, 1.0, seed=seed)
+    ix = [np.diff(p, axis=0).astype(np.float32) for p in synth.split(X, lx)]
+    iy = [np.diff(p, axis=0).astype(np.float32) for p in synth.split(Y, ly)][:2]
+    IX, lix = synth.pack(ix)
+    IY, liy = synth.pack(iy)
+    W = np.random.default_rng(seed).standard_normal((3, 2))
+    o = S.Opts(order=12, rings=6, max_len=128, flags=S.FLAG_INCREMENTS)
+    gX, gY, G = S.backward(S.OP_GRAM, torch.from_numpy(IX).to(dev()), torch.from_numpy(lix).to(dev()),
+                           torch.from_numpy(IY).to(dev()), torch.from_numpy(liy).to(dev()),
+                           torch.from_numpy(W), o)
+    a64 = [v.astype(np.float64) for v in ix]
+    b64 = [v.astype(np.float64) for v in iy]
+    ref_G = np.array([[orc.series_pair(a, b) for b in b64] for a in a64])
+    np.testing.assert_allclose(G.cpu().numpy(), ref_G, rtol=1e-5)
+    gX = synth.split(gX.cpu().numpy(), lix)
+    gY = synth.split(gY.cpu().numpy(), liy)
+    rng = np.random.default_rng(seed + 1)
+    for which, grads, p in ((0, gX, 2), (1, gY, 1)):
+        if which == 0:
+            terms = [(W[p, b], (lambda z, b=b: orc.series_pair(z, b64[b]))) for b in range(2)]
+            inc = a64[p]
+        else:
+            terms = [(W[a, p], (lambda z, a=a: orc.series_pair(a64[a], z))) for a in range(3)]
+            inc = b64[p]
+        coords = rng.choice(grads[p].size, size=10, replace=False)
+        ref, scale = increment_gradient_terms(terms, inc, coords)
+        assert_grad_close(grads[p].reshape(-1)[coords], ref, scale)
+
+
+def test_large_dimension_points_gradient(S, orc):
+    # d = 40, points input, a pair whose row path spans several strips and a
+    # refined rough pair: point gradients against the oracle
+    from paper_2502_20392_gb300 import synth
+    (X, lx), (Y, ly) = synth.ragged_pairs(2, 40, 100, 40, 0.5, 1.0, seed=123)
+    xs, ys = synth.split(X, lx), synth.split(Y, ly)
+    xs[0] = synth.brownian(1, 140, 40, 1.0, seed=124)[0]
+    X, lx = synth.pack(xs)
+    w = np.array([0.7, -1.3])
+    gX, gY, val = S.backward(S.OP_PAIRS, torch.from_numpy(X).to(dev()), torch.from_numpy(lx).to(dev()),
+                             torch.from_numpy(Y).to(dev()), torch.from_numpy(ly).to(dev()),
+                             torch.from_numpy(w), S.Opts(order=12, rings=6, max_len=256))
+    gX = synth.split(gX.cpu().numpy(), lx)
+    rng = np.random.default_rng(125)
+    for p in range(2):
+        ix, iy = incs([xs[p], ys[p]])
+        assert val.cpu().numpy()[p] == pytest.approx(orc.series_pair(ix, iy), rel=1e-5)
+        coords = rng.choice(gX[p].size, size=10, replace=False)
+        ref, scale = point_gradient_terms([(w[p], lambda z: orc.series_pair(z, iy))], ix, coords)
+        assert_grad_close(gX[p].reshape(-1)[coords], ref, scale)
