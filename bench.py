@@ -68,10 +68,11 @@ def tile_flops(P: int, nr: int, d: int) -> int:
 
 
 def adjoint_tile_flops(P: int, nr: int, d: int, replay: bool = True) -> int:
-    """FP32 operations per tile of the adjoint kernel as executed (FMA = 2): in
-    pass B the increment dot, the inverse bottom-edge update, the tile adjoint
-    and the two gradient FMAs; with `replay`, also pass A's forward replay
-    (tile_flops), which is skipped when the forward stored the tile records."""
+    """FP32 operations per tile of the adjoint kernel as executed (FMA = 2): the
+    coefficient (phase 0, 2d), the inverse bottom-edge update and the tile
+    adjoint (pass B), the two contractions of the chain to the increments
+    (phase C, 4d); with `replay`, also pass A's forward replay (tile_flops),
+    which is skipped when the forward stored the tile records."""
     nrm = min(P, 8)
     nr = min(nr, nrm)
     inv = 2 * (nr - 1) + sum(2 * (1 + 2 * (P - p)) for p in range(1, nr + 1))
@@ -400,7 +401,7 @@ def main():
     kms = statistics.mean(r[1] for r in b_kern)
     # pass B over every tile (useful: twice the forward's work); pass A's
     # replay of the forward is recomputation (executed, not useful)
-    entry(f"bwd_kernel<P={P},D=16> (adjoint, recomputes each strip from its seam)", kms,
+    entry(f"bwd2_kernel<P={P},NR={nr}> (adjoint, recomputes each strip from its seam)", kms,
           bcnt[2] * useful_tile_flops(P, nr, DIM, adjoint=True),
           bcnt[2] * adjoint_tile_flops(P, nr, DIM, replay=False) + bcnt[3] * tile_flops(P, nr, DIM),
           sg, P, nr, {"replayed_tiles": bcnt[3],

@@ -22,10 +22,10 @@
 //            g_ij = dk/dc_ij times the pair's upstream weight written over c_ij
 //            in cs;
 //   phase C  the chain to the increments, two contractions over the strip:
-//            dL/ddx_i = sum_j g_ij dy_j and dL/ddy_j += sum_i g_ij dx_i, again
-//            as FMA micro-GEMMs (lane = dimension), the first summed over the
-//            whole strip before one atomic add per row and dimension, the
-//            second added with atomics per column block.
+//            dL/ddx_i = sum_j g_ij dy_j (lane = row, summed over the whole
+//            strip before one atomic add per row and dimension) and
+//            dL/ddy_j += sum_i g_ij dx_i (lane = column, added with atomics
+//            per column block), in chunks of 8, 16 or 32 dimensions.
 // Neither pass A nor pass B holds an increment: their registers go to the
 // edge polynomials and the tile adjoint, and the kernel serves every d.
 #pragma once
@@ -36,8 +36,13 @@
 
 namespace sigk {
 
-constexpr int kB2KC = 32;   // contraction chunk of phases 0 and C
+constexpr int kB2KC = 32;   // contraction chunk of phase 0
 constexpr int kB2PF = 2;    // coefficient loads in flight per lane in passes A and B
+constexpr int kB2Blk = 32 * 34;        // a 32 x 32 block of c or g (row stride 34)
+// the strip rows' and a column block's points or increments, [33][up to 32
+// dimensions + 4] each (33 points give 32 increments)
+constexpr int kB2XS = 33 * 36;
+constexpr int kB2YS = 33 * 36;
 
 template <int P>
 struct Bwd2Smem {
@@ -46,32 +51,281 @@ struct Bwd2Smem {
     static constexpr int RB = 32 * (S > RS ? S : RS);   // record block / seam-in block
     static constexpr int SA = adj_seam_floats(P);
     static constexpr int sweep = 2 * RB + 2 * 32 * SA;  // passes A and B
-    // phases 0 and C: the row increments (phase 0: [dim][row], stride 36 for
-    // 16-byte reads; phase C: [row][dim], stride 33), the column increments
-    // ([column][dim], stride 33) and a 32 x 34 block of coefficients or of g
-    // (row stride 34: the skewed reads and the row-wise writes hit distinct
-    // banks)
-    static constexpr int gemm = kB2KC * 36 + 32 * 33 + 32 * 34;
+    // phases 0 and C: one 32 x 32 block (c, then g and the transposed
+    // gradients), the strip rows' increments and one column block's
+    static constexpr int gemm = kB2Blk + kB2XS + kB2YS;
     static constexpr int per_warp = (sweep > gemm ? sweep : gemm);
 };
 
-// Copy the 32 x 32 block of skewed entries of columns [j0, j0 + 32) (all
-// rows) between cs and blk[r * 34 + col]; to_blk: cs -> blk.  Columns at or
-// past L2 are zero in blk and untouched in cs.
-__device__ __forceinline__ void skew_block(float* cs, float* blk, int j0, int L2, bool to_blk, int lane) {
+// Async copy (cp.async, one wait for all of them) of the skewed entries of
+// columns [j0, j0 + 32) into blk[r * 34 + col] = entry (row r, column
+// j0 + col); each step tt reads one contiguous 128-byte line of cs (entry
+// t * 32 + l = row l, column t - l) and the lanes write distinct banks.
+// Columns at or past L2 are zeros.
+__device__ __forceinline__ void skew_to_block_async(const float* cs, float* blk, int j0, int L2, int lane) {
+#pragma unroll 7
     for (int tt = 0; tt < 63; ++tt) {
         const int col = tt - lane;
         if (col >= 0 && col < 32) {
-            const int j = j0 + col;
-            float* e = cs + (int64_t)(j0 + tt) * 32 + lane;
-            if (to_blk) blk[lane * 34 + col] = j < L2 ? *e : 0.0f;
-            else if (j < L2) *e = blk[lane * 34 + col];
+            if (j0 + col < L2) cp_async4(blk + lane * 34 + col, cs + (int64_t)(j0 + tt) * 32 + lane);
+            else blk[lane * 34 + col] = 0.0f;
         }
     }
 }
 
+// The reverse: blk[r * 34 + col] -> skewed entries of cs (columns < L2).
+__device__ __forceinline__ void block_to_skew(float* cs, const float* blk, int j0, int L2, int lane) {
+#pragma unroll 7
+    for (int tt = 0; tt < 63; ++tt) {
+        const int col = tt - lane;
+        if (col >= 0 && col < 32 && j0 + col < L2) cs[(int64_t)(j0 + tt) * 32 + lane] = blk[lane * 34 + col];
+    }
+}
+
+// Staging of 32 increments (rows v0 .. v0 + 31 of a path with Lv segments,
+// dimensions k0 .. k0 + DC - 1, zero past the path or past d) into
+// dst[r * ds + e'].  Unrefined paths with d a multiple of 4 and 16-byte
+// aligned rows are copied with 16-byte cp.async (points: 33 rows, differenced
+// by finish_rows after the wait; the caller commits and waits); otherwise the
+// rows are loaded and differenced at once (stage_increments: refined paths,
+// odd d).  Returns true when finish_rows is needed.
+template <int DC>
+__device__ __forceinline__ bool stage_rows(float* dst, int ds, const float* z, int v0, int Lv, int d, int k0,
+                                           int inc_mode, int s, int lane) {
+    const bool async = s == 1 && (d & 3) == 0 && ((reinterpret_cast<uintptr_t>(z) & 15) == 0);
+    if (!async) {
+        if (lane < DC) stage_increments(dst + lane, ds, z, v0, Lv, d, k0 + lane, inc_mode, s);
+        return false;
+    }
+    const int dn = min(DC, d - k0);  // a multiple of 4
+    const int nq = dn >> 2;
+    const int nrow = inc_mode ? 32 : 33;
+    const int vend = inc_mode ? Lv : Lv + 1;  // rows of z that exist
+    for (int idx = lane; idx < nrow * nq; idx += 32) {
+        const int r = idx / nq, q = idx - r * nq;
+        const int v = v0 + r;
+        const bool in = v < vend;
+        cp_async16z(dst + r * ds + 4 * q, z + (int64_t)(in ? v : v0) * d + k0 + 4 * q, in ? 16 : 0);
+    }
+    if (dn < DC) {  // dimensions past d
+        for (int idx = lane; idx < nrow * (DC - dn); idx += 32) {
+            const int r = idx / (DC - dn);
+            dst[r * ds + dn + (idx - r * (DC - dn))] = 0.0f;
+        }
+    }
+    return inc_mode == 0;
+}
+
+// After the copies of stage_rows (points) have landed: increments
+// dst[r] = dst[r + 1] - dst[r] in place (zero for rows past the path).
+template <int DC>
+__device__ __forceinline__ void finish_rows(float* dst, int ds, int v0, int Lv, int lane) {
+    if (lane < DC) {
+        float p = dst[lane];
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            const float q = dst[(r + 1) * ds + lane];
+            dst[r * ds + lane] = v0 + r < Lv ? q - p : 0.0f;
+            p = q;
+        }
+    }
+}
+
+// Phase 0 of the adjoint: the strip's coefficients c_ij = <dx_i, dy_j> for all
+// columns, by 32-column blocks: a register-blocked FMA micro-GEMM (lane =
+// column, 32 row accumulators; the rows' increments broadcast from shared
+// memory, four dimensions per 128-bit load; chunks of 32 dimensions summed in
+// two levels, as in the two-phase forward), written into the skewed area cs
+// through the block blk.  The strip's rows are staged once when d <= 32.
+__device__ __forceinline__ void strip_coefficients(float* cs, float* wsm, const float* xr, const float* yr,
+                                                   int i0, int L1, int L2, int d, int inc_mode, int sx,
+                                                   int sy, int lane) {
+    float* blk = wsm;
+    float* xs = blk + kB2Blk;  // [33][36]
+    float* ys = xs + kB2XS;    // [33][36]
+    for (int j0 = 0; j0 < L2; j0 += 32) {
+        float acc[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) acc[r] = 0.0f;
+        for (int k0 = 0; k0 < d; k0 += kB2KC) {
+            __syncwarp();
+            const bool rows = j0 == 0 || d > kB2KC;
+            bool fx = false;
+            if (rows) fx = stage_rows<kB2KC>(xs, 36, xr, i0, L1, d, k0, inc_mode, sx, lane);
+            const bool fy = stage_rows<kB2KC>(ys, 36, yr, j0, L2, d, k0, inc_mode, sy, lane);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp();
+            if (fx) finish_rows<kB2KC>(xs, 36, i0, L1, lane);
+            if (fy) finish_rows<kB2KC>(ys, 36, j0, L2, lane);
+            __syncwarp();
+            const int kn = min(kB2KC, d - k0);
+            float part[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) part[r] = 0.0f;
+            for (int e = 0; e < kn; e += 4) {
+                const float4 y = *reinterpret_cast<const float4*>(ys + lane * 36 + e);
+#pragma unroll
+                for (int r = 0; r < 32; ++r) {
+                    const float4 x = *reinterpret_cast<const float4*>(xs + r * 36 + e);
+                    part[r] = fmaf(x.x, y.x, part[r]);
+                    part[r] = fmaf(x.y, y.y, part[r]);
+                    part[r] = fmaf(x.z, y.z, part[r]);
+                    part[r] = fmaf(x.w, y.w, part[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 32; ++r) acc[r] += part[r];
+        }
+        __syncwarp();
+        // lane = column: blk[r][col] = c(row r, column j0 + col), then skewed into cs
+#pragma unroll
+        for (int r = 0; r < 32; ++r) blk[r * 34 + lane] = acc[r];
+        __syncwarp();
+        block_to_skew(cs, blk, j0, L2, lane);
+    }
+    __syncwarp();
+}
+
+// Gradient of one strip's rows or of one column block, added to the path's
+// gradient rows with atomics, 32 consecutive floats per warp instruction:
+// tb[r * (DC + 1) + e'] holds the gradient of increment v0 + r, dimension
+// k0 + e'.  With increments (inc_mode 1) it is added to the increment's row
+// (a refined path's increment v to its segment v / s, scaled by 1/s).  With
+// points, increment v = point v + 1 - point v: for unrefined paths the
+// point gradients of the block are formed first (point v0 + r gets
+// tb[r - 1] - tb[r], one atomic per point and dimension; the block's two end
+// points get one term each, the other comes from the neighbouring block),
+// otherwise each increment adds to its two end points.
+template <int DC>
+__device__ __forceinline__ void add_gradient_rows(float* g, const float* tb, int v0, int Lv, int s,
+                                                  int k0, int d, int inc_mode, int lane) {
+    if (!inc_mode && s == 1) {
+#pragma unroll 4
+        for (int idx = lane; idx < 33 * DC; idx += 32) {
+            const int r = idx / DC, ee = idx - r * DC;
+            const int e = k0 + ee, v = v0 + r;  // point v
+            float val = 0.0f;
+            if (r >= 1 && v - 1 < Lv) val += tb[(r - 1) * (DC + 1) + ee];
+            if (r < 32 && v < Lv) val -= tb[r * (DC + 1) + ee];
+            if (e < d && v <= Lv && val != 0.0f) atomicAdd(g + (int64_t)v * d + e, val);
+        }
+        return;
+    }
+    const float rs = 1.0f / (float)s;
+#pragma unroll 4
+    for (int idx = lane; idx < 32 * DC; idx += 32) {
+        const int r = idx / DC, ee = idx - r * DC;
+        const int v = v0 + r, e = k0 + ee;
+        const float val = tb[r * (DC + 1) + ee];
+        if (v < Lv && e < d && val != 0.0f) {
+            const int64_t seg = v / s;
+            const float w = s == 1 ? val : val * rs;
+            if (inc_mode) {
+                atomicAdd(g + seg * d + e, w);
+            } else {
+                atomicAdd(g + (seg + 1) * d + e, w);
+                atomicAdd(g + seg * d + e, -w);
+            }
+        }
+    }
+}
+
+// Phase C of the adjoint: the chain from g_ij = w dk/dc_ij (the strip's
+// skewed area cs) to the increments, in chunks of DC dimensions:
+//   dL/ddx_i = sum_j g_ij dy_j   (lane = row i; the strip's sum over all
+//                                 column blocks, in two levels)
+//   dL/ddy_j += sum_i g_ij dx_i  (lane = column j of the block)
+// Each lane accumulates DC dimensions in registers; the other operand's row
+// is read from shared memory with 128-bit broadcast loads, so every lane does
+// useful work for any d (an FMA per 1.25 instructions).  Each column block's
+// g and increments arrive by cp.async with one wait.  Shared memory of the
+// warp: blk [32][34] (the block of g, later the transposed gradients), xs
+// and ys [33][DC + 4] (the increments of the strip's rows and of
+// the block's columns).
+template <int DC>
+__device__ __forceinline__ void chain_strip(const float* cs, float* wsm, const float* xr, const float* yr,
+                                            float* gxr, float* gyr, int i0, int L1, int L2, int d,
+                                            int inc_mode, int sx, int sy, int lane) {
+    constexpr int DS = DC + 4;
+    float* blk = wsm;
+    float* xs = blk + kB2Blk;
+    float* ys = xs + kB2XS;
+    for (int k0 = 0; k0 < d; k0 += DC) {
+        __syncwarp();
+        const bool fx = stage_rows<DC>(xs, DS, xr, i0, L1, d, k0, inc_mode, sx, lane);
+        float gx[DC];
+#pragma unroll
+        for (int e = 0; e < DC; ++e) gx[e] = 0.0f;
+        for (int j0 = 0; j0 < L2; j0 += 32) {
+            __syncwarp();
+            skew_to_block_async(cs, blk, j0, L2, lane);  // blk[r * 34 + col] = g(row r, column j0 + col)
+            const bool fy = stage_rows<DC>(ys, DS, yr, j0, L2, d, k0, inc_mode, sy, lane);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp();
+            if (fx && j0 == 0) finish_rows<DC>(xs, DS, i0, L1, lane);
+            if (fy) finish_rows<DC>(ys, DS, j0, L2, lane);
+            __syncwarp();
+            if (gxr) {
+                float gb[DC];
+#pragma unroll
+                for (int e = 0; e < DC; ++e) gb[e] = 0.0f;
+#pragma unroll 4
+                for (int c = 0; c < 32; ++c) {
+                    const float gv = blk[lane * 34 + c];
+                    const float4* y4 = reinterpret_cast<const float4*>(ys + c * DS);
+#pragma unroll
+                    for (int q = 0; q < DC / 4; ++q) {
+                        const float4 y = y4[q];
+                        gb[4 * q + 0] = fmaf(gv, y.x, gb[4 * q + 0]);
+                        gb[4 * q + 1] = fmaf(gv, y.y, gb[4 * q + 1]);
+                        gb[4 * q + 2] = fmaf(gv, y.z, gb[4 * q + 2]);
+                        gb[4 * q + 3] = fmaf(gv, y.w, gb[4 * q + 3]);
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < DC; ++e) gx[e] += gb[e];
+            }
+            if (gyr) {
+                float gy[DC];
+#pragma unroll
+                for (int e = 0; e < DC; ++e) gy[e] = 0.0f;
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r) {
+                    const float gv = blk[r * 34 + lane];
+                    const float4* x4 = reinterpret_cast<const float4*>(xs + r * DS);
+#pragma unroll
+                    for (int q = 0; q < DC / 4; ++q) {
+                        const float4 x = x4[q];
+                        gy[4 * q + 0] = fmaf(gv, x.x, gy[4 * q + 0]);
+                        gy[4 * q + 1] = fmaf(gv, x.y, gy[4 * q + 1]);
+                        gy[4 * q + 2] = fmaf(gv, x.z, gy[4 * q + 2]);
+                        gy[4 * q + 3] = fmaf(gv, x.w, gy[4 * q + 3]);
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int e = 0; e < DC; ++e) blk[lane * (DC + 1) + e] = gy[e];
+                __syncwarp();
+                add_gradient_rows<DC>(gyr, blk, j0, L2, sy, k0, d, inc_mode, lane);
+            }
+        }
+        if (gxr) {
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < DC; ++e) blk[lane * (DC + 1) + e] = gx[e];
+            __syncwarp();
+            add_gradient_rows<DC>(gxr, blk, i0, L1, sx, k0, d, inc_mode, lane);
+        }
+    }
+    __syncwarp();
+}
+
+// 168 registers at three CTAs per SM: measured 80.9 ms on the 64-path Gram
+// against 93.0 ms at four CTAs per SM and 128 registers (which spill).
 template <int P, int NR>
-__global__ void __launch_bounds__(128, 4) bwd2_kernel(BwdArgs A, float* cscratch, int64_t cstride) {
+__global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch, int64_t cstride) {
     constexpr int S = P + 4;
     constexpr int SA = adj_seam_floats(P);
     using Sm = Bwd2Smem<P>;
@@ -87,10 +341,7 @@ __global__ void __launch_bounds__(128, 4) bwd2_kernel(BwdArgs A, float* cscratch
     float* rbuf1 = sin_ + Sm::RB;           // record buffer 1
     float* ain = rbuf1 + Sm::RB;            // adjoint seam-in block
     float* aout = ain + 32 * SA;            // adjoint seam-out block
-    // phases 0 and C (the same memory)
-    float* opa = wsm;                       // [32][36] or [32][33]
-    float* opb = opa + kB2KC * 36;          // [32][33]
-    float* blk = opb + 32 * 33;             // [32][34]
+    // phases 0 and C use the same memory (strip_coefficients, chain_strip)
     float* rec = A.rec + (size_t)gwarp * A.rec_stride;
     float* cs = cscratch + (size_t)gwarp * cstride;
     const int n_items = A.sched.hdr[2];
@@ -133,44 +384,7 @@ __global__ void __launch_bounds__(128, 4) bwd2_kernel(BwdArgs A, float* cscratch
 #endif
 
         // ------------------------- phase 0: coefficients -------------------------
-        for (int j0 = 0; j0 < L2; j0 += 32) {
-            float acc[32];
-#pragma unroll
-            for (int r = 0; r < 32; ++r) acc[r] = 0.0f;
-            for (int k0 = 0; k0 < d; k0 += kB2KC) {
-                __syncwarp();
-                const int e = k0 + lane;
-                // rows transposed to [dim][row], columns to [column][dim]
-                stage_increments(opa + lane * 36, 1, pd.xr, i0, L1, d, e, A.inc_mode, pd.sx);
-                stage_increments(opb + lane, 33, pd.yr, j0, L2, d, e, A.inc_mode, pd.sy);
-                __syncwarp();
-                const int kn = min(kB2KC, d - k0);
-                float part[32];
-#pragma unroll
-                for (int r = 0; r < 32; ++r) part[r] = 0.0f;
-                for (int ee = 0; ee < kn; ++ee) {
-                    const float y = opb[lane * 33 + ee];
-                    const float4* xr = reinterpret_cast<const float4*>(opa + ee * 36);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 x = xr[q];
-                        part[4 * q + 0] = fmaf(x.x, y, part[4 * q + 0]);
-                        part[4 * q + 1] = fmaf(x.y, y, part[4 * q + 1]);
-                        part[4 * q + 2] = fmaf(x.z, y, part[4 * q + 2]);
-                        part[4 * q + 3] = fmaf(x.w, y, part[4 * q + 3]);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < 32; ++r) acc[r] += part[r];
-            }
-            __syncwarp();
-            // lane = column: blk[r][col] = c(row r, column j0 + col), then skewed into cs
-#pragma unroll
-            for (int r = 0; r < 32; ++r) blk[r * 34 + lane] = acc[r];
-            __syncwarp();
-            skew_block(cs, blk, j0, L2, false, lane);
-        }
-        __syncwarp();
+        strip_coefficients(cs, wsm, pd.xr, pd.yr, i0, L1, L2, d, A.inc_mode, pd.sx, pd.sy, lane);
 
         // ------------------------- pass A: forward replay ------------------------
         float a[P + 1], a1lo = 0.0f;
@@ -479,83 +693,13 @@ __global__ void __launch_bounds__(128, 4) bwd2_kernel(BwdArgs A, float* cscratch
         }
 
         // ------------------------- phase C: chain to the increments ----------------
-        // dL/ddx (rows of this strip) and dL/ddy (every column), by dimension
-        // chunks of 32 with lane = dimension
         if (ok) {
-            const float rsx = 1.0f / (float)pd.sx, rsy = 1.0f / (float)pd.sy;
-            for (int k0 = 0; k0 < d; k0 += kB2KC) {
-                const int e = k0 + lane;
-                __syncwarp();
-                // this chunk's row increments, [row][dim] (refined rows scaled)
-                stage_increments(opa + lane, 33, pd.xr, i0, L1, d, e, A.inc_mode, pd.sx);
-                float gxt[32];  // dL/ddx of the strip's rows, this dimension (lane)
-#pragma unroll
-                for (int r = 0; r < 32; ++r) gxt[r] = 0.0f;
-                for (int j0 = 0; j0 < L2; j0 += 32) {
-                    __syncwarp();
-                    skew_block(cs, blk, j0, L2, true, lane);  // blk[r][col] = g(row r, column j0 + col)
-                    // columns' increments, [column][dim]
-                    stage_increments(opb + lane, 33, pd.yr, j0, L2, d, e, A.inc_mode, pd.sy);
-                    __syncwarp();
-                    // dL/ddy_j (lane = dimension e): sum over the strip's rows
-                    if (pd.gyr) {
-                        float gy[32];
-#pragma unroll
-                        for (int c = 0; c < 32; ++c) gy[c] = 0.0f;
-                        for (int r = 0; r < 32; ++r) {
-                            const float x = opa[r * 33 + lane];
-#pragma unroll
-                            for (int c = 0; c < 32; ++c) gy[c] = fmaf(blk[r * 34 + c], x, gy[c]);
-                        }
-                        if (e < d) {
-                            for (int c = 0; c < 32; ++c) {
-                                const int j = j0 + c;
-                                if (j < L2 && gy[c] != 0.0f) {
-                                    const int64_t jcol = j / pd.sy;
-                                    const float w = gy[c] * rsy;
-                                    if (A.inc_mode) {
-                                        atomicAdd(pd.gyr + jcol * d + e, w);
-                                    } else {
-                                        atomicAdd(pd.gyr + (jcol + 1) * d + e, w);
-                                        atomicAdd(pd.gyr + jcol * d + e, -w);
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    // dL/ddx_i (lane = dimension e): this block's sum, added to the
-                    // strip's total (two-level sums)
-                    if (pd.gxr) {
-                        float gx[32];
-#pragma unroll
-                        for (int r = 0; r < 32; ++r) gx[r] = 0.0f;
-                        for (int c = 0; c < 32; ++c) {
-                            const float y = opb[c * 33 + lane];
-#pragma unroll
-                            for (int r = 0; r < 32; ++r) gx[r] = fmaf(blk[r * 34 + c], y, gx[r]);
-                        }
-#pragma unroll
-                        for (int r = 0; r < 32; ++r) gxt[r] += gx[r];
-                    }
-                }
-                if (pd.gxr && e < d) {
-#pragma unroll
-                    for (int r = 0; r < 32; ++r) {
-                        const int v = i0 + r;
-                        const float g = gxt[r];
-                        if (v < L1 && g != 0.0f) {
-                            const int64_t seg = v / pd.sx;
-                            const float w = g * rsx;
-                            if (A.inc_mode) {
-                                atomicAdd(pd.gxr + seg * d + e, w);
-                            } else {
-                                atomicAdd(pd.gxr + (seg + 1) * d + e, w);
-                                atomicAdd(pd.gxr + seg * d + e, -w);
-                            }
-                        }
-                    }
-                }
-            }
+            if (d <= 8)
+                chain_strip<8>(cs, wsm, pd.xr, pd.yr, pd.gxr, pd.gyr, i0, L1, L2, d, A.inc_mode, pd.sx, pd.sy, lane);
+            else if (d <= 16)
+                chain_strip<16>(cs, wsm, pd.xr, pd.yr, pd.gxr, pd.gyr, i0, L1, L2, d, A.inc_mode, pd.sx, pd.sy, lane);
+            else
+                chain_strip<32>(cs, wsm, pd.xr, pd.yr, pd.gxr, pd.gyr, i0, L1, L2, d, A.inc_mode, pd.sx, pd.sy, lane);
         }
         __syncwarp();
         if (!ok) break;
