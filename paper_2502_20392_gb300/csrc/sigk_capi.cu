@@ -188,7 +188,7 @@ struct Layout {
     bool tc;             // tensor-core increment Gram (d > 16, FP32, d <= kTcMaxDim)
     int d_pad;           // its digit rows: d rounded up to 16
     int64_t n_slots;     // paths of the call (digit cache slots)
-    size_t ycache, yexp, ablk, aexp, cst;  // its sections
+    size_t ycache, yexp, ablk, cst;  // its sections
     int64_t cst_stride;
     int strip_quantum;   // the pair table's strips per work unit (tc: 4)
     size_t elem;         // bytes per seam / strip element (4 or 8)
@@ -310,7 +310,9 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     if (w > o.max_len) w = o.max_len;
     w = (w + 31) & ~(int64_t)31;
     if (w < 32) w = 32;
-    if (L->strip_major) w = wfull < 32 ? 32 : wfull;
+    // the tensor-core solver's producer runs ahead of its sweeps, so its
+    // seam slots hold whole strips (no flow control between strips)
+    if (L->strip_major || L->tc) w = wfull < 32 ? 32 : wfull;
     L->wcols = (int)w;
     L->n_paths_x = n_x;
     L->n_paths_y = (op == SIGK_OP_GRAM && n_y == 0) ? 0 : n_y;
@@ -336,18 +338,17 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->cscratch = off;
     L->n_slots = n_x + L->n_paths_y;
     L->cst_stride = 0;
-    L->ycache = L->yexp = L->ablk = L->aexp = L->cst = off;
+    L->ycache = L->yexp = L->ablk = L->cst = off;
     if (L->tc) {
         // digits of every path's first max_len segments, exponents; per CTA
         // the digits of a block's rows and the skewed (c, clo) of its strips
         L->ycache = off;
         off = align256(off + sizeof(uint16_t) * (size_t)L->n_slots * o.max_len * kTcDigits * L->d_pad);
         L->yexp = off; off = align256(off + sizeof(int32_t) * (size_t)L->n_slots * o.max_len);
-        const size_t workers = (size_t)L->grid * kTcGroups;  // block workers (4-warp groups)
-        L->ablk = off; off = align256(off + sizeof(uint16_t) * workers * kTcDigits * kTcRows * L->d_pad);
-        L->aexp = off; off = align256(off + sizeof(int32_t) * workers * kTcRows);
+        const size_t ctas = (size_t)L->grid;
+        L->ablk = off; off = align256(off + sizeof(uint16_t) * ctas * kTcDigits * kTcRows * L->d_pad);
         L->cst_stride = (o.max_len + 32 + kTcPF) * 32;
-        L->cst = off; off = align256(off + sizeof(float2) * workers * 4 * L->cst_stride);
+        L->cst = off; off = align256(off + sizeof(float2) * ctas * kTcSlots * 4 * L->cst_stride);
     } else if (L->cm) {  // one [max_len][32] coefficient strip per warp
         L->cstride = 32 * ((o.max_len + 31) & ~(int64_t)31);
         off = align256(off + L->elem * (size_t)L->nwarps * L->cstride);
@@ -1251,7 +1252,6 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
             ta.max_len = o.max_len;
             ta.d_pad = L.d_pad;
             ta.ablk = (uint16_t*)(base + L.ablk);
-            ta.aexp = (int32_t*)(base + L.aexp);
             ta.cst = (float2*)(base + L.cst);
             ta.cst_stride = L.cst_stride;
             ta.block_counter = &hdr->item_counter;

@@ -152,8 +152,8 @@ cudaError_t bwd2_launch<SIGK_P, SIGK_NR>(const BwdArgs& a, float* cs, int64_t cs
 
 template <>
 int fwd_tc_info<SIGK_P, SIGK_NR>(KernelInfo* info) {
-    const int r = occupancy(fwd_tc_kernel<SIGK_P, SIGK_NR>, kTcGroups * 128, TcSmem<SIGK_P>::bytes, 1, info);
-    // one CTA per SM holds the whole TMEM (kTcGroups x 128 columns)
+    const int r = occupancy(fwd_tc_kernel<SIGK_P, SIGK_NR>, kTcThreads, TcSmem<SIGK_P>::bytes, 1, info);
+    // one CTA per SM: it holds all of TMEM
     if (r == 0 && info->blocks_per_sm > 1) info->blocks_per_sm = 1;
     return r;
 }
@@ -164,7 +164,7 @@ cudaError_t fwd_tc_launch<SIGK_P, SIGK_NR>(const TcArgs& a, int grid, cudaStream
     auto kern = fwd_tc_kernel<SIGK_P, SIGK_NR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kTcGroups * 128, smem, s>>>(a);
+    kern<<<grid, kTcThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -20,22 +20,24 @@
 //
 // Work unit: a block of 128 rows = four 32-row strips of one pair (the pair
 // table counts 32-row strips, padded to a multiple of four; the schedule is
-// pair-major, so the four strips are consecutive work items).  A group of
-// four warps owns a block (four groups per CTA, one CTA per SM):
-//   phase 1  the block's rows are cut into digits in a per-CTA global area;
-//            for every 32-column chunk of the swept path, the CTA stages the
-//            digit tiles (16 dimensions per step, two stages, cp.async) in the
-//            tensor core's shared-memory layout, one thread issues the ten
-//            128x32x16 MMAs of each step into TMEM, and every warp reads its
-//            32 rows back (tcgen05.ld) and stores (c, clo) into its strip's
-//            coefficient area, skewed so that the 32 values a warp's lanes
-//            read in one sweep step are contiguous;
-//   phase 2  warp w sweeps strip w of the block (the wavefront sweep of
-//            sigk_fwd_cm.cuh with one row per lane), seams between strips and
-//            blocks through the global seam ring as in every other solver.
-// The groups of a CTA are in different phases, so the tensor-core phase of
-// one overlaps the FMA sweep of the others.  The L1 x L2 coefficient
-// matrix is never stored: only one block's strips per CTA exist at a time.
+// pair-major, so the four strips are consecutive work items).  One CTA per SM
+// (it holds all of TMEM) splits the work between a producer and sweepers:
+//   producer (warps 0-3)  claims a block whenever one of the CTA's kTcSlots
+//            block slots is free, cuts the block's rows into digits in a
+//            per-CTA global area, and forms the coefficients 64 columns at a
+//            time: a four-stage cp.async pipeline stages the digit tiles (16
+//            dimensions per step) in the tensor core's shared-memory layout,
+//            one thread issues the ten 128x64x16 MMAs of each step into one
+//            of two TMEM buffers, and the previous chunk is read back
+//            (tcgen05.ld) meanwhile into the strips' coefficient areas,
+//            skewed so that the 32 values a warp's lanes read in one sweep
+//            step are contiguous; each finished chunk is published;
+//   sweepers (kTcSlots x 4 warps)  warp q of a slot sweeps strip q of the
+//            slot's block (one row per lane), waiting only for the chunks
+//            it is about to read, with seams between strips and blocks through
+//            the global seam ring as in every other solver.
+// The L1 x L2 coefficient matrix is never stored: only the strips of the
+// blocks in a CTA's slots exist at a time.
 #pragma once
 #include <type_traits>
 #include "sigk_device.cuh"
@@ -44,48 +46,35 @@
 namespace sigk {
 
 constexpr int kTcRows = 128;       // rows per block: the MMA's M (four strips)
-constexpr int kTcN = 32;           // columns per chunk: the MMA's N
+constexpr int kTcN = 64;           // columns per chunk: the MMA's N
 constexpr int kTcK = 16;           // contraction per MMA (BF16)
 constexpr int kTcDigits = 4;       // 8-bit digits per operand
 constexpr int kTcMaxDim = 1024;    // exact accumulation of the leading group
 constexpr int kTcPF = 2;           // sweep: coefficient loads in flight per lane
-// A CTA of this kernel holds TMEM, and the occupancy calculation then allows
-// one CTA per SM whatever its shared memory (measured on this GPU: a kernel
-// that contains tcgen05.alloc gets 1 CTA per SM at 16 KB of shared memory, the
-// same kernel without it 13).  So one CTA per SM runs kTcGroups independent
-// 4-warp groups, each a block worker with its own quarter of TMEM.
-constexpr int kTcGroups = 4;
+constexpr int kTcStages = 4;       // operand stages of the producer's copy pipeline
+constexpr int kTcSlots = 3;        // blocks being swept at once per CTA
+constexpr int kTcSweepWarps = 4 * kTcSlots;
+constexpr int kTcThreads = 128 + 32 * kTcSweepWarps;  // producer group + sweep warps
+// TMEM columns: two chunk buffers of four digit-order accumulators
+constexpr int kTcTmemCols = 2 * 4 * kTcN;
+static_assert(kTcTmemCols <= 512, "TMEM holds 512 columns");
 
-// Barriers of one 128-thread group (named barrier 1 + gr; barrier 0 is
-// __syncthreads).
-__device__ __forceinline__ void group_sync(int gr) {
-    asm volatile("bar.sync %0, 128;" ::"r"(gr + 1) : "memory");
-}
-__device__ __forceinline__ bool group_and(int gr, bool v) {
-    int r;
-    asm volatile("{\n.reg .pred p, q;\nsetp.ne.s32 p, %1, 0;\nbar.red.and.pred q, %2, 128, p;\nselp.s32 %0, 1, 0, q;\n}"
-                 : "=r"(r)
-                 : "r"((int)v), "r"(gr + 1)
-                 : "memory");
-    return r != 0;
-}
+// Named barrier of the producer group (barrier 0 is __syncthreads).
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// Dynamic shared memory of the tensor-core kernel (bytes).  Phase 1: two
-// stages of the digit tiles (A: 4 digits x 128 rows x 16 dims, B: 4 digits x
-// 32 columns x 16 dims, BF16); phase 2: per warp the seam-in and seam-out
-// blocks.  The two phases share one region.  The total is padded so that at
-// most four CTAs fit an SM (their TMEM: 4 x 128 columns).
+// Dynamic shared memory of the tensor-core kernel (bytes): the producer's
+// operand stages (A: 4 digits x 128 rows x 16 dimensions, B: 4 digits x 64
+// columns x 16 dimensions, BF16, 24 KB per stage) and every sweep warp's
+// seam-in and seam-out blocks; 1 KB of slack to align the operand tiles.
 template <int P>
 struct TcSmem {
     static constexpr int a_tile = kTcRows * kTcK * 2;           // one digit of A: 4 KB
-    static constexpr int b_tile = kTcN * kTcK * 2;              // one digit of B: 1 KB
-    static constexpr int stage = kTcDigits * (a_tile + b_tile);  // 20 KB
-    static constexpr int phase1 = 2 * stage;
-    static constexpr int phase2 = 4 * 2 * kG * (P + 4) * 4;
-    // per group, 1 KB aligned (tcgen05 operand tiles)
-    static constexpr int group = ((phase1 > phase2 ? phase1 : phase2) + 1023) / 1024 * 1024;
-    static constexpr int bytes = kTcGroups * group + 1024;  // + 1 KB alignment slack
-    static_assert(bytes <= 227 * 1024, "one CTA of kTcGroups groups per SM");
+    static constexpr int b_tile = kTcN * kTcK * 2;              // one digit of B: 2 KB
+    static constexpr int stage = kTcDigits * (a_tile + b_tile);  // 24 KB
+    static constexpr int stages = kTcStages * stage;
+    static constexpr int seams = kTcSweepWarps * 2 * kG * (P + 4) * 4;
+    static constexpr int bytes = stages + seams + 1024;
+    static_assert(bytes <= 200 * 1024, "fits the SM with the static shared memory");
 };
 
 struct TcArgs {
@@ -95,8 +84,7 @@ struct TcArgs {
     int64_t max_len;               // segments per slot
     int32_t d_pad;                 // d rounded up to a multiple of 16
     uint16_t* ablk;                // per CTA: digits of the block's rows [4][128][d_pad]
-    int32_t* aexp;                 // per CTA: their exponents [128]
-    float2* cst;                   // per CTA: skewed (c, clo) of the four strips
+    float2* cst;                   // per CTA: skewed (c, clo) of kTcSlots x 4 strips
     int64_t cst_stride;            // float2 per strip: (max_len + 32 + kTcPF) * 32
     int* block_counter;
 };
@@ -193,7 +181,7 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
-// Instruction descriptor: D FP32, A and B BF16, both K-major, N = 32, M = 128.
+// Instruction descriptor: D FP32, A and B BF16, both K-major, N = kTcN, M = 128.
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                               ((uint32_t)(kTcRows >> 4) << 24);
 // Byte offsets of the tiles' core matrices: two along K (lbo), rows in
@@ -254,12 +242,49 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 // ---------------------------------------------------------------------------
 // phase 2: the sweep of one 32-row strip with (c, clo) from the skewed area
 
+// CTA-scope acquire load of a shared-memory word.
+__device__ __forceinline__ int ld_acquire_cta(const int* p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(int* p, int v) {
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+
+// Bounded wait (every lane) until the producer has published `need` chunks
+// of this strip's coefficients (*ready >= need); false when the wait runs
+// out (kErrTimeout recorded) or the CTA aborts (*err set).
+__device__ __forceinline__ bool wait_chunks(const int* ready, int need, const int* err, int* status) {
+    if (ld_acquire_cta(ready) >= need) return true;
+    const unsigned long long t0 = global_ns();
+    const unsigned long long budget = wait_budget(status);
+    for (int it = 0; it < kWaitMaxIter; ++it) {
+        if (ld_acquire_cta(ready) >= need) return true;
+        if (ld_acquire_cta(err)) return false;
+        __nanosleep(64);
+        if ((it & 63) == 63 && global_ns() - t0 > budget) break;
+    }
+    record_timeout(status, ready, need, ld_acquire_cta(ready));
+    return false;
+}
+
+// The sweep reads coefficient entry t * 32 + l (row l, column t - l) at step
+// t - kTcPF; entry t is complete once the chunk holding column t is: before
+// step t (a multiple of kTcN) the strip needs the chunks of the columns up to
+// t + kTcN - 1 + kTcPF.
+__device__ __forceinline__ int chunks_needed(int t, int nch) {
+    const int n = (t + kTcN - 1 + kTcPF) / kTcN + 1;
+    return n < nch ? n : nch;
+}
+
 template <int P, int NR>
 __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDesc& pd, int lo_p,
                                                int s, int item, int prev, int next, const float2* cw,
                                                float* sin_, float* sout,
                                                unsigned long long& tiles_done,
-                                               unsigned long long& lane_tiles, unsigned (&rhist)[4]) {
+                                               unsigned long long& lane_tiles, unsigned (&rhist)[4],
+                                               const int* ready, const int* err) {
     constexpr int S = P + 4;
     const int lane = threadIdx.x & 31;
     const int L1 = pd.L1, L2 = pd.L2;
@@ -279,11 +304,18 @@ __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDe
     int oE = 0;
     const int Tn = L2 + 31;
     const bool has_row = i0 + lane < L1;
-    // coefficients of step t at cw[t * 32 + lane]: loads kTcPF steps ahead
+    const int nch = (L2 + kTcN - 1) / kTcN;
+    // coefficients of step t at cw[t * 32 + lane]: loads kTcPF steps ahead,
+    // each chunk of columns once the producer has published it
+    ok = wait_chunks(ready, chunks_needed(0, nch), err, A.status);
     float2 cq[kTcPF];
 #pragma unroll
     for (int k = 0; k < kTcPF; ++k) cq[k] = __ldcg(cw + k * 32 + lane);
     for (int t = 0; t < Tn && ok; ++t) {
+        if (t > 0 && t % kTcN == 0 && t < L2 && !wait_chunks(ready, chunks_needed(t, nch), err, A.status)) {
+            ok = false;
+            break;
+        }
         const float2 cc = cq[0];
 #pragma unroll
         for (int k = 0; k + 1 < kTcPF; ++k) cq[k] = cq[k + 1];
@@ -425,122 +457,152 @@ __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDe
 
 // ---------------------------------------------------------------------------
 
-template <int P, int NR>
-__global__ void __launch_bounds__(kTcGroups * 128, 1) fwd_tc_kernel(TcArgs T) {
+// State of one CTA shared between its producer group and its sweep warps.
+struct TcShared {
+    uint64_t mbar[kTcStages];     // stage s: the MMAs that read it have completed
+    uint32_t tmem_base;
+    int blk;                      // the producer's block (broadcast within the group)
+    int stop;                     // no more blocks (the normal end)
+    int err;                      // abort: a wait ran out
+    int slot_seq[kTcSlots];       // blocks published into each slot so far
+    int slot_blk[kTcSlots];       // the slot's current block
+    int slot_ready[kTcSlots];     // chunks of its coefficients published
+    int slot_done[kTcSlots];      // of its four strips swept (4: the slot is free)
+    int aexp[kTcRows];            // exponents of the producer's block rows
+};
+
+__device__ __forceinline__ bool producer_and(bool v) {
+    int r;
+    asm volatile("{\n.reg .pred p, q;\nsetp.ne.s32 p, %1, 0;\nbar.red.and.pred q, 1, 128, p;\nselp.s32 %0, 1, 0, q;\n}"
+                 : "=r"(r)
+                 : "r"((int)v)
+                 : "memory");
+    return r != 0;
+}
+
+// Bounded wait of the producer's thread 0 for a free slot; returns its index,
+// or -1 (abort, or the wait ran out: kErrTimeout recorded).
+__device__ __forceinline__ int wait_free_slot(TcShared& sh, int* status) {
+    const unsigned long long t0 = global_ns();
+    const unsigned long long budget = wait_budget(status);
+    for (int it = 0; it < kWaitMaxIter; ++it) {
+#pragma unroll
+        for (int k = 0; k < kTcSlots; ++k)
+            if (ld_acquire_cta(&sh.slot_done[k]) == 4) return k;
+        if (ld_acquire_cta(&sh.err)) return -1;
+        __nanosleep(128);
+        if ((it & 63) == 63 && global_ns() - t0 > budget) break;
+    }
+    record_timeout(status, &sh.slot_done[0], 4, ld_acquire_cta(&sh.slot_done[0]));
+    return -1;
+}
+
+// Bounded wait of a sweep warp for the next block of its slot; false at the
+// end (no more blocks) or on abort.
+__device__ __forceinline__ bool wait_slot_block(TcShared& sh, int slot, int gen, int* status) {
+    const unsigned long long t0 = global_ns();
+    const unsigned long long budget = wait_budget(status);
+    for (int it = 0; it < kWaitMaxIter; ++it) {
+        if (ld_acquire_cta(&sh.slot_seq[slot]) > gen) return true;
+        if (ld_acquire_cta(&sh.err)) return false;
+        if (ld_acquire_cta(&sh.stop)) return ld_acquire_cta(&sh.slot_seq[slot]) > gen;
+        __nanosleep(128);
+        if ((it & 63) == 63 && global_ns() - t0 > budget) break;
+    }
+    record_timeout(status, &sh.slot_seq[slot], gen + 1, ld_acquire_cta(&sh.slot_seq[slot]));
+    return false;
+}
+
+// The producer group (threads 0..127 of the CTA): claims blocks while a slot
+// is free, cuts the block's rows into digits, and forms the coefficients of
+// the block's four strips 64 columns at a time: a kTcStages-deep pipeline of
+// cp.async copies of the digit tiles (16 dimensions per step), thread 0 issues
+// each step's ten 128x64x16 MMAs and commits them to the stage's mbarrier,
+// and the chunk's (c, clo) are read back from TMEM (warp w: rows 32w..32w+31,
+// strip w) while the tensor core already works on the next chunk (two TMEM
+// buffers).  Each finished chunk is published to the slot's sweep warps.
+template <int P>
+__device__ __forceinline__ void tc_producer(const TcArgs& T, TcShared& sh, unsigned char* stg, int tid) {
     const SolverArgs& A = T.A;
-    constexpr int S = P + 4;
     using Sm = TcSmem<P>;
-    extern __shared__ float4 smem_tc_raw[];
-    __shared__ __align__(8) uint64_t mbar_g[kTcGroups][2];
-    __shared__ uint32_t tmem_base_s;
-    __shared__ int blk_g[kTcGroups], st_g[kTcGroups], stop_g[kTcGroups];
-    __shared__ int32_t yexp_g[kTcGroups][2][kTcN];  // column exponents of the chunk (double buffered)
-    // group gr = warps 4 gr .. 4 gr + 3: an independent block worker with its
-    // own shared memory, TMEM columns [128 gr, 128 gr + 128), mbarriers and
-    // named barrier 1 + gr; warp w % 4 of a group reaches TMEM lanes 32 (w % 4)
-    const int gr = threadIdx.x >> 7;
-    const int tid = threadIdx.x & 127, lane = tid & 31, warp = tid >> 5;
-    const int wid = (int)(blockIdx.x * kTcGroups + gr);  // worker index: per-worker scratch
-    uint64_t* mbar = mbar_g[gr];
-    int& blk_s = blk_g[gr];
-    int& st_s = st_g[gr];
-    int& stop_s = stop_g[gr];
-    int32_t (*yexp_s)[kTcN] = yexp_g[gr];
-    const int d = A.d, d_pad = T.d_pad;
-    const int KS = d_pad / kTcK;
-    uint16_t* ablk = T.ablk + (int64_t)wid * kTcDigits * kTcRows * d_pad;
-    int32_t* aexp = T.aexp + (int64_t)wid * kTcRows;
-    float2* cblk = T.cst + (int64_t)wid * 4 * T.cst_stride;
-    // operand tiles 1 KB aligned (the dynamic area is 1 KB larger than needed)
-    unsigned char* st0 = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_tc_raw) + 1023) & ~(uintptr_t)1023) + gr * Sm::group;
-    float* seam_w = reinterpret_cast<float*>(st0) + warp * 2 * kG * S;  // phase 2 (aliases phase 1)
-    unsigned long long tiles_done = 0, lane_tiles = 0;
-
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
-                     "r"(128 * kTcGroups));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        stop_s = 0;
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tbase = tmem_base_s + 128 * gr;
-    unsigned rhist[4] = {0u, 0u, 0u, 0u};  // tiles by ring count (adaptive launches)
-    uint32_t step = 0;         // MMA steps of this CTA so far (stage = step & 1)
-    int64_t issued = -1;       // last step whose MMAs were committed (CTA-uniform)
-    int64_t waited = -1;       // last step whose completion was observed
+    constexpr int S = kTcStages;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int d = A.d, d_pad = T.d_pad, KS = d_pad / kTcK;
+    uint16_t* ablk = T.ablk + (int64_t)blockIdx.x * kTcDigits * kTcRows * d_pad;
     const int n_blocks = A.sched.hdr[2] >> 2;
-
+    const uint32_t tmem = sh.tmem_base;
+    uint32_t gstep = 0;   // operand steps so far: stage g % S, its use number g / S
+    uint32_t gchunk = 0;  // chunks so far: TMEM buffer gchunk & 1
+    int64_t issued = -1, waited = -1;
+    bool ok = true;
     for (;;) {
+        // ---- a free slot, and the next block -------------------------------
         if (tid == 0) {
-            blk_s = atomicAdd(T.block_counter, 1);
-            st_s = ld_volatile_s32(A.status);
+            int blk = -1;
+            const int slot = wait_free_slot(sh, A.status);
+            if (slot >= 0) {
+                blk = atomicAdd(T.block_counter, 1);
+                if (blk >= n_blocks || ld_volatile_s32(A.status) != 0) blk = -1;
+            }
+            sh.blk = blk < 0 ? -1 : blk * kTcSlots + slot;
         }
-        group_sync(gr);
-        const int blk = blk_s, st = st_s;
-        group_sync(gr);  // read before thread 0 can overwrite them
-        if (blk >= n_blocks || st != 0) break;
-        const int item = 4 * blk + warp;
-        const ItemRef ir = decode_item(A.sched, A.pairs, item);
-        const int lo_p = ir.pair;
-        const PairDesc pd = A.pairs[lo_p];
-        const int s = ir.k;                   // this warp's strip
+        producer_sync();
+        const int code = sh.blk;
+        producer_sync();  // read before thread 0 can overwrite it
+        if (code < 0) break;
+        const int blk = code / kTcSlots, slot = code % kTcSlots;
+        const ItemRef ir = decode_item(A.sched, A.pairs, 4 * blk);
+        const PairDesc pd = A.pairs[ir.pair];
         const int L1 = pd.L1, L2 = pd.L2;
-        const int r0 = (s & ~3) * 32;         // first row of the block
-        bool ok = true;
+        const int r0 = ir.k * 32;  // the block's first row (strips come in fours)
 #ifdef SIGK_DEBUG
-        ok = dbg_in(A.status, 41, lo_p, A.n_pairs - 1) && dbg_in(A.status, 42, (int64_t)(L2 + 31 + kTcPF) * 32, T.cst_stride) &&
-             dbg_in(A.status, 43, item % A.nslot, A.nslot - 1) &&
-             dbg_in(A.status, 45, pd.out0, A.out_cap - 1) && dbg_in(A.status, 46, pd.out1 < 0 ? 0 : pd.out1, A.out_cap - 1) &&
+        ok = dbg_in(A.status, 41, ir.pair, A.n_pairs - 1) &&
+             dbg_in(A.status, 42, (int64_t)(L2 + 31 + kTcPF) * 32, T.cst_stride) &&
              dbg_in(A.status, 47, (int64_t)(L2 + pd.sy - 1) / pd.sy, T.max_len) &&
-             dbg_in(A.status, 48, (int64_t)(s & 3), warp) && dbg_in(A.status, 49, (int64_t)warp, s & 3);
+             dbg_in(A.status, 48, (int64_t)(ir.k & 3), 0);
+        ok = producer_and(ok);
+        if (!ok) break;
 #endif
-        ok = group_and(gr, ok);
-
-        // ---- phase 1a: digits of the block's 128 rows (32 per warp) -----------
-        if (ok) {
+        // ---- digits of the block's 128 rows (32 per warp) -------------------
+        {
             const int lsx = 31 - __clz(pd.sx);  // refinement factors are powers of two
             for (int rr = 0; rr < 32; ++rr) {
                 const int r = warp * 32 + rr;
-                const int v = r0 + r;           // virtual row
+                const int v = r0 + r;  // virtual row
                 const int ex = slice_row(pd.xr, (int64_t)(v >> lsx), v < L1, d, d_pad, A.inc_mode, lsx,
                                          ablk + (int64_t)r * d_pad, (int64_t)kTcRows * d_pad, lane);
-                if (lane == 0) aexp[r] = ex;
+                if (lane == 0) sh.aexp[r] = ex;
             }
         }
-        group_sync(gr);
-        // ---- phase 1b: the coefficients, 32 columns at a time --------------------
-        // step n of the block: chunk n / KS, dimensions 16 (n % KS); its digit
-        // tiles are copied one step ahead into stage (step + n) & 1
+        __threadfence_block();
+        producer_sync();
+        // ---- publish the block to the slot's sweep warps --------------------
+        if (tid == 0) {
+            sh.slot_blk[slot] = blk;
+            sh.slot_ready[slot] = 0;
+            sh.slot_done[slot] = 0;
+            st_release_cta(&sh.slot_seq[slot], sh.slot_seq[slot] + 1);
+        }
+        // ---- the coefficients, kTcN columns at a time -----------------------
         const int lsy = 31 - __clz(pd.sy);
         const uint16_t* yc = T.ycache + (int64_t)pd.yslot * T.max_len * kTcDigits * d_pad;
         const int32_t* ye = T.yexp + (int64_t)pd.yslot * T.max_len;
-        float2* cw = cblk + (int64_t)warp * T.cst_stride;
+        float2* cw = T.cst + ((int64_t)blockIdx.x * kTcSlots + slot) * 4 * T.cst_stride + (int64_t)warp * T.cst_stride;
         const int nch = (L2 + kTcN - 1) / kTcN;
-        const int nst = ok ? nch * KS : 0;
+        const int nst = nch * KS;
+        // copies of step n (chunk n / KS, dimensions 16 (n % KS)) into stage (gstep + n) % S
         auto issue = [&](int n) {
             const int c0 = (n / KS) * kTcN, kk = n % KS;
-            unsigned char* sa = st0 + ((step + n) & 1) * Sm::stage;
+            unsigned char* sa = stg + ((gstep + n) % S) * Sm::stage;
             unsigned char* sb = sa + kTcDigits * Sm::a_tile;
-            if (kk == 0 && tid < kTcN) {
-                const int j = c0 + tid;
-                yexp_s[(n / KS) & 1][tid] = j < L2 ? ye[j >> lsy] - lsy : 0;
-            }
-            // A: 4 digits x 128 rows x 2 halves of 8 dims; B: 4 digits x 32 columns x 2 halves
+            // A: 4 digits x 128 rows x 2 halves of 8 dims; B: 4 digits x 64 columns x 2 halves
             for (int idx = tid; idx < kTcDigits * kTcRows * 2; idx += 128) {
-                const int h = idx & 1, r = (idx >> 1) & 127, k = idx >> 8;
+                const int h = idx & 1, r = (idx >> 1) & (kTcRows - 1), k = idx >> 8;
                 cp_async16(smem_u32(sa + k * Sm::a_tile + (r >> 3) * kTcSbo + h * kTcLbo + (r & 7) * 16),
                            ablk + ((int64_t)k * kTcRows + r) * d_pad + kk * kTcK + 8 * h, 16u);
             }
             for (int idx = tid; idx < kTcDigits * kTcN * 2; idx += 128) {
-                const int h = idx & 1, jj = (idx >> 1) & 31, k = idx >> 6;
+                const int h = idx & 1, jj = (idx >> 1) & (kTcN - 1), k = idx >> 7;
                 const int j = c0 + jj;
                 const bool in = j < L2;
                 cp_async16(smem_u32(sb + k * Sm::b_tile + (jj >> 3) * kTcSbo + h * kTcLbo + (jj & 7) * 16),
@@ -548,110 +610,201 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1) fwd_tc_kernel(TcArgs T) {
                            in ? 16u : 0u);
             }
         };
-        if (nst > 0) issue(0);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        for (int n = 0; n < nst; ++n) {
-            const uint32_t g = step + n;  // this step's global index
-            if (n + 1 < nst) {
-                // stage (g + 1) & 1 was last read by the MMAs of step g - 1
-                if (g >= 1 && !mbar_wait(&mbar[(g + 1) & 1], ((g - 1) >> 1) & 1, A.status)) ok = false;
-                issue(n + 1);
+        // (c, clo) of chunk c from TMEM into the strips' skewed areas, then
+        // published: chunk c's last MMAs are complete once its last step's
+        // commit has arrived
+        auto epilogue = [&](int c) {
+            const uint32_t m = gstep + (uint32_t)((c + 1) * KS - 1);
+            if (!mbar_wait(&sh.mbar[m % S], (m / S) & 1, A.status)) ok = false;
+            waited = m;
+            tc_fence_after();
+            const int c0 = c * kTcN;
+            const int ea = sh.aexp[warp * 32 + lane];
+            // column exponents, lane l: columns c0 + l and c0 + 32 + l
+            int ecol[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = c0 + 32 * h + lane;
+                ecol[h] = j < L2 ? ye[j >> lsy] - lsy : 0;
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group 1;" ::: "memory");  // step n's tiles have landed
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + ((gchunk + c) & 1) * 4 * kTcN;
+#pragma unroll 1
+            for (int qt = 0; qt < kTcN / 16; ++qt) {
+                uint32_t g0[16], g1[16], g2[16], g3[16];
+                tmem_ld16<16>(tl + 0 * kTcN + 16 * qt, g0);
+                tmem_ld16<16>(tl + 1 * kTcN + 16 * qt, g1);
+                tmem_ld16<16>(tl + 2 * kTcN + 16 * qt, g2);
+                tmem_ld16<16>(tl + 3 * kTcN + 16 * qt, g3);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int jj = 16 * qt + q;
+                    const int j = c0 + jj;
+                    const int eb = __shfl_sync(kFull, ecol[jj >> 5], jj & 31);
+                    // c = 2^(ea + eb) (G0 + G1 2^-8 + G2 2^-16 + G3 2^-24), rounded once to (hi, lo)
+                    const float s0 = __uint_as_float(g0[q]);
+                    const float t1 = __uint_as_float(g1[q]) * 0.00390625f;
+                    const float sh_ = s0 + t1;
+                    const float bv = sh_ - s0;
+                    float e = (s0 - (sh_ - bv)) + (t1 - bv);
+                    e += fmaf(__uint_as_float(g2[q]), 1.52587890625e-05f,
+                              __uint_as_float(g3[q]) * 5.9604644775390625e-08f);
+                    const float hi = sh_ + e;
+                    const float lo = e - (hi - sh_);
+                    const int ex = ea + eb;
+                    if (j < L2) cw[(int64_t)(j + lane) * 32 + lane] = make_float2(ldexpf(hi, ex), ldexpf(lo, ex));
+                }
+            }
             tc_fence_before();
-            ok = group_and(gr, ok);
-            if (!ok) break;
-            const int kk = n % KS;
+            __threadfence_block();
+            producer_sync();  // every warp's rows of the chunk are written; its TMEM buffer is free
+            if (tid == 0) st_release_cta(&sh.slot_ready[slot], c + 1);
+        };
+#pragma unroll 1
+        for (int n = 0; n < S - 1; ++n) {
+            if (n < nst) issue(n);
+            cp_async_commit();
+        }
+#pragma unroll 1
+        for (int n = 0; n < nst; ++n) {
+            const uint32_t g = gstep + n;
+            asm volatile("cp.async.wait_group %0;" ::"n"(S - 2) : "memory");  // step n's copies (this thread's)
+            fence_proxy_async_smem();
+            producer_sync();  // every thread's copies of step n have landed
+            const int c = n / KS, kk = n % KS;
             if (tid == 0) {
                 tc_fence_after();
-                unsigned char* sa = st0 + (g & 1) * Sm::stage;
+                unsigned char* sa = stg + (g % S) * Sm::stage;
                 unsigned char* sb = sa + kTcDigits * Sm::a_tile;
-                // group q = k + l accumulates at TMEM columns 32 q
+                const uint32_t dbuf = tmem + ((gchunk + c) & 1) * 4 * kTcN;
+                // digit orders k + l = q accumulate at TMEM columns dbuf + 64 q
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
 #pragma unroll
                     for (int k = 0; k <= q; ++k) {
                         const uint64_t da = tc_desc(smem_u32(sa + k * Sm::a_tile), kTcLbo, kTcSbo);
                         const uint64_t db = tc_desc(smem_u32(sb + (q - k) * Sm::b_tile), kTcLbo, kTcSbo);
-                        tc_mma(tbase + 32 * q, da, db, (kk > 0 || k > 0) ? 1u : 0u);
+                        tc_mma(dbuf + kTcN * q, da, db, (kk > 0 || k > 0) ? 1u : 0u);
                     }
                 }
-                tc_commit(&mbar[g & 1]);
+                tc_commit(&sh.mbar[g % S]);
             }
             issued = g;
-            if (kk == KS - 1) {
-                // the chunk's MMAs are done (the last commit covers all before it)
-                if (!mbar_wait(&mbar[g & 1], (g >> 1) & 1, A.status)) ok = false;
-                ok = group_and(gr, ok);
-                if (!ok) break;
-                waited = g;
-                tc_fence_after();
-                {
-                    const int c0 = (n / KS) * kTcN;
-                    const int32_t* yx = yexp_s[(n / KS) & 1];
-                    const int row = warp * 32 + lane;
-                    const int ea = aexp[row];
-                    const uint32_t tl = tbase + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-                    for (int half = 0; half < 2; ++half) {
-                        uint32_t g0[16], g1[16], g2[16], g3[16];
-                        tmem_ld16<16>(tl + 0 * 32 + 16 * half, g0);
-                        tmem_ld16<16>(tl + 1 * 32 + 16 * half, g1);
-                        tmem_ld16<16>(tl + 2 * 32 + 16 * half, g2);
-                        tmem_ld16<16>(tl + 3 * 32 + 16 * half, g3);
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const int jj = 16 * half + q;
-                            const int j = c0 + jj;
-                            // c = 2^(ea + eb) (G0 + G1 2^-8 + G2 2^-16 + G3 2^-24), rounded once to (hi, lo)
-                            const float s0 = __uint_as_float(g0[q]);
-                            const float t1 = __uint_as_float(g1[q]) * 0.00390625f;
-                            const float sh = s0 + t1;
-                            const float bv = sh - s0;
-                            float e = (s0 - (sh - bv)) + (t1 - bv);
-                            e += fmaf(__uint_as_float(g2[q]), 1.52587890625e-05f,
-                                      __uint_as_float(g3[q]) * 5.9604644775390625e-08f);
-                            const float hi = sh + e;
-                            const float lo = e - (hi - sh);
-                            const int ex = ea + yx[jj];
-                            if (j < L2)
-                                cw[(int64_t)(j + lane) * 32 + lane] = make_float2(ldexpf(hi, ex), ldexpf(lo, ex));
-                        }
-                    }
-                }
-                tc_fence_before();
-                group_sync(gr);  // TMEM is free for the next chunk
+            // refill: step n + S - 1 goes to stage (g - 1) % S, which the MMAs of step g - 1 read
+            if (n + S - 1 < nst) {
+                if (g >= 1 && !mbar_wait(&sh.mbar[(g - 1) % S], ((g - 1) / S) & 1, A.status)) ok = false;
+                issue(n + S - 1);
             }
+            cp_async_commit();
+            // the previous chunk's epilogue overlaps this chunk's MMAs
+            if (kk == 0 && c >= 1) epilogue(c - 1);
+            ok = producer_and(ok);
+            if (!ok) break;
         }
+        if (ok && nst > 0) epilogue(nch - 1);
         asm volatile("cp.async.wait_all;" ::: "memory");
-        step += nst;  // (after an early exit the loop below ends the kernel)
-        // ---- phase 2: warp w sweeps strip w of the block -------------------------
-        group_sync(gr);
-        if (ok) {
-            if (ir.next >= 0) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
-            if (ok)
-                ok = sweep_strip_tc<P, NR>(A, pd, lo_p, s, item, ir.prev, ir.next, cw, seam_w,
-                                           seam_w + kG * S, tiles_done, lane_tiles, rhist);
-        }
-        __syncwarp();
-        if (lane == 0) {
-            __threadfence();
-            st_release_s64(&A.done[item % A.nslot], (long long)item);
-        }
-        if (!ok && lane == 0) atomicExch(&stop_s, 1);
-        group_sync(gr);
-        if (stop_s) break;
+        gstep += nst;
+        gchunk += nch;
+        ok = producer_and(ok);
+        if (!ok) break;
     }
-    // in-flight MMAs (after an early exit) complete before TMEM is freed
-    if (issued > waited) mbar_wait(&mbar[issued & 1], (uint32_t)(issued >> 1) & 1, A.status);
+    // the end of the blocks, or an abort
+    if (tid == 0) {
+        if (!ok) st_release_cta(&sh.err, 1);
+        st_release_cta(&sh.stop, 1);
+    }
+    // MMAs still in flight (after an abort) complete before TMEM is freed
+    if (issued > waited) mbar_wait(&sh.mbar[issued % S], (uint32_t)(issued / S) & 1, A.status);
+}
+
+// One CTA per SM (it holds all of TMEM): warps 0-3 are the producer group,
+// warps 4 .. 4 + kTcSweepWarps - 1 sweep: warp 4 + 4 k + q sweeps strip q of
+// the block in slot k, reading its chunks as the producer publishes them.
+// Deadlock freedom: a block is claimed only when a slot (four sweep warps) is
+// free, the producer never waits on a sweep while it forms a block, and the
+// seam ring holds whole strips (no flow control), so every wait of a sweep
+// points to a lower work item or to its own producer.
+template <int P, int NR>
+__global__ void __launch_bounds__(kTcThreads, 1) fwd_tc_kernel(TcArgs T) {
+    const SolverArgs& A = T.A;
+    constexpr int S = P + 4;
+    using Sm = TcSmem<P>;
+    extern __shared__ float4 smem_tc_raw[];
+    __shared__ TcShared sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // operand stages 1 KB aligned (the dynamic area is 1 KB larger than needed)
+    unsigned char* stg = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_tc_raw) + 1023) & ~(uintptr_t)1023);
+    float* seams = reinterpret_cast<float*>(stg + Sm::stages);
+    unsigned long long tiles_done = 0, lane_tiles = 0;
+    unsigned rhist[4] = {0u, 0u, 0u, 0u};  // tiles by ring count (adaptive launches)
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem_base)),
+                     "r"(kTcTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < kTcStages; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.mbar[k])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh.stop = 0;
+        sh.err = 0;
+#pragma unroll
+        for (int k = 0; k < kTcSlots; ++k) {
+            sh.slot_seq[k] = 0;
+            sh.slot_blk[k] = 0;
+            sh.slot_ready[k] = 0;
+            sh.slot_done[k] = 4;
+        }
+    }
     tc_fence_before();
-    __syncthreads();  // every group is done with TMEM
+    __syncthreads();
     tc_fence_after();
-    if (threadIdx.x < 32)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base_s), "r"(128 * kTcGroups));
+
+    if (warp < 4) {
+        tc_producer<P>(T, sh, stg, threadIdx.x);
+    } else {
+        const int sw = warp - 4, slot = sw >> 2, q = sw & 3;
+        float* seam_w = seams + sw * 2 * kG * S;
+        for (int gen = 0;; ++gen) {
+            if (!wait_slot_block(sh, slot, gen, A.status)) break;
+            const int blk = sh.slot_blk[slot];
+            const int item = 4 * blk + q;
+            const ItemRef ir = decode_item(A.sched, A.pairs, item);
+            const PairDesc pd = A.pairs[ir.pair];
+            const float2* cw = T.cst + ((int64_t)blockIdx.x * kTcSlots + slot) * 4 * T.cst_stride +
+                               (int64_t)q * T.cst_stride;
+            bool ok = true;
+#ifdef SIGK_DEBUG
+            ok = dbg_in(A.status, 43, item % A.nslot, A.nslot - 1) &&
+                 dbg_in(A.status, 45, pd.out0, A.out_cap - 1) &&
+                 dbg_in(A.status, 46, pd.out1 < 0 ? 0 : pd.out1, A.out_cap - 1) &&
+                 dbg_in(A.status, 49, (int64_t)(ir.k & 3), q) && dbg_in(A.status, 49, (int64_t)q, ir.k & 3);
+            ok = __all_sync(kFull, ok);
+#endif
+            if (ok && ir.next >= 0) ok = wait_slot_free(A.sched, A.pairs, item, A.nslot, A.done, A.status);
+            if (ok)
+                ok = sweep_strip_tc<P, NR>(A, pd, ir.pair, ir.k, item, ir.prev, ir.next, cw, seam_w,
+                                           seam_w + kG * S, tiles_done, lane_tiles, rhist,
+                                           &sh.slot_ready[slot], &sh.err);
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                st_release_s64(&A.done[item % A.nslot], (long long)item);
+                if (!ok) st_release_cta(&sh.err, 1);
+                atomicAdd(&sh.slot_done[slot], 1);
+            }
+            __syncwarp();
+            if (!ok) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();  // the producer's MMAs are complete and every TMEM read is done
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sh.tmem_base), "r"(kTcTmemCols));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         tiles_done += __shfl_down_sync(kFull, tiles_done, o);
@@ -663,11 +816,11 @@ __global__ void __launch_bounds__(kTcGroups * 128, 1) fwd_tc_kernel(TcArgs T) {
     }
     if (A.ring_adaptive) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            unsigned v = rhist[q];
+        for (int k = 0; k < 4; ++k) {
+            unsigned v = rhist[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-            if (lane == 0 && v) atomicAdd(&A.ring_hist[q], v);
+            if (lane == 0 && v) atomicAdd(&A.ring_hist[k], v);
         }
     }
 }
