@@ -86,6 +86,18 @@ def adjoint_tile_flops(P: int, nr: int, d: int, replay: bool = True) -> int:
     return (tile_flops(P, nr, d) if replay else 0) + 2 * d + inv + adj + 4 * d
 
 
+def sources_digest(files) -> str:
+    """SHA-256 over the given source files (paths relative to the repository
+    root, each hashed with its path): the identity of the build of a kernel
+    whose ncu counters are recorded in profiles/traffic.json."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in files:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(rel.encode() + b"\0" + f.read())
+    return h.hexdigest() if files else ""
+
+
 def rank_workloads(rank: int, n_paths: int):
     """The batches rank `rank` solves: the Gram workload with per-rank seeds
     (independent problems per GPU: weak scaling, no data-path collective)."""
@@ -412,9 +424,9 @@ def main():
     try:
         with open(tpath) as f:
             tj = json.load(f)
-        with open(os.path.join(ROOT, "paper_2502_20392_gb300", "_build", "libsigk.sha256")) as f:
-            digest = f.read().strip()
-        if tj.get("digest") == digest and tj.get("kernel") == roof[dom]["kernel"]:
+        # the counters hold while the measured kernel's sources are unchanged
+        if (tj.get("kernel") == roof[dom]["kernel"] and
+                tj.get("digest") == sources_digest(tj.get("sources", []))):
             traffic = tj.get("bytes_per_launch")
     except (OSError, ValueError):
         traffic = None
