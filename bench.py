@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_PATHS, N_SEG, DIM = 64, 1024, 16
-SIGMAS = ((1.0, 2001, 8, 4), (4.0, 2004, 16, 6))   # sigma, seed, order P, rings
+SIGMAS = ((1.0, 2001, 8, 4), (4.0, 2004, 12, 6))   # sigma, seed, order P, rings (as launched)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 L2_FLUSH_BYTES = 512 << 20
 ORACLE_SAMPLE_PAIRS = 16
@@ -35,14 +35,37 @@ METRIC = ("fwd & fwd+bwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=
           "sigma in {1,4}")
 
 
+def launch_order(P: int, nr: int) -> int:
+    """Edge degree the FP32 solvers launch with: the truncation keeps entries
+    of weighted degree 2m + k <= 2 nr + 1, which reach no degree above 2 nr,
+    so a larger order is clamped (the results are the same)."""
+    return min(P, 2 * nr)
+
+
+def keep_entry(P: int, nt: int, nr: int, m: int, k: int) -> bool:
+    """The tile-matrix entries the FP32 solvers keep (ring m, offset k)."""
+    return 1 <= m <= nr and k >= 0 and m + k <= P and 2 * m + k <= 2 * nt + 1
+
+
+def kept_entries(P: int, nt: int, nr: int) -> int:
+    return sum((1 if k == 0 else 2) for m in range(1, P + 1) for k in range(P + 1)
+               if keep_entry(P, nt, nr, m, k))
+
+
 def useful_tile_fma(P: int, nr: int, d: int) -> int:
-    """Algorithmic FMAs of one tile (the work model of the method, counted
-    from the truncation actually used, not the executed instructions): the
+    """Algorithmic FMAs of one tile by the work model of the method: the
     increment inner product (d), ring m = 1..n adding 2(P - m) + 1
-    multiply-adds into the two outgoing edges, and the 2P additions of the
-    exact transport (ring 0)."""
+    multiply-adds into the two outgoing edges (every entry of the square
+    truncation of order P), and the 2P additions of the exact transport
+    (ring 0).  P is the order the kernel runs with."""
     nr = min(nr, P, 8)
     return d + sum(2 * (P - m) + 1 for m in range(1, nr + 1)) + 2 * P
+
+
+def kept_tile_fma(P: int, nr: int, d: int) -> int:
+    """The same model counting only the entries the truncation keeps."""
+    nr = min(nr, P, 8)
+    return d + kept_entries(P, nr, nr) + 2 * P
 
 
 def useful_tile_flops(P: int, nr: int, d: int, adjoint: bool = False) -> int:
@@ -53,17 +76,12 @@ def useful_tile_flops(P: int, nr: int, d: int, adjoint: bool = False) -> int:
 
 def tile_flops(P: int, nr: int, d: int) -> int:
     """FP32 operations per tile of the solver kernel as executed (FMA = 2): the
-    increment inner product (2d), the ring powers, the Hankel sums of both
-    edges, the edge evaluation, the convolutions, the float-float corner and
-    the compensated first-order terms."""
-    nrm = min(P, 8)
-    nr = min(nr, nrm)
-    f = 2 * (nr - 1)
-    f += sum(2 * (1 + 2 * (P - p)) for p in range(1, nr + 1))
-    f += 2 * P
-    for p in range(1, P + 1):
-        f += 4 * min(p - 1, nr) + (4 if p <= nr else 0)
-    f += 10 + 18  # float-float corner; compensated first-order coefficients
+    increment inner product (2d), the ring powers, two FMAs per kept entry of
+    the tile matrix (one into each outgoing edge) plus one multiply per ring
+    for the corner's term, the edge evaluation, the float-float corner and
+    the compensated first-order terms (tile_flops in sigk_device.cuh)."""
+    nr = min(nr, P, 8)
+    f = 2 * (nr - 1) + 2 * nr + 4 * kept_entries(P, nr, nr) + 2 * P + 10 + 18
     return f + 2 * d
 
 
@@ -72,17 +90,12 @@ def adjoint_tile_flops(P: int, nr: int, d: int, replay: bool = True) -> int:
     coefficient (phase 0, 2d), the inverse bottom-edge update and the tile
     adjoint (pass B), the two contractions of the chain to the increments
     (phase C, 4d); with `replay`, also pass A's forward replay (tile_flops),
-    which is skipped when the forward stored the tile records."""
-    nrm = min(P, 8)
-    nr = min(nr, nrm)
-    inv = 2 * (nr - 1) + sum(2 * (1 + 2 * (P - p)) for p in range(1, nr + 1))
-    inv += sum(2 * min(p - 1, nr) + (2 if p <= nr else 0) for p in range(1, P + 1))
-    adj = 2 * (nr - 1) + sum(2 * (1 + 2 * (P - p)) for p in range(1, nr + 1))  # hb
-    adj += sum(4 * (P - m) + 6 for m in range(1, nr + 1))                     # chb, cbar
-    adj += 2 * nr                                                              # hab, hbb
-    for s_ in range(1, P + 1):
-        adj += 4 * min(nr, P - s_) + 2 + 4 * min(nr, P - s_)                   # conv^T, S, Hankel^T
-    adj += 2 * nr
+    which is skipped when the forward stored the tile records.  K1 counts the
+    kept off-diagonal entries on one side of the diagonal."""
+    nr = min(nr, P, 8)
+    k1 = (kept_entries(P, nr, nr) - nr) // 2
+    inv = 2 * (nr - 1) + 3 * nr + 4 * k1
+    adj = 2 * (nr - 1) + 14 * nr + 14 * k1 + 2 * P
     return (tile_flops(P, nr, d) if replay else 0) + 2 * d + inv + adj + 4 * d
 
 
@@ -387,28 +400,35 @@ def main():
     bcnt = sigk.counters(bws)
     roof = []
 
-    def entry(name, kms, useful, executed, sg, P, nr, extra=None):
+    def entry(name, kms, useful, executed, sg, P, nr, extra=None, kept=None):
         e = {"kernel": name, "sigma": sg, "order": P, "rings": nr, "kernel_ms": round(kms, 4),
              "useful_flops": useful, "achieved": round(useful / (kms * 1e-3) / 1e12, 3),
              "frac": round(useful / (kms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 4),
              "executed_flops": executed,
              "executed_tflops": round(executed / (kms * 1e-3) / 1e12, 3)}
+        if kept is not None:  # the model over the kept entries of the truncation only
+            e["kept_entry_flops"] = kept
+            e["kept_entry_frac"] = round(kept / (kms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 4)
         if extra:
             e.update(extra)
         roof.append(e)
 
-    for k, (sg, _, P, nr) in enumerate(SIGMAS):
+    for k, (sg, _, Pk, nr) in enumerate(SIGMAS):
+        P = launch_order(Pk, nr)
         kms = statistics.mean(r[k] for r in f_kern)
         # compulsory increment reads: each pair's two paths once (points, FP32)
         inc_bytes = pairs_of_gram(N_PATHS) * 2 * (N_SEG + 1) * DIM * 4
         useful, executed = tiles[k] * useful_tile_flops(P, nr, DIM), tiles[k] * tile_flops(P, nr, DIM)
         entry(f"fwd_kernel<P={P},D=16> (inference)", kms, useful, executed, sg, P, nr,
               {"increment_read_gbs": round(inc_bytes / (kms * 1e-3) / 1e9, 1),
-               "launch": sigk.launch_info(sigk.OP_GRAM, N_PATHS, 0, DIM, opts[k])})
-    sg, _, P, nr = SIGMAS[BWD_SIGMA]
+               "launch": sigk.launch_info(sigk.OP_GRAM, N_PATHS, 0, DIM, opts[k])},
+              kept=tiles[k] * 2 * kept_tile_fma(P, nr, DIM))
+    sg, _, Pk, nr = SIGMAS[BWD_SIGMA]
+    P = launch_order(Pk, nr)
     kms = statistics.mean(r[0] for r in b_kern)
     entry(f"fwd_kernel<P={P},D=16> (training: keeps the strip seams)", kms,
-          bcnt[0] * useful_tile_flops(P, nr, DIM), bcnt[0] * tile_flops(P, nr, DIM), sg, P, nr)
+          bcnt[0] * useful_tile_flops(P, nr, DIM), bcnt[0] * tile_flops(P, nr, DIM), sg, P, nr,
+          kept=bcnt[0] * 2 * kept_tile_fma(P, nr, DIM))
     roof[-1]["launch"] = sigk.launch_info(sigk.OP_GRAM, N_PATHS, 0, DIM, bopts)
     kms = statistics.mean(r[1] for r in b_kern)
     # pass B over every tile (useful: twice the forward's work); pass A's
@@ -417,7 +437,8 @@ def main():
           bcnt[2] * useful_tile_flops(P, nr, DIM, adjoint=True),
           bcnt[2] * adjoint_tile_flops(P, nr, DIM, replay=False) + bcnt[3] * tile_flops(P, nr, DIM),
           sg, P, nr, {"replayed_tiles": bcnt[3],
-                      "launch": sigk.launch_info(sigk.OP_GRAM, N_PATHS, 0, DIM, bopts, train=True)})
+                      "launch": sigk.launch_info(sigk.OP_GRAM, N_PATHS, 0, DIM, bopts, train=True)},
+          kept=bcnt[2] * 4 * kept_tile_fma(P, nr, DIM))
     dom = max(range(len(roof)), key=lambda k: roof[k]["kernel_ms"])
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
@@ -433,8 +454,11 @@ def main():
     roofline = {"bound": "alu", "achieved": roof[dom]["achieved"], "peak": round(FP32_PEAK_TFLOPS, 2),
                 "unit": "TFLOP/s", "frac": roof[dom]["frac"], "traffic": traffic,
                 "kernel": roof[dom]["kernel"],
-                "work_model": "useful flops = 2 x (d + sum_{m=1..n} (2(P-m)+1) + 2P) per tile; "
-                              "adjoint 2x the forward; peak = 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "work_model": "useful flops = 2 x (d + sum_{m=1..n} (2(P-m)+1) + 2P) per tile at the "
+                              "launched order P; adjoint 2x the forward; peak = 152 SMs x 128 FP32 "
+                              "lanes x 2 x 2.07 GHz; kept_entry_frac: the same model over the "
+                              "tile-matrix entries the truncation keeps (2m + k <= 2n + 1)",
+                "kept_entry_frac": roof[dom].get("kept_entry_frac"),
                 "executed_tflops": roof[dom]["executed_tflops"], "per_launch": roof}
 
     # end to end through the public API: pinned host inputs -> device, the
@@ -470,7 +494,7 @@ def main():
         "data": "synthetic (seeded Brownian, PCG64)",
         "config": {"workload": "gram_B64_L1024_d16_sigma1+4", "paths": N_PATHS, "segments": N_SEG,
                    "d": DIM, "sigmas": [s_ for s_, *_ in SIGMAS],
-                   "order_rings": [[P_, nr_] for _, _, P_, nr_ in SIGMAS],
+                   "order_rings": [[launch_order(P_, nr_), nr_] for _, _, P_, nr_ in SIGMAS],
                    "unique_pairs_per_gram": pairs_of_gram(N_PATHS), "l2": "flushed between steps",
                    "step": "forward: the Grams for sigma = 1 and sigma = 4 (inference); "
                            "fwd_bwd: training forward + adjoint of the sigma = 1 Gram "

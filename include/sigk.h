@@ -119,6 +119,13 @@ enum {
  *          Sec. 2.3 / App. B: the local Neumann iteration), 1 <= n <= min(order, 8);
  *          rounded up to an even value (the ring count is compiled into the
  *          kernels).
+ *   The FP32 solvers keep the entry c^m w B of the tile matrix (ring m,
+ *   edge coefficient of degree k) when m <= n, m + k <= P and
+ *   2m + k <= 2n + 1: a power of c counts twice against the degree of the
+ *   edge data, as c (a product of two increments) is of the order of the
+ *   square of a coupling or smaller.  No kept entry reaches a degree above
+ *   2n, so these solvers run with P clamped to 2n (same results).  The FP64
+ *   solver (SIGK_FLAG_FP64) keeps every entry with m <= n and p, q <= P.
  *   flags: SIGK_FLAG_*.
  *   grid_ctas: persistent grid size (0 = occupancy-derived, one wave).
  *   max_len: upper bound on the segments of the path that a pair sweeps
@@ -300,7 +307,9 @@ sigk_status sigk_static_sync_status(void* stream);
  * columns of |<dx_i, y_J - y_0>| and |<x_I - x_0, dy_j>| (the size of the
  * edge coefficients, a_p ~ C^p/(p!)^2); then picks the smallest order P and
  * rings n (even) with max(L1,L2) C^(P+1)/((P+1)!)^2 <= tol/10 and
- * sum|c|^(n+1)/((n+1)!)^2 <= tol/10.  If a tile has |c| > 1 or no order up
+ * sum|c|^(n+1)/((n+1)!)^2 <= tol/10, and raises n until 2n >= P - 4, so
+ * that the FP32 truncation (see order above) reaches degree P - 4 or more.
+ * If a tile has |c| > 1 or no order up
  * to 16 fits, it sets refine_c = 1, 1/4, ... and plans the refined problem.
  * Synchronises `stream`.  Writes into *opts_out (other fields copied from
  * opts_in when given; max_len raised to the longest swept path, refined).

@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch
                             for (int q = 1; q <= P; ++q) b[q] *= sc;
                         }
                     }
-                    tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, NR);
+                    tile_update<P, NR>(c, a, a1lo, hi, lo, b, b1lo, NR);
                     int bump = 0;
                     if (fabsf(hi) > 1.8446744e19f) {
                         const float sc = 5.421011e-20f;
@@ -613,8 +613,8 @@ __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch
                     }
                 }
                 float ain_[P + 1], ha[P + 1];
-                tile_inverse_a<P>(c, a, hi, b, NR, ain_, ha);
-                const float cbar = tile_adjoint<P>(c, ain_, hi, b, ha, Ab, B0, Bb, NR);
+                tile_inverse_a<P, NR>(c, a, hi, b, NR, ain_, ha);
+                const float cbar = tile_adjoint<P, NR>(c, ain_, hi, b, ha, Ab, B0, Bb, NR);
 #pragma unroll
                 for (int p = 1; p <= P; ++p) a[p] = ain_[p];
                 if (!plain) {

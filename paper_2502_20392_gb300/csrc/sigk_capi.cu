@@ -80,6 +80,11 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
     int nrmax = r->order < kMaxRings ? r->order : kMaxRings;
     if (r->rings < 1 || r->rings > nrmax) return false;
     r->rings += (r->rings & 1);  // compiled ring counts are even (nrmax is even)
+    // The FP32 solvers keep the tile-matrix entries of weighted degree
+    // 2m + k <= 2 rings + 1 (keep_entry): no entry reaches an edge degree
+    // above 2 rings, so a larger order would only carry zeros.  The FP64
+    // solver keeps the whole square truncation of order P.
+    if (!(r->flags & SIGK_FLAG_FP64) && r->order > 2 * r->rings) r->order = 2 * r->rings;
     if (r->grid_ctas < 0 || r->max_len > (int64_t)INT32_MAX) return false;
     return true;
 }
@@ -1027,6 +1032,11 @@ static void choose_order(const double* st, int64_t n, double tol, int* P_out, in
     if (P < nr) P = nr;
     P += (P & 1);
     if (P > kMaxP) P = kMaxP;
+    // the FP32 truncation keeps edge degrees up to 2 nr (keep_entry): enough
+    // rings that the degree it reaches is within 4 of the coupling rule's P
+    // (that rule bounds every edge by the largest coupling of the pair, which
+    // overstates the edges of most tiles by orders of magnitude)
+    if (2 * nr < P - 4) nr = (P - 4 + 1) / 2;
     if (nr > (P < kMaxRings ? P : kMaxRings)) nr = P < kMaxRings ? P : kMaxRings;
     nr += (nr & 1);  // compiled ring counts are even
     *P_out = P;
@@ -1582,7 +1592,7 @@ sigk_status sigk_plan(int op, const float* X, const int64_t* len_x, int64_t n_x,
     Opts o;
     if (!resolve_opts(opts_in, &o)) return fail(SIGK_ERR_ARG, "invalid sigk_opts");
     o.order = kMaxP;  // layout for the largest order (the planner's seam stride)
-    o.rings = 2;
+    o.rings = kMaxRings;
     Layout L;
     if ((st = make_layout(op, n_x, n_y, d, o, &L)) != SIGK_OK) return st;
     if ((st = check_ws(L, ws, ws_bytes)) != SIGK_OK) return st;

@@ -476,9 +476,29 @@ __device__ __forceinline__ int rings_needed(float ac, const float (&th)[3]) {
     return ac <= th[0] ? 2 : (ac <= th[1] ? 4 : (ac <= th[2] ? 6 : 8));
 }
 
+// Entries of the tile matrix that the truncation keeps.  An entry of ring m
+// (the power c^m, 1 <= m <= nr) multiplies an edge coefficient of degree k
+// (k = 0: the corner); it is kept when its total degree m + k is at most P
+// and its weighted degree 2m + k at most 2 NT + 1, NT being the launch's ring
+// count.  Each power of c counts twice: a tile coefficient is the product of
+// two increments, a coupling (which sets the size of an edge coefficient of
+// degree k, ~ C^k / (k!)^2) is the product of an increment and a whole path
+// prefix, so c is of the order of C^2 or smaller on Brownian-type paths.  An
+// FP64 emulation of the scheme on the 1024-segment Grams measured the error
+// of this truncation against the exact kernel at 2.4e-10 (sigma = 1, P = 8,
+// NT = 4: 36 of the square's 48 entries) and 1.9e-8 (sigma = 4, NT = 6: 78
+// of 156 entries at P = 16).  No entry reaches degree 2 NT + 1, so an edge
+// degree P > 2 NT computes exactly what P = 2 NT computes (the solver
+// launches with P clamped to 2 NT).
+__host__ __device__ constexpr bool keep_entry(int P, int NT, int nr, int m, int k) {
+    return m >= 1 && m <= nr && k >= 0 && m + k <= P && 2 * m + k <= 2 * NT + 1;
+}
+
 // ---------------------------------------------------------------------------
 // One tile.  a[1..P]: scaled bottom edge (overwritten by the top edge);
-// (hi, lo), b[1..P]: scaled left edge (overwritten by the right edge).
+// (hi, lo), b[1..P]: scaled left edge (overwritten by the right edge).  NT:
+// the launch's ring count (the truncation's weighted degree); nr <= NT: the
+// rings of this tile (a compile-time constant at every call site).
 //
 // CLO: the coefficient is the unevaluated float-float pair c + clo (an
 // increment Gram computed beyond FP32 precision).  Rounding c to one float
@@ -489,11 +509,11 @@ __device__ __forceinline__ int rings_needed(float ac, const float (&th)[3]) {
 // the result is first order in c: the m = 1 ring of every edge coefficient
 // (clo * a_{p-1}) and the first-order coefficients, whose product c * ha_1 is
 // then formed exactly (TwoProduct) before the compensated accumulation.
-template <int P, bool CLO = false>
+template <int P, int NT, bool CLO = false>
 __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a1lo, float& hi,
                                             float& lo, float (&b)[P + 1], float& b1lo, int nr,
                                             float clo = 0.0f) {
-    constexpr int NRM = P < kMaxRings ? P : kMaxRings;
+    constexpr int NRM = P < NT ? P : NT;
     float cp[NRM + 1], ch[NRM + 1];
     cp[1] = c;
     ch[1] = c;
@@ -502,7 +522,8 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
         cp[m] = cp[m - 1] * c;
         ch[m] = cp[m] * c_inv_fact[m];
     }
-    // ring-p Hankel sums from the incoming edges (b_0 = a_0 := hi)
+    // ring-p Hankel sums of the incoming edges over the kept offsets
+    // (b_0 = a_0 := hi)
     float ha[NRM + 1], hb[NRM + 1];
 #pragma unroll
     for (int p = 1; p <= NRM; ++p) {
@@ -513,8 +534,10 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
             float sb = sa;
 #pragma unroll
             for (int r = 1; r <= P - p; ++r) {
-                sa = fmaf(b[r], c_inv_fact[p + r], sa);
-                sb = fmaf(a[r], c_inv_fact[p + r], sb);
+                if (keep_entry(P, NT, nr, p, r)) {
+                    sa = fmaf(b[r], c_inv_fact[p + r], sa);
+                    sb = fmaf(a[r], c_inv_fact[p + r], sb);
+                }
             }
             ha[p] = sa;
             hb[p] = sb;
@@ -530,9 +553,10 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
         float v = a[p];
 #pragma unroll
         for (int m = 1; m < p && m <= NRM; ++m)
-            if (m <= nr) v = fmaf(ch[m], a[p - m], v);
+            if (keep_entry(P, NT, nr, m, p - m)) v = fmaf(ch[m], a[p - m], v);
         if (p <= NRM && p <= nr) v = fmaf(cp[p], ha[p], v);
-        if constexpr (CLO) v = fmaf(clo, a[p - 1], v);
+        if constexpr (CLO)
+            if (keep_entry(P, NT, nr, 1, p - 1)) v = fmaf(clo, a[p - 1], v);
         a[p] = v;
     }
     // right edge
@@ -541,9 +565,10 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
         float v = b[q];
 #pragma unroll
         for (int m = 1; m < q && m <= NRM; ++m)
-            if (m <= nr) v = fmaf(ch[m], b[q - m], v);
+            if (keep_entry(P, NT, nr, m, q - m)) v = fmaf(ch[m], b[q - m], v);
         if (q <= NRM && q <= nr) v = fmaf(cp[q], hb[q], v);
-        if constexpr (CLO) v = fmaf(clo, b[q - 1], v);
+        if constexpr (CLO)
+            if (keep_entry(P, NT, nr, 1, q - 1)) v = fmaf(clo, b[q - 1], v);
         b[q] = v;
     }
     // first-order coefficients: compensated (TwoSum) accumulation.  Along a
@@ -579,15 +604,16 @@ __device__ __forceinline__ void tile_update(float c, float (&a)[P + 1], float& a
 
 // Inverse of the bottom-to-top edge update of tile_update, given the tile's
 // left edge (hi, b) and its top edge a2: the update is unit lower triangular
-// in the degree (a'_p = a_p + sum_{m<p} ch_m a_{p-m} + c^p ha_p(b)), so the
-// bottom edge is recovered degree by degree.  Used by the reverse sweep to
-// rebuild each tile's inputs from the stored left edges instead of storing
-// every tile.  ha (rings p <= nr) is returned for the adjoint.
-template <int P>
+// in the degree (a'_p = a_p + sum_m ch_m a_{p-m} + c^p ha_p(b) over the kept
+// entries), so the bottom edge is recovered degree by degree.  Used by the
+// reverse sweep to rebuild each tile's inputs from the stored left edges
+// instead of storing every tile.  ha (rings p <= nr) is returned for the
+// adjoint.
+template <int P, int NT>
 __device__ __forceinline__ void tile_inverse_a(float c, const float (&a2)[P + 1], float hi,
                                                const float (&b)[P + 1], int nr,
                                                float (&a)[P + 1], float (&ha)[P + 1]) {
-    constexpr int NRM = P < kMaxRings ? P : kMaxRings;
+    constexpr int NRM = P < NT ? P : NT;
     float cp[NRM + 1], ch[NRM + 1];
     cp[1] = c;
     ch[1] = c;
@@ -603,13 +629,16 @@ __device__ __forceinline__ void tile_inverse_a(float c, const float (&a2)[P + 1]
         if (p <= NRM && p <= nr) {
             float sa = hi * c_inv_fact[p];
 #pragma unroll
-            for (int r = 1; r <= P - p; ++r) sa = fmaf(b[r], c_inv_fact[p + r], sa);
+            for (int r = 1; r <= P - p; ++r)
+                if (keep_entry(P, NT, nr, p, r)) sa = fmaf(b[r], c_inv_fact[p + r], sa);
             ha[p] = sa;
             v = fmaf(-cp[p], sa, v);
         }
+        // highest ring first: a[p - 1], the value computed last, enters last,
+        // so the degree-by-degree recovery waits one FMA per degree
 #pragma unroll
-        for (int m = 1; m < p && m <= NRM; ++m)
-            if (m <= nr) v = fmaf(-ch[m], a[p - m], v);
+        for (int m = (p - 1 < NRM ? p - 1 : NRM); m >= 1; --m)
+            if (keep_entry(P, NT, nr, m, p - m)) v = fmaf(-ch[m], a[p - m], v);
         a[p] = v;
     }
     a[0] = 0.0f;
@@ -621,12 +650,12 @@ __device__ __forceinline__ void tile_inverse_a(float c, const float (&a2)[P + 1]
 // of b, from tile_inverse_a).  Adjoint inputs: A2 (top edge), B02 (corner),
 // B2 (right edge).  Outputs overwrite them with the adjoints of the bottom edge
 // (A), the corner (B0) and the left edge (B); returns dk/dc.
-template <int P>
+template <int P, int NT>
 __device__ __forceinline__ float tile_adjoint(float c, const float (&a)[P + 1], float hi,
                                               const float (&b)[P + 1], const float (&ha)[P + 1],
                                               float (&A)[P + 1], float& B0, float (&B)[P + 1],
                                               int nr) {
-    constexpr int NRM = P < kMaxRings ? P : kMaxRings;
+    constexpr int NRM = P < NT ? P : NT;
     float cp[NRM + 1], ch[NRM + 1];
     cp[1] = c;
     ch[1] = c;
@@ -643,24 +672,28 @@ __device__ __forceinline__ float tile_adjoint(float c, const float (&a)[P + 1], 
         if (p <= nr) {
             float sb = hi * c_inv_fact[p];
 #pragma unroll
-            for (int r = 1; r <= P - p; ++r) sb = fmaf(a[r], c_inv_fact[p + r], sb);
+            for (int r = 1; r <= P - p; ++r)
+                if (keep_entry(P, NT, nr, p, r)) sb = fmaf(a[r], c_inv_fact[p + r], sb);
             hb[p] = sb;
         }
     }
     // c-bar contributions: d ch_m / dc = ch_{m-1}, d cp_m / dc = m cp_{m-1}
     float cbar = 0.0f;
-    // correlation sums chb_m = sum_p A2_p a_{p-m} + B2_p b_{p-m}
+    // correlation sums chb_m = sum_p A2_p a_{p-m} + B2_p b_{p-m} (kept entries)
 #pragma unroll
     for (int m = 1; m <= NRM; ++m) {
         if (m <= nr) {
-            float chb = 0.0f;
+            // two independent accumulators (bottom- and left-edge terms)
+            float chA = 0.0f, chB = 0.0f;
 #pragma unroll
             for (int p = m + 1; p <= P; ++p) {
-                chb = fmaf(A[p], a[p - m], chb);
-                chb = fmaf(B[p], b[p - m], chb);
+                if (keep_entry(P, NT, nr, m, p - m)) {
+                    chA = fmaf(A[p], a[p - m], chA);
+                    chB = fmaf(B[p], b[p - m], chB);
+                }
             }
             const float dch = (m == 1) ? 1.0f : ch[m - 1];
-            cbar = fmaf(chb, dch, cbar);
+            cbar = fmaf(chA + chB, dch, cbar);
             // ring-m Hankel term: d/dcp_m (cp_m (A2_m ha_m + B2_m hb_m))
             const float dcp = (m == 1) ? 1.0f : (float)m * cp[m - 1];
             cbar = fmaf(fmaf(A[m], ha[m], B[m] * hb[m]), dcp, cbar);
@@ -680,15 +713,17 @@ __device__ __forceinline__ float tile_adjoint(float c, const float (&a)[P + 1], 
         float va = A[s], vb = B[s];
 #pragma unroll
         for (int m = 1; m <= NRM && s + m <= P; ++m)
-            if (m <= nr) {
+            if (keep_entry(P, NT, nr, m, s)) {
                 va = fmaf(ch[m], A[s + m], va);
                 vb = fmaf(ch[m], B[s + m], vb);
             }
         va = fmaf(Sbar, c_inv_fact[s], va);  // corner b0' = b0 + sum_p a_p / p!
 #pragma unroll
         for (int p = 1; p <= NRM && p + s <= P; ++p) {
-            va = fmaf(hbb[p], c_inv_fact[p + s], va);  // hb_p reads a_s
-            vb = fmaf(hab[p], c_inv_fact[p + s], vb);  // ha_p reads b_s
+            if (keep_entry(P, NT, nr, p, s)) {
+                va = fmaf(hbb[p], c_inv_fact[p + s], va);  // hb_p reads a_s
+                vb = fmaf(hab[p], c_inv_fact[p + s], vb);  // ha_p reads b_s
+            }
         }
         A[s] = va;
         B[s] = vb;
@@ -702,21 +737,27 @@ __device__ __forceinline__ float tile_adjoint(float c, const float (&a)[P + 1], 
     return cbar;
 }
 
+// Kept entries of the tile matrix: 1 for a diagonal entry (k = 0), 2 for an
+// off-diagonal one (it appears above and below the diagonal).
+__host__ __device__ constexpr int kept_entries(int P, int NT, int nr) {
+    int n = 0;
+    for (int m = 1; m <= P; ++m)
+        for (int k = 0; k <= P; ++k)
+            if (keep_entry(P, NT, nr, m, k)) n += (k == 0) ? 1 : 2;
+    return n;
+}
+
 // FP32 operations of tile_update (FMA counted as 2), for the roofline.
-__host__ __device__ constexpr long long tile_flops(int P, int nr) {
+__host__ __device__ constexpr long long tile_flops(int P, int NT, int nr) {
     long long f = 0;
-    int nrm = P < kMaxRings ? P : kMaxRings;
+    const int nrm = P < NT ? P : NT;
     if (nr > nrm) nr = nrm;
-    f += 2 * (nr - 1);                                  // powers
-    for (int p = 1; p <= nr; ++p) f += 2 * (1 + 2 * (P - p));  // Hankel sums (2 edges)
-    f += 2 * P;                                         // S
-    for (int p = 1; p <= P; ++p) {
-        int k = (p - 1) < nr ? (p - 1) : nr;
-        f += 2 * 2 * k;                                 // convolution, 2 edges
-        if (p <= nr) f += 2 * 2;                        // ring-p term, 2 edges
-    }
-    f += 10;                                            // float-float corner
-    f += 18;                                            // compensated a1, b1
+    f += 2 * (nr - 1);                           // powers
+    f += 2 * nr;                                 // corner terms of the Hankel sums (1 mul each)
+    f += 2 * 2 * kept_entries(P, NT, nr);        // 2 FMAs per kept entry (one per outgoing edge)
+    f += 2 * P;                                  // S
+    f += 10;                                     // float-float corner
+    f += 18;                                     // compensated a1, b1
     return f;
 }
 

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                     float c = 0.0f;
 #pragma unroll
                     for (int e = 0; e < D; ++e) c = fmaf(dx[k][e], dy[e], c);
-                    tile_update<P>(c, a[k], a1lo[k], hi, lo, b, b1lo, NR);
+                    tile_update<P, NR>(c, a[k], a1lo[k], hi, lo, b, b1lo, NR);
                 }
                 // renormalise when the corner value grows past 2^64
                 int bump = 0;

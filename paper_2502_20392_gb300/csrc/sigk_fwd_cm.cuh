@@ -253,7 +253,7 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
             }
             const T c = cring[(j & 63) * 32 + lane];
             if constexpr (F32) {
-                tile_update<P>(c, a, a1lo, hi, lo, b, b1lo, NR);
+                tile_update<P, NR>(c, a, a1lo, hi, lo, b, b1lo, NR);
                 if (fabsf(hi) > 1.8446744e19f) {  // 2^64
                     const float sc = 5.421011e-20f;  // 2^-64
                     a1lo *= sc;

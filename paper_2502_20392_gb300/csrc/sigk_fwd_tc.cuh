@@ -386,7 +386,7 @@ __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDe
             }
             // rows past the end of the path have zero digits: c = clo = 0
             auto tile = [&](auto nrc) {
-                tile_update<P, true>(cc.x, a, a1lo, hi, lo, b, b1lo, decltype(nrc)::value, cc.y);
+                tile_update<P, NR, true>(cc.x, a, a1lo, hi, lo, b, b1lo, decltype(nrc)::value, cc.y);
             };
             if (nw == NR) tile(std::integral_constant<int, NR>{});
             else if (nw <= 2) tile(std::integral_constant<int, 2>{});

@@ -456,7 +456,7 @@ def plan(op: int, X, len_x, Y=None, len_y=None, tol: float = 1e-5, opts: Opts | 
         n_y = len_y.numel()
     else:
         n_y = 0 if op == OP_GRAM else n_x
-    big = Opts(order=16, rings=1, flags=opts.flags, grid_ctas=opts.grid_ctas, max_len=opts.max_len,
+    big = Opts(order=16, rings=8, flags=opts.flags, grid_ctas=opts.grid_ctas, max_len=opts.max_len,
                refine_c=opts.refine_c, wait_ms=opts.wait_ms)
     nb = workspace_size(op, n_x, n_y if op != OP_PAIRS else n_x, d, big)
     npairs = n_x if op == OP_PAIRS else (n_x * (n_x + 1) // 2 if n_y == 0 else

@@ -12,9 +12,19 @@ sys.path.insert(0, ROOT)
 def test_flop_model():
     import bench
     # per-tile FP32 operations (FMA = 2) of the solver and of the adjoint
-    assert bench.tile_flops(8, 4, 16) == 282
-    assert bench.tile_flops(16, 6, 16) == 738
-    assert bench.adjoint_tile_flops(8, 4, 16, replay=False) == 672
+    # kept entries of the truncation 2m + k <= 2n + 1, m + k <= P, written out:
+    # P = 8, n = 4: ring 1 offsets 0..7, ring 2 0..5, ring 3 0..3, ring 4 0..1,
+    # each off-diagonal offset on both sides of the diagonal
+    assert bench.kept_entries(8, 4, 4) == (1 + 2 * 7) + (1 + 2 * 5) + (1 + 2 * 3) + (1 + 2 * 1) == 36
+    assert bench.kept_entries(12, 6, 6) == sum(1 + 2 * (13 - 2 * m) for m in range(1, 7)) == 78
+    # no kept entry reaches a degree above 2n: a larger order adds nothing
+    assert bench.kept_entries(16, 6, 6) == bench.kept_entries(12, 6, 6)
+    assert bench.launch_order(16, 6) == 12 and bench.launch_order(8, 4) == 8
+    # the square truncation (the whole (P+1)^2 matrix up to ring n) as a bound
+    assert bench.kept_entries(8, 4, 4) < sum(2 * (8 - m) + 1 for m in range(1, 5)) == 48
+    assert bench.tile_flops(8, 4, 16) == 2 * 3 + 2 * 4 + 4 * 36 + 2 * 8 + 28 + 2 * 16 == 234
+    assert bench.tile_flops(12, 6, 16) == 2 * 5 + 2 * 6 + 4 * 78 + 2 * 12 + 28 + 2 * 16 == 418
+    assert bench.adjoint_tile_flops(8, 4, 16, replay=False) == 480
     for P, nr, d in ((8, 4, 16), (12, 6, 4), (16, 8, 8)):
         # the replayed pass adds exactly one forward tile
         assert (bench.adjoint_tile_flops(P, nr, d) - bench.adjoint_tile_flops(P, nr, d, replay=False)
@@ -29,6 +39,7 @@ def test_useful_work_model():
     # out for the bench's two launches (P = 8, n = 4 and P = 16, n = 6, d = 16)
     assert bench.useful_tile_fma(8, 4, 16) == 16 + (15 + 13 + 11 + 9) + 16 == 80
     assert bench.useful_tile_fma(16, 6, 16) == 16 + (31 + 29 + 27 + 25 + 23 + 21) + 32 == 204
+    assert bench.useful_tile_fma(12, 6, 16) == 16 + (23 + 21 + 19 + 17 + 15 + 13) + 24 == 148
     assert bench.useful_tile_flops(8, 4, 16) == 160
     assert bench.useful_tile_flops(8, 4, 16, adjoint=True) == 320
     # the executed count is never below the useful one
