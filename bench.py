@@ -28,7 +28,8 @@ N_PATHS, N_SEG, DIM = 64, 1024, 16
 SIGMAS = ((1.0, 2001, 8, 4), (4.0, 2004, 12, 6))   # sigma, seed, order P, rings (as launched)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 L2_FLUSH_BYTES = 512 << 20
-ORACLE_SAMPLE_PAIRS = 16
+ORACLE_SAMPLE_PAIRS = 80   # per sigma: ~10-15 s of FP64 oracle work on 16 host cores
+REF_PAIRS_PER_STEP = 16    # reference arm, per sigma and step (at least one per oracle thread)
 
 
 METRIC = ("fwd & fwd+bwd sig-kernel cells/s (pairs*L1*L2/s), Gram B=64 L=1024 d=16 "
@@ -770,7 +771,7 @@ def run_reference(args, world, rank):
     from paper_2502_20392_gb300 import synth
     oracle.build()
     host = [synth.workload_gram_1024(s_, seed) for s_, seed, _, _ in SIGMAS]
-    per_step = max(ORACLE_SAMPLE_PAIRS, oracle.num_threads())
+    per_step = max(REF_PAIRS_PER_STEP, oracle.num_threads())
     for w in range(args.warmup):
         oracle_sample(host, 1, seed=1000 + w)
     times = []
