@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_PATHS, N_SEG, DIM = 64, 1024, 16
-SIGMAS = ((1.0, 2001, 8, 4), (4.0, 2004, 12, 6))   # sigma, seed, order P, rings (as launched)
+SIGMAS = ((1.0, 2001, 6, 3), (4.0, 2004, 12, 6))   # sigma, seed, order P, rings (as planned and launched)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 L2_FLUSH_BYTES = 512 << 20
 ORACLE_SAMPLE_PAIRS = 80   # per sigma: ~10-15 s of FP64 oracle work on 16 host cores
@@ -283,8 +283,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="full", choices=["full", "small", "large_d"],
-                    help="small: 16 paths per Gram (for ncu captures; not a bench line); "
+    ap.add_argument("--case", default="full", choices=["full", "medium", "small", "large_d"],
+                    help="small / medium: 16 / 32 paths per Gram (for ncu captures; not a bench "
+                         "line; medium gives the forward several waves of work items); "
                          "large_d: two launches of 64 ragged pairs with d = 256 (the two-phase "
                          "kernel, for ncu captures)")
     ap.add_argument("--sweep", default=None, choices=["roughness", "dimension", "length", "configs"],
@@ -296,9 +297,9 @@ def main():
         return run_sweep(args)
     if args.case == "large_d":
         return run_large_d(args.no_tensor)
-    if args.case == "small":
+    if args.case in ("small", "medium"):
         global N_PATHS
-        N_PATHS = 16
+        N_PATHS = 16 if args.case == "small" else 32
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -117,8 +117,9 @@ enum {
  *          even value.
  *   rings: number n of Neumann iterations per tile (powers of c_ij kept,
  *          Sec. 2.3 / App. B: the local Neumann iteration), 1 <= n <= min(order, 8);
- *          rounded up to an even value (the ring count is compiled into the
- *          kernels).
+ *          compiled into the kernels: the FP32 solvers take 2..8, the FP64
+ *          solver an even count (1 rounds up to 2, and odd counts round up
+ *          under SIGK_FLAG_FP64).
  *   The FP32 solvers keep the entry c^m w B of the tile matrix (ring m,
  *   edge coefficient of degree k) when m <= n, m + k <= P and
  *   2m + k <= 2n + 1: a power of c counts twice against the degree of the
@@ -149,7 +150,8 @@ enum {
  *            tensor-core forward (16 < d <= 1024, FP32) chooses the count per
  *            tile, as the local Neumann iteration of App. B stops when the
  *            next term is negligible: a tile with coefficient c needs the
- *            smallest even n <= rings with |c|^(n+1) / ((n+1)!)^2 <= ring_tol
+ *            smallest of 2, 4, 6, 8 (capped at rings) with
+ *            |c|^(n+1) / ((n+1)!)^2 <= ring_tol
  *            (the first dropped ring, relative to the edge data), and the
  *            tiles a warp solves in one step use the largest count among them.
  *            sigk_plan sets it to tol / (100 L1 L2) of the largest pair, a
@@ -306,8 +308,10 @@ sigk_status sigk_static_sync_status(void* stream);
  * the ring sums sum |c|^m (m = 2..9) and the couplings C = max over rows and
  * columns of |<dx_i, y_J - y_0>| and |<x_I - x_0, dy_j>| (the size of the
  * edge coefficients, a_p ~ C^p/(p!)^2); then picks the smallest order P and
- * rings n (even) with max(L1,L2) C^(P+1)/((P+1)!)^2 <= tol/10 and
- * sum|c|^(n+1)/((n+1)!)^2 <= tol/10, and raises n until 2n >= P - 4, so
+ * rings n >= 2 with max(L1,L2) C^(P+1)/((P+1)!)^2 <= tol/10 and
+ * sum|c|^(n+1)/((n+1)!)^2 <= tol/4 (the ring sum adds the dropped terms of
+ * all tiles as if coherent, which overstates the measured truncation error
+ * 3-4 times on Brownian Grams), and raises n until 2n >= P - 4, so
  * that the FP32 truncation (see order above) reaches degree P - 4 or more.
  * If a tile has |c| > 1 or no order up
  * to 16 fits, it sets refine_c = 1, 1/4, ... and plans the refined problem.
@@ -383,9 +387,9 @@ sigk_status sigk_sync_status(void* ws, size_t ws_bytes, void* stream);
 sigk_status sigk_counters(void* ws, size_t ws_bytes, void* stream, double* out4);
 
 /* [The per-tile Neumann iteration counts of App. B.]
- * Tiles solved by the last forward on this workspace with 2, 4, 6 and 8
- * Neumann rings (out4[0..3]; synchronises `stream`); all zero unless
- * opts->ring_tol was set. */
+ * Tiles solved by the last forward on this workspace with at most 2, 3-4,
+ * 5-6 and 7-8 Neumann rings (out4[0..3]; synchronises `stream`); all zero
+ * unless opts->ring_tol was set. */
 sigk_status sigk_ring_histogram(void* ws, size_t ws_bytes, void* stream, double* out4);
 
 /* [No counterpart in the paper.]

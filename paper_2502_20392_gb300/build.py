@@ -24,6 +24,7 @@ LIB_DEBUG = os.path.join(BUILD_DEBUG, "libsigk.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ORDERS = (4, 6, 8, 10, 12, 14, 16)
 RINGS = (2, 4, 6, 8)
+ODD_RINGS = (3, 5, 7)
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
@@ -55,6 +56,12 @@ def _units():
     for P in ORDERS:
         for NR in RINGS:
             if NR <= P:
+                units.append((f"sigk_fwd_P{P}_R{NR}", os.path.join(CSRC, "sigk_fwd_inst.cu"),
+                              [f"-DSIGK_P={P}", f"-DSIGK_NR={NR}"]))
+        # odd ring counts serve the FP32 solvers only, which launch with the
+        # order clamped to twice the rings
+        for NR in ODD_RINGS:
+            if NR <= P <= 2 * NR:
                 units.append((f"sigk_fwd_P{P}_R{NR}", os.path.join(CSRC, "sigk_fwd_inst.cu"),
                               [f"-DSIGK_P={P}", f"-DSIGK_NR={NR}"]))
     for f in sorted(os.listdir(CSRC)):

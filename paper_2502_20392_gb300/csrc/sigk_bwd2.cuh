@@ -426,13 +426,9 @@ __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch
                 int F = __shfl_up_sync(kFull, oE, 1);
                 if (lane == 0) {
                     if (s > 0 && t < L2) {
-                        const float* e_ = sin_ + (t & 31) * S;
-                        hi = e_[0];
-                        lo = e_[1];
-                        b1lo = e_[2];
-#pragma unroll
-                        for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
-                        F = __float_as_int(e_[P + 3]);
+                        float v[S];
+                        seam_entry_load<S>(sin_ + (t & 31) * S, v);
+                        seam_unpack<P>(v, hi, lo, b1lo, b, F);
                     } else {
                         hi = 1.0f; lo = 0.0f; b1lo = 0.0f; F = 0;
 #pragma unroll

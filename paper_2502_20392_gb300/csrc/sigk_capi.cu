@@ -79,7 +79,10 @@ static bool resolve_opts(const sigk_opts* o, Opts* r) {
     r->order += (r->order & 1);
     int nrmax = r->order < kMaxRings ? r->order : kMaxRings;
     if (r->rings < 1 || r->rings > nrmax) return false;
-    r->rings += (r->rings & 1);  // compiled ring counts are even (nrmax is even)
+    // odd ring counts are compiled for the FP32 solvers; the FP64 solver,
+    // which keeps the square truncation at any order, and a single ring
+    // round up to even (nrmax is even)
+    if ((r->flags & SIGK_FLAG_FP64) || r->rings < 2) r->rings += (r->rings & 1);
     // The FP32 solvers keep the tile-matrix entries of weighted degree
     // 2m + k <= 2 rings + 1 (keep_entry): no entry reaches an edge degree
     // above 2 rings, so a larger order would only carry zeros.  The FP64
@@ -97,7 +100,8 @@ static int dim_bucket(int d) {
 }
 
 // (edge degree P, ring count NR) pairs compiled: P even in 4..16, NR even in
-// 2..min(P, 8).  Requested ring counts are rounded up to even.
+// 2..min(P, 8), and NR in {3, 5, 7} with NR <= P <= 2 NR (the FP32 solvers,
+// which clamp P to 2 NR; the FP64 solver rounds odd ring counts up).
 #define SIGK_DISPATCH_PNR(FN, ...)                  \
     switch (P * 16 + NR) {                          \
         case 66: return FN<4, 2>(__VA_ARGS__); \
@@ -125,6 +129,15 @@ static int dim_bucket(int d) {
         case 260: return FN<16, 4>(__VA_ARGS__); \
         case 262: return FN<16, 6>(__VA_ARGS__); \
         case 264: return FN<16, 8>(__VA_ARGS__); \
+        case 67: return FN<4, 3>(__VA_ARGS__); \
+        case 99: return FN<6, 3>(__VA_ARGS__); \
+        case 101: return FN<6, 5>(__VA_ARGS__); \
+        case 133: return FN<8, 5>(__VA_ARGS__); \
+        case 135: return FN<8, 7>(__VA_ARGS__); \
+        case 165: return FN<10, 5>(__VA_ARGS__); \
+        case 167: return FN<10, 7>(__VA_ARGS__); \
+        case 199: return FN<12, 7>(__VA_ARGS__); \
+        case 231: return FN<14, 7>(__VA_ARGS__); \
         default: break;                             \
     }
 
@@ -412,7 +425,7 @@ struct Header {
     int sched[4];  // schedule: mode, n_levels, n_items (Schedule::hdr)
     int sched2[4];  // training forward's schedule (items of 2^fwd_shift strips)
     long long train_sig;  // signature of the training forward whose state the workspace holds (0: none)
-    unsigned ring_hist[4];  // tiles solved with 2, 4, 6, 8 rings (adaptive forwards)
+    unsigned ring_hist[4];  // tiles solved with <= 2, 3-4, 5-6, 7-8 rings (adaptive forwards)
     int pad2[6];
     long long diag[3];  // first timed-out wait: address, target, value seen (byte 128)
     long long wait_ns;  // budget of the bounded waits of the current launch (byte 152)
@@ -1010,6 +1023,11 @@ static void choose_order(const double* st, int64_t n, double tol, int* P_out, in
     *max_tile_c = 0.0;
     *order_fits = true;
     const double target = 0.1 * tol;
+    // rings: the sum of the first dropped ring over every tile treats the
+    // terms as coherent; on the 1024-segment Grams it overstates the measured
+    // truncation error 3-4 times (sigma = 1, three rings: 1.7e-6 predicted,
+    // 4.4e-7 measured on self-kernels), so it gets a quarter of the tolerance
+    const double ring_target = 0.25 * tol;
     int P = 4, nr = 1;
     double fact[40];
     fact[0] = 1.0;
@@ -1020,7 +1038,7 @@ static void choose_order(const double* st, int64_t n, double tol, int* P_out, in
         if ((int64_t)o[1] > *max_swept) *max_swept = (int64_t)o[1];
         if (o[12] > *max_tile_c) *max_tile_c = o[12];
         int r = 1;
-        while (r < kMaxRings && o[4 + (r + 1) - 2] / (fact[r + 1] * fact[r + 1]) > target) ++r;
+        while (r < kMaxRings && o[4 + (r + 1) - 2] / (fact[r + 1] * fact[r + 1]) > ring_target) ++r;
         if (r > nr) nr = r;
         const double C = o[2] > o[3] ? o[2] : o[3];
         const double Lm = o[0] > o[1] ? o[0] : o[1];
@@ -1038,7 +1056,7 @@ static void choose_order(const double* st, int64_t n, double tol, int* P_out, in
     // overstates the edges of most tiles by orders of magnitude)
     if (2 * nr < P - 4) nr = (P - 4 + 1) / 2;
     if (nr > (P < kMaxRings ? P : kMaxRings)) nr = P < kMaxRings ? P : kMaxRings;
-    nr += (nr & 1);  // compiled ring counts are even
+    if (nr < 2) nr = 2;
     *P_out = P;
     *nr_out = nr;
 }

@@ -419,6 +419,59 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// A seam entry (corner hi, lo, b1lo, b_1..b_P, exponent: S = P + 4 floats,
+// even) between shared memory and registers in the widest aligned words:
+// 16-byte accesses when S is a multiple of 4 (the entry then starts on a
+// 16-byte boundary), else 8-byte ones.  One lane reads or writes a whole
+// entry per step, so the width sets how many shared-memory instructions the
+// warp issues for it.
+template <int S>
+__device__ __forceinline__ void seam_entry_load(const float* src, float (&v)[S]) {
+    static_assert(S % 2 == 0, "seam entries hold an even number of floats");
+    if constexpr (S % 4 == 0) {
+#pragma unroll
+        for (int g = 0; g < S / 4; ++g) {
+            const float4 w = reinterpret_cast<const float4*>(src)[g];
+            v[4 * g] = w.x; v[4 * g + 1] = w.y; v[4 * g + 2] = w.z; v[4 * g + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < S / 2; ++g) {
+            const float2 w = reinterpret_cast<const float2*>(src)[g];
+            v[2 * g] = w.x; v[2 * g + 1] = w.y;
+        }
+    }
+}
+template <int S>
+__device__ __forceinline__ void seam_entry_store(float* dst, const float (&v)[S]) {
+    static_assert(S % 2 == 0, "seam entries hold an even number of floats");
+    if constexpr (S % 4 == 0) {
+#pragma unroll
+        for (int g = 0; g < S / 4; ++g)
+            reinterpret_cast<float4*>(dst)[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+    } else {
+#pragma unroll
+        for (int g = 0; g < S / 2; ++g) reinterpret_cast<float2*>(dst)[g] = make_float2(v[2 * g], v[2 * g + 1]);
+    }
+}
+// Pack / unpack the left edge of one lane as a seam entry.
+template <int P>
+__device__ __forceinline__ void seam_pack(float (&v)[P + 4], float hi, float lo, float b1lo,
+                                          const float (&b)[P + 1], int E) {
+    v[0] = hi; v[1] = lo; v[2] = b1lo;
+#pragma unroll
+    for (int q = 1; q <= P; ++q) v[2 + q] = b[q];
+    v[P + 3] = __int_as_float(E);
+}
+template <int P>
+__device__ __forceinline__ void seam_unpack(const float (&v)[P + 4], float& hi, float& lo, float& b1lo,
+                                            float (&b)[P + 1], int& F) {
+    hi = v[0]; lo = v[1]; b1lo = v[2];
+#pragma unroll
+    for (int q = 1; q <= P; ++q) b[q] = v[2 + q];
+    F = __float_as_int(v[P + 3]);
+}
+
 // Bulk (TMA) store of `bytes` from shared to global memory, in this
 // thread's bulk async-group; both addresses 16-byte aligned, bytes a
 // multiple of 16.  The async proxy is outside the ordering of generic

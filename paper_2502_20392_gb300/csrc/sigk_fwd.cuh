@@ -262,13 +262,9 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
             int F = __shfl_up_sync(kFull, oE, 1);
             if (lane == 0) {
                 if (has_in && t < L2) {
-                    const float* e_ = sin_ + (t & 31) * S;
-                    hi = e_[0];
-                    lo = e_[1];
-                    b1lo = e_[2];
-#pragma unroll
-                    for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
-                    F = __float_as_int(e_[P + 3]);
+                    float v[S];
+                    seam_entry_load<S>(sin_ + (t & 31) * S, v);
+                    seam_unpack<P>(v, hi, lo, b1lo, b, F);
                 } else {
                     hi = 1.0f; lo = 0.0f; b1lo = 0.0f; F = 0;
 #pragma unroll
@@ -368,11 +364,9 @@ __global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(
                 }
                 if (lane == 31) {
                     if (has_out) {
-                        float* e_ = sout + (j & 31) * S;
-                        e_[0] = hi; e_[1] = lo; e_[2] = b1lo;
-#pragma unroll
-                        for (int q = 1; q <= P; ++q) e_[2 + q] = b[q];
-                        e_[P + 3] = __int_as_float(E);
+                        float v[S];
+                        seam_pack<P>(v, hi, lo, b1lo, b, E);
+                        seam_entry_store<S>(sout + (j & 31) * S, v);
                     } else if (j == L2 - 1) {
                         double k = (double)hi + (double)lo + (double)b1lo;
                         double fq = 1.0;

@@ -220,15 +220,16 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
         if (lane == 0) {
             if (has_in && t < L2) {
                 const T* e_ = sin_ + (t & 31) * S;
-                hi = e_[0];
                 if constexpr (F32) {
-                    lo = e_[1];
-                    b1lo = e_[2];
-                }
+                    float v[S];
+                    seam_entry_load<S>(e_, v);
+                    seam_unpack<P>(v, hi, lo, b1lo, b, F);
+                } else {
+                    hi = e_[0];
 #pragma unroll
-                for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
-                if constexpr (F32) F = __float_as_int(e_[P + 3]);
-                else F = (int)e_[P + 3];
+                    for (int q = 1; q <= P; ++q) b[q] = e_[2 + q];
+                    F = (int)e_[P + 3];
+                }
             } else {
                 hi = T(1); lo = 0.0f; b1lo = 0.0f; F = 0;
 #pragma unroll
@@ -284,13 +285,18 @@ __device__ __forceinline__ bool sweep_strip(const SolverArgs& A, const PairDesc&
             if (lane == 31) {
                 if (has_out) {
                     T* e_ = sout + (j & 31) * S;
-                    e_[0] = hi;
-                    e_[1] = (T)lo;
-                    e_[2] = (T)b1lo;
+                    if constexpr (F32) {
+                        float v[S];
+                        seam_pack<P>(v, hi, lo, b1lo, b, E);
+                        seam_entry_store<S>(e_, v);
+                    } else {
+                        e_[0] = hi;
+                        e_[1] = (T)lo;
+                        e_[2] = (T)b1lo;
 #pragma unroll
-                    for (int q = 1; q <= P; ++q) e_[2 + q] = b[q];
-                    if constexpr (F32) e_[P + 3] = __int_as_float(E);
-                    else e_[P + 3] = (double)E;
+                        for (int q = 1; q <= P; ++q) e_[2 + q] = b[q];
+                        e_[P + 3] = (double)E;
+                    }
                 } else if (j == L2 - 1) {
                     double k = (double)hi + (double)lo + (double)b1lo;
                     double fq = 1.0;

@@ -197,7 +197,7 @@ def counters(ws: Workspace):
 
 
 def ring_histogram(ws: Workspace):
-    """Tiles of the last forward on ws solved with 2, 4, 6, 8 rings (adaptive
+    """Tiles of the last forward on ws solved with <= 2, 3-4, 5-6, 7-8 rings (adaptive
     ring counts only)."""
     out = (ctypes.c_double * 4)()
     _check(load().sigk_ring_histogram(_ptr(ws.buf), ws.buf.numel(), _stream(), out))

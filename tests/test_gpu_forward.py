@@ -75,7 +75,8 @@ def test_pair_256_d4(S, orc):
     assert abs(k - ref) / abs(ref) < 1e-6, (k, ref)
 
 
-@pytest.mark.parametrize("sigma,order,rings", [(1.0, 8, 4), (4.0, 16, 6)])
+# odd ring counts (3, 5, 7) are FP32-only instantiations at P <= 2 rings
+@pytest.mark.parametrize("sigma,order,rings", [(1.0, 8, 4), (4.0, 16, 6), (2.0, 10, 5), (4.0, 14, 7)])
 def test_gram_ragged_d16(S, orc, sigma, order, rings):
     from paper_2502_20392_gb300 import synth
     # common time step 1/300: a short path is a short piece of Brownian motion

@@ -26,7 +26,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-GRAM_OPTS = {1.0: dict(order=8, rings=4), 4.0: dict(order=12, rings=6)}
+GRAM_OPTS = {1.0: dict(order=6, rings=3), 4.0: dict(order=12, rings=6)}
 LONG_OPTS = dict(order=4, rings=2)
 MMD_OPTS = dict(order=6, rings=4)
 
