@@ -14,8 +14,13 @@ struct KernelInfo {
 };
 
 // Rows per lane as a function of (P, D): fewer rows when the register
-// footprint (R*(P + D) state floats) would push occupancy too low.
-constexpr int rows_per_lane(int P, int D) { return (P + D) <= 16 ? 4 : 2; }
+// footprint (R*(P + D) state floats) would push occupancy too low.  Four rows
+// amortise the per-step shuffles, seam staging and control over four tiles:
+// at P = 6, D = 16 (168 registers, three CTAs per SM) the 64-path Gram's
+// forward took 12.2 ms against 13.8 ms with two rows at four CTAs per SM;
+// at P = 12, D = 16 one row per lane at four CTAs per SM was slower than two
+// (30.8 against 26.0 ms).
+constexpr int rows_per_lane(int P, int D) { return ((P + D) <= 16 || (D == 16 && P <= 6)) ? 4 : 2; }
 // The same for the training forward that stores the tile records (its
 // per-row record state adds registers): two rows while that fits without
 // spills, else one.  The records are laid out per work item and step, so a
