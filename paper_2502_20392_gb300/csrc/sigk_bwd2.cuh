@@ -137,6 +137,10 @@ __device__ __forceinline__ void finish_rows(float* dst, int ds, int v0, int Lv, 
 // memory, four dimensions per 128-bit load; chunks of 32 dimensions summed in
 // two levels, as in the two-phase forward), written into the skewed area cs
 // through the block blk.  The strip's rows are staged once when d <= 32.
+// ONE: d <= 32, a single chunk: the products are summed straight into the
+// accumulators (the two-level sum would only add zero, and its second set of
+// 32 accumulators costs registers).
+template <bool ONE>
 __device__ __forceinline__ void strip_coefficients(float* cs, float* wsm, const float* xr, const float* yr,
                                                    int i0, int L1, int L2, int d, int inc_mode, int sx,
                                                    int sy, int lane) {
@@ -160,22 +164,36 @@ __device__ __forceinline__ void strip_coefficients(float* cs, float* wsm, const 
             if (fy) finish_rows<kB2KC>(ys, 36, j0, L2, lane);
             __syncwarp();
             const int kn = min(kB2KC, d - k0);
-            float part[32];
+            if constexpr (ONE) {
+                for (int e = 0; e < kn; e += 4) {
+                    const float4 y = *reinterpret_cast<const float4*>(ys + lane * 36 + e);
 #pragma unroll
-            for (int r = 0; r < 32; ++r) part[r] = 0.0f;
-            for (int e = 0; e < kn; e += 4) {
-                const float4 y = *reinterpret_cast<const float4*>(ys + lane * 36 + e);
-#pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    const float4 x = *reinterpret_cast<const float4*>(xs + r * 36 + e);
-                    part[r] = fmaf(x.x, y.x, part[r]);
-                    part[r] = fmaf(x.y, y.y, part[r]);
-                    part[r] = fmaf(x.z, y.z, part[r]);
-                    part[r] = fmaf(x.w, y.w, part[r]);
+                    for (int r = 0; r < 32; ++r) {
+                        const float4 x = *reinterpret_cast<const float4*>(xs + r * 36 + e);
+                        acc[r] = fmaf(x.x, y.x, acc[r]);
+                        acc[r] = fmaf(x.y, y.y, acc[r]);
+                        acc[r] = fmaf(x.z, y.z, acc[r]);
+                        acc[r] = fmaf(x.w, y.w, acc[r]);
+                    }
                 }
-            }
+            } else {
+                float part[32];
 #pragma unroll
-            for (int r = 0; r < 32; ++r) acc[r] += part[r];
+                for (int r = 0; r < 32; ++r) part[r] = 0.0f;
+                for (int e = 0; e < kn; e += 4) {
+                    const float4 y = *reinterpret_cast<const float4*>(ys + lane * 36 + e);
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        const float4 x = *reinterpret_cast<const float4*>(xs + r * 36 + e);
+                        part[r] = fmaf(x.x, y.x, part[r]);
+                        part[r] = fmaf(x.y, y.y, part[r]);
+                        part[r] = fmaf(x.z, y.z, part[r]);
+                        part[r] = fmaf(x.w, y.w, part[r]);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 32; ++r) acc[r] += part[r];
+            }
         }
         __syncwarp();
         // lane = column: blk[r][col] = c(row r, column j0 + col), then skewed into cs
@@ -323,7 +341,8 @@ __device__ __forceinline__ void chain_strip(const float* cs, float* wsm, const f
 }
 
 // 168 registers at three CTAs per SM: measured 80.9 ms on the 64-path Gram
-// against 93.0 ms at four CTAs per SM and 128 registers (which spill).
+// against 93.0 ms at four CTAs per SM and 128 registers (which spill) at order
+// 8, and 70.8 against 72.0 ms at order 6 with three rings (60 bytes spilled).
 template <int P, int NR>
 __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch, int64_t cstride) {
     constexpr int S = P + 4;
@@ -384,7 +403,8 @@ __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch
 #endif
 
         // ------------------------- phase 0: coefficients -------------------------
-        strip_coefficients(cs, wsm, pd.xr, pd.yr, i0, L1, L2, d, A.inc_mode, pd.sx, pd.sy, lane);
+        if (d <= kB2KC) strip_coefficients<true>(cs, wsm, pd.xr, pd.yr, i0, L1, L2, d, A.inc_mode, pd.sx, pd.sy, lane);
+        else strip_coefficients<false>(cs, wsm, pd.xr, pd.yr, i0, L1, L2, d, A.inc_mode, pd.sx, pd.sy, lane);
 
         // ------------------------- pass A: forward replay ------------------------
         float a[P + 1], a1lo = 0.0f;
