@@ -422,6 +422,15 @@ __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch
         const float* rbase = stored ? A.rec_store + A.rec_off[lo_p] + (int64_t)(s / RR) * (L2 + 32) * 32 * RR * RS
                                     : rec;
         if (stored) rec_get_state<P>(rbase + ((int64_t)T * 32 * RR + rw) * RS, a1lo, a);
+        // BULK: records of a multiple of 4 floats leave the replay as one
+        // bulk copy per step (staged in the two buffers that the replay does
+        // not use, the second record buffer and the adjoint seam-in block);
+        // pass B then reads them past L1 (16-byte cp.async.cg), which does
+        // not see the bulk copies' writes
+        constexpr bool BULK = (RS % 4) == 0;
+        static_assert(2 * Sm::RB + 32 * RS <= Sm::per_warp, "the second staging block fits the warp's area");
+        float* const stg0 = rbuf1;
+        float* const stg1 = ain;
         if (!stored) {
             float cq[kB2PF];
 #pragma unroll
@@ -455,9 +464,14 @@ __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch
                         for (int q = 1; q <= P; ++q) b[q] = 0.0f;
                     }
                 }
+                if constexpr (BULK) {
+                    // the bulk copy of step t - 2 has read this step's staging block
+                    if (lane == 0) bulk_wait_read<1>();
+                    __syncwarp();
+                }
                 const int j = t - lane;
                 if (j >= 0 && j < L2) {
-                    float* rslot = rec + (size_t)t * RS * 32 + lane * RS;
+                    float* rslot = BULK ? ((t & 1) ? stg1 : stg0) + lane * RS : rec + (size_t)t * RS * 32 + lane * RS;
                     rec_put_head<P>(rslot, hi, b1lo, b);
                     const float rbP = b[P];
                     const int Eb = E;
@@ -494,6 +508,24 @@ __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch
                     for (int q = 1; q <= P; ++q) ob[q] = b[q];
                     replayed += has_row ? 1ull : 0ull;
                 }
+                if constexpr (BULK) {
+                    // the step's 32 records (slots of lanes outside the grid
+                    // carry stale values that no reader asks for)
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        bulk_store(rec + (size_t)t * RS * 32, (t & 1) ? stg1 : stg0, 32 * RS * (uint32_t)sizeof(float));
+                        bulk_commit();
+                    }
+                }
+            }
+            if constexpr (BULK) {
+                // every record is in global memory and visible to the generic
+                // proxy before pass B reads it (and the staging blocks are free)
+                if (lane == 0) {
+                    bulk_wait_all();
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
             }
         }
         __syncwarp();
@@ -523,8 +555,13 @@ __global__ void __launch_bounds__(128, 3) bwd2_kernel(BwdArgs A, float* cscratch
             if (j >= 0 && j < L2) {
                 const float* src = rbase + ((int64_t)(j + rw / RR) * 32 * RR + rw) * RS;
                 float* dst = rbuf(tpp) + lane * RS;
+                if constexpr (BULK) {
 #pragma unroll
-                for (int g = 0; g < RS / 2; ++g) cp_async8(dst + 2 * g, src + 2 * g);
+                    for (int g = 0; g < RS / 4; ++g) cp_async16z(dst + 4 * g, src + 4 * g, 16);
+                } else {
+#pragma unroll
+                    for (int g = 0; g < RS / 2; ++g) cp_async8(dst + 2 * g, src + 2 * g);
+                }
             }
             cp_async_commit();
         };
