@@ -358,10 +358,12 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
     L->cst_stride = 0;
     L->ycache = L->yexp = L->ablk = L->cst = off;
     if (L->tc) {
-        // digits of every path's first max_len segments, exponents; per CTA
-        // the digits of a block's rows and the skewed (c, clo) of its strips
+        // digits of every path's first max_len segments (a tiled matrix of
+        // whole 64-row chunks per path), exponents; per CTA the digits of a
+        // block's rows and the skewed (c, clo) of its strips
         L->ycache = off;
-        off = align256(off + sizeof(uint16_t) * (size_t)L->n_slots * o.max_len * kTcDigits * L->d_pad);
+        off = align256(off + sizeof(uint16_t) * (size_t)L->n_slots * (size_t)tc_cache_rows(o.max_len) *
+                                 kTcDigits * L->d_pad);
         L->yexp = off; off = align256(off + sizeof(int32_t) * (size_t)L->n_slots * o.max_len);
         const size_t ctas = (size_t)L->grid;
         L->ablk = off; off = align256(off + sizeof(uint16_t) * ctas * kTcDigits * kTcRows * L->d_pad);
@@ -1261,7 +1263,7 @@ static sigk_status run_solver(int op, const float* X, const int64_t* len_x, int6
         sl.max_len = o.max_len;
         sl.cache = (uint16_t*)(base + L.ycache);
         sl.exps = (int32_t*)(base + L.yexp);
-        const int64_t rows = L.n_slots * o.max_len;
+        const int64_t rows = L.n_slots * tc_cache_rows(o.max_len);
         const int64_t blocks = (rows + 7) / 8;
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);

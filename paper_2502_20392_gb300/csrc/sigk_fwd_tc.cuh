@@ -79,11 +79,12 @@ struct TcSmem {
 
 struct TcArgs {
     SolverArgs A;                  // pair table, schedule (items = 32-row strips), seams, outputs
-    const uint16_t* ycache;        // digits of every path's segments [slot][max_len][4][d_pad] (BF16 bits)
+    const uint16_t* ycache;        // digits of every path's segments: per slot a tiled matrix of
+                                   // tc_cache_rows(max_len) rows (tile_index; BF16 bits)
     const int32_t* yexp;           // their exponents [slot][max_len]
     int64_t max_len;               // segments per slot
     int32_t d_pad;                 // d rounded up to a multiple of 16
-    uint16_t* ablk;                // per CTA: digits of the block's rows [4][128][d_pad]
+    uint16_t* ablk;                // per CTA: digits of the block's 128 rows, tiled (16 row groups)
     float2* cst;                   // per CTA: skewed (c, clo) of kTcSlots x 4 strips
     int64_t cst_stride;            // float2 per strip: (max_len + 32 + kTcPF) * 32
     int* block_counter;
@@ -111,12 +112,28 @@ __device__ __forceinline__ void digits4(float x, int e, uint16_t (&t)[kTcDigits]
     }
 }
 
+// Digits in global memory are kept in the operand layout of the MMAs: for
+// digit k and 16-dimension step s, the rows in groups of eight, each group
+// one 256-byte block [half h of the step][row & 7][8 dimensions] -- the
+// core-matrix layout of the shared-memory tiles (kTcLbo = 128, kTcSbo = 256
+// bytes), so that one bulk copy moves a whole tile of consecutive rows.
+// Element offset of (row r, dimension e, digit k) in a matrix of nrg row
+// groups and ks steps of 16 dimensions:
+__host__ __device__ constexpr int64_t tile_index(int64_t r, int e, int k, int ks, int64_t nrg) {
+    return ((((int64_t)k * ks + (e >> 4)) * nrg + (r >> 3)) << 7) + (((e >> 3) & 1) << 6) + ((r & 7) << 3) +
+           (e & 7);
+}
+// Rows of a path's digit matrix in the cache: max_len rounded up to whole
+// 64-row chunks, so that a chunk's tile never runs past the matrix.
+__host__ __device__ constexpr int64_t tc_cache_rows(int64_t max_len) { return (max_len + 63) / 64 * 64; }
+
 // One warp cuts row `row` of a path (points or increments; `valid` false: a
-// zero row) into digits: dst[k * kstride + e] for k < 4, e < d_pad; returns
-// the exponent (lane-uniform).  esub is subtracted from the exponent (the
-// refinement scale 1/s of a virtual row).
+// zero row) into digits, stored as row `trow` of the tiled matrix at base
+// (nrg row groups, d_pad / 16 steps); returns the exponent (lane-uniform).
+// esub is subtracted from the exponent (the refinement scale 1/s of a virtual
+// row).
 __device__ __forceinline__ int slice_row(const float* z, int64_t row, bool valid, int d, int d_pad,
-                                         int inc_mode, int esub, uint16_t* dst, int64_t kstride,
+                                         int inc_mode, int esub, uint16_t* base, int64_t trow, int64_t nrg,
                                          int lane) {
     float m = 0.0f;
     for (int e = lane; e < d; e += 32) {
@@ -131,14 +148,15 @@ __device__ __forceinline__ int slice_row(const float* z, int64_t row, bool valid
         uint16_t t[kTcDigits];
         digits4(v, ex, t);
 #pragma unroll
-        for (int k = 0; k < kTcDigits; ++k) dst[k * kstride + e] = t[k];
+        for (int k = 0; k < kTcDigits; ++k) base[tile_index(trow, e, k, d_pad >> 4, nrg)] = t[k];
     }
     return m > 0.0f ? ex - esub : 0;
 }
 
 // Pre-pass: the digits of every path's first min(segments, max_len) segments
-// (unrefined), one warp per segment; a path can be the swept path of a pair
-// only within that range.
+// (unrefined), one warp per segment, into the path's tiled matrix of
+// tc_cache_rows(max_len) rows (rows past the path are zero digits); a path
+// can be the swept path of a pair only within that range.
 struct SliceArgs {
     const float* X;
     const float* Y;
@@ -157,17 +175,17 @@ struct SliceArgs {
 static __global__ void __launch_bounds__(256) slice_paths_kernel(SliceArgs S) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t total = S.n_slots * S.max_len;
+    const int64_t rows = tc_cache_rows(S.max_len);
+    const int64_t total = S.n_slots * rows;
     for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += warps) {
-        const int64_t slot = w / S.max_len, r = w % S.max_len;
+        const int64_t slot = w / rows, r = w % rows;
         const bool fy = slot >= S.n_x;
         const int64_t i = fy ? slot - S.n_x : slot;
         const int64_t segs = S.inc_mode ? (fy ? S.len_y : S.len_x)[i] : (fy ? S.len_y : S.len_x)[i] - 1;
-        if (r >= segs) continue;  // warp-uniform
         const float* z = (fy ? S.Y : S.X) + (fy ? S.oy : S.ox)[i] * S.d;
-        const int ex = slice_row(z, r, true, S.d, S.d_pad, S.inc_mode, 0,
-                                 S.cache + w * kTcDigits * S.d_pad, S.d_pad, lane);
-        if (lane == 0) S.exps[w] = ex;
+        const int ex = slice_row(z, r, r < segs, S.d, S.d_pad, S.inc_mode, 0,
+                                 S.cache + slot * rows * kTcDigits * S.d_pad, r, rows >> 3, lane);
+        if (lane == 0 && r < S.max_len) S.exps[slot * S.max_len + r] = ex;
     }
 }
 
@@ -226,6 +244,23 @@ __device__ __forceinline__ void cp_async16(uint32_t sdst, const void* gsrc, uint
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Arrive on an mbarrier expecting `bytes` of bulk copies (the phase completes
+// when they have landed), or arrive without copies.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completing on mbar.
+__device__ __forceinline__ void bulk_g2s(uint32_t sdst, const void* gsrc, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sdst),
+                 "l"(gsrc), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
 
 template <int NC>
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -454,6 +489,7 @@ __device__ __forceinline__ bool sweep_strip_tc(const SolverArgs& A, const PairDe
 // State of one CTA shared between its producer group and its sweep warps.
 struct TcShared {
     uint64_t mbar[kTcStages];     // stage s: the MMAs that read it have completed
+    uint64_t full[kTcStages];     // stage s: its operand tiles have landed (bulk copies)
     uint32_t tmem_base;
     int blk;                      // the producer's block (broadcast within the group)
     int stop;                     // no more blocks (the normal end)
@@ -528,6 +564,7 @@ __device__ __forceinline__ void tc_producer(const TcArgs& T, TcShared& sh, unsig
     uint32_t gstep = 0;   // operand steps so far: stage g % S, its use number g / S
     uint32_t gchunk = 0;  // chunks so far: TMEM buffer gchunk & 1
     int64_t issued = -1, waited = -1;
+    int64_t filled = -1, consumed = -1;  // thread 0: last step whose bulk copies were issued / awaited
     bool ok = true;
     for (;;) {
         // ---- a free slot, and the next block -------------------------------
@@ -564,11 +601,13 @@ __device__ __forceinline__ void tc_producer(const TcArgs& T, TcShared& sh, unsig
                 const int r = warp * 32 + rr;
                 const int v = r0 + r;  // virtual row
                 const int ex = slice_row(pd.xr, (int64_t)(v >> lsx), v < L1, d, d_pad, A.inc_mode, lsx,
-                                         ablk + (int64_t)r * d_pad, (int64_t)kTcRows * d_pad, lane);
+                                         ablk, r, kTcRows / 8, lane);
                 if (lane == 0) sh.aexp[r] = ex;
             }
         }
         __threadfence_block();
+        // the bulk copies (async proxy) read what these generic stores wrote
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         producer_sync();
         // ---- publish the block to the slot's sweep warps --------------------
         if (tid == 0) {
@@ -579,7 +618,15 @@ __device__ __forceinline__ void tc_producer(const TcArgs& T, TcShared& sh, unsig
         }
         // ---- the coefficients, kTcN columns at a time -----------------------
         const int lsy = 31 - __clz(pd.sy);
-        const uint16_t* yc = T.ycache + (int64_t)pd.yslot * T.max_len * kTcDigits * d_pad;
+        const int64_t yrows = tc_cache_rows(T.max_len);
+        const uint16_t* yc = T.ycache + (int64_t)pd.yslot * yrows * kTcDigits * d_pad;
+        // an unrefined swept path: a chunk's 64 columns are consecutive rows
+        // of the path's tiled digit matrix, so every operand tile of a step
+        // is one contiguous block and leaves global memory in one bulk copy
+        // (issued by thread 0, completing on the stage's `full` mbarrier);
+        // a refined one repeats rows, and all producer threads copy 16-byte
+        // pieces (cp.async)
+        const bool bulk = pd.sy == 1;
         const int32_t* ye = T.yexp + (int64_t)pd.yslot * T.max_len;
         float2* cw = T.cst + ((int64_t)blockIdx.x * kTcSlots + slot) * 4 * T.cst_stride + (int64_t)warp * T.cst_stride;
         const int nch = (L2 + kTcN - 1) / kTcN;
@@ -593,16 +640,33 @@ __device__ __forceinline__ void tc_producer(const TcArgs& T, TcShared& sh, unsig
             for (int idx = tid; idx < kTcDigits * kTcRows * 2; idx += 128) {
                 const int h = idx & 1, r = (idx >> 1) & (kTcRows - 1), k = idx >> 8;
                 cp_async16(smem_u32(sa + k * Sm::a_tile + (r >> 3) * kTcSbo + h * kTcLbo + (r & 7) * 16),
-                           ablk + ((int64_t)k * kTcRows + r) * d_pad + kk * kTcK + 8 * h, 16u);
+                           ablk + tile_index(r, kk * kTcK + 8 * h, k, KS, kTcRows / 8), 16u);
             }
             for (int idx = tid; idx < kTcDigits * kTcN * 2; idx += 128) {
                 const int h = idx & 1, jj = (idx >> 1) & (kTcN - 1), k = idx >> 7;
                 const int j = c0 + jj;
                 const bool in = j < L2;
                 cp_async16(smem_u32(sb + k * Sm::b_tile + (jj >> 3) * kTcSbo + h * kTcLbo + (jj & 7) * 16),
-                           yc + ((int64_t)(in ? (j >> lsy) : 0) * kTcDigits + k) * d_pad + kk * kTcK + 8 * h,
+                           yc + tile_index(in ? (j >> lsy) : 0, kk * kTcK + 8 * h, k, KS, yrows >> 3),
                            in ? 16u : 0u);
             }
+        };
+        // thread 0: the eight tiles of step n (four digits of A and of B) into
+        // stage (gstep + n) % S, one bulk copy each
+        auto issue_bulk = [&](int n) {
+            const int c0 = (n / KS) * kTcN, kk = n % KS;
+            const uint32_t st = (gstep + n) % S;
+            unsigned char* sa = stg + st * Sm::stage;
+            unsigned char* sb = sa + kTcDigits * Sm::a_tile;
+            mbar_expect_tx(&sh.full[st], (uint32_t)(kTcDigits * (Sm::a_tile + Sm::b_tile)));
+#pragma unroll
+            for (int k = 0; k < kTcDigits; ++k) {
+                bulk_g2s(smem_u32(sa + k * Sm::a_tile), ablk + tile_index(0, kk * kTcK, k, KS, kTcRows / 8),
+                         (uint32_t)Sm::a_tile, &sh.full[st]);
+                bulk_g2s(smem_u32(sb + k * Sm::b_tile), yc + tile_index(c0, kk * kTcK, k, KS, yrows >> 3),
+                         (uint32_t)Sm::b_tile, &sh.full[st]);
+            }
+            filled = (int64_t)gstep + n;
         };
         // (c, clo) of chunk c from TMEM into the strips' skewed areas, then
         // published: chunk c's last MMAs are complete once its last step's
@@ -656,17 +720,34 @@ __device__ __forceinline__ void tc_producer(const TcArgs& T, TcShared& sh, unsig
         };
 #pragma unroll 1
         for (int n = 0; n < S - 1; ++n) {
-            if (n < nst) issue(n);
-            cp_async_commit();
+            if (bulk) {
+                if (tid == 0 && n < nst) issue_bulk(n);
+            } else {
+                if (n < nst) issue(n);
+                cp_async_commit();
+            }
         }
 #pragma unroll 1
         for (int n = 0; n < nst; ++n) {
             const uint32_t g = gstep + n;
-            asm volatile("cp.async.wait_group %0;" ::"n"(S - 2) : "memory");  // step n's copies (this thread's)
-            fence_proxy_async_smem();
-            producer_sync();  // every thread's copies of step n have landed
+            bool ready = true;
+            if (bulk) {
+                // step n's tiles have landed (thread 0 issues the MMAs)
+                if (tid == 0) {
+                    ready = mbar_wait(&sh.full[g % S], (g / S) & 1, A.status);
+                    consumed = g;
+                }
+            } else {
+                asm volatile("cp.async.wait_group %0;" ::"n"(S - 2) : "memory");  // step n's copies (this thread's)
+                fence_proxy_async_smem();
+                producer_sync();  // every thread's copies of step n have landed
+                // one arrival per step keeps the stage's `full` phases in step
+                // with the bulk blocks
+                if (tid == 0) mbar_arrive(&sh.full[g % S]);
+            }
+            if (!ready) ok = false;
             const int c = n / KS, kk = n % KS;
-            if (tid == 0) {
+            if (tid == 0 && ready) {
                 tc_fence_after();
                 unsigned char* sa = stg + (g % S) * Sm::stage;
                 unsigned char* sb = sa + kTcDigits * Sm::a_tile;
@@ -686,10 +767,17 @@ __device__ __forceinline__ void tc_producer(const TcArgs& T, TcShared& sh, unsig
             issued = g;
             // refill: step n + S - 1 goes to stage (g - 1) % S, which the MMAs of step g - 1 read
             if (n + S - 1 < nst) {
-                if (g >= 1 && !mbar_wait(&sh.mbar[(g - 1) % S], ((g - 1) / S) & 1, A.status)) ok = false;
-                issue(n + S - 1);
+                if (bulk) {
+                    if (tid == 0 && ok) {
+                        if (g >= 1 && !mbar_wait(&sh.mbar[(g - 1) % S], ((g - 1) / S) & 1, A.status)) ok = false;
+                        if (ok) issue_bulk(n + S - 1);
+                    }
+                } else {
+                    if (g >= 1 && !mbar_wait(&sh.mbar[(g - 1) % S], ((g - 1) / S) & 1, A.status)) ok = false;
+                    issue(n + S - 1);
+                }
             }
-            cp_async_commit();
+            if (!bulk) cp_async_commit();
             // the previous chunk's epilogue overlaps this chunk's MMAs
             if (kk == 0 && c >= 1) epilogue(c - 1);
             ok = producer_and(ok);
@@ -709,6 +797,10 @@ __device__ __forceinline__ void tc_producer(const TcArgs& T, TcShared& sh, unsig
     }
     // MMAs still in flight (after an abort) complete before TMEM is freed
     if (issued > waited) mbar_wait(&sh.mbar[issued % S], (uint32_t)(issued / S) & 1, A.status);
+    // and bulk copies still in flight land before the CTA's shared memory is released
+    if (tid == 0)
+        for (int64_t q = consumed + 1; q <= filled; ++q)
+            if (!mbar_wait(&sh.full[q % S], (uint32_t)(q / S) & 1, A.status)) break;
 }
 
 // One CTA per SM (it holds all of TMEM): warps 0-3 are the producer group,
@@ -740,8 +832,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) fwd_tc_kernel(TcArgs T) {
     }
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < kTcStages; ++k)
+        for (int k = 0; k < kTcStages; ++k) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.mbar[k])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sh.full[k])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sh.stop = 0;
         sh.err = 0;
