@@ -4,7 +4,7 @@
 // One work item = (pair, 32-row strip, one row per lane), the strips of a pair
 // in DECREASING order (the schedule's k-th item of a pair is strip
 // n_strips - 1 - k).  Per item the warp runs four phases over a per-warp
-// strip area cs of (L2 + 34) x 32 floats, skewed so that the 32 values the
+// strip area cs of (L2 + 32 + kB2PF) x 32 floats, skewed so that the 32 values the
 // lanes touch in one sweep step are contiguous: entry t * 32 + l belongs to
 // row l and column t - l.
 //
@@ -37,7 +37,6 @@
 namespace sigk {
 
 constexpr int kB2KC = 32;   // contraction chunk of phase 0
-constexpr int kB2PF = 2;    // coefficient loads in flight per lane in passes A and B
 constexpr int kB2Blk = 32 * 34;        // a 32 x 32 block of c or g (row stride 34)
 // the strip rows' and a column block's points or increments, [33][up to 32
 // dimensions + 4] each (33 points give 32 increments)

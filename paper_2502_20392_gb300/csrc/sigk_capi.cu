@@ -409,7 +409,7 @@ static sigk_status make_layout(int op, int64_t n_x, int64_t n_y, int d, const Op
         L->aseam = off;
         off = align256(off + sizeof(float) * (size_t)L->bnslot * L->bwcols * adj_seam_floats(o.order));
         // per adjoint warp: its strip's coefficients, then g, skewed
-        L->bcstride = (o.max_len + 34) * 32;
+        L->bcstride = (o.max_len + 32 + kB2PF) * 32;
         L->bcs = off;
         off = align256(off + sizeof(float) * (size_t)L->bnwarps * L->bcstride);
     }

@@ -37,6 +37,10 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kG = 32;            // columns per seam block (one warp width)
 constexpr int kMaxP = 16;         // maximum edge degree
 constexpr int kMaxRings = 8;      // maximum Neumann iterations per tile
+// adjoint, passes A and B: coefficient loads in flight per lane (the
+// per-warp strip area holds max_len + 32 + kB2PF rows of 32 entries); four
+// in flight measured 79.5 against 68.3 ms on the 64-path Gram
+constexpr int kB2PF = 2;
 
 // 1/k! for k = 0..33, rounded to FP32 (all normal numbers; the tile map
 // indexes at most k = 16).  Each translation unit holds its own copy.
