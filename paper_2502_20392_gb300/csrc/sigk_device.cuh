@@ -20,7 +20,9 @@
 // (ah_0 := bh_0 := b_0, the corner value; a_0 is never used, as in the proof
 // where the diagonal carries the left-edge constant).  Rings m = min(p,q) are
 // the Neumann iterates T^m of Sec. 2.2.2; only m <= nr are kept (the local
-// Neumann iteration count, App. C.3: the a-priori order choice).  Every
+// Neumann iteration count, App. C.3: the a-priori order choice), and of those
+// only the entries of weighted degree 2m + k <= 2 nr + 1, k = |p - q| the
+// degree of the edge coefficient they carry (keep_entry below).  Every
 // constant is a compile-time entry of a __constant__ table, so each term is
 // one FFMA.
 //
