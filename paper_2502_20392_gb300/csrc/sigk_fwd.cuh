@@ -117,15 +117,19 @@ __device__ __forceinline__ void warp_copy_cg(float* dst, const float* src, int n
 }
 
 // CTAs per SM the register allocation must allow (128 threads each): the
-// largest count that ptxas meets without spilling for that instantiation.
-constexpr int fwd_min_blocks(int P, int D, int R, bool REC) {
+// largest count that ptxas meets without spilling more than a few words for
+// that instantiation.  Two rows per lane at orders 10-12 with up to six rings
+// take four CTAs at 128 registers (12-20 bytes spilled): the order-12,
+// six-ring Gram forward took 24.9 against 26.0 ms at three CTAs and 162
+// registers; seven rings would spill 220 bytes and keep three.
+constexpr int fwd_min_blocks(int P, int D, int R, int NR, bool REC) {
     return REC ? ((R == 1 && !(P >= 14 && D >= 16)) || P <= 8 ? 4 : 3)
-               : (R == 1 ? 4 : (R == 2 ? (P <= 8 ? 4 : 3) : (P <= 4 ? 4 : 3)));
+               : (R == 1 ? 4 : (R == 2 ? ((P <= 8 || (P <= 12 && NR <= 6)) ? 4 : 3) : (P <= 4 ? 4 : 3)));
 }
 
 // REC: training forward that also stores every tile's record (SolverArgs::rec).
 template <int P, int D, int R, int NR, bool REC = false>
-__global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, REC)) fwd_kernel(SolverArgs A) {
+__global__ void __launch_bounds__(128, fwd_min_blocks(P, D, R, NR, REC)) fwd_kernel(SolverArgs A) {
     constexpr int S = P + 4;
     constexpr int DS = DyStride<D>::value;
     constexpr int RS = rec_floats(P);
