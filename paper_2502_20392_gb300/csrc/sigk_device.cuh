@@ -820,4 +820,14 @@ __host__ __device__ constexpr long long tile_flops(int P, int NT, int nr) {
     return f;
 }
 
+// The kept-entry counts and per-tile operation counts that the roofline
+// figures use (bench.py mirrors them; tests/test_bench_cpu.py pins the same
+// numbers), checked here against keep_entry itself.
+static_assert(kept_entries(8, 4, 4) == 36 && kept_entries(6, 3, 3) == 21 && kept_entries(12, 6, 6) == 78,
+              "kept entries of the weighted-degree truncation");
+static_assert(kept_entries(16, 6, 6) == kept_entries(12, 6, 6), "no kept entry above degree 2n");
+static_assert(tile_flops(8, 4, 4) == 234 - 2 * 16 && tile_flops(6, 3, 3) == 166 - 2 * 16 &&
+                  tile_flops(12, 6, 6) == 418 - 2 * 16,
+              "tile operations without the increment inner product");
+
 }  // namespace sigk
